@@ -1,0 +1,565 @@
+"""CPU oracle: plain, slow FP64 restarted BFOM/BGMRES with low-sync block Arnoldi.
+
+TEST INFRASTRUCTURE ONLY.  Nothing in the product path imports this module:
+only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline
+leg may use it.  It shares no code with the CUDA path.
+
+What it computes (K. Lund, "Adaptively restarted block Krylov subspace methods
+with low-synchronization skeletons", arXiv 2208.09899):
+
+* Problem A X = B, A n x n sparse, B n x s (Sec. 2, Eq. (1)); real FP64 only.
+* Classical block inner product <X, Y> = X^T Y and scaling quotient
+  N(X) = R of X = Q R (Sec. 2.2, Table 1).
+* Muscle CholQR: R = chol(X^T X), Q = X R^{-1} (Sec. 2.3; the muscle list of Sec. 5).
+* Skeletons, each written from its algorithm in the paper's order:
+  BMGS-Arnoldi (Alg. 2), BCGS (the condensed loop of Sec. 3.1),
+  BCGS-PIP-Arnoldi (Alg. 3), BMGS-CWY / BMGS-ICWY-Arnoldi (Alg. 6, both branches),
+  BCGSI+LS-Arnoldi (Alg. 7).
+* Modified BFOM  X_m = V_m (H_m + M)^{-1} E_1 B  (Eq. (7)); M = 0 gives BFOM,
+  M = H_m^{-T} E_m H_{m+1,m}^T H_{m+1,m} E_m^T gives BGMRES (Sec. 2.4.1).
+* Cospatial residual R_m = U_m (E_m^T Xi_m), U_m = V_{m+1} [M; -H_{m+1,m}]
+  (Thm. 1, Eq. (8)) and the local residual norm estimate (Eq. (9)).
+* Static restarting X <- X + D (Sec. 2.4.2), applied cycle after cycle.
+* Adaptive restarting on a Cholesky NaN-flag (Sec. 4).
+
+Readings taken where the paper is silent or garbled (each also listed in the
+design notes of the repository):
+  R1  chol's NaN-flag fires iff some pivot d_j = G_jj - sum_{i<j} R_ij^2 is <= 0
+      or non-finite, or any entry of G's upper triangle is non-finite; only the
+      upper triangle of G is read (MATLAB chol convention, Sec. 4).
+  R2  Sec. 3.1's condensed BCGS update "W - W H" is read as W - V_k H_{1:k,k}.
+  R3  Alg. 6's last two lines do not apply at k = 1 (H_{1,0} is undefined);
+      for k >= 2 the product V_{k-1} H_{1:k,k} is read as V_k H_{1:k,k}, with
+      the V_k just formed.
+  R4  Alg. 7 sets H_{1,1} = J at k = 1 and overwrites the first block column
+      with J + Y at k = 2; the final value is kept.
+  R5  The lagged skeletons (Alg. 6, 7) run k = 1..m+1; iteration k completes
+      Arnoldi relation j = k - 1.
+  R6  The residual estimate is checked after every completed relation j; if
+      H_j + M is singular the estimate at that j is skipped.
+  R7  Restart bookkeeping across cycles: X += V_j Xi_j C, U = V_{j+1}[M; -H],
+      C <- (E_j^T Xi_j) C, the next cycle starts from CholQR(U); the estimate is
+      ||[M; -H] c C||_F / ||B||_F (Thm. 1 applied cycle after cycle, Sec. 2.4.2).
+  R8  Adaptive restart (Sec. 4): a flag while completing relation j+1 ends the
+      cycle with relation j and sets the maximum basis size to j for all later
+      cycles; j = 0, or more than max_restarts restarts, ends the solve
+      unconverged.  With adaptive restarting off, a flag ends the solve after
+      the cycle's update.
+  R9  Counting: an A-call or sync performed by a step that then flags is
+      counted; the step itself is not.  V-application counts per cycle of j
+      completed relations are defined to reproduce the appendix tables:
+      BMGS 2j, BCGS 2j, PIP 3j, CWY/ICWY 3j+1, BCGSI+LS 4j+1.
+  R10 (extension) verify_true_residual: when the estimate says converged but
+      ||B - A X||_F / ||B||_F > tol, one more cycle starts from B - A X with C = I.
+  R11 The paper's benchmark tables stop at a relative *error* tolerance
+      ||X_k - X_*||_F / ||X_*||_F <= tol with X_* from a direct solve (Sec. 5,
+      "reach a specified error tolerance"); ``X_star`` selects that stopping
+      test instead of the residual estimate (used only to compare with the
+      paper's tables).
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+import scipy.sparse
+
+SKELETONS = ("bmgs", "bcgs", "bcgs_pip", "bmgs_cwy", "bmgs_icwy", "bcgsi_ls")
+LAGGED = ("bmgs_cwy", "bmgs_icwy", "bcgsi_ls")
+
+OK, NOT_CONVERGED, BREAKDOWN = 0, 1, 2
+
+
+# ---------------------------------------------------------------- primitives
+
+def spmm(A, V: np.ndarray) -> np.ndarray:
+    """W = A V for A in CSR form (the ``matvec`` of Sec. 2.1 on a block vector)."""
+    M = scipy.sparse.csr_matrix((A.vals, A.colidx, A.rowptr), shape=(A.n, A.n))
+    return np.asarray(M @ V)
+
+
+def inner(X: np.ndarray, Y: np.ndarray) -> np.ndarray:
+    """Classical block inner product <X, Y> = X^T Y (Table 1)."""
+    return X.T @ Y
+
+
+def chol_flag(G: np.ndarray):
+    """Upper Cholesky factor R (G = R^T R) read from the upper triangle of G,
+    with the NaN-flag of Sec. 4 (reading R1).  Returns (R, flag)."""
+    G = np.asarray(G, dtype=np.float64)
+    s = G.shape[0]
+    R = np.zeros((s, s))
+    if not np.all(np.isfinite(np.triu(G))):
+        return R, True
+    for j in range(s):
+        d = G[j, j] - np.dot(R[:j, j], R[:j, j])
+        if not np.isfinite(d) or d <= 0.0:
+            return R, True
+        R[j, j] = np.sqrt(d)
+        for c in range(j + 1, s):
+            R[j, c] = (G[j, c] - np.dot(R[:j, j], R[:j, c])) / R[j, j]
+    return R, False
+
+
+def right_solve_upper(X: np.ndarray, R: np.ndarray) -> np.ndarray:
+    """X R^{-1} for upper-triangular R, by forward substitution over the columns."""
+    Q = np.array(X, dtype=np.float64, copy=True)
+    s = R.shape[0]
+    for c in range(s):
+        Q[:, c] = (X[:, c] - Q[:, :c] @ R[:c, c]) / R[c, c]
+    return Q
+
+
+def left_solve_upper_T(R: np.ndarray, Y: np.ndarray) -> np.ndarray:
+    """R^{-T} Y for upper-triangular R (forward substitution with R^T)."""
+    s = R.shape[0]
+    Z = np.array(Y, dtype=np.float64, copy=True)
+    for r in range(s):
+        Z[r] = (Y[r] - R[:r, r] @ Z[:r]) / R[r, r]
+    return Z
+
+
+def cholqr(X: np.ndarray):
+    """CholQR muscle: R = chol(X^T X), Q = X R^{-1}.  Returns (Q, R, flag)."""
+    R, flag = chol_flag(inner(X, X))
+    if flag:
+        return None, R, True
+    return right_solve_upper(X, R), R, False
+
+
+def unit_upper_T_solve(T: np.ndarray, Y: np.ndarray) -> np.ndarray:
+    """T^{-T} Y for unit upper-triangular T (forward substitution with T^T)."""
+    Z = np.array(Y, dtype=np.float64, copy=True)
+    for r in range(T.shape[0]):
+        Z[r] = Y[r] - T[:r, r] @ Z[:r]
+    return Z
+
+
+# ---------------------------------------------------------------- skeletons
+
+class _Arnoldi:
+    """State of one block Arnoldi cycle.  ``advance()`` performs one loop
+    iteration of the skeleton's algorithm and returns ("rel", j) when Arnoldi
+    relation j is complete, ("flag", j) when chol flagged while completing
+    relation j, or ("none", 0)."""
+
+    def __init__(self, A, V1: np.ndarray, m: int, counts: dict, grams: list | None):
+        self.A, self.m = A, m
+        n, s = V1.shape
+        self.n, self.s = n, s
+        self.V = [V1]
+        self.H = np.zeros(((m + 2) * s, (m + 1) * s))
+        self.k = 0
+        self.counts = counts
+        self.grams = grams
+
+    def _blk(self, i, j):
+        s = self.s
+        return slice((i - 1) * s, i * s), slice((j - 1) * s, j * s)
+
+    def Hb(self, i, j):
+        r, c = self._blk(i, j)
+        return self.H[r, c]
+
+    def set_Hb(self, i, j, val):
+        r, c = self._blk(i, j)
+        self.H[r, c] = val
+
+    def Hcol(self, i0, i1, j):
+        """H_{i0:i1, j} (block rows i0..i1 inclusive)."""
+        s = self.s
+        return self.H[(i0 - 1) * s:i1 * s, (j - 1) * s:j * s]
+
+    def set_Hcol(self, i0, i1, j, val):
+        s = self.s
+        self.H[(i0 - 1) * s:i1 * s, (j - 1) * s:j * s] = val
+
+    def basis(self, k):
+        return np.hstack(self.V[:k])
+
+    def _matvec(self, X):
+        self.counts["a_calls"] += 1
+        return spmm(self.A, X)
+
+    def _sync(self):
+        self.counts["syncs"] += 1
+
+    def _record(self, G):
+        if self.grams is not None:
+            self.grams.append(np.array(G))
+
+
+class BMGS(_Arnoldi):
+    """BMGS-Arnoldi, Alg. 2."""
+
+    def advance(self, force_flag=False):
+        self.k += 1
+        k = self.k
+        W = self._matvec(self.V[k - 1])
+        for j in range(1, k + 1):
+            Hjk = inner(self.V[j - 1], W)
+            self._sync()
+            if j == 1:
+                self._record(Hjk)
+            self.set_Hb(j, k, Hjk)
+            W = W - self.V[j - 1] @ Hjk
+        self._sync()
+        Q, R, flag = cholqr(W)
+        if flag or force_flag:
+            return ("flag", k)
+        self.V.append(Q)
+        self.set_Hb(k + 1, k, R)
+        return ("rel", k)
+
+
+class BCGS(_Arnoldi):
+    """Block classical Gram-Schmidt Arnoldi, Sec. 3.1 (reading R2)."""
+
+    def advance(self, force_flag=False):
+        self.k += 1
+        k = self.k
+        W = self._matvec(self.V[k - 1])
+        Vk = self.basis(k)
+        Hc = inner(Vk, W)
+        self._sync()
+        self._record(Hc)
+        self.set_Hcol(1, k, k, Hc)
+        W = W - Vk @ Hc
+        self._sync()
+        Q, R, flag = cholqr(W)
+        if flag or force_flag:
+            return ("flag", k)
+        self.V.append(Q)
+        self.set_Hb(k + 1, k, R)
+        return ("rel", k)
+
+
+class BCGS_PIP(_Arnoldi):
+    """BCGS-PIP-Arnoldi, Alg. 3."""
+
+    def advance(self, force_flag=False):
+        self.k += 1
+        k, s = self.k, self.s
+        W = self._matvec(self.V[k - 1])
+        Vk = self.basis(k)
+        G = inner(np.hstack([Vk, W]), W)          # [H_{1:k,k}; Omega]
+        self._sync()
+        self._record(G)
+        Hc, Om = G[:k * s], G[k * s:]
+        R, flag = chol_flag(Om - Hc.T @ Hc)
+        if flag or force_flag:
+            return ("flag", k)
+        self.set_Hcol(1, k, k, Hc)
+        self.set_Hb(k + 1, k, R)
+        self.V.append(right_solve_upper(W - Vk @ Hc, R))
+        return ("rel", k)
+
+
+class BMGS_CWY(_Arnoldi):
+    """BMGS-CWY (red) / BMGS-ICWY (blue) Arnoldi, Alg. 6 (readings R3, R5)."""
+    inverse = False
+
+    def __init__(self, *a, **kw):
+        super().__init__(*a, **kw)
+        self.T = np.eye((self.m + 2) * self.s)
+        self.U = self.V[0]
+
+    def advance(self, force_flag=False):
+        self.k += 1
+        k, s = self.k, self.s
+        W = self._matvec(self.U)
+        if k == 1:
+            H11 = inner(self.U, W)
+            self._sync()
+            self._record(H11)
+            self.set_Hb(1, 1, H11)
+            self.U = W - self.V[0] @ H11
+            return ("none", 0)
+        Vkm1 = self.basis(k - 1)
+        G = inner(np.hstack([Vkm1, self.U]), np.hstack([self.U, W]))
+        self._sync()
+        self._record(G)
+        Y, Z = G[:(k - 1) * s, :s], G[:(k - 1) * s, s:]
+        Om, Pt = G[(k - 1) * s:, :s], G[(k - 1) * s:, s:]
+        R, flag = chol_flag(Om)
+        if flag or force_flag:
+            return ("flag", k - 1)
+        self.set_Hb(k, k - 1, R)
+        P = left_solve_upper_T(R, Pt)
+        YRi = right_solve_upper(Y, R)
+        ZP = right_solve_upper(np.vstack([Z, P]), R)
+        if self.inverse:
+            self.T[:(k - 1) * s, (k - 1) * s:k * s] = YRi
+            Hc = unit_upper_T_solve(self.T[:k * s, :k * s], ZP)
+        else:
+            self.T[:(k - 1) * s, (k - 1) * s:k * s] = -self.T[:(k - 1) * s, :(k - 1) * s] @ YRi
+            Hc = self.T[:k * s, :k * s].T @ ZP
+        self.set_Hcol(1, k, k, Hc)
+        Vk = right_solve_upper(self.U, R)
+        self.V.append(Vk)
+        self.U = right_solve_upper(W, R) - self.basis(k) @ Hc
+        return ("rel", k - 1)
+
+
+class BMGS_ICWY(BMGS_CWY):
+    inverse = True
+
+
+class BCGSI_LS(_Arnoldi):
+    """BCGSI+LS-Arnoldi, Alg. 7 (readings R4, R5)."""
+
+    def __init__(self, *a, **kw):
+        super().__init__(*a, **kw)
+        self.U = self.V[0]
+        self.J = None
+
+    def advance(self, force_flag=False):
+        self.k += 1
+        k, s = self.k, self.s
+        W = self._matvec(self.U)
+        if k == 1:
+            J = inner(self.U, W)
+            self._sync()
+            self._record(J)
+            self.J = J
+            self.set_Hb(1, 1, J)
+            self.U = W - self.V[0] @ J
+            return ("none", 0)
+        Vkm1 = self.basis(k - 1)
+        G = inner(np.hstack([Vkm1, self.U]), np.hstack([self.U, W]))
+        self._sync()
+        self._record(G)
+        Y, Z = G[:(k - 1) * s, :s], G[:(k - 1) * s, s:]
+        Omt, Pt = G[(k - 1) * s:, :s], G[(k - 1) * s:, s:]
+        R, flag = chol_flag(Omt - Y.T @ Y)
+        if flag or force_flag:
+            return ("flag", k - 1)
+        self.set_Hb(k, k - 1, R)
+        self.set_Hcol(1, k - 1, k - 1, self.J + Y)
+        P = left_solve_upper_T(R, Pt - Y.T @ Z)
+        ZP = np.vstack([Z, P])
+        Hk = self.H[:k * s, :(k - 1) * s]
+        self.J = right_solve_upper(ZP - Hk @ Y, R)
+        Vk = right_solve_upper(self.U - Vkm1 @ Y, R)
+        self.V.append(Vk)
+        self.U = right_solve_upper(W - self.basis(k) @ ZP, R)
+        return ("rel", k - 1)
+
+
+_CLASSES = {"bmgs": BMGS, "bcgs": BCGS, "bcgs_pip": BCGS_PIP,
+            "bmgs_cwy": BMGS_CWY, "bmgs_icwy": BMGS_ICWY, "bcgsi_ls": BCGSI_LS}
+
+_VAPPS = {"bmgs": (2, 0), "bcgs": (2, 0), "bcgs_pip": (3, 0),
+          "bmgs_cwy": (3, 1), "bmgs_icwy": (3, 1), "bcgsi_ls": (4, 1)}
+
+
+def arnoldi(A, B: np.ndarray, m: int, skeleton: str):
+    """m steps of a block Arnoldi skeleton from B (no restarts, no flags expected).
+    Returns (V_{m+1} as n x (m+1)s, H_{m+1,m}, Beta)."""
+    counts = {"a_calls": 0, "syncs": 0}
+    V1, Beta, flag = cholqr(B)
+    if flag:
+        raise FloatingPointError("CholQR of B flagged")
+    ar = _CLASSES[skeleton](A, V1, m, counts, None)
+    j = 0
+    while j < m:
+        kind, jj = ar.advance()
+        if kind == "flag":
+            raise FloatingPointError(f"chol flag at relation {jj}")
+        if kind == "rel":
+            j = jj
+    s = B.shape[1]
+    return ar.basis(m + 1), ar.H[:(m + 1) * s, :m * s].copy(), Beta
+
+
+# ---------------------------------------------------------------- small solves
+
+def cycle_coefficients(H: np.ndarray, j: int, s: int, Beta: np.ndarray, modification: str):
+    """For relation j of a cycle: M vector, Xi_j and the cospatial factor.
+
+    H_j = H[:js,:js], H_{j+1,j} = H[js:(j+1)s, (j-1)s:js].
+    BFOM: M = 0.  BGMRES: M = H_j^{-T} E_j (H_{j+1,j}^T H_{j+1,j})  (Sec. 2.4.1).
+    Xi_j = (H_j + M E_j^T)^{-1} E_1 Beta  (Eq. (7)); c = E_j^T Xi_j.
+    Returns (Mvec, Xi, c) or None if the small system is singular (reading R6).
+    """
+    js = j * s
+    Hj = H[:js, :js]
+    Hsub = H[js:js + s, js - s:js]
+    Ej = np.zeros((js, s))
+    Ej[js - s:, :] = np.eye(s)
+    E1B = np.zeros((js, s))
+    E1B[:s, :] = Beta
+    try:
+        if modification == "gmres":
+            Mvec = np.linalg.solve(Hj.T, Ej @ (Hsub.T @ Hsub))
+        else:
+            Mvec = np.zeros((js, s))
+        Xi = np.linalg.solve(Hj + Mvec @ Ej.T, E1B)
+    except np.linalg.LinAlgError:
+        return None
+    if not np.all(np.isfinite(Xi)):
+        return None
+    return Mvec, Xi, Xi[js - s:]
+
+
+def residual_estimate(H, j, s, Mvec, c, C, normB):
+    """||[M; -H_{j+1,j}] c C||_F / ||B||_F  (Eq. (9), reading R7)."""
+    js = j * s
+    Hsub = H[js:js + s, js - s:js]
+    return np.linalg.norm(np.vstack([Mvec, -Hsub]) @ c @ C) / normB
+
+
+# ---------------------------------------------------------------- driver
+
+@dataclass
+class Result:
+    X: np.ndarray
+    status: int
+    cycles: int = 0
+    steps: int = 0
+    a_calls: int = 0
+    syncs: int = 0
+    v_apps: int = 0
+    flags: int = 0
+    cycle_m: list = field(default_factory=list)       # relations completed per cycle
+    cycle_flag: list = field(default_factory=list)    # relation that flagged (0 = none)
+    m_cur: list = field(default_factory=list)         # max basis size in force per cycle
+    est_history: list = field(default_factory=list)   # (cycle, j, estimate)
+    relres_est: float = float("nan")
+    relres_true: float = float("nan")
+    first_cycle: dict | None = None
+
+
+def solve(A, B: np.ndarray, m: int, tol: float, skeleton: str = "bcgsi_ls",
+          modification: str = "gmres", max_restarts: int = 50, adaptive: bool = True,
+          verify_true_residual: bool = True, inject_flags=(), record_first_cycle: bool = False,
+          true_residual_each_cycle: bool = False, X_star: np.ndarray | None = None) -> Result:
+    """Restarted, adaptively restarted modified BFOM (BFOM or BGMRES) for A X = B
+    with the given block Arnoldi skeleton; X_0 = 0.
+
+    ``inject_flags`` is a set of (cycle, relation) pairs at which the chol flag
+    is forced (test hook: a host-decided input, reading R8 applies).
+    """
+    if skeleton not in _CLASSES:
+        raise ValueError(skeleton)
+    B = np.asarray(B, dtype=np.float64)
+    n, s = B.shape
+    normB = np.linalg.norm(B)
+    X = np.zeros((n, s))
+    C = np.eye(s)
+    m_cur = m
+    R_start = B
+    inject = set(tuple(x) for x in inject_flags)
+    counts = {"a_calls": 0, "syncs": 0}
+    res = Result(X=X, status=NOT_CONVERGED)
+    vper, vcyc = _VAPPS[skeleton]
+    cycle = 0
+    while True:
+        cycle += 1
+        if cycle > max_restarts + 1:
+            res.status = NOT_CONVERGED
+            break
+        counts["syncs"] += 1
+        V1, Beta, flag = cholqr(R_start)
+        if flag:
+            res.status = BREAKDOWN if cycle == 1 else NOT_CONVERGED
+            res.cycles = cycle
+            break
+        grams = [] if (record_first_cycle and cycle == 1) else None
+        ar = _CLASSES[skeleton](A, V1, m_cur, counts, grams)
+        res.m_cur.append(m_cur)
+        j, converged, flagged = 0, False, 0
+        coeffs = None
+        ests = []
+        while j < m_cur:
+            target = j + 1
+            kind, jj = ar.advance(force_flag=(cycle, target) in inject and _lagged_ready(ar, skeleton))
+            if kind == "none":
+                continue
+            if kind == "flag":
+                flagged = jj
+                res.flags += 1
+                break
+            j = jj
+            cf = cycle_coefficients(ar.H, j, s, Beta, modification)
+            if cf is None:
+                ests.append(float("nan"))
+                res.est_history.append((cycle, j, float("nan")))
+                coeffs = None
+                continue
+            coeffs = cf
+            est = residual_estimate(ar.H, j, s, cf[0], cf[2], C, normB)
+            ests.append(est)
+            res.est_history.append((cycle, j, est))
+            res.relres_est = est
+            if X_star is not None:
+                Xj = X + ar.basis(j) @ (cf[1] @ C)
+                if np.linalg.norm(Xj - X_star) <= tol * np.linalg.norm(X_star):
+                    converged = True
+                    break
+            elif est <= tol:
+                converged = True
+                break
+        res.cycles = cycle
+        res.cycle_m.append(j)
+        res.cycle_flag.append(flagged)
+        res.steps += j
+        res.v_apps += vper * j + (vcyc if j > 0 else 0)
+        if record_first_cycle and cycle == 1:
+            res.first_cycle = {"H": ar.H[:(j + 1) * s, :j * s].copy(), "Beta": Beta.copy(),
+                               "grams": grams, "V": ar.basis(j + 1) if j > 0 else V1,
+                               "est": list(ests), "j": j}
+        if flagged and adaptive:
+            m_cur = flagged - 1
+        if j == 0:
+            res.status = NOT_CONVERGED
+            break
+        if coeffs is None:
+            res.status = NOT_CONVERGED
+            break
+        Mvec, Xi, c = coeffs
+        Vj = ar.basis(j)
+        X = X + Vj @ (Xi @ C)
+        Hsub = ar.H[j * s:(j + 1) * s, (j - 1) * s:j * s]
+        U = ar.basis(j + 1) @ np.vstack([Mvec, -Hsub])
+        C = c @ C
+        if flagged and not adaptive:
+            res.status = NOT_CONVERGED
+            break
+        if true_residual_each_cycle or (converged and verify_true_residual):
+            Rt = B - spmm(A, X)
+            res.relres_true = np.linalg.norm(Rt) / normB
+        if converged:
+            if verify_true_residual and res.relres_true > tol:
+                R_start = Rt
+                C = np.eye(s)
+                continue
+            res.status = OK
+            break
+        R_start = U
+    res.X = X
+    res.a_calls = counts["a_calls"]
+    res.syncs = counts["syncs"]
+    if np.isnan(res.relres_true):
+        res.relres_true = np.linalg.norm(B - spmm(A, X)) / normB
+    return res
+
+
+def _lagged_ready(ar, skeleton):
+    """A forced flag applies to the iteration that would complete the target
+    relation: for lagged skeletons that is any iteration k >= 2."""
+    if skeleton in LAGGED:
+        return ar.k + 1 >= 2
+    return True
+
+
+# ---------------------------------------------------------------- diagnostics
+
+def loss_of_orthogonality(Q: np.ndarray) -> float:
+    """||I - <Q, Q>||_2  (Eq. (5))."""
+    return np.linalg.norm(np.eye(Q.shape[1]) - Q.T @ Q, 2)
+
+
+def arnoldi_residual(A, V: np.ndarray, H: np.ndarray, m: int, s: int) -> float:
+    """||A V_m - V_{m+1} H_{m+1,m}||_F  (Eq. (6))."""
+    return np.linalg.norm(spmm(A, V[:, :m * s]) - V[:, :(m + 1) * s] @ H[:(m + 1) * s, :m * s])
