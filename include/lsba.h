@@ -1,0 +1,181 @@
+/*
+ * lsba.h -- C ABI of the GB300 (sm_103a) low-synchronization block Arnoldi
+ * solver for A X = B: restarted, adaptively restarted BFOM / BGMRES.
+ *
+ * Method: K. Lund, "Adaptively restarted block Krylov subspace methods with
+ * low-synchronization skeletons" (arXiv 2208.09899).
+ *   - problem A X = B, A n x n sparse, B n x s, s << n            (Sec. 2, Eq. (1))
+ *   - classical block inner product <X,Y> = X^T Y                  (Table 1)
+ *   - skeletons: BCGS (Sec. 3.1), BCGS-PIP (Alg. 3), BMGS-CWY and
+ *     BMGS-ICWY (Alg. 6), BCGSI+LS (Alg. 7); muscle CholQR        (Sec. 2.3, Sec. 5)
+ *   - modified BFOM / BGMRES solution and cospatial residual      (Eq. (7), Thm. 1, Eq. (9))
+ *   - static restarts (Sec. 2.4.2) with adaptive restarting on a
+ *     Cholesky NaN-flag                                            (Sec. 4)
+ *
+ * Conventions for every entry point:
+ *   - Pointers named d_* are DEVICE pointers on the handle's device; h_* are
+ *     host pointers.  The caller owns every buffer it passes and keeps it alive
+ *     until the call returns.
+ *   - Block vectors are n x s, FP64, row-major (the s values of a row are
+ *     contiguous; a C-contiguous (n, s) array).  s must be 1..32.
+ *   - CSR matrices are 0-based, int32 row pointers and column indices (columns
+ *     sorted within a row), FP64 values; nnz < 2^31.
+ *   - Every call is ordered on the handle's CUDA stream and returns when its
+ *     results are complete (blocking).  One handle per host thread.
+ *   - Errors are returned as lsba_status codes, never thrown; no call aborts
+ *     the process.  A failed CUDA call leaves the handle usable only for
+ *     lsba_destroy.
+ */
+#ifndef LSBA_H
+#define LSBA_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lsba_ctx* lsba_handle;
+
+/* Status codes. */
+enum {
+  LSBA_OK = 0,
+  LSBA_NOT_CONVERGED = 1,   /* X holds the last iterate                        */
+  LSBA_BREAKDOWN = 2,       /* CholQR of B flagged (numerically rank-deficient B) */
+  LSBA_INVALID_ARG = 3,
+  LSBA_OUT_OF_MEMORY = 4,
+  LSBA_CUDA_ERROR = 5,
+  LSBA_DEVICE_TIMEOUT = 6   /* reserved */
+};
+
+/* Block Arnoldi skeletons (names as in the paper, Sec. 3). */
+typedef enum {
+  LSBA_BCGS = 0,            /* Sec. 3.1, 2 syncs per step                     */
+  LSBA_BCGS_PIP = 1,        /* Alg. 3, 1 sync per step                        */
+  LSBA_BCGSI_LS = 2,        /* Alg. 7, 1 sync per step, lagged normalization  */
+  LSBA_BMGS_ICWY = 3,       /* Alg. 6 (inverse compact WY branch)             */
+  LSBA_BMGS_CWY = 4         /* Alg. 6 (compact WY branch)                     */
+} lsba_skeleton;
+
+/* Low-rank modification of BFOM (Sec. 2.4.1, Eq. (7)). */
+enum { LSBA_FOM = 0, LSBA_GMRES = 1 };
+
+/* CSR matrix; all pointers are device pointers. */
+typedef struct {
+  int64_t n;
+  int64_t nnz;
+  const int32_t* d_rowptr;  /* n+1 */
+  const int32_t* d_colidx;  /* nnz */
+  const double* d_vals;     /* nnz */
+} lsba_csr;
+
+/* Solver options.  lsba_default_options() fills the defaults shown. */
+typedef struct {
+  int32_t modification;          /* LSBA_GMRES (default) or LSBA_FOM                    */
+  int32_t max_restarts;          /* 50: at most max_restarts+1 cycles                   */
+  int32_t adaptive_restart;      /* 1: on a Cholesky flag shrink m and restart (Sec. 4);
+                                    0: a flag ends the solve (NOT_CONVERGED)            */
+  int32_t verify_true_residual;  /* 1: confirm convergence with ||B - A X||_F/||B||_F;
+                                    if above tol, restart from B - A X                  */
+  int32_t record_history;        /* 1: keep per-step estimates, the first cycle's Gram
+                                    outputs and Hessenberg matrix (lsba_get_history)    */
+  int32_t inject_flag_cycle;     /* test hook: force the Cholesky flag while completing */
+  int32_t inject_flag_relation;  /* relation inject_flag_relation of cycle
+                                    inject_flag_cycle (1-based); -1 disables            */
+  int32_t reserved[8];
+} lsba_options;
+
+/* Counters and outcome of the last lsba_solve. */
+typedef struct {
+  int32_t status;
+  int32_t cycles;          /* restart cycles run                                 */
+  int32_t steps;           /* completed Arnoldi relations over all cycles        */
+  int32_t a_calls;         /* applications of A (SpMM launches that did work)    */
+  int32_t syncs;           /* sync points: block inner products + IntraOrtho     */
+  int32_t v_apps;          /* applications of the basis (paper's counting)       */
+  int32_t flags;           /* Cholesky NaN-flags raised                          */
+  int32_t m_final;         /* maximum basis size in force at the end             */
+  double relres_est;       /* last residual estimate ||[M;-H] c C||_F / ||B||_F  */
+  double relres_true;      /* ||B - A X||_F / ||B||_F (NaN if not computed)       */
+  double solve_ms;         /* wall time of lsba_solve                            */
+} lsba_stats;
+
+/* Host-side copies kept by the handle when record_history = 1; valid until the
+ * next lsba_solve or lsba_destroy.  Matrices are column-major. */
+typedef struct {
+  int32_t n_est;                 /* entries in est / est_cycle / est_j             */
+  const double* est;             /* residual estimate after each relation          */
+  const int32_t* est_cycle;      /* its cycle (1-based)                            */
+  const int32_t* est_j;          /* its relation index j                           */
+  int32_t n_cycles;
+  const int32_t* cycle_m;        /* relations completed per cycle                  */
+  const int32_t* cycle_flag;     /* relation that flagged per cycle (0 none)       */
+  const int32_t* cycle_mcur;     /* maximum basis size in force per cycle          */
+  int32_t first_j;               /* relations completed in the first cycle         */
+  const double* first_H;         /* (first_j+1)s x first_j*s, ld = (first_j+1)s    */
+  const double* first_beta;      /* s x s, the CholQR factor of B                  */
+  int32_t n_grams;               /* skeleton inner products recorded, first cycle  */
+  const int32_t* gram_rows;      /* rows of each (row-major data, concatenated)    */
+  const int32_t* gram_cols;
+  const double* gram_data;
+} lsba_history;
+
+/* Fill *opt with the defaults. */
+void lsba_default_options(lsba_options* opt);
+
+/* Create a solver handle on `device`, ordered on `cuda_stream` (a cudaStream_t;
+ * NULL = the legacy default stream).  opt may be NULL (defaults).  The handle
+ * owns its workspace, allocated on first use and grown on demand. */
+int lsba_create(lsba_handle* out, int device, void* cuda_stream, const lsba_options* opt);
+
+/* Replace the handle's options. */
+int lsba_set_options(lsba_handle h, const lsba_options* opt);
+
+/* Solve A X = B with restarted block Arnoldi of maximum basis size m (m >= 1,
+ * (m+1)*s <= 2048) to relative residual tol: ||B - A X||_F / ||B||_F <= tol
+ * (by the estimate of Eq. (9), confirmed on the true residual when
+ * verify_true_residual is set).  X_0 = 0.
+ *   A:   CSR on the device (see lsba_csr)
+ *   d_B: n x s input, d_X: n x s output (the caller's device buffers)
+ * Returns LSBA_OK, LSBA_NOT_CONVERGED (X = last iterate), LSBA_BREAKDOWN, or an
+ * error code. */
+int lsba_solve(lsba_handle h, const lsba_csr* A, const double* d_B, double* d_X,
+               int s, int m, double tol, lsba_skeleton skel);
+
+/* Same solve with HOST buffers for the matrix and the blocks: the handle copies
+ * A and B to the device, solves, and copies X back (timed end to end). */
+int lsba_solve_host(lsba_handle h, int64_t n, int64_t nnz, const int32_t* h_rowptr,
+                    const int32_t* h_colidx, const double* h_vals, const double* h_B,
+                    double* h_X, int s, int m, double tol, lsba_skeleton skel);
+
+int lsba_get_stats(lsba_handle h, lsba_stats* out);
+int lsba_get_history(lsba_handle h, lsba_history* out);
+const char* lsba_status_string(int status);
+int lsba_destroy(lsba_handle h);
+
+/* ---- kernel-level entry points (one hot-path step each; used for parity and
+ * roofline measurement).  All are blocking on the handle's stream. ---------- */
+
+/* W = A V  (the paper's matvec on a block vector, Sec. 2.1).  V, W: n x s. */
+int lsba_spmm(lsba_handle h, const lsba_csr* A, const double* d_V, double* d_W, int s);
+
+/* Block inner product G = [L_1 .. L_a]^T [R_1 .. R_b] (Table 1; the one-pass
+ * sync point of Alg. 3 line 4, Alg. 6 line 10, Alg. 7 line 10).
+ *   d_L: a blocks of n x s, contiguous ([a][n][s]); d_R: b blocks likewise.
+ *   d_G: (a*s) x (b*s) output, row-major.  1 <= a <= 2048/s, 1 <= b <= 2.
+ * Summation order is fixed: the result is bitwise reproducible run to run. */
+int lsba_gram(lsba_handle h, const double* d_L, int a, const double* d_R, int b,
+              int64_t n, int s, double* d_G);
+
+/* Block combination (the basis update of Alg. 3 line 6 / Alg. 7 lines 16-17):
+ *   out[r,:] = ( sum_i in_i[r,:] * C_i ) * T^{-1}
+ *   d_in: nin blocks n x s contiguous; d_C: nin*s x s row-major (block i of rows
+ *   is C_i); d_T: s x s upper-triangular (row-major) or NULL for no solve. */
+int lsba_combine(lsba_handle h, const double* d_in, int nin, int64_t n, int s,
+                 const double* d_C, const double* d_T, double* d_out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LSBA_H */

@@ -1,0 +1,717 @@
+// Host engine and C ABI: restarted, adaptively restarted BFOM / BGMRES with a
+// low-synchronization block Arnoldi skeleton (arXiv 2208.09899, Sec. 2.4 and 4).
+//
+// Each restart cycle is enqueued on the handle's stream as one batch: the
+// CholQR of the start block, then every loop iteration the cycle may need
+// (SpMM, one-pass Gram, small step kernel, basis update).  The small kernel
+// clears the device-side `active` flag when the cycle ends (estimate below tol,
+// a Cholesky NaN-flag, or the basis size limit), which turns the remaining
+// launches of the batch into no-ops; the host then reads the 100-byte control
+// record once per cycle and enqueues the cycle end (X and U update) with the
+// next cycle.
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/lsba.h"
+#include "lsba_internal.cuh"
+
+using namespace lsba;
+
+struct lsba_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  lsba_options opt;
+  int num_sms = 0;
+  // workspace capacity
+  int64_t cap_n = 0;
+  int cap_s = 0, cap_m = 0;
+  double* basis = nullptr;     // (m+1) blocks
+  double* Wb = nullptr;        // n x s
+  double* Ub = nullptr;        // n x s
+  double* partials = nullptr;
+  size_t partials_cap = 0;
+  double* Gbuf = nullptr;
+  size_t G_cap = 0;
+  double* small = nullptr;     // all small matrices
+  size_t small_cap = 0;
+  int* ismall = nullptr;
+  size_t ismall_cap = 0;
+  Ctl* d_ctl = nullptr;
+  Ctl* h_ctl = nullptr;        // pinned mirror
+  SmallWs ws;
+  // host-buffer solve
+  int32_t* hA_rowptr = nullptr;
+  int32_t* hA_colidx = nullptr;
+  double* hA_vals = nullptr;
+  double* hB = nullptr;
+  double* hX = nullptr;
+  int64_t host_n = 0, host_nnz = 0;
+  int host_s = 0;
+  // results
+  lsba_stats stats;
+  std::vector<double> h_est;
+  std::vector<int32_t> h_est_cycle, h_est_j, h_cycle_m, h_cycle_flag, h_cycle_mcur;
+  std::vector<double> h_first_H, h_first_beta, h_gram_data;
+  std::vector<int32_t> h_gram_rows, h_gram_cols;
+  int first_j = 0;
+};
+
+#define CK(x)                                         \
+  do {                                                \
+    cudaError_t e_ = (x);                             \
+    if (e_ != cudaSuccess) {                          \
+      fprintf(stderr, "lsba: CUDA error %s at %s:%d\n", cudaGetErrorString(e_), __FILE__, __LINE__); \
+      return LSBA_CUDA_ERROR;                         \
+    }                                                 \
+  } while (0)
+
+static void free_ws(lsba_ctx* h) {
+  cudaFree(h->basis);
+  cudaFree(h->Wb);
+  cudaFree(h->Ub);
+  cudaFree(h->partials);
+  cudaFree(h->Gbuf);
+  cudaFree(h->small);
+  cudaFree(h->ismall);
+  h->basis = h->Wb = h->Ub = h->partials = h->Gbuf = h->small = nullptr;
+  h->ismall = nullptr;
+  h->cap_n = 0;
+  h->cap_s = h->cap_m = 0;
+  h->partials_cap = h->G_cap = h->small_cap = h->ismall_cap = 0;
+}
+
+static size_t max_partials(int64_t n, int s, int mmax, int sms, size_t* qmax_out) {
+  size_t best = 0, qmax = 0;
+  for (int a = 1; a <= mmax + 2; ++a)
+    for (int b = 1; b <= 2; ++b) {
+      GramPlan p = plan_gram(n, s, a, b, sms);
+      size_t v = (size_t)p.grid_x * p.q;
+      if (v > best) best = v;
+      if ((size_t)p.q > qmax) qmax = p.q;
+    }
+  *qmax_out = qmax;
+  return best;
+}
+
+// Allocate (or grow) the workspace for n x s blocks and basis size m.
+static int ensure_ws(lsba_ctx* h, int64_t n, int s, int m) {
+  if (n <= h->cap_n && s == h->cap_s && m <= h->cap_m && h->basis) return LSBA_OK;
+  free_ws(h);
+  const size_t blk = (size_t)n * s;
+  if (cudaMalloc(&h->basis, sizeof(double) * blk * (m + 1)) != cudaSuccess ||
+      cudaMalloc(&h->Wb, sizeof(double) * blk) != cudaSuccess ||
+      cudaMalloc(&h->Ub, sizeof(double) * blk) != cudaSuccess) {
+    cudaGetLastError();
+    free_ws(h);
+    return LSBA_OUT_OF_MEMORY;
+  }
+  size_t qmax = 0;
+  h->partials_cap = max_partials(n, s, m, h->num_sms, &qmax);
+  h->G_cap = qmax;
+  const int ldH = (m + 2) * s, ldR = (m + 1) * s;
+  const size_t ss = (size_t)s * s;
+  const size_t hist_cap = (size_t)(h->opt.max_restarts + 3) * (m + 2) + 16;
+  const size_t gram_hist_cap = (size_t)(m + 3) * (m + 3) * 2 * ss + 64;
+  size_t off = 0;
+  auto take = [&](size_t count) {
+    size_t o = off;
+    off += (count + 31) & ~(size_t)31;
+    return o;
+  };
+  const size_t oH = take((size_t)ldH * (m + 1) * s), oT = take((size_t)ldH * ldH),
+               oJ = take((size_t)ldH * s), oc1 = take((size_t)(m + 4) * ss),
+               oc2 = take((size_t)(m + 4) * ss), och = take(ss), ot1 = take(ss), ot2 = take(ss),
+               oRb = take((size_t)ldR * ldR), orf = take((size_t)(m + 1) * 2 * ss),
+               otau = take((size_t)(m + 1) * s), og = take((size_t)ldH * s), oTf = take(ss),
+               ogf = take(ss), ocf = take(ss), ouf = take((size_t)ldH * s), oC = take(ss),
+               oBc = take(ss), oXi = take((size_t)ldH * s), oMv = take((size_t)ldH * s),
+               owk = take((size_t)6 * ldH * s + 16 * ss), ohe = take(hist_cap),
+               ogh = take(gram_hist_cap);
+  h->small_cap = off;
+  if (cudaMalloc(&h->small, sizeof(double) * off) != cudaSuccess ||
+      cudaMalloc(&h->partials, sizeof(double) * h->partials_cap) != cudaSuccess ||
+      cudaMalloc(&h->Gbuf, sizeof(double) * h->G_cap) != cudaSuccess) {
+    cudaGetLastError();
+    free_ws(h);
+    return LSBA_OUT_OF_MEMORY;
+  }
+  h->ismall_cap = 2 * hist_cap + 2 * (m + 4);
+  if (cudaMalloc(&h->ismall, sizeof(int) * h->ismall_cap) != cudaSuccess) {
+    cudaGetLastError();
+    free_ws(h);
+    return LSBA_OUT_OF_MEMORY;
+  }
+  cudaMemsetAsync(h->small, 0, sizeof(double) * off, h->stream);
+  SmallWs& w = h->ws;
+  w.s = s;
+  w.m = m;
+  w.ldH = ldH;
+  w.ldT = ldH;
+  w.ldR = ldR;
+  double* b = h->small;
+  w.H = b + oH;
+  w.T = b + oT;
+  w.J = b + oJ;
+  w.G = h->Gbuf;
+  w.coef1 = b + oc1;
+  w.coef2 = b + oc2;
+  w.chain = b + och;
+  w.tri1 = b + ot1;
+  w.tri2 = b + ot2;
+  w.Rbar = b + oRb;
+  w.refl = b + orf;
+  w.tau = b + otau;
+  w.g = b + og;
+  w.Tfom = b + oTf;
+  w.gfom = b + ogf;
+  w.cfom = b + ocf;
+  w.ufom = b + ouf;
+  w.Cfac = b + oC;
+  w.Bcyc = b + oBc;
+  w.Xi = b + oXi;
+  w.Mvec = b + oMv;
+  w.work = b + owk;
+  w.hist_est = b + ohe;
+  w.gram_hist = b + ogh;
+  w.hist_cycle = h->ismall;
+  w.hist_j = h->ismall + hist_cap;
+  w.gram_dims = h->ismall + 2 * hist_cap;
+  w.ctl = h->d_ctl;
+  h->h_ctl->hist_cap = (int)hist_cap;
+  h->h_ctl->gram_hist_cap = (int)gram_hist_cap;
+  h->cap_n = n;
+  h->cap_s = s;
+  h->cap_m = m;
+  return LSBA_OK;
+}
+
+static BlockPtrs basis_list(const lsba_ctx* h, int64_t n, int s, int count) {
+  BlockPtrs p;
+  memset(&p, 0, sizeof(p));
+  for (int i = 0; i < count; ++i) p.p[i] = h->basis + (size_t)i * n * s;
+  return p;
+}
+
+static int push_ctl(lsba_ctx* h) {
+  CK(cudaMemcpyAsync(h->d_ctl, h->h_ctl, sizeof(Ctl), cudaMemcpyHostToDevice, h->stream));
+  return LSBA_OK;
+}
+static int pull_ctl(lsba_ctx* h) {
+  CK(cudaMemcpyAsync(h->h_ctl, h->d_ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return LSBA_OK;
+}
+
+enum { SK_BCGS = 0, SK_PIP = 1, SK_LS = 2, SK_ICWY = 3, SK_CWY = 4 };
+static bool lagged(int skel) { return skel == SK_LS || skel == SK_ICWY || skel == SK_CWY; }
+
+// Enqueue the CholQR of R_start and every loop iteration of one cycle.
+static void enqueue_cycle(lsba_ctx* h, const lsba_csr* A, const double* Rstart, int64_t n, int s,
+                          int m_cur, int start_flags) {
+  cudaStream_t st = h->stream;
+  const SmallWs& w = h->ws;
+  const int skel = w.skel;
+  BlockPtrs one;
+  memset(&one, 0, sizeof(one));
+  one.p[0] = Rstart;
+  {
+    GramPlan p = plan_gram(n, s, 1, 1, h->num_sms);
+    launch_gram(st, p, one, 1, one, 1, n, s, h->partials, h->Gbuf, h->d_ctl, 0);
+  }
+  launch_small_start(st, w, start_flags);
+  launch_update(st, one, 1, n, s, h->basis, w.coef1, w.tri1, nullptr, nullptr, nullptr, nullptr,
+                h->d_ctl, 0);
+  const int kmax = lagged(skel) ? m_cur + 1 : m_cur;
+  const size_t blk = (size_t)n * s;
+  for (int k = 1; k <= kmax; ++k) {
+    if (skel == SK_PIP || skel == SK_BCGS) {
+      const double* Vk = h->basis + (size_t)(k - 1) * blk;
+      launch_spmm(st, n, A->d_rowptr, A->d_colidx, A->d_vals, Vk, h->Wb, s, h->d_ctl, 1);
+      BlockPtrs L = basis_list(h, n, s, k);
+      BlockPtrs R;
+      memset(&R, 0, sizeof(R));
+      R.p[0] = h->Wb;
+      BlockPtrs in = basis_list(h, n, s, k);
+      in.p[k] = h->Wb;
+      double* Vnext = h->basis + (size_t)k * blk;
+      if (skel == SK_PIP) {
+        L.p[k] = h->Wb;
+        GramPlan p = plan_gram(n, s, k + 1, 1, h->num_sms);
+        launch_gram(st, p, L, k + 1, R, 1, n, s, h->partials, h->Gbuf, h->d_ctl, 1);
+        launch_small_step(st, w, k, 0);
+        launch_update(st, in, k + 1, n, s, Vnext, w.coef1, w.tri1, nullptr, nullptr, nullptr,
+                      nullptr, h->d_ctl, k);
+      } else {
+        GramPlan p = plan_gram(n, s, k, 1, h->num_sms);
+        launch_gram(st, p, L, k, R, 1, n, s, h->partials, h->Gbuf, h->d_ctl, 1);
+        launch_small_step(st, w, k, 0);
+        launch_update(st, in, k + 1, n, s, h->Wb, w.coef1, nullptr, nullptr, nullptr, nullptr,
+                      nullptr, h->d_ctl, k);
+        GramPlan p2 = plan_gram(n, s, 1, 1, h->num_sms);
+        launch_gram(st, p2, R, 1, R, 1, n, s, h->partials, h->Gbuf, h->d_ctl, 1);
+        launch_small_step(st, w, k, 1);
+        launch_update(st, R, 1, n, s, Vnext, w.coef1, w.tri1, nullptr, nullptr, nullptr, nullptr,
+                      h->d_ctl, k);
+      }
+    } else {
+      const double* U = (k == 1) ? h->basis : h->Ub;
+      launch_spmm(st, n, A->d_rowptr, A->d_colidx, A->d_vals, U, h->Wb, s, h->d_ctl, 1);
+      if (k == 1) {
+        BlockPtrs L = basis_list(h, n, s, 1);
+        BlockPtrs R;
+        memset(&R, 0, sizeof(R));
+        R.p[0] = h->Wb;
+        GramPlan p = plan_gram(n, s, 1, 1, h->num_sms);
+        launch_gram(st, p, L, 1, R, 1, n, s, h->partials, h->Gbuf, h->d_ctl, 1);
+        launch_small_step(st, w, 1, 0);
+        BlockPtrs in = basis_list(h, n, s, 1);
+        in.p[1] = h->Wb;
+        launch_update(st, in, 2, n, s, h->Ub, w.coef1, nullptr, nullptr, nullptr, nullptr, nullptr,
+                      h->d_ctl, 1);
+      } else {
+        BlockPtrs L = basis_list(h, n, s, k - 1);
+        L.p[k - 1] = h->Ub;
+        BlockPtrs R;
+        memset(&R, 0, sizeof(R));
+        R.p[0] = h->Ub;
+        R.p[1] = h->Wb;
+        GramPlan p = plan_gram(n, s, k, 2, h->num_sms);
+        launch_gram(st, p, L, k, R, 2, n, s, h->partials, h->Gbuf, h->d_ctl, 1);
+        launch_small_step(st, w, k, 0);
+        BlockPtrs in = basis_list(h, n, s, k - 1);
+        in.p[k - 1] = h->Ub;
+        in.p[k] = h->Wb;
+        double* Vk = h->basis + (size_t)(k - 1) * blk;
+        launch_update(st, in, k + 1, n, s, Vk, w.coef1, w.tri1, h->Ub, w.coef2, w.chain,
+                      skel == SK_LS ? w.tri2 : nullptr, h->d_ctl, k);
+      }
+    }
+  }
+}
+
+extern "C" {
+
+void lsba_default_options(lsba_options* o) {
+  if (!o) return;
+  memset(o, 0, sizeof(*o));
+  o->modification = LSBA_GMRES;
+  o->max_restarts = 50;
+  o->adaptive_restart = 1;
+  o->verify_true_residual = 1;
+  o->record_history = 0;
+  o->inject_flag_cycle = -1;
+  o->inject_flag_relation = -1;
+}
+
+const char* lsba_status_string(int st) {
+  switch (st) {
+    case LSBA_OK: return "ok";
+    case LSBA_NOT_CONVERGED: return "not converged";
+    case LSBA_BREAKDOWN: return "breakdown: CholQR of B flagged";
+    case LSBA_INVALID_ARG: return "invalid argument";
+    case LSBA_OUT_OF_MEMORY: return "out of device memory";
+    case LSBA_CUDA_ERROR: return "CUDA error";
+    case LSBA_DEVICE_TIMEOUT: return "device timeout";
+    default: return "unknown status";
+  }
+}
+
+int lsba_create(lsba_handle* out, int device, void* cuda_stream, const lsba_options* opt) {
+  if (!out) return LSBA_INVALID_ARG;
+  *out = nullptr;
+  int ndev = 0;
+  CK(cudaGetDeviceCount(&ndev));
+  if (device < 0 || device >= ndev) return LSBA_INVALID_ARG;
+  CK(cudaSetDevice(device));
+  lsba_ctx* h = new (std::nothrow) lsba_ctx();
+  if (!h) return LSBA_OUT_OF_MEMORY;
+  h->device = device;
+  h->stream = (cudaStream_t)cuda_stream;
+  if (opt) h->opt = *opt;
+  else lsba_default_options(&h->opt);
+  cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, device);
+  if (cudaMalloc(&h->d_ctl, sizeof(Ctl)) != cudaSuccess ||
+      cudaMallocHost(&h->h_ctl, sizeof(Ctl)) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(h->d_ctl);
+    delete h;
+    return LSBA_OUT_OF_MEMORY;
+  }
+  memset(h->h_ctl, 0, sizeof(Ctl));
+  memset(&h->ws, 0, sizeof(h->ws));
+  memset(&h->stats, 0, sizeof(h->stats));
+  *out = h;
+  return LSBA_OK;
+}
+
+int lsba_set_options(lsba_handle h, const lsba_options* opt) {
+  if (!h || !opt) return LSBA_INVALID_ARG;
+  const int old_restarts = h->opt.max_restarts;
+  h->opt = *opt;
+  if (opt->max_restarts > old_restarts) free_ws(h);  // history capacity depends on it
+  return LSBA_OK;
+}
+
+int lsba_destroy(lsba_handle h) {
+  if (!h) return LSBA_INVALID_ARG;
+  cudaSetDevice(h->device);
+  free_ws(h);
+  cudaFree(h->d_ctl);
+  cudaFreeHost(h->h_ctl);
+  cudaFree(h->hA_rowptr);
+  cudaFree(h->hA_colidx);
+  cudaFree(h->hA_vals);
+  cudaFree(h->hB);
+  cudaFree(h->hX);
+  delete h;
+  return LSBA_OK;
+}
+
+static int skel_code(lsba_skeleton s) {
+  switch (s) {
+    case LSBA_BCGS: return SK_BCGS;
+    case LSBA_BCGS_PIP: return SK_PIP;
+    case LSBA_BCGSI_LS: return SK_LS;
+    case LSBA_BMGS_ICWY: return SK_ICWY;
+    case LSBA_BMGS_CWY: return SK_CWY;
+    default: return -1;
+  }
+}
+
+static int solve_impl(lsba_handle h, const lsba_csr* A, const double* d_B, double* d_X, int s, int m,
+                      double tol, lsba_skeleton skel_in) {
+  auto t0 = std::chrono::steady_clock::now();
+  memset(&h->stats, 0, sizeof(h->stats));
+  h->stats.relres_true = NAN;
+  h->stats.relres_est = NAN;
+  const int skel = skel_code(skel_in);
+  if (!A || !d_B || !d_X || skel < 0 || s < 1 || s > LSBA_MAX_S || m < 1 ||
+      (int64_t)(m + 1) * s > LSBA_MAX_MS || m + 3 > LSBA_MAXB || A->n < 1 || A->nnz < 0 ||
+      A->nnz >= (int64_t)1 << 31 || !A->d_rowptr || (A->nnz > 0 && (!A->d_colidx || !A->d_vals)) ||
+      !(tol >= 0.0) || h->opt.max_restarts < 0)
+    return h->stats.status = LSBA_INVALID_ARG;
+  const int64_t n = A->n;
+  CK(cudaSetDevice(h->device));
+  int rc = ensure_ws(h, n, s, m);
+  if (rc != LSBA_OK) return h->stats.status = rc;
+  SmallWs& w = h->ws;
+  w.skel = skel;
+  w.modification = h->opt.modification == LSBA_FOM ? 0 : 1;
+  cudaStream_t st = h->stream;
+  const size_t blk = (size_t)n * s;
+  CK(cudaMemsetAsync(d_X, 0, sizeof(double) * blk, st));
+  Ctl* c = h->h_ctl;
+  const int hist_cap = c->hist_cap, gram_cap = c->gram_hist_cap;
+  memset(c, 0, sizeof(Ctl));
+  c->hist_cap = hist_cap;
+  c->gram_hist_cap = gram_cap;
+  c->tol = tol;
+  c->record = h->opt.record_history ? 1 : 0;
+  c->update_step = -1;
+  h->h_est.clear();
+  h->h_est_cycle.clear();
+  h->h_est_j.clear();
+  h->h_cycle_m.clear();
+  h->h_cycle_flag.clear();
+  h->h_cycle_mcur.clear();
+  h->h_first_H.clear();
+  h->h_first_beta.clear();
+  h->h_gram_data.clear();
+  h->h_gram_rows.clear();
+  h->h_gram_cols.clear();
+  h->first_j = 0;
+
+  const int vper = (skel == SK_LS) ? 4 : (skel == SK_PIP || lagged(skel)) ? 3 : 2;
+  const int vcyc = lagged(skel) ? 1 : 0;
+  int m_cur = m;
+  const double* Rstart = d_B;
+  int start_flags = 3;
+  int status = LSBA_NOT_CONVERGED;
+  lsba_stats& S = h->stats;
+  int cycle = 0;
+  bool have_true = false;
+  while (true) {
+    ++cycle;
+    if (cycle > h->opt.max_restarts + 1) {
+      status = LSBA_NOT_CONVERGED;
+      --cycle;
+      break;
+    }
+    c->cycle = cycle;
+    c->m_cur = m_cur;
+    c->inject_relation = (cycle == h->opt.inject_flag_cycle) ? h->opt.inject_flag_relation : -1;
+    if ((rc = push_ctl(h)) != LSBA_OK) return S.status = rc;
+    enqueue_cycle(h, A, Rstart, n, s, m_cur, start_flags);
+    CK(cudaGetLastError());
+    if ((rc = pull_ctl(h)) != LSBA_OK) return S.status = rc;
+    S.syncs += 1;
+    if (c->start_flag) {
+      status = (cycle == 1) ? LSBA_BREAKDOWN : LSBA_NOT_CONVERGED;
+      break;
+    }
+    const int j = c->j;
+    const int f = c->flagged ? 1 : 0;
+    S.flags += f;
+    h->h_cycle_m.push_back(j);
+    h->h_cycle_flag.push_back(c->flagged);
+    h->h_cycle_mcur.push_back(m_cur);
+    S.steps += j;
+    int a_calls;
+    if (lagged(skel)) a_calls = j + 1 + f;
+    else a_calls = j + f;
+    S.a_calls += a_calls;
+    S.syncs += (skel == SK_BCGS) ? 2 * a_calls : a_calls;
+    S.v_apps += vper * j + (j > 0 ? vcyc : 0);
+    if (!std::isnan(c->est)) S.relres_est = c->est;
+    if (cycle == 1 && h->opt.record_history) {
+      h->first_j = j;
+      if (j > 0) {
+        const int rows = (j + 1) * s, cols = j * s;
+        h->h_first_H.resize((size_t)rows * cols);
+        CK(cudaMemcpy2D(h->h_first_H.data(), sizeof(double) * rows, w.H, sizeof(double) * w.ldH,
+                        sizeof(double) * rows, cols, cudaMemcpyDeviceToHost));
+      }
+      h->h_first_beta.resize((size_t)s * s);
+      CK(cudaMemcpy(h->h_first_beta.data(), w.Bcyc, sizeof(double) * s * s, cudaMemcpyDeviceToHost));
+    }
+    if (c->flagged && h->opt.adaptive_restart) m_cur = c->flagged - 1;
+    if (j == 0) {
+      status = LSBA_NOT_CONVERGED;
+      break;
+    }
+    if (w.modification == 0 && c->fom_singular) {
+      status = LSBA_NOT_CONVERGED;
+      break;
+    }
+    // Cycle end: X += V_j Xi C, U = V_{j+1} [M; -H], C <- c C.
+    launch_small_end(st, w);
+    {
+      BlockPtrs in = basis_list(h, n, s, j + 1);
+      in.p[j + 1] = d_X;
+      launch_update(st, in, j + 2, n, s, d_X, w.coef1, nullptr, h->Ub, w.coef2, nullptr, nullptr,
+                    h->d_ctl, LSBA_END_STEP);
+    }
+    CK(cudaGetLastError());
+    if (c->flagged && !h->opt.adaptive_restart) {
+      status = LSBA_NOT_CONVERGED;
+      break;
+    }
+    if (c->converged) {
+      if (h->opt.verify_true_residual) {
+        // R = B - A X into Ub; ||R||_F / ||B||_F from its Gram.
+        launch_spmm(st, n, A->d_rowptr, A->d_colidx, A->d_vals, d_X, h->Wb, s, nullptr, 0);
+        launch_axpby(st, n, s, d_B, h->Wb, h->Ub);
+        BlockPtrs one;
+        memset(&one, 0, sizeof(one));
+        one.p[0] = h->Ub;
+        GramPlan p = plan_gram(n, s, 1, 1, h->num_sms);
+        launch_gram(st, p, one, 1, one, 1, n, s, h->partials, h->Gbuf, nullptr, 0);
+        launch_true_relres(st, h->Gbuf, s, h->d_ctl);
+        if ((rc = pull_ctl(h)) != LSBA_OK) return S.status = rc;
+        S.relres_true = c->relres_true;
+        have_true = true;
+        if (!(c->relres_true <= tol)) {
+          Rstart = h->Ub;
+          start_flags = 2;
+          continue;
+        }
+      }
+      status = LSBA_OK;
+      break;
+    }
+    Rstart = h->Ub;
+    start_flags = 0;
+  }
+  S.cycles = cycle;
+  S.m_final = m_cur;
+  S.status = status;
+  // True residual of the returned X.
+  if (!have_true && status != LSBA_INVALID_ARG) {
+    launch_spmm(st, n, A->d_rowptr, A->d_colidx, A->d_vals, d_X, h->Wb, s, nullptr, 0);
+    launch_axpby(st, n, s, d_B, h->Wb, h->Ub);
+    BlockPtrs one;
+    memset(&one, 0, sizeof(one));
+    one.p[0] = h->Ub;
+    GramPlan p = plan_gram(n, s, 1, 1, h->num_sms);
+    launch_gram(st, p, one, 1, one, 1, n, s, h->partials, h->Gbuf, nullptr, 0);
+    launch_true_relres(st, h->Gbuf, s, h->d_ctl);
+    if ((rc = pull_ctl(h)) != LSBA_OK) return S.status = rc;
+    S.relres_true = c->relres_true;
+  }
+  CK(cudaStreamSynchronize(st));
+  if (h->opt.record_history) {
+    const int ne = c->n_hist;
+    h->h_est.resize(ne);
+    h->h_est_cycle.resize(ne);
+    h->h_est_j.resize(ne);
+    if (ne > 0) {
+      CK(cudaMemcpy(h->h_est.data(), w.hist_est, sizeof(double) * ne, cudaMemcpyDeviceToHost));
+      CK(cudaMemcpy(h->h_est_cycle.data(), w.hist_cycle, sizeof(int) * ne, cudaMemcpyDeviceToHost));
+      CK(cudaMemcpy(h->h_est_j.data(), w.hist_j, sizeof(int) * ne, cudaMemcpyDeviceToHost));
+    }
+    const int ng = c->n_gram_hist;
+    std::vector<int> dims(2 * ng);
+    if (ng > 0)
+      CK(cudaMemcpy(dims.data(), w.gram_dims, sizeof(int) * 2 * ng, cudaMemcpyDeviceToHost));
+    h->h_gram_rows.resize(ng);
+    h->h_gram_cols.resize(ng);
+    for (int i = 0; i < ng; ++i) {
+      h->h_gram_rows[i] = dims[2 * i];
+      h->h_gram_cols[i] = dims[2 * i + 1];
+    }
+    h->h_gram_data.resize(c->gram_hist_used);
+    if (c->gram_hist_used > 0)
+      CK(cudaMemcpy(h->h_gram_data.data(), w.gram_hist, sizeof(double) * c->gram_hist_used,
+                    cudaMemcpyDeviceToHost));
+  }
+  auto t1 = std::chrono::steady_clock::now();
+  S.solve_ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
+  return status;
+}
+
+int lsba_solve(lsba_handle h, const lsba_csr* A, const double* d_B, double* d_X, int s, int m,
+               double tol, lsba_skeleton skel) {
+  if (!h) return LSBA_INVALID_ARG;
+  return solve_impl(h, A, d_B, d_X, s, m, tol, skel);
+}
+
+int lsba_solve_host(lsba_handle h, int64_t n, int64_t nnz, const int32_t* h_rowptr,
+                    const int32_t* h_colidx, const double* h_vals, const double* h_B, double* h_X,
+                    int s, int m, double tol, lsba_skeleton skel) {
+  if (!h || n < 1 || nnz < 0 || !h_rowptr || !h_B || !h_X || s < 1 || s > LSBA_MAX_S ||
+      (nnz > 0 && (!h_colidx || !h_vals)))
+    return LSBA_INVALID_ARG;
+  CK(cudaSetDevice(h->device));
+  if (n != h->host_n || nnz != h->host_nnz || s != h->host_s) {
+    cudaFree(h->hA_rowptr);
+    cudaFree(h->hA_colidx);
+    cudaFree(h->hA_vals);
+    cudaFree(h->hB);
+    cudaFree(h->hX);
+    h->hA_rowptr = nullptr;
+    h->hA_colidx = nullptr;
+    h->hA_vals = nullptr;
+    h->hB = h->hX = nullptr;
+    h->host_n = h->host_nnz = 0;
+    if (cudaMalloc(&h->hA_rowptr, sizeof(int32_t) * (n + 1)) != cudaSuccess ||
+        cudaMalloc(&h->hA_colidx, sizeof(int32_t) * (nnz > 0 ? nnz : 1)) != cudaSuccess ||
+        cudaMalloc(&h->hA_vals, sizeof(double) * (nnz > 0 ? nnz : 1)) != cudaSuccess ||
+        cudaMalloc(&h->hB, sizeof(double) * n * s) != cudaSuccess ||
+        cudaMalloc(&h->hX, sizeof(double) * n * s) != cudaSuccess) {
+      cudaGetLastError();
+      return LSBA_OUT_OF_MEMORY;
+    }
+    h->host_n = n;
+    h->host_nnz = nnz;
+    h->host_s = s;
+  }
+  cudaStream_t st = h->stream;
+  CK(cudaMemcpyAsync(h->hA_rowptr, h_rowptr, sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice, st));
+  if (nnz > 0) {
+    CK(cudaMemcpyAsync(h->hA_colidx, h_colidx, sizeof(int32_t) * nnz, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(h->hA_vals, h_vals, sizeof(double) * nnz, cudaMemcpyHostToDevice, st));
+  }
+  CK(cudaMemcpyAsync(h->hB, h_B, sizeof(double) * n * s, cudaMemcpyHostToDevice, st));
+  lsba_csr A;
+  A.n = n;
+  A.nnz = nnz;
+  A.d_rowptr = h->hA_rowptr;
+  A.d_colidx = h->hA_colidx;
+  A.d_vals = h->hA_vals;
+  int rc = solve_impl(h, &A, h->hB, h->hX, s, m, tol, skel);
+  if (rc == LSBA_INVALID_ARG || rc == LSBA_CUDA_ERROR || rc == LSBA_OUT_OF_MEMORY) return rc;
+  CK(cudaMemcpyAsync(h_X, h->hX, sizeof(double) * n * s, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  return rc;
+}
+
+int lsba_get_stats(lsba_handle h, lsba_stats* out) {
+  if (!h || !out) return LSBA_INVALID_ARG;
+  *out = h->stats;
+  return LSBA_OK;
+}
+
+int lsba_get_history(lsba_handle h, lsba_history* out) {
+  if (!h || !out) return LSBA_INVALID_ARG;
+  memset(out, 0, sizeof(*out));
+  out->n_est = (int32_t)h->h_est.size();
+  out->est = h->h_est.data();
+  out->est_cycle = h->h_est_cycle.data();
+  out->est_j = h->h_est_j.data();
+  out->n_cycles = (int32_t)h->h_cycle_m.size();
+  out->cycle_m = h->h_cycle_m.data();
+  out->cycle_flag = h->h_cycle_flag.data();
+  out->cycle_mcur = h->h_cycle_mcur.data();
+  out->first_j = h->first_j;
+  out->first_H = h->h_first_H.data();
+  out->first_beta = h->h_first_beta.data();
+  out->n_grams = (int32_t)h->h_gram_rows.size();
+  out->gram_rows = h->h_gram_rows.data();
+  out->gram_cols = h->h_gram_cols.data();
+  out->gram_data = h->h_gram_data.data();
+  return LSBA_OK;
+}
+
+// ---------------------------------------------------------------- kernel-level entry points
+
+int lsba_spmm(lsba_handle h, const lsba_csr* A, const double* d_V, double* d_W, int s) {
+  if (!h || !A || !d_V || !d_W || s < 1 || s > LSBA_MAX_S || A->n < 1 || !A->d_rowptr ||
+      (A->nnz > 0 && (!A->d_colidx || !A->d_vals)))
+    return LSBA_INVALID_ARG;
+  CK(cudaSetDevice(h->device));
+  launch_spmm(h->stream, A->n, A->d_rowptr, A->d_colidx, A->d_vals, d_V, d_W, s, nullptr, 0);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(h->stream));
+  return LSBA_OK;
+}
+
+int lsba_gram(lsba_handle h, const double* d_L, int a, const double* d_R, int b, int64_t n, int s,
+              double* d_G) {
+  if (!h || !d_L || !d_R || !d_G || a < 1 || b < 1 || b > 2 || s < 1 || s > LSBA_MAX_S || n < 1 ||
+      a + b > LSBA_MAXB || (int64_t)a * s > LSBA_MAX_MS)
+    return LSBA_INVALID_ARG;
+  CK(cudaSetDevice(h->device));
+  GramPlan p = plan_gram(n, s, a, b, h->num_sms);
+  const size_t need = (size_t)p.grid_x * p.q;
+  if (need > h->partials_cap) {
+    cudaFree(h->partials);
+    h->partials = nullptr;
+    h->partials_cap = 0;
+    if (cudaMalloc(&h->partials, sizeof(double) * need) != cudaSuccess) {
+      cudaGetLastError();
+      return LSBA_OUT_OF_MEMORY;
+    }
+    h->partials_cap = need;
+  }
+  BlockPtrs L, R;
+  memset(&L, 0, sizeof(L));
+  memset(&R, 0, sizeof(R));
+  for (int i = 0; i < a; ++i) L.p[i] = d_L + (size_t)i * n * s;
+  for (int i = 0; i < b; ++i) R.p[i] = d_R + (size_t)i * n * s;
+  launch_gram(h->stream, p, L, a, R, b, n, s, h->partials, d_G, nullptr, 0);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(h->stream));
+  return LSBA_OK;
+}
+
+int lsba_combine(lsba_handle h, const double* d_in, int nin, int64_t n, int s, const double* d_C,
+                 const double* d_T, double* d_out) {
+  if (!h || !d_in || !d_C || !d_out || nin < 1 || nin > LSBA_MAXB || s < 1 || s > LSBA_MAX_S ||
+      n < 1)
+    return LSBA_INVALID_ARG;
+  CK(cudaSetDevice(h->device));
+  BlockPtrs in;
+  memset(&in, 0, sizeof(in));
+  for (int i = 0; i < nin; ++i) in.p[i] = d_in + (size_t)i * n * s;
+  launch_update(h->stream, in, nin, n, s, d_out, d_C, d_T, nullptr, nullptr, nullptr, nullptr,
+                nullptr, -1);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(h->stream));
+  return LSBA_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,887 @@
+// Small FP64 kernels of the block Arnoldi step: one CTA each, working on the
+// s x s and (k s) x s matrices that follow one sync point.
+//
+//  k_small_start   CholQR of the cycle's start block (Sec. 2.3 muscle; Alg. 3/6/7 line 1)
+//  k_small_step    one loop iteration of a skeleton after its Gram pass:
+//                    BCGS (Sec. 3.1), BCGS-PIP (Alg. 3), BMGS-CWY/ICWY (Alg. 6),
+//                    BCGSI+LS (Alg. 7); Cholesky NaN-flag and adaptive restart (Sec. 4);
+//                    then, when an Arnoldi relation j completes, the residual
+//                    estimate of Eq. (9) for BFOM / BGMRES (Eq. (7), Thm. 1).
+//  k_small_end     end of a cycle: Xi_j, the cospatial factor, the BGMRES
+//                    modification M, and the coefficients of X += V Xi C and
+//                    U = V_{j+1} [M; -H_{j+1,j}] (Sec. 2.4.2).
+//
+// Least squares: the block Hessenberg matrix is reduced column by column with
+// block Householder reflectors (one set of s reflectors per block column, each
+// acting on 2s rows).  With Q_{1..j-1} the first j-1 sets:
+//   BGMRES Xi = Rbar^{-1} g (the minimiser of ||E_1 Beta - Hbar Xi||_F, which the
+//     harmonic modification of Eq. (7) reproduces), estimate ||g_{j+1} C||_F;
+//   BFOM: with T = last s x s block of H_j's last column after Q_{1..j-1}^T,
+//     c = T^{-1} g_j, estimate ||H_{j+1,j} c C||_F;
+//   BGMRES modification M = H_j^{-T} E_j H_{j+1,j}^T H_{j+1,j} = Q_{1..j-1} [0; T^{-T} S].
+// All three equal the paper's formulas in exact arithmetic; the CPU oracle
+// evaluates the formulas literally.
+#include <cmath>
+
+#include "lsba_internal.cuh"
+
+namespace lsba {
+
+#define NT LSBA_SMALL_THREADS
+#define NWARPS (NT / 32)
+
+enum { SK_BCGS = 0, SK_PIP = 1, SK_LS = 2, SK_ICWY = 3, SK_CWY = 4 };
+
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// C(MxN, ldc) = alpha * op(A) op(B) + beta * C.  op(A) is M x K.
+__device__ void cta_gemm(int M, int N, int K, double alpha, const double* A, int lda, bool ta,
+                         const double* B, int ldb, bool tb, double beta, double* C, int ldc) {
+  for (int e = threadIdx.x; e < M * N; e += NT) {
+    const int i = e % M, j = e / M;
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    int q = 0;
+    for (; q + 3 < K; q += 4) {
+      a0 = fma(ta ? A[q + i * lda] : A[i + q * lda], tb ? B[j + q * ldb] : B[q + j * ldb], a0);
+      a1 = fma(ta ? A[q + 1 + i * lda] : A[i + (q + 1) * lda],
+               tb ? B[j + (q + 1) * ldb] : B[q + 1 + j * ldb], a1);
+      a2 = fma(ta ? A[q + 2 + i * lda] : A[i + (q + 2) * lda],
+               tb ? B[j + (q + 2) * ldb] : B[q + 2 + j * ldb], a2);
+      a3 = fma(ta ? A[q + 3 + i * lda] : A[i + (q + 3) * lda],
+               tb ? B[j + (q + 3) * ldb] : B[q + 3 + j * ldb], a3);
+    }
+    for (; q < K; ++q)
+      a0 = fma(ta ? A[q + i * lda] : A[i + q * lda], tb ? B[j + q * ldb] : B[q + j * ldb], a0);
+    const double v = (a0 + a1) + (a2 + a3);
+    C[i + j * ldc] = alpha * v + (beta == 0.0 ? 0.0 : beta * C[i + j * ldc]);
+  }
+  __syncthreads();
+}
+
+__device__ void cta_copy(double* dst, int ldd, const double* src, int lds, int rows, int cols,
+                         double alpha = 1.0) {
+  for (int e = threadIdx.x; e < rows * cols; e += NT) {
+    const int i = e % rows, j = e / rows;
+    dst[i + j * ldd] = alpha * src[i + j * lds];
+  }
+  __syncthreads();
+}
+
+// Upper Cholesky factor R (s x s, col-major, ld s, shared) of the symmetric
+// matrix whose upper triangle is read from S (col-major, lds).  Returns 1 (the
+// NaN-flag) if an upper entry is non-finite or a pivot is <= 0 or non-finite.
+__device__ int cta_chol(const double* S, int lds, int s, double* R, int* sflag) {
+  if (threadIdx.x == 0) *sflag = 0;
+  __syncthreads();
+  for (int e = threadIdx.x; e < s * s; e += NT) {
+    const int a = e % s, c = e / s;
+    double v = 0.0;
+    if (a <= c) {
+      v = S[a + c * lds];
+      if (!isfinite(v)) *sflag = 1;
+    }
+    R[a + c * s] = v;
+  }
+  __syncthreads();
+  if (*sflag) return 1;
+  for (int p = 0; p < s; ++p) {
+    if (threadIdx.x == 0) {
+      const double d = R[p + p * s];
+      if (!(d > 0.0) || !isfinite(d)) *sflag = 1;
+      else R[p + p * s] = sqrt(d);
+    }
+    __syncthreads();
+    if (*sflag) return 1;
+    const double rpp = R[p + p * s];
+    for (int c = p + 1 + threadIdx.x; c < s; c += NT) R[p + c * s] = R[p + c * s] / rpp;
+    __syncthreads();
+    const int nt = s - p - 1;
+    for (int e = threadIdx.x; e < nt * nt; e += NT) {
+      const int a = p + 1 + e % nt, c = p + 1 + e / nt;
+      if (a <= c) R[a + c * s] = fma(-R[p + a * s], R[p + c * s], R[a + c * s]);
+    }
+    __syncthreads();
+  }
+  return 0;
+}
+
+// X (rows x s, ldx) <- X R^{-1}, R upper s x s col-major (ld s).
+__device__ void cta_trsm_right(double* X, int ldx, int rows, const double* R, int s) {
+  for (int q = 0; q < s; ++q) {
+    const double rq = R[q + q * s];
+    for (int r = threadIdx.x; r < rows; r += NT) X[r + q * ldx] = X[r + q * ldx] / rq;
+    __syncthreads();
+    const int nc = s - q - 1;
+    for (int e = threadIdx.x; e < rows * nc; e += NT) {
+      const int r = e % rows, c = q + 1 + e / rows;
+      X[r + c * ldx] = fma(-X[r + q * ldx], R[q + c * s], X[r + c * ldx]);
+    }
+    __syncthreads();
+  }
+}
+
+// Y (s x cols, ldy) <- R^{-T} Y, R upper s x s col-major (ld s).
+__device__ void cta_trsm_left_T(const double* R, int s, double* Y, int ldy, int cols) {
+  for (int q = 0; q < s; ++q) {
+    const double rq = R[q + q * s];
+    for (int c = threadIdx.x; c < cols; c += NT) Y[q + c * ldy] = Y[q + c * ldy] / rq;
+    __syncthreads();
+    const int nr = s - q - 1;
+    for (int e = threadIdx.x; e < nr * cols; e += NT) {
+      const int r = q + 1 + e % nr, c = e / nr;
+      Y[r + c * ldy] = fma(-R[q + r * s], Y[q + c * ldy], Y[r + c * ldy]);
+    }
+    __syncthreads();
+  }
+}
+
+// Inverse of an upper-triangular s x s R (col-major) into Ri (col-major).
+__device__ void cta_tri_inverse(const double* R, int s, double* Ri) {
+  for (int e = threadIdx.x; e < s * s; e += NT) Ri[e] = (e % s == e / s) ? 1.0 : 0.0;
+  __syncthreads();
+  // Ri <- I R^{-1}: rows of the identity times R^{-1}.
+  cta_trsm_right(Ri, s, s, R, s);
+}
+
+// Y (kb*s x cols, ldy) <- T^{-T} Y for unit upper-triangular T (ldt) given by
+// its strictly upper blocks: block forward substitution Y_i -= sum_{l<i} T_{l,i}^T Y_l.
+__device__ void cta_unit_upper_T_solve(const double* T, int ldt, int kb, int s, double* Y, int ldy,
+                                       int cols) {
+  for (int i = 1; i < kb; ++i) {
+    // Y_i -= T(0:i s, i s:(i+1) s)^T Y(0:i s, :)
+    for (int e = threadIdx.x; e < s * cols; e += NT) {
+      const int a = e % s, c = e / s;
+      double acc0 = 0.0, acc1 = 0.0;
+      const double* tcol = T + (i * s + a) * ldt;
+      int q = 0;
+      for (; q + 1 < i * s; q += 2) {
+        acc0 = fma(tcol[q], Y[q + c * ldy], acc0);
+        acc1 = fma(tcol[q + 1], Y[q + 1 + c * ldy], acc1);
+      }
+      if (q < i * s) acc0 = fma(tcol[q], Y[q + c * ldy], acc0);
+      Y[i * s + a + c * ldy] -= (acc0 + acc1);
+    }
+    __syncthreads();
+  }
+}
+
+// Y <- T^T Y for unit upper-triangular T (the compact-WY branch of Alg. 6).
+__device__ void cta_unit_upper_T_mult(const double* T, int ldt, int kb, int s, double* Y, int ldy,
+                                      int cols, double* tmp) {
+  const int rows = kb * s;
+  for (int e = threadIdx.x; e < rows * cols; e += NT) {
+    const int r = e % rows, c = e / rows;
+    const int ib = r / s;
+    double acc = Y[r + c * ldy];
+    const double* tcol = T + r * ldt;
+    for (int q = 0; q < ib * s; ++q) acc = fma(tcol[q], Y[q + c * ldy], acc);
+    tmp[r + c * rows] = acc;
+  }
+  __syncthreads();
+  cta_copy(Y, ldy, tmp, rows, rows, cols);
+}
+
+// LU with partial pivoting: solve T x = B (s x s each, col-major ld s) into X.
+// Returns 1 if a pivot is zero or the result is not finite.  One warp.
+__device__ int warp_lu_solve(const double* Tin, const double* Bin, int s, double* X, double* sT,
+                             int* spiv, int* sflag) {
+  const int lane = threadIdx.x & 31;
+  if (threadIdx.x < 32) {
+    for (int e = lane; e < s * s; e += 32) {
+      sT[e] = Tin[e];
+      X[e] = Bin[e];
+    }
+    if (lane == 0) *sflag = 0;
+    __syncwarp();
+    for (int p = 0; p < s; ++p) {
+      if (lane == 0) {
+        int piv = p;
+        double best = fabs(sT[p + p * s]);
+        for (int i = p + 1; i < s; ++i) {
+          const double v = fabs(sT[i + p * s]);
+          if (v > best) {
+            best = v;
+            piv = i;
+          }
+        }
+        *spiv = piv;
+        if (!(best > 0.0)) *sflag = 1;
+      }
+      __syncwarp();
+      const int piv = *spiv;
+      if (piv != p && lane < s) {
+        double t = sT[p + lane * s];
+        sT[p + lane * s] = sT[piv + lane * s];
+        sT[piv + lane * s] = t;
+        t = X[p + lane * s];
+        X[p + lane * s] = X[piv + lane * s];
+        X[piv + lane * s] = t;
+      }
+      __syncwarp();
+      if (*sflag) break;
+      const double d = sT[p + p * s];
+      // lane c updates column c of T (c > p) and of X.
+      if (lane < s) {
+        for (int i = p + 1; i < s; ++i) {
+          const double l = sT[i + p * s] / d;
+          if (lane > p) sT[i + lane * s] = fma(-l, sT[p + lane * s], sT[i + lane * s]);
+          X[i + lane * s] = fma(-l, X[p + lane * s], X[i + lane * s]);
+        }
+      }
+      __syncwarp();
+    }
+    if (!*sflag && lane < s) {
+      for (int i = s - 1; i >= 0; --i) {
+        double v = X[i + lane * s];
+        for (int q = i + 1; q < s; ++q) v = fma(-sT[i + q * s], X[q + lane * s], v);
+        v = v / sT[i + i * s];
+        if (!isfinite(v)) *sflag = 1;
+        X[i + lane * s] = v;
+      }
+    }
+    __syncwarp();
+  }
+  __syncthreads();
+  return *sflag;
+}
+
+// Apply Q_i^T (transpose = 1) or Q_i (transpose = 0) of reflector set i to the
+// 2s rows starting at row r0 of X (col-major, ldx, ncols columns).  One warp
+// per column; a column's 2s <= 64 entries live two per lane.
+__device__ void apply_set(const double* v, const double* tau, int s, double* X, int ldx, int r0,
+                          int ncols, int transpose) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int h = 2 * s;
+  for (int c = warp; c < ncols; c += NWARPS) {
+    double* x = X + r0 + c * ldx;
+    double x0 = lane < h ? x[lane] : 0.0;
+    double x1 = lane + 32 < h ? x[lane + 32] : 0.0;
+    for (int t = 0; t < s; ++t) {
+      const int l = transpose ? t : s - 1 - t;
+      const double tl = tau[l];
+      if (tl == 0.0) continue;
+      const double* vl = v + l * h;
+      const double v0 = (lane >= l && lane < h) ? vl[lane] : 0.0;
+      const double v1 = (lane + 32 >= l && lane + 32 < h) ? vl[lane + 32] : 0.0;
+      const double d = warp_sum(fma(v0, x0, v1 * x1));
+      x0 = fma(-tl * d, v0, x0);
+      x1 = fma(-tl * d, v1, x1);
+    }
+    if (lane < h) x[lane] = x0;
+    if (lane + 32 < h) x[lane + 32] = x1;
+  }
+  __syncthreads();
+}
+
+// Householder QR of the 2s x s block at rows r0.. of X (col-major, ldx):
+// stores reflectors (unit leading entry, zeros above) in v (2s x s, ld 2s) and
+// tau; the block is overwritten by [R; 0].
+__device__ void house_qr(double* X, int ldx, int r0, int s, double* v, double* tau, double* sh) {
+  const int h = 2 * s;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int l = 0; l < s; ++l) {
+    double* xl = X + r0 + l * ldx;
+    if (warp == 0) {
+      const double a0 = (lane >= l + 1 && lane < h) ? xl[lane] : 0.0;
+      const double a1 = (lane + 32 >= l + 1 && lane + 32 < h) ? xl[lane + 32] : 0.0;
+      const double xn2 = warp_sum(fma(a0, a0, a1 * a1));
+      if (lane == 0) {
+        const double alpha = xl[l];
+        double t = 0.0, beta = alpha, scale = 0.0;
+        if (xn2 > 0.0) {
+          const double nrm = sqrt(fma(alpha, alpha, xn2));
+          beta = alpha >= 0.0 ? -nrm : nrm;
+          t = (beta - alpha) / beta;
+          scale = 1.0 / (alpha - beta);
+        }
+        sh[0] = t;
+        sh[1] = beta;
+        sh[2] = scale;
+        tau[l] = t;
+      }
+    }
+    __syncthreads();
+    const double t = sh[0], beta = sh[1], scale = sh[2];
+    for (int r = threadIdx.x; r < h; r += NT) {
+      double vr;
+      if (r < l) vr = 0.0;
+      else if (r == l) vr = 1.0;
+      else vr = (t == 0.0) ? 0.0 : xl[r] * scale;
+      v[r + l * h] = vr;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) xl[l] = beta;
+    for (int r = l + 1 + threadIdx.x; r < h; r += NT) xl[r] = 0.0;
+    __syncthreads();
+    // Apply H_l to the remaining columns l+1..s-1 (one warp per column).
+    if (t != 0.0) {
+      const double* vl = v + l * h;
+      for (int c = l + 1 + warp; c < s; c += NWARPS) {
+        double* x = X + r0 + c * ldx;
+        const double v0 = (lane >= l && lane < h) ? vl[lane] : 0.0;
+        const double v1 = (lane + 32 >= l && lane + 32 < h) ? vl[lane + 32] : 0.0;
+        double x0 = lane < h ? x[lane] : 0.0;
+        double x1 = lane + 32 < h ? x[lane + 32] : 0.0;
+        const double d = warp_sum(fma(v0, x0, v1 * x1));
+        x0 = fma(-t * d, v0, x0);
+        x1 = fma(-t * d, v1, x1);
+        if (lane < h) x[lane] = x0;
+        if (lane + 32 < h) x[lane + 32] = x1;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ||X C||_F for s x s X (col-major, ldx) and C (col-major ld s).
+__device__ double cta_norm_prod(const double* X, int ldx, const double* C, int s, double* red) {
+  double part = 0.0;
+  for (int e = threadIdx.x; e < s * s; e += NT) {
+    const int i = e % s, j = e / s;
+    double acc = 0.0;
+    for (int q = 0; q < s; ++q) acc = fma(X[i + q * ldx], C[q + j * s], acc);
+    part = fma(acc, acc, part);
+  }
+  part = warp_sum(part);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = part;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < NWARPS; ++w) t += red[w];
+    red[NWARPS] = sqrt(t);
+  }
+  __syncthreads();
+  const double r = red[NWARPS];
+  __syncthreads();
+  return r;
+}
+
+// Write coefficient block b of a [nin][s][s] row-major array from a col-major
+// matrix M (s x s, ldm) times alpha; M == nullptr writes alpha * I.
+__device__ void put_coef(double* coef, int b, int s, const double* M, int ldm, double alpha) {
+  double* dst = coef + (size_t)b * s * s;
+  for (int e = threadIdx.x; e < s * s; e += NT) {
+    const int a = e / s, c = e % s;
+    dst[a * s + c] = M ? alpha * M[a + c * ldm] : (a == c ? alpha : 0.0);
+  }
+}
+
+__device__ void put_zero_coef(double* coef, int b, int s) {
+  double* dst = coef + (size_t)b * s * s;
+  for (int e = threadIdx.x; e < s * s; e += NT) dst[e] = 0.0;
+}
+
+// Row-major copy of an upper-triangular col-major s x s matrix (triangular solve operand).
+__device__ void put_tri(double* tri, const double* R, int s) {
+  for (int e = threadIdx.x; e < s * s; e += NT) {
+    const int a = e / s, c = e % s;
+    tri[a * s + c] = R[a + c * s];
+  }
+}
+
+struct Shared {
+  double R[LSBA_MAX_S * LSBA_MAX_S];
+  double A[LSBA_MAX_S * LSBA_MAX_S];
+  double B[LSBA_MAX_S * LSBA_MAX_S];
+  double red[NWARPS + 4];
+  int flag, flag2, piv;
+};
+
+__device__ void record_gram(const SmallWs& w, const double* G, int rows, int cols) {
+  Ctl* ctl = w.ctl;
+  if (!ctl->record || ctl->cycle != 1) return;
+  const int used = ctl->gram_hist_used, idx = ctl->n_gram_hist;
+  if (used + rows * cols > ctl->gram_hist_cap || idx >= 2 * (w.m + 2)) return;
+  for (int e = threadIdx.x; e < rows * cols; e += NT) w.gram_hist[used + e] = G[e];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    w.gram_dims[2 * idx] = rows;
+    w.gram_dims[2 * idx + 1] = cols;
+    ctl->gram_hist_used = used + rows * cols;
+    ctl->n_gram_hist = idx + 1;
+  }
+  __syncthreads();
+}
+
+// Relation j of the current cycle is complete: H(1:j+1, j) is final.
+__device__ void relation_complete(const SmallWs& w, int j, Shared& sh) {
+  const int s = w.s, ldH = w.ldH, ldg = w.ldH, ldR = w.ldR;
+  Ctl* ctl = w.ctl;
+  double* col = w.work;                   // (j+1)s x s, ld = ldH
+  const double* Hj = w.H + (size_t)(j - 1) * s * ldH;
+  cta_copy(col, ldH, Hj, ldH, (j + 1) * s, s);
+  for (int i = 1; i < j; ++i)
+    apply_set(w.refl + (size_t)(i - 1) * 2 * s * s, w.tau + (i - 1) * s, s, col, ldH, (i - 1) * s,
+              s, 1);
+  // BFOM pieces (before reflector set j).
+  cta_copy(w.Tfom, s, col + (j - 1) * s, ldH, s, s);
+  cta_copy(w.ufom, ldH, col, ldH, (j - 1) * s, s);
+  cta_copy(w.gfom, s, w.g + (j - 1) * s, ldg, s, s);
+  int sing = 0;
+  if (w.modification == 0) sing = warp_lu_solve(w.Tfom, w.gfom, s, w.cfom, sh.A, &sh.piv, &sh.flag2);
+  // Reflector set j and the R factor's block column j.
+  house_qr(col, ldH, (j - 1) * s, s, w.refl + (size_t)(j - 1) * 2 * s * s, w.tau + (j - 1) * s, sh.red);
+  cta_copy(w.Rbar + (size_t)(j - 1) * s * ldR, ldR, col, ldH, j * s, s);
+  apply_set(w.refl + (size_t)(j - 1) * 2 * s * s, w.tau + (j - 1) * s, s, w.g, ldg, (j - 1) * s, s, 1);
+  double est;
+  if (w.modification == 1) {
+    est = cta_norm_prod(w.g + j * s, ldg, w.Cfac, s, sh.red) / ctl->normB;
+  } else if (!sing) {
+    // ||H_{j+1,j} c C||_F
+    cta_gemm(s, s, s, 1.0, w.H + j * s + (size_t)(j - 1) * s * ldH, ldH, false, w.cfom, s, false, 0.0,
+             sh.B, s);
+    est = cta_norm_prod(sh.B, s, w.Cfac, s, sh.red) / ctl->normB;
+  } else {
+    est = nan("");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ctl->j = j;
+    ctl->fom_singular = sing;
+    ctl->est = est;
+    if (ctl->record && ctl->n_hist < ctl->hist_cap) {
+      w.hist_est[ctl->n_hist] = est;
+      w.hist_cycle[ctl->n_hist] = ctl->cycle;
+      w.hist_j[ctl->n_hist] = j;
+      ctl->n_hist += 1;
+    }
+    if (!sing && est <= ctl->tol) {
+      ctl->converged = 1;
+      ctl->active = 0;
+    }
+    if (j >= ctl->m_cur) ctl->active = 0;
+  }
+  __syncthreads();
+}
+
+__device__ void flag_exit(const SmallWs& w, int relation) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    w.ctl->flagged = relation;
+    w.ctl->active = 0;
+    w.ctl->update_step = -1;
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ bool injected(const SmallWs& w, int relation) {
+  return w.ctl->inject_relation == relation;
+}
+
+// ---------------------------------------------------------------- cycle start
+// flags: bit 0 = first cycle (compute ||B||_F from the Gram), bit 1 = reset C = I.
+__global__ void __launch_bounds__(NT) k_small_start(SmallWs w, int flags) {
+  const int first_cycle = flags & 1;
+  __shared__ Shared sh;
+  const int s = w.s;
+  Ctl* ctl = w.ctl;
+  // G = R_start^T R_start (s x s row-major == col-major since symmetric in exact
+  // arithmetic; the upper triangle read as G[a*s + c], a <= c).
+  int flag = cta_chol(w.G, s, s, sh.R, &sh.flag);
+  if (first_cycle) {
+    if (threadIdx.x == 0) {
+      double tr = 0.0;
+      for (int a = 0; a < s; ++a) tr += w.G[a * s + a];
+      ctl->normB = sqrt(tr);
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ctl->start_flag = flag;
+    ctl->active = flag ? 0 : 1;
+    ctl->j = 0;
+    ctl->k = 0;
+    ctl->flagged = 0;
+    ctl->converged = 0;
+    ctl->fom_singular = 0;
+    ctl->update_step = flag ? -1 : 0;
+  }
+  if (flag) return;
+  cta_copy(w.Bcyc, s, sh.R, s, s, s);
+  // g = E_1 Beta
+  for (int e = threadIdx.x; e < w.ldH * s; e += NT) {
+    const int r = e % w.ldH, c = e / w.ldH;
+    w.g[e] = r < s ? sh.R[r + c * s] : 0.0;
+  }
+  if (flags & 2) {
+    for (int e = threadIdx.x; e < s * s; e += NT) w.Cfac[e] = (e % s == e / s) ? 1.0 : 0.0;
+  }
+  put_coef(w.coef1, 0, s, nullptr, 0, 1.0);
+  put_tri(w.tri1, sh.R, s);
+}
+
+// ---------------------------------------------------------------- one step
+__device__ void step_pip(const SmallWs& w, int k, Shared& sh) {
+  const int s = w.s, ks = k * s, ldH = w.ldH;
+  const double* G = w.G;  // ((k+1)s x s) row-major: element (i, c) at G[i*s + c]
+  record_gram(w, G, (k + 1) * s, s);
+  // S = Omega - Hc^T Hc ; Hc(i,c) = G[i*s+c] is, as a col-major matrix, Hc^T with ld s.
+  cta_gemm(s, s, ks, -1.0, G, s, false, G, s, true, 0.0, sh.A, s);
+  for (int e = threadIdx.x; e < s * s; e += NT) {
+    const int a = e % s, c = e / s;
+    sh.A[a + c * s] += G[(ks + a) * s + c];
+  }
+  __syncthreads();
+  int flag = cta_chol(sh.A, s, s, sh.R, &sh.flag);
+  if (flag || injected(w, k)) {
+    flag_exit(w, k);
+    return;
+  }
+  double* Hk = w.H + (size_t)(k - 1) * s * ldH;
+  for (int e = threadIdx.x; e < ks * s; e += NT) {
+    const int i = e % ks, c = e / ks;
+    Hk[i + c * ldH] = G[i * s + c];
+  }
+  for (int e = threadIdx.x; e < s * s; e += NT) {
+    const int a = e % s, c = e / s;
+    Hk[ks + a + c * ldH] = sh.R[a + c * s];
+  }
+  // V_{k+1} = (W - V_k Hc) R^{-1}: inputs [V_1..V_k, W].
+  for (int e = threadIdx.x; e < ks * s; e += NT) w.coef1[e] = -G[e];
+  put_coef(w.coef1, k, s, nullptr, 0, 1.0);
+  put_tri(w.tri1, sh.R, s);
+  __syncthreads();
+  if (threadIdx.x == 0) w.ctl->update_step = k;
+  relation_complete(w, k, sh);
+}
+
+__device__ void step_bcgs(const SmallWs& w, int k, int phase, Shared& sh) {
+  const int s = w.s, ks = k * s, ldH = w.ldH;
+  const double* G = w.G;
+  double* Hk = w.H + (size_t)(k - 1) * s * ldH;
+  if (phase == 0) {
+    // Hc = V_k^T W (ks x s row-major); W' = W - V_k Hc in place.
+    record_gram(w, G, ks, s);
+    for (int e = threadIdx.x; e < ks * s; e += NT) {
+      const int i = e % ks, c = e / ks;
+      Hk[i + c * ldH] = G[i * s + c];
+    }
+    for (int e = threadIdx.x; e < ks * s; e += NT) w.coef1[e] = -G[e];
+    put_coef(w.coef1, k, s, nullptr, 0, 1.0);
+    __syncthreads();
+    if (threadIdx.x == 0) w.ctl->update_step = k;
+    return;
+  }
+  // phase 1: G = W'^T W' ; [V_{k+1}, H_{k+1,k}] = CholQR(W').
+  int flag = cta_chol(G, s, s, sh.R, &sh.flag);
+  if (flag || injected(w, k)) {
+    flag_exit(w, k);
+    return;
+  }
+  for (int e = threadIdx.x; e < s * s; e += NT) {
+    const int a = e % s, c = e / s;
+    Hk[ks + a + c * ldH] = sh.R[a + c * s];
+  }
+  put_coef(w.coef1, 0, s, nullptr, 0, 1.0);
+  put_tri(w.tri1, sh.R, s);
+  __syncthreads();
+  if (threadIdx.x == 0) w.ctl->update_step = k;
+  relation_complete(w, k, sh);
+}
+
+// Lagged skeletons, iteration k = 1: H_{1,1} = <U, W> (= J), U <- W - V_1 H_{1,1}.
+// Inputs [V_1, W]; out1 = U.
+__device__ void step_lagged_first(const SmallWs& w, Shared& sh) {
+  const int s = w.s, ldH = w.ldH;
+  const double* G = w.G;
+  record_gram(w, G, s, s);
+  for (int e = threadIdx.x; e < s * s; e += NT) {
+    const int a = e % s, c = e / s;
+    w.H[a + c * ldH] = G[a * s + c];
+    if (w.skel == SK_LS) w.J[a + c * ldH] = G[a * s + c];
+  }
+  for (int e = threadIdx.x; e < s * s; e += NT) w.coef1[e] = -G[e];
+  put_coef(w.coef1, 1, s, nullptr, 0, 1.0);
+  __syncthreads();
+  if (threadIdx.x == 0) w.ctl->update_step = 1;
+  __syncthreads();
+}
+
+// BMGS-CWY / BMGS-ICWY iteration k >= 2 (Alg. 6).  Inputs [V_1..V_{k-1}, U, W];
+// out1 = V_k, out2 = U.
+__device__ void step_cwy(const SmallWs& w, int k, bool inverse, Shared& sh) {
+  const int s = w.s, ldH = w.ldH, ldT = w.ldT;
+  const int k1s = (k - 1) * s, ks = k * s, cols = 2 * s;
+  const double* G = w.G;  // (ks x 2s) row-major
+  record_gram(w, G, ks, cols);
+  // Omega = G[(k-1)s:, 0:s] (upper triangle read)
+  for (int e = threadIdx.x; e < s * s; e += NT) {
+    const int a = e % s, c = e / s;
+    sh.A[a + c * s] = G[(k1s + a) * cols + c];
+  }
+  __syncthreads();
+  int flag = cta_chol(sh.A, s, s, sh.R, &sh.flag);
+  if (flag || injected(w, k - 1)) {
+    flag_exit(w, k - 1);
+    return;
+  }
+  double* ZP = w.work;                 // ks x s, ld ks
+  double* YR = w.work + ks * s;        // (k-1)s x s
+  double* tmp = w.work + 2 * ks * s;   // ks x s
+  // P = R^{-T} Ptilde
+  for (int e = threadIdx.x; e < s * s; e += NT) {
+    const int a = e % s, c = e / s;
+    ZP[k1s + a + c * ks] = G[(k1s + a) * cols + s + c];
+  }
+  for (int e = threadIdx.x; e < k1s * s; e += NT) {
+    const int i = e % k1s, c = e / k1s;
+    ZP[i + c * ks] = G[i * cols + s + c];
+    YR[i + c * k1s] = G[i * cols + c];
+  }
+  __syncthreads();
+  cta_trsm_left_T(sh.R, s, ZP + k1s, ks, s);
+  // [Z; P] R^{-1} and Y R^{-1}
+  cta_trsm_right(ZP, ks, ks, sh.R, s);
+  cta_trsm_right(YR, k1s, k1s, sh.R, s);
+  // T_{1:k-1,k}
+  double* Tk = w.T + (size_t)k1s * ldT;  // column block k (0-based k-1)
+  if (inverse) {
+    cta_copy(Tk, ldT, YR, k1s, k1s, s);
+  } else {
+    // -T_{1:k-1,1:k-1} (Y R^{-1}); T unit upper.
+    for (int e = threadIdx.x; e < k1s * s; e += NT) {
+      const int r = e % k1s, c = e / k1s;
+      double acc = YR[r + c * k1s];
+      for (int q = (r / s + 1) * s; q < k1s; ++q) acc = fma(w.T[r + q * ldT], YR[q + c * k1s], acc);
+      tmp[r + c * k1s] = -acc;
+    }
+    __syncthreads();
+    cta_copy(Tk, ldT, tmp, k1s, k1s, s);
+  }
+  // H_{1:k,k} = T^{-T} ZP (ICWY) or T^T ZP (CWY)
+  if (inverse) cta_unit_upper_T_solve(w.T, ldT, k, s, ZP, ks, s);
+  else cta_unit_upper_T_mult(w.T, ldT, k, s, ZP, ks, s, tmp);
+  double* Hk = w.H + (size_t)(k - 1) * s * ldH;
+  double* Hkm1 = w.H + (size_t)(k - 2) * s * ldH;
+  for (int e = threadIdx.x; e < ks * s; e += NT) {
+    const int i = e % ks, c = e / ks;
+    Hk[i + c * ldH] = ZP[i + c * ks];
+  }
+  for (int e = threadIdx.x; e < s * s; e += NT) {
+    const int a = e % s, c = e / s;
+    Hkm1[k1s + a + c * ldH] = sh.R[a + c * s];
+  }
+  // Coefficients: out1 = V_k = U R^{-1};
+  // out2 = W R^{-1} - V_{1:k-1} Hc_{1:k-1} - V_k Hc_k.
+  cta_tri_inverse(sh.R, s, sh.B);
+  for (int b = 0; b < k - 1; ++b) {
+    put_zero_coef(w.coef1, b, s);
+    put_coef(w.coef2, b, s, ZP + b * s, ks, -1.0);
+  }
+  put_coef(w.coef1, k - 1, s, nullptr, 0, 1.0);
+  put_zero_coef(w.coef2, k - 1, s);
+  put_zero_coef(w.coef1, k, s);
+  put_coef(w.coef2, k, s, sh.B, s, 1.0);
+  put_coef(w.chain, 0, s, ZP + k1s, ks, -1.0);
+  put_tri(w.tri1, sh.R, s);
+  __syncthreads();
+  if (threadIdx.x == 0) w.ctl->update_step = k;
+  relation_complete(w, k - 1, sh);
+}
+
+// BCGSI+LS iteration k >= 2 (Alg. 7).  Inputs [V_1..V_{k-1}, U, W]; out1 = V_k, out2 = U.
+__device__ void step_ls(const SmallWs& w, int k, Shared& sh) {
+  const int s = w.s, ldH = w.ldH;
+  const int k1s = (k - 1) * s, ks = k * s, cols = 2 * s;
+  const double* G = w.G;
+  record_gram(w, G, ks, cols);
+  // Omega = Omega~ - Y^T Y.  Y(i,c) = G[i*cols + c] is Y^T col-major with ld cols.
+  cta_gemm(s, s, k1s, -1.0, G, cols, false, G, cols, true, 0.0, sh.A, s);
+  for (int e = threadIdx.x; e < s * s; e += NT) {
+    const int a = e % s, c = e / s;
+    sh.A[a + c * s] += G[(k1s + a) * cols + c];
+  }
+  __syncthreads();
+  int flag = cta_chol(sh.A, s, s, sh.R, &sh.flag);
+  if (flag || injected(w, k - 1)) {
+    flag_exit(w, k - 1);
+    return;
+  }
+  double* Hkm1 = w.H + (size_t)(k - 2) * s * ldH;
+  // H_{k,k-1} = R ; H_{1:k-1,k-1} = J + Y
+  for (int e = threadIdx.x; e < s * s; e += NT) {
+    const int a = e % s, c = e / s;
+    Hkm1[k1s + a + c * ldH] = sh.R[a + c * s];
+  }
+  for (int e = threadIdx.x; e < k1s * s; e += NT) {
+    const int i = e % k1s, c = e / k1s;
+    Hkm1[i + c * ldH] = w.J[i + c * ldH] + G[i * cols + c];
+  }
+  // P = R^{-T} (P~ - Y^T Z):  sh.B = Y^T Z  (Y^T as col-major (s x k1s) from G, Z likewise)
+  cta_gemm(s, s, k1s, 1.0, G, cols, false, G + s, cols, true, 0.0, sh.B, s);
+  double* ZP = w.work;                // ks x s, ld ks
+  double* tmp = w.work + ks * s;      // ks x s
+  for (int e = threadIdx.x; e < s * s; e += NT) {
+    const int a = e % s, c = e / s;
+    ZP[k1s + a + c * ks] = G[(k1s + a) * cols + s + c] - sh.B[a + c * s];
+  }
+  for (int e = threadIdx.x; e < k1s * s; e += NT) {
+    const int i = e % k1s, c = e / k1s;
+    ZP[i + c * ks] = G[i * cols + s + c];
+  }
+  __syncthreads();
+  cta_trsm_left_T(sh.R, s, ZP + k1s, ks, s);
+  // J = ([Z; P] - H_{1:k,1:k-1} Y) R^{-1}.  Y as a (k-1)s x s col-major matrix is
+  // G^T-indexed: Y(i,c) = G[i*cols + c]  -> pass as op(B) with tb = true, ldb = cols.
+  cta_gemm(ks, s, k1s, -1.0, w.H, ldH, false, G, cols, true, 0.0, tmp, ks);
+  for (int e = threadIdx.x; e < ks * s; e += NT) tmp[e] += ZP[e];
+  __syncthreads();
+  cta_trsm_right(tmp, ks, ks, sh.R, s);
+  cta_copy(w.J, ldH, tmp, ks, ks, s);
+  // out1 = V_k = (U - V_{1:k-1} Y) R^{-1};  out2 = (W - V_{1:k-1} Z - V_k P) R^{-1}
+  for (int b = 0; b < k - 1; ++b) {
+    double* c1 = w.coef1 + (size_t)b * s * s;
+    double* c2 = w.coef2 + (size_t)b * s * s;
+    for (int e = threadIdx.x; e < s * s; e += NT) {
+      const int a = e / s, c = e % s;
+      c1[a * s + c] = -G[(b * s + a) * cols + c];
+      c2[a * s + c] = -G[(b * s + a) * cols + s + c];
+    }
+  }
+  put_coef(w.coef1, k - 1, s, nullptr, 0, 1.0);
+  put_zero_coef(w.coef2, k - 1, s);
+  put_zero_coef(w.coef1, k, s);
+  put_coef(w.coef2, k, s, nullptr, 0, 1.0);
+  put_coef(w.chain, 0, s, ZP + k1s, ks, -1.0);
+  put_tri(w.tri1, sh.R, s);
+  put_tri(w.tri2, sh.R, s);
+  __syncthreads();
+  if (threadIdx.x == 0) w.ctl->update_step = k;
+  relation_complete(w, k - 1, sh);
+}
+
+__global__ void __launch_bounds__(NT) k_small_step(SmallWs w, int k, int phase) {
+  __shared__ Shared sh;
+  if (!*(volatile int*)&w.ctl->active) return;
+  if (threadIdx.x == 0) {
+    w.ctl->update_step = -1;
+    w.ctl->k = k;
+  }
+  __syncthreads();
+  switch (w.skel) {
+    case SK_PIP: step_pip(w, k, sh); break;
+    case SK_BCGS: step_bcgs(w, k, phase, sh); break;
+    case SK_ICWY:
+    case SK_CWY:
+      if (k == 1) step_lagged_first(w, sh);
+      else step_cwy(w, k, w.skel == SK_ICWY, sh);
+      break;
+    case SK_LS:
+      if (k == 1) step_lagged_first(w, sh);
+      else step_ls(w, k, sh);
+      break;
+  }
+}
+
+// ---------------------------------------------------------------- cycle end
+// Relation j = ctl->j.  Computes Xi_j, c = E_j^T Xi_j, M (BGMRES), and the
+// coefficients of the pass over [V_1..V_{j+1}, X]:
+//   out1 = X + V_{1:j} (Xi C),   out2 = U = V_{1:j+1} [M; -H_{j+1,j}];
+// then C <- c C.
+__global__ void __launch_bounds__(NT) k_small_end(SmallWs w) {
+  __shared__ Shared sh;
+  Ctl* ctl = w.ctl;
+  const int j = ctl->j;
+  const int s = w.s, ldH = w.ldH, ldR = w.ldR, ldg = w.ldH;
+  if (j == 0 || (w.modification == 0 && ctl->fom_singular)) {
+    if (threadIdx.x == 0) ctl->update_step = -2;
+    return;
+  }
+  const int js = j * s;
+  double* Xi = w.Xi;     // js x s, ld ldH
+  double* Mv = w.Mvec;   // js x s, ld ldH
+  // Xi_j (last block)
+  if (w.modification == 1) {
+    cta_copy(Xi, ldH, w.g, ldg, js, s);
+  } else {
+    cta_copy(Xi + (j - 1) * s, ldH, w.cfom, s, s, s);
+    cta_copy(Xi, ldH, w.g, ldg, (j - 1) * s, s);
+    // g_{1:j-1} - u c
+    cta_gemm((j - 1) * s, s, s, -1.0, w.ufom, ldH, false, w.cfom, s, false, 1.0, Xi, ldH);
+  }
+  // Block back substitution with Rbar (BGMRES: blocks 1..j; BFOM: blocks 1..j-1).
+  const int top = (w.modification == 1) ? j : j - 1;
+  for (int i = top; i >= 1; --i) {
+    double* Xii = Xi + (i - 1) * s;
+    const int rest = top - i;  // blocks i+1..top already known
+    if (rest > 0)
+      cta_gemm(s, s, rest * s, -1.0, w.Rbar + (i - 1) * s + (size_t)i * s * ldR, ldR, false,
+               Xi + i * s, ldH, false, 1.0, Xii, ldH);
+    // Xii <- Rbar_ii^{-1} Xii  (upper triangular): copy Rbar_ii, solve column by column.
+    cta_copy(sh.R, s, w.Rbar + (i - 1) * s + (size_t)(i - 1) * s * ldR, ldR, s, s);
+    for (int q = s - 1; q >= 0; --q) {
+      for (int c = threadIdx.x; c < s; c += NT) Xii[q + c * ldH] = Xii[q + c * ldH] / sh.R[q + q * s];
+      __syncthreads();
+      for (int e = threadIdx.x; e < q * s; e += NT) {
+        const int r = e % q, c = e / q;
+        Xii[r + c * ldH] = fma(-sh.R[r + q * s], Xii[q + c * ldH], Xii[r + c * ldH]);
+      }
+      __syncthreads();
+    }
+  }
+  // c = Xi_j (s x s) -> sh.A
+  cta_copy(sh.A, s, Xi + (j - 1) * s, ldH, s, s);
+  // M (BGMRES): Q_{1..j-1} [0; T^{-T} S], S = H_{j+1,j}^T H_{j+1,j}
+  const double* Hsub = w.H + js + (size_t)(j - 1) * s * ldH;
+  if (w.modification == 1) {
+    cta_gemm(s, s, s, 1.0, Hsub, ldH, true, Hsub, ldH, false, 0.0, sh.B, s);
+    // T^{-T} S: solve T^T Y = S  -> LU solve with T^T.
+    for (int e = threadIdx.x; e < s * s; e += NT) {
+      const int a = e % s, c = e / s;
+      sh.R[a + c * s] = w.Tfom[c + a * s];
+    }
+    __syncthreads();
+    double* Ylast = w.work;  // s x s
+    warp_lu_solve(sh.R, sh.B, s, Ylast, w.work + s * s, &sh.piv, &sh.flag2);
+    for (int e = threadIdx.x; e < js * s; e += NT) {
+      const int r = e % js, c = e / js;
+      Mv[r + c * ldH] = (r >= (j - 1) * s) ? Ylast[(r - (j - 1) * s) + c * s] : 0.0;
+    }
+    __syncthreads();
+    for (int i = j - 1; i >= 1; --i)
+      apply_set(w.refl + (size_t)(i - 1) * 2 * s * s, w.tau + (i - 1) * s, s, Mv, ldH, (i - 1) * s, s, 0);
+  }
+  // Coefficients.  Xi C -> coef1 blocks 0..j-1; coef1 block j = 0; block j+1 (X) = I.
+  double* XiC = w.work + 2 * s * s;  // js x s, ld js
+  cta_gemm(js, s, s, 1.0, Xi, ldH, false, w.Cfac, s, false, 0.0, XiC, js);
+  for (int b = 0; b < j; ++b) {
+    put_coef(w.coef1, b, s, XiC + b * s, js, 1.0);
+    if (w.modification == 1) put_coef(w.coef2, b, s, Mv + b * s, ldH, 1.0);
+    else put_zero_coef(w.coef2, b, s);
+  }
+  put_zero_coef(w.coef1, j, s);
+  put_coef(w.coef2, j, s, Hsub, ldH, -1.0);
+  put_coef(w.coef1, j + 1, s, nullptr, 0, 1.0);
+  put_zero_coef(w.coef2, j + 1, s);
+  // C <- c C
+  cta_gemm(s, s, s, 1.0, sh.A, s, false, w.Cfac, s, false, 0.0, sh.B, s);
+  cta_copy(w.Cfac, s, sh.B, s, s, s);
+  if (threadIdx.x == 0) ctl->update_step = LSBA_END_STEP;
+}
+
+// ||R||_F / ||B||_F from the Gram R^T R (s x s) into ctl->relres_true.
+__global__ void k_true_relres(const double* G, int s, Ctl* ctl) {
+  if (threadIdx.x == 0) {
+    double tr = 0.0;
+    for (int a = 0; a < s; ++a) tr += G[a * s + a];
+    ctl->relres_true = sqrt(tr) / ctl->normB;
+  }
+}
+
+void launch_small_start(cudaStream_t st, const SmallWs& w, int flags) {
+  k_small_start<<<1, NT, 0, st>>>(w, flags);
+}
+void launch_true_relres(cudaStream_t st, const double* G, int s, Ctl* ctl) {
+  k_true_relres<<<1, 32, 0, st>>>(G, s, ctl);
+}
+void launch_small_step(cudaStream_t st, const SmallWs& w, int k, int phase) {
+  k_small_step<<<1, NT, 0, st>>>(w, k, phase);
+}
+void launch_small_end(cudaStream_t st, const SmallWs& w) {
+  k_small_end<<<1, NT, 0, st>>>(w);
+}
+
+}  // namespace lsba

@@ -1,0 +1,115 @@
+// Internal declarations shared by the CUDA translation units of the solver.
+// Not part of the public C ABI (include/lsba.h).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#define LSBA_MAXB 72          // blocks in one input list of a pass
+#define LSBA_MAX_S 32
+#define LSBA_MAX_MS 2048      // (m+1)*s limit
+#define LSBA_SMALL_THREADS 512
+#define LSBA_END_STEP (1 << 20)   // update_step value that enables the cycle-end pass
+
+namespace lsba {
+
+// Device-side control record of one solve.  Written by the small (single-CTA)
+// kernels, read by every launch of the step so that a cycle that has ended
+// turns the remaining launches of the enqueued cycle into no-ops.
+struct Ctl {
+  int active;          // 1 while the current cycle may complete more relations
+  int j;               // relations completed in the current cycle
+  int k;               // skeleton loop iterations done in the current cycle
+  int flagged;         // relation whose Cholesky flagged (0: none)
+  int converged;       // estimate <= tol at relation j
+  int update_step;     // loop index whose basis update must run (-1: none)
+  int start_flag;      // CholQR of the cycle's start block flagged
+  int fom_singular;    // FOM small system singular at relation j
+  int m_cur;           // maximum basis size of the current cycle
+  int inject_relation; // force a flag when completing this relation (-1: none)
+  int cycle;           // 1-based cycle number
+  int record;          // record history
+  int n_hist;          // estimates recorded so far
+  int hist_cap;
+  int n_gram_hist;     // Gram outputs recorded (first cycle)
+  int gram_hist_used;  // doubles used in the Gram history buffer
+  int gram_hist_cap;
+  int pad;
+  double est;          // last residual estimate
+  double normB;        // ||B||_F
+  double tol;
+  double relres_true;
+};
+
+// Pointers of up to LSBA_MAXB blocks (each n x s, row-major, FP64).
+struct BlockPtrs {
+  const double* p[LSBA_MAXB];
+};
+
+// Device workspace of the small kernels (all device pointers).
+struct SmallWs {
+  int s, m, skel, modification;
+  int ldH;             // (m+2)*s
+  int ldT;             // (m+2)*s
+  int ldR;             // (m+1)*s
+  double* H;           // Hessenberg, ldH x (m+1)s, column-major
+  double* T;           // ICWY/CWY auxiliary, ldT x ldT, column-major (strict upper part used)
+  double* J;           // BCGSI+LS auxiliary, (m+1)s x s, column-major
+  const double* G;     // reduced Gram output, row-major (rows x cols)
+  double* coef1;       // update coefficients, [nin][s][s] row-major
+  double* coef2;
+  double* chain;       // s x s row-major
+  double* tri1;        // s x s row-major upper (or unused)
+  double* tri2;
+  double* Rbar;        // QR of the block Hessenberg: R factor, ldR x ldR col-major
+  double* refl;        // Householder vectors per block column: [(m+1)][2s x s] col-major
+  double* tau;         // [(m+1)][s]
+  double* g;           // transformed right-hand side E_1 Beta, (m+2)s x s col-major, ld (m+2)s
+  double* Tfom;        // s x s col-major: last block of H_j's last column after j-1 reflector sets
+  double* gfom;        // s x s: g block j before reflector set j
+  double* cfom;        // s x s: FOM cospatial factor T_fom^{-1} gfom
+  double* ufom;        // (m+1)s x s col-major: upper part of the last column after j-1 sets
+  double* Cfac;        // s x s col-major: cumulative cospatial factor C
+  double* Bcyc;        // s x s col-major: CholQR factor of the cycle's start block
+  double* Xi;          // (m+1)s x s col-major
+  double* Mvec;        // (m+1)s x s col-major
+  double* work;        // scratch, >= 4*(m+2)s*s + 8*s*s doubles
+  double* hist_est;    // [hist_cap]
+  int* hist_cycle;
+  int* hist_j;
+  double* gram_hist;   // [gram_hist_cap]
+  int* gram_dims;      // [2 * (m+2)]
+  Ctl* ctl;
+};
+
+// ---- launchers (stream-ordered, asynchronous) ----
+// W = A V.  guard: skip when ctl->active == 0.
+void launch_spmm(cudaStream_t st, int64_t n, const int32_t* rowptr, const int32_t* colidx,
+                 const double* vals, const double* V, double* W, int s, const Ctl* ctl, int guard);
+// R = B - W (elementwise), n x s.
+void launch_axpby(cudaStream_t st, int64_t n, int s, const double* B, const double* W, double* R);
+
+// Gram [L]^T [R] into per-CTA partials, then a fixed-order reduction into G.
+struct GramPlan {
+  int grid_x, grid_y, q, tile;
+  size_t smem;
+  int rows_per_chunk;
+  int64_t rows_per_cta;
+};
+GramPlan plan_gram(int64_t n, int s, int a, int b, int num_sms);
+void launch_gram(cudaStream_t st, const GramPlan& p, const BlockPtrs& L, int a, const BlockPtrs& R,
+                 int b, int64_t n, int s, double* partials, double* G, const Ctl* ctl, int guard);
+
+// out_o = (sum_i in_i C_o[i] (+ out1 * chain for o = 2)) * tri_o^{-1}.
+// Runs iff step < 0 or ctl->update_step == step.
+void launch_update(cudaStream_t st, const BlockPtrs& in, int nin, int64_t n, int s,
+                   double* out1, const double* coef1, const double* tri1,
+                   double* out2, const double* coef2, const double* chain, const double* tri2,
+                   const Ctl* ctl, int step);
+
+// Small single-CTA kernels (skeleton logic, Cholesky, least squares, estimate).
+void launch_small_start(cudaStream_t st, const SmallWs& w, int flags);
+void launch_true_relres(cudaStream_t st, const double* G, int s, Ctl* ctl);
+void launch_small_step(cudaStream_t st, const SmallWs& w, int k, int phase);
+void launch_small_end(cudaStream_t st, const SmallWs& w);
+
+}  // namespace lsba

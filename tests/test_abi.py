@@ -1,0 +1,59 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every entry point
+declared in include/lsba.h (no GPU needed)."""
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "lsba.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(lsba_[a-z_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2208_09899_gb300 import build, lsba
+    build.build()
+    return lsba.load()
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for n in ("lsba_create", "lsba_solve", "lsba_destroy", "lsba_get_stats", "lsba_status_string",
+              "lsba_spmm", "lsba_gram", "lsba_combine"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    from paper_2208_09899_gb300 import lsba
+    so = lsba.LIB_PATH
+    out = subprocess.run(["nm", "-D", "--defined-only", so], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\bT (lsba_\w+)", out))
+    for n in _declared():
+        assert n in exported, n
+        assert hasattr(lib, n)
+    assert set(lsba.EXPORTED) == set(_declared())
+
+
+def test_status_strings_and_defaults(lib):
+    import ctypes as C
+
+    from paper_2208_09899_gb300 import lsba
+    assert lsba.status_string(0) == "ok"
+    assert "not converged" in lsba.status_string(1)
+    o = lsba.Options()
+    lib.lsba_default_options(C.byref(o))
+    assert o.modification == 1 and o.max_restarts == 50 and o.adaptive_restart == 1
+    assert o.inject_flag_cycle == -1
+
+
+def test_invalid_arguments_without_gpu(lib):
+    import ctypes as C
+    assert lib.lsba_get_stats(None, None) == 3
+    assert lib.lsba_destroy(None) == 3
+    assert lib.lsba_create(None, 0, None, None) == 3

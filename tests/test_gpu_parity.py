@@ -1,0 +1,232 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle on the
+same seeded inputs."""
+import numpy as np
+import pytest
+
+from oracle import lsba_oracle as O
+from paper_2208_09899_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+# Normwise tolerances (relative Frobenius): Gram outputs and Hessenberg blocks
+# of the first cycle 1e-11; final X 1e-8; both relative residuals <= tol.
+TOL_GRAM = 1e-11
+TOL_X = 1e-8
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2208_09899_gb300 import build, lsba
+    build.build()
+    lsba.load()
+    return torch, lsba
+
+
+def _rel(a, b):
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
+
+
+def _rand_csr(n, per_row, seed, empty_rows=0):
+    rng = np.random.default_rng(seed)
+    rows, cols, vals = [], [], []
+    for i in range(n):
+        if i < empty_rows:
+            continue
+        k = rng.integers(1, per_row + 1)
+        c = rng.choice(n, size=k, replace=False)
+        rows += [i] * k
+        cols += list(c)
+        vals += list(rng.standard_normal(k))
+    return W._from_coo(n, np.array(rows), np.array(cols), np.array(vals))
+
+
+@pytest.mark.parametrize("s", [1, 3, 4, 8, 16, 32])
+def test_spmm_matches_oracle(env, s):
+    torch, lsba = env
+    A = _rand_csr(3001, 9, s, empty_rows=5)
+    V = W.gaussian_block(A.n, s, 1)
+    sv = lsba.Solver(0)
+    dA = lsba.DeviceCSR.from_host(A)
+    dV = torch.from_numpy(V).cuda()
+    dW = torch.empty_like(dV)
+    sv.spmm(dA, dV, dW)
+    got = dW.cpu().numpy()
+    ref = O.spmm(A, V)
+    assert _rel(got, ref) <= 1e-14
+    assert np.all(got[:5] == 0.0)
+
+
+@pytest.mark.parametrize("s,a,b,n", [(1, 1, 1, 1), (4, 3, 2, 1000), (8, 21, 1, 70001),
+                                     (8, 21, 2, 70001), (16, 17, 2, 40003), (32, 9, 2, 5003),
+                                     (5, 33, 1, 777)])
+def test_gram_matches_oracle_and_is_reproducible(env, s, a, b, n):
+    torch, lsba = env
+    rng = np.random.default_rng(a * 100 + s)
+    L = rng.standard_normal((a, n, s))
+    R = rng.standard_normal((b, n, s))
+    sv = lsba.Solver(0)
+    dL, dR = torch.from_numpy(L).cuda(), torch.from_numpy(R).cuda()
+    dG = torch.empty((a * s, b * s), dtype=torch.float64, device="cuda")
+    sv.gram(dL, dR, dG)
+    G1 = dG.cpu().numpy()
+    ref = O.inner(np.hstack(list(L)), np.hstack(list(R)))
+    assert _rel(G1, ref) <= 1e-13
+    sv.gram(dL, dR, dG)
+    assert np.array_equal(G1, dG.cpu().numpy())
+
+
+@pytest.mark.parametrize("s,nin,n,tri", [(4, 3, 1001, True), (8, 22, 9999, True),
+                                         (16, 18, 4097, False), (3, 2, 17, True), (32, 4, 300, True)])
+def test_combine_matches_oracle(env, s, nin, n, tri):
+    torch, lsba = env
+    rng = np.random.default_rng(s + nin)
+    IN = rng.standard_normal((nin, n, s))
+    Cf = rng.standard_normal((nin * s, s))
+    T = np.triu(rng.standard_normal((s, s))) + 4 * np.eye(s)
+    sv = lsba.Solver(0)
+    dIN, dC = torch.from_numpy(IN).cuda(), torch.from_numpy(Cf).cuda()
+    dT = torch.from_numpy(T).cuda() if tri else None
+    dO = torch.empty((n, s), dtype=torch.float64, device="cuda")
+    sv.combine(dIN, dC, dT, dO)
+    ref = np.hstack(list(IN)) @ Cf
+    if tri:
+        ref = O.right_solve_upper(ref, T)
+    assert _rel(dO.cpu().numpy(), ref) <= 1e-13
+
+
+def _compare_solve(lsba, A, B, m, tol, sk, mod, max_restarts=50, first_cycle_tol=TOL_GRAM, **kw):
+    X, st, hist = lsba.solve(A, B, m, tol, sk, device=0, modification=mod,
+                             max_restarts=max_restarts, record_history=True, **kw)
+    inject = []
+    if kw.get("inject_flag_cycle", -1) > 0:
+        inject = [(kw["inject_flag_cycle"], kw["inject_flag_relation"])]
+    ref = O.solve(A, B, m, tol, sk, modification=mod, max_restarts=max_restarts,
+                  record_first_cycle=True, inject_flags=inject,
+                  adaptive=bool(kw.get("adaptive_restart", 1)),
+                  verify_true_residual=bool(kw.get("verify_true_residual", 1)))
+    # Same restart decisions.
+    assert hist["cycle_m"] == ref.cycle_m, (hist["cycle_m"], ref.cycle_m)
+    assert hist["cycle_flag"] == ref.cycle_flag
+    assert hist["cycle_mcur"] == ref.m_cur
+    assert st["status"] == ref.status
+    assert (st["cycles"], st["steps"], st["a_calls"], st["syncs"], st["v_apps"]) == \
+        (ref.cycles, ref.steps, ref.a_calls, ref.syncs, ref.v_apps)
+    # First cycle: Gram outputs and Hessenberg.
+    fc = ref.first_cycle
+    assert len(hist["grams"]) == len(fc["grams"])
+    for g_gpu, g_ref in zip(hist["grams"], fc["grams"]):
+        assert g_gpu.shape == g_ref.shape
+        assert _rel(g_gpu, g_ref) <= first_cycle_tol
+    assert _rel(hist["first_beta"], fc["Beta"]) <= first_cycle_tol
+    j = fc["j"]
+    s = B.shape[1]
+    Hr = fc["H"]
+    Hg = hist["first_H"]
+    assert Hg.shape == Hr.shape
+    for c in range(j):
+        col_r = Hr[:(c + 2) * s, c * s:(c + 1) * s]
+        col_g = Hg[:(c + 2) * s, c * s:(c + 1) * s]
+        assert _rel(col_g, col_r) <= first_cycle_tol, c
+    # Estimates relation by relation.
+    est_ref = np.array([e for (_, _, e) in ref.est_history])
+    assert len(hist["est"]) == len(est_ref)
+    ok = np.isfinite(est_ref)
+    assert np.allclose(hist["est"][ok], est_ref[ok], rtol=1e-6, atol=0)
+    # Final X and residuals.
+    assert _rel(X, ref.X) <= TOL_X
+    if ref.status == O.OK:
+        assert st["relres_true"] <= tol and ref.relres_true <= tol
+    return X, st, hist, ref
+
+
+def test_config1_tridiag_bgmres_bcgsi_ls(env):
+    """tridiag(-1,4,-1), n=2000, B 2000x4 N(0,1), BGMRES(10), BCGSI+LS, tol 1e-10."""
+    torch, lsba = env
+    A, B = W.workload("tridiag2000_s4", 0)
+    _compare_solve(lsba, A, B, 10, 1e-10, "bcgsi_ls", "gmres")
+
+
+@pytest.mark.parametrize("mod", ["gmres", "fom"])
+@pytest.mark.parametrize("sk", ["bcgs", "bcgs_pip", "bcgsi_ls", "bmgs_icwy", "bmgs_cwy"])
+def test_all_skeletons_laplacian(env, sk, mod):
+    torch, lsba = env
+    A = W.laplacian_2d(40, 37)
+    B = W.gaussian_block(A.n, 4, 3)
+    _compare_solve(lsba, A, B, 8, 1e-10, sk, mod, max_restarts=200)
+
+
+@pytest.mark.parametrize("sk", ["bcgs_pip", "bcgsi_ls", "bmgs_icwy", "bcgs"])
+def test_adaptive_restart_injected_flag(env, sk):
+    torch, lsba = env
+    A = W.laplacian_2d(30)
+    B = W.gaussian_block(A.n, 3, 4)
+    X, st, hist, ref = _compare_solve(lsba, A, B, 8, 1e-9, sk, "gmres", max_restarts=300,
+                                      inject_flag_cycle=1, inject_flag_relation=5)
+    assert hist["cycle_m"][0] == 4 and all(mc == 4 for mc in hist["cycle_mcur"][1:])
+    # A flag on the first relation cannot be resolved.
+    X0, st0, h0 = lsba.solve(A, B, 8, 1e-9, sk, device=0, record_history=True,
+                             inject_flag_cycle=1, inject_flag_relation=1)
+    assert st0["status"] == lsba.LSBA_NOT_CONVERGED and h0["cycle_m"] == [0]
+
+
+def test_paper_multithread_example_pip_flag(env):
+    """Sec. 4 example: tridiag n=100, m=50, no restarts.  BCGS-PIP cannot reach
+    m = 50: chol raises the NaN-flag once kappa([B, A V_k]) is far past 1e8
+    (around step 15).  Where exactly depends on rounding: the paper shows it
+    moving with the thread count (16 to 35 steps), single-threaded MATLAB and the
+    x86 oracle reach 35, the aarch64 oracle 40, the GPU 22.  Past kappa ~ 1e8
+    the O(eps) kappa^2 bound of Table 2 no longer holds, so the GPU's flag step
+    is checked against that band, not a value."""
+    torch, lsba = env
+    A, B = W.paper_tridiag(100)
+    X, st, hist = lsba.solve(A, B, 50, 0.0, "bcgs_pip", device=0, modification="fom",
+                             max_restarts=0, adaptive_restart=0, verify_true_residual=0,
+                             record_history=True)
+    ref = O.solve(A, B, 50, 0.0, "bcgs_pip", modification="fom", max_restarts=0, adaptive=False,
+                  verify_true_residual=False)
+    print("PIP relations before the flag: gpu", hist["cycle_m"], "oracle", ref.cycle_m)
+    assert 15 <= hist["cycle_m"][0] <= 49 and 15 <= ref.cycle_m[0] <= 49
+    assert hist["cycle_flag"][0] == hist["cycle_m"][0] + 1
+    assert st["status"] == lsba.LSBA_NOT_CONVERGED
+
+
+def test_breakdown_on_rank_deficient_rhs(env):
+    torch, lsba = env
+    A = W.laplacian_2d(10)
+    B = W.gaussian_block(A.n, 3, 1)
+    B[:, 1] = 0.0
+    X, st, _ = lsba.solve(A, B, 5, 1e-8, "bcgsi_ls", device=0)
+    assert st["status"] == lsba.LSBA_BREAKDOWN
+
+
+def test_bitwise_reproducible_and_host_api(env):
+    torch, lsba = env
+    A, B = W.workload("tridiag2000_s4", 1)
+    X1, st1, _ = lsba.solve(A, B, 10, 1e-10, "bcgsi_ls", device=0)
+    X2, st2, _ = lsba.solve(A, B, 10, 1e-10, "bcgsi_ls", device=0)
+    assert np.array_equal(X1, X2)
+    sv = lsba.Solver(0)
+    X3, code = sv.solve_host(A, B, 10, 1e-10, "bcgsi_ls")
+    assert code == 0 and np.array_equal(X1, X3)
+
+
+@pytest.mark.parametrize("sk", ["bcgsi_ls", "bcgs_pip", "bmgs_icwy", "bcgs"])
+def test_lapl512_first_cycle_full_size(env, sk):
+    """The 512x512 Laplacian (n=262144), B n x 8, BGMRES(20): first cycle Gram
+    outputs and Hessenberg within 1e-11 of the oracle, at full size."""
+    torch, lsba = env
+    A, B = W.workload("lapl512_s8", 0)
+    X, st, hist = lsba.solve(A, B, 20, 1e-30, sk, device=0, max_restarts=0,
+                             verify_true_residual=0, record_history=True)
+    ref = O.solve(A, B, 20, 1e-30, sk, modification="gmres", max_restarts=0,
+                  verify_true_residual=False, record_first_cycle=True)
+    fc = ref.first_cycle
+    assert hist["cycle_m"] == ref.cycle_m == [20]
+    for g_gpu, g_ref in zip(hist["grams"], fc["grams"]):
+        assert _rel(g_gpu, g_ref) <= TOL_GRAM
+    assert _rel(hist["first_H"], fc["H"]) <= TOL_GRAM
+    assert _rel(X, ref.X) <= TOL_X
