@@ -82,7 +82,9 @@ typedef struct {
   int32_t inject_flag_cycle;     /* test hook: force the Cholesky flag while completing */
   int32_t inject_flag_relation;  /* relation inject_flag_relation of cycle
                                     inject_flag_cycle (1-based); -1 disables            */
-  int32_t reserved[8];
+  int32_t profile;               /* 1: time every kernel launch with CUDA events on the
+                                    handle's stream (lsba_get_profile)                  */
+  int32_t reserved[7];
 } lsba_options;
 
 /* Counters and outcome of the last lsba_solve. */
@@ -149,6 +151,16 @@ int lsba_solve_host(lsba_handle h, int64_t n, int64_t nnz, const int32_t* h_rowp
                     double* h_X, int s, int m, double tol, lsba_skeleton skel);
 
 int lsba_get_stats(lsba_handle h, lsba_stats* out);
+
+/* Kernel classes of lsba_get_profile. */
+enum { LSBA_K_SPMM = 0, LSBA_K_GRAM = 1, LSBA_K_UPDATE = 2, LSBA_K_SMALL = 3, LSBA_K_NCLASS = 4 };
+
+/* Device time (ms, from CUDA events recorded around each launch on the
+ * handle's stream) and launch counts per kernel class, accumulated over the
+ * solves since the last lsba_reset_profile, when options.profile = 1.
+ * ms and launches are caller arrays of nclass entries (nclass <= LSBA_K_NCLASS). */
+int lsba_get_profile(lsba_handle h, double* ms, int64_t* launches, int nclass);
+int lsba_reset_profile(lsba_handle h);
 int lsba_get_history(lsba_handle h, lsba_history* out);
 const char* lsba_status_string(int status);
 int lsba_destroy(lsba_handle h);

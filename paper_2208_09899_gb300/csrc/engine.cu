@@ -58,7 +58,44 @@ struct lsba_ctx {
   std::vector<double> h_first_H, h_first_beta, h_gram_data;
   std::vector<int32_t> h_gram_rows, h_gram_cols;
   int first_j = 0;
+  // profiling: CUDA event pairs around launches, collected at each host sync
+  std::vector<cudaEvent_t> ev;
+  std::vector<int> ev_class;
+  size_t ev_used = 0;
+  double prof_ms[LSBA_K_NCLASS] = {0, 0, 0, 0};
+  int64_t prof_n[LSBA_K_NCLASS] = {0, 0, 0, 0};
 };
+
+// Record the start event of a launch of kernel class `cls` (no-op unless profiling).
+static void prof_begin(lsba_ctx* h, int cls) {
+  if (!h->opt.profile) return;
+  if (h->ev_used + 2 > h->ev.size()) {
+    for (int i = 0; i < 2; ++i) {
+      cudaEvent_t e;
+      cudaEventCreate(&e);
+      h->ev.push_back(e);
+    }
+    h->ev_class.resize(h->ev.size() / 2);
+  }
+  h->ev_class[h->ev_used / 2] = cls;
+  cudaEventRecord(h->ev[h->ev_used], h->stream);
+}
+static void prof_end(lsba_ctx* h) {
+  if (!h->opt.profile) return;
+  cudaEventRecord(h->ev[h->ev_used + 1], h->stream);
+  h->ev_used += 2;
+}
+// Accumulate the recorded pairs (the stream must be synchronized).
+static void prof_collect(lsba_ctx* h) {
+  for (size_t i = 0; i + 1 < h->ev_used; i += 2) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, h->ev[i], h->ev[i + 1]) == cudaSuccess) {
+      h->prof_ms[h->ev_class[i / 2]] += ms;
+      h->prof_n[h->ev_class[i / 2]] += 1;
+    }
+  }
+  h->ev_used = 0;
+}
 
 #define CK(x)                                         \
   do {                                                \
@@ -203,8 +240,17 @@ static int push_ctl(lsba_ctx* h) {
 static int pull_ctl(lsba_ctx* h) {
   CK(cudaMemcpyAsync(h->h_ctl, h->d_ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
+  prof_collect(h);
   return LSBA_OK;
 }
+
+// Profiled launch wrappers.
+#define PROF(cls, call)     \
+  do {                      \
+    prof_begin(h, cls);     \
+    call;                   \
+    prof_end(h);            \
+  } while (0)
 
 enum { SK_BCGS = 0, SK_PIP = 1, SK_LS = 2, SK_ICWY = 3, SK_CWY = 4 };
 static bool lagged(int skel) { return skel == SK_LS || skel == SK_ICWY || skel == SK_CWY; }
@@ -220,17 +266,17 @@ static void enqueue_cycle(lsba_ctx* h, const lsba_csr* A, const double* Rstart, 
   one.p[0] = Rstart;
   {
     GramPlan p = plan_gram(n, s, 1, 1, h->num_sms);
-    launch_gram(st, p, one, 1, one, 1, n, s, h->partials, h->Gbuf, h->d_ctl, 0);
+    PROF(LSBA_K_GRAM, launch_gram(st, p, one, 1, one, 1, n, s, h->partials, h->Gbuf, h->d_ctl, 0));
   }
-  launch_small_start(st, w, start_flags);
-  launch_update(st, one, 1, n, s, h->basis, w.coef1, w.tri1, nullptr, nullptr, nullptr, nullptr,
-                h->d_ctl, 0);
+  PROF(LSBA_K_SMALL, launch_small_start(st, w, start_flags));
+  PROF(LSBA_K_UPDATE, launch_update(st, one, 1, n, s, h->basis, w.coef1, w.tri1, nullptr, nullptr, nullptr, nullptr,
+                h->d_ctl, 0));
   const int kmax = lagged(skel) ? m_cur + 1 : m_cur;
   const size_t blk = (size_t)n * s;
   for (int k = 1; k <= kmax; ++k) {
     if (skel == SK_PIP || skel == SK_BCGS) {
       const double* Vk = h->basis + (size_t)(k - 1) * blk;
-      launch_spmm(st, n, A->d_rowptr, A->d_colidx, A->d_vals, Vk, h->Wb, s, h->d_ctl, 1);
+      PROF(LSBA_K_SPMM, launch_spmm(st, n, A->d_rowptr, A->d_colidx, A->d_vals, Vk, h->Wb, s, h->d_ctl, 1));
       BlockPtrs L = basis_list(h, n, s, k);
       BlockPtrs R;
       memset(&R, 0, sizeof(R));
@@ -241,37 +287,37 @@ static void enqueue_cycle(lsba_ctx* h, const lsba_csr* A, const double* Rstart, 
       if (skel == SK_PIP) {
         L.p[k] = h->Wb;
         GramPlan p = plan_gram(n, s, k + 1, 1, h->num_sms);
-        launch_gram(st, p, L, k + 1, R, 1, n, s, h->partials, h->Gbuf, h->d_ctl, 1);
-        launch_small_step(st, w, k, 0);
-        launch_update(st, in, k + 1, n, s, Vnext, w.coef1, w.tri1, nullptr, nullptr, nullptr,
-                      nullptr, h->d_ctl, k);
+        PROF(LSBA_K_GRAM, launch_gram(st, p, L, k + 1, R, 1, n, s, h->partials, h->Gbuf, h->d_ctl, 1));
+        PROF(LSBA_K_SMALL, launch_small_step(st, w, k, 0));
+        PROF(LSBA_K_UPDATE, launch_update(st, in, k + 1, n, s, Vnext, w.coef1, w.tri1, nullptr, nullptr, nullptr,
+                      nullptr, h->d_ctl, k));
       } else {
         GramPlan p = plan_gram(n, s, k, 1, h->num_sms);
-        launch_gram(st, p, L, k, R, 1, n, s, h->partials, h->Gbuf, h->d_ctl, 1);
-        launch_small_step(st, w, k, 0);
-        launch_update(st, in, k + 1, n, s, h->Wb, w.coef1, nullptr, nullptr, nullptr, nullptr,
-                      nullptr, h->d_ctl, k);
+        PROF(LSBA_K_GRAM, launch_gram(st, p, L, k, R, 1, n, s, h->partials, h->Gbuf, h->d_ctl, 1));
+        PROF(LSBA_K_SMALL, launch_small_step(st, w, k, 0));
+        PROF(LSBA_K_UPDATE, launch_update(st, in, k + 1, n, s, h->Wb, w.coef1, nullptr, nullptr, nullptr, nullptr,
+                      nullptr, h->d_ctl, k));
         GramPlan p2 = plan_gram(n, s, 1, 1, h->num_sms);
-        launch_gram(st, p2, R, 1, R, 1, n, s, h->partials, h->Gbuf, h->d_ctl, 1);
-        launch_small_step(st, w, k, 1);
-        launch_update(st, R, 1, n, s, Vnext, w.coef1, w.tri1, nullptr, nullptr, nullptr, nullptr,
-                      h->d_ctl, k);
+        PROF(LSBA_K_GRAM, launch_gram(st, p2, R, 1, R, 1, n, s, h->partials, h->Gbuf, h->d_ctl, 1));
+        PROF(LSBA_K_SMALL, launch_small_step(st, w, k, 1));
+        PROF(LSBA_K_UPDATE, launch_update(st, R, 1, n, s, Vnext, w.coef1, w.tri1, nullptr, nullptr, nullptr, nullptr,
+                      h->d_ctl, k));
       }
     } else {
       const double* U = (k == 1) ? h->basis : h->Ub;
-      launch_spmm(st, n, A->d_rowptr, A->d_colidx, A->d_vals, U, h->Wb, s, h->d_ctl, 1);
+      PROF(LSBA_K_SPMM, launch_spmm(st, n, A->d_rowptr, A->d_colidx, A->d_vals, U, h->Wb, s, h->d_ctl, 1));
       if (k == 1) {
         BlockPtrs L = basis_list(h, n, s, 1);
         BlockPtrs R;
         memset(&R, 0, sizeof(R));
         R.p[0] = h->Wb;
         GramPlan p = plan_gram(n, s, 1, 1, h->num_sms);
-        launch_gram(st, p, L, 1, R, 1, n, s, h->partials, h->Gbuf, h->d_ctl, 1);
-        launch_small_step(st, w, 1, 0);
+        PROF(LSBA_K_GRAM, launch_gram(st, p, L, 1, R, 1, n, s, h->partials, h->Gbuf, h->d_ctl, 1));
+        PROF(LSBA_K_SMALL, launch_small_step(st, w, 1, 0));
         BlockPtrs in = basis_list(h, n, s, 1);
         in.p[1] = h->Wb;
-        launch_update(st, in, 2, n, s, h->Ub, w.coef1, nullptr, nullptr, nullptr, nullptr, nullptr,
-                      h->d_ctl, 1);
+        PROF(LSBA_K_UPDATE, launch_update(st, in, 2, n, s, h->Ub, w.coef1, nullptr, nullptr, nullptr, nullptr, nullptr,
+                      h->d_ctl, 1));
       } else {
         BlockPtrs L = basis_list(h, n, s, k - 1);
         L.p[k - 1] = h->Ub;
@@ -280,14 +326,14 @@ static void enqueue_cycle(lsba_ctx* h, const lsba_csr* A, const double* Rstart, 
         R.p[0] = h->Ub;
         R.p[1] = h->Wb;
         GramPlan p = plan_gram(n, s, k, 2, h->num_sms);
-        launch_gram(st, p, L, k, R, 2, n, s, h->partials, h->Gbuf, h->d_ctl, 1);
-        launch_small_step(st, w, k, 0);
+        PROF(LSBA_K_GRAM, launch_gram(st, p, L, k, R, 2, n, s, h->partials, h->Gbuf, h->d_ctl, 1));
+        PROF(LSBA_K_SMALL, launch_small_step(st, w, k, 0));
         BlockPtrs in = basis_list(h, n, s, k - 1);
         in.p[k - 1] = h->Ub;
         in.p[k] = h->Wb;
         double* Vk = h->basis + (size_t)(k - 1) * blk;
-        launch_update(st, in, k + 1, n, s, Vk, w.coef1, w.tri1, h->Ub, w.coef2, w.chain,
-                      skel == SK_LS ? w.tri2 : nullptr, h->d_ctl, k);
+        PROF(LSBA_K_UPDATE, launch_update(st, in, k + 1, n, s, Vk, w.coef1, w.tri1, h->Ub, w.coef2, w.chain,
+                      skel == SK_LS ? w.tri2 : nullptr, h->d_ctl, k));
       }
     }
   }
@@ -367,6 +413,7 @@ int lsba_destroy(lsba_handle h) {
   cudaFree(h->hA_vals);
   cudaFree(h->hB);
   cudaFree(h->hX);
+  for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
   delete h;
   return LSBA_OK;
 }
@@ -488,12 +535,12 @@ static int solve_impl(lsba_handle h, const lsba_csr* A, const double* d_B, doubl
       break;
     }
     // Cycle end: X += V_j Xi C, U = V_{j+1} [M; -H], C <- c C.
-    launch_small_end(st, w);
+    PROF(LSBA_K_SMALL, launch_small_end(st, w));
     {
       BlockPtrs in = basis_list(h, n, s, j + 1);
       in.p[j + 1] = d_X;
-      launch_update(st, in, j + 2, n, s, d_X, w.coef1, nullptr, h->Ub, w.coef2, nullptr, nullptr,
-                    h->d_ctl, LSBA_END_STEP);
+      PROF(LSBA_K_UPDATE, launch_update(st, in, j + 2, n, s, d_X, w.coef1, nullptr, h->Ub, w.coef2, nullptr, nullptr,
+                    h->d_ctl, LSBA_END_STEP));
     }
     CK(cudaGetLastError());
     if (c->flagged && !h->opt.adaptive_restart) {
@@ -503,14 +550,14 @@ static int solve_impl(lsba_handle h, const lsba_csr* A, const double* d_B, doubl
     if (c->converged) {
       if (h->opt.verify_true_residual) {
         // R = B - A X into Ub; ||R||_F / ||B||_F from its Gram.
-        launch_spmm(st, n, A->d_rowptr, A->d_colidx, A->d_vals, d_X, h->Wb, s, nullptr, 0);
-        launch_axpby(st, n, s, d_B, h->Wb, h->Ub);
+        PROF(LSBA_K_SPMM, launch_spmm(st, n, A->d_rowptr, A->d_colidx, A->d_vals, d_X, h->Wb, s, nullptr, 0));
+        PROF(LSBA_K_UPDATE, launch_axpby(st, n, s, d_B, h->Wb, h->Ub));
         BlockPtrs one;
         memset(&one, 0, sizeof(one));
         one.p[0] = h->Ub;
         GramPlan p = plan_gram(n, s, 1, 1, h->num_sms);
-        launch_gram(st, p, one, 1, one, 1, n, s, h->partials, h->Gbuf, nullptr, 0);
-        launch_true_relres(st, h->Gbuf, s, h->d_ctl);
+        PROF(LSBA_K_GRAM, launch_gram(st, p, one, 1, one, 1, n, s, h->partials, h->Gbuf, nullptr, 0));
+        PROF(LSBA_K_SMALL, launch_true_relres(st, h->Gbuf, s, h->d_ctl));
         if ((rc = pull_ctl(h)) != LSBA_OK) return S.status = rc;
         S.relres_true = c->relres_true;
         have_true = true;
@@ -531,14 +578,14 @@ static int solve_impl(lsba_handle h, const lsba_csr* A, const double* d_B, doubl
   S.status = status;
   // True residual of the returned X.
   if (!have_true && status != LSBA_INVALID_ARG) {
-    launch_spmm(st, n, A->d_rowptr, A->d_colidx, A->d_vals, d_X, h->Wb, s, nullptr, 0);
-    launch_axpby(st, n, s, d_B, h->Wb, h->Ub);
+    PROF(LSBA_K_SPMM, launch_spmm(st, n, A->d_rowptr, A->d_colidx, A->d_vals, d_X, h->Wb, s, nullptr, 0));
+    PROF(LSBA_K_UPDATE, launch_axpby(st, n, s, d_B, h->Wb, h->Ub));
     BlockPtrs one;
     memset(&one, 0, sizeof(one));
     one.p[0] = h->Ub;
     GramPlan p = plan_gram(n, s, 1, 1, h->num_sms);
-    launch_gram(st, p, one, 1, one, 1, n, s, h->partials, h->Gbuf, nullptr, 0);
-    launch_true_relres(st, h->Gbuf, s, h->d_ctl);
+    PROF(LSBA_K_GRAM, launch_gram(st, p, one, 1, one, 1, n, s, h->partials, h->Gbuf, nullptr, 0));
+    PROF(LSBA_K_SMALL, launch_true_relres(st, h->Gbuf, s, h->d_ctl));
     if ((rc = pull_ctl(h)) != LSBA_OK) return S.status = rc;
     S.relres_true = c->relres_true;
   }
@@ -627,6 +674,25 @@ int lsba_solve_host(lsba_handle h, int64_t n, int64_t nnz, const int32_t* h_rowp
   CK(cudaMemcpyAsync(h_X, h->hX, sizeof(double) * n * s, cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   return rc;
+}
+
+int lsba_get_profile(lsba_handle h, double* ms, int64_t* launches, int nclass) {
+  if (!h || nclass < 0 || nclass > LSBA_K_NCLASS || (nclass > 0 && (!ms || !launches)))
+    return LSBA_INVALID_ARG;
+  for (int i = 0; i < nclass; ++i) {
+    ms[i] = h->prof_ms[i];
+    launches[i] = h->prof_n[i];
+  }
+  return LSBA_OK;
+}
+
+int lsba_reset_profile(lsba_handle h) {
+  if (!h) return LSBA_INVALID_ARG;
+  for (int i = 0; i < LSBA_K_NCLASS; ++i) {
+    h->prof_ms[i] = 0.0;
+    h->prof_n[i] = 0;
+  }
+  return LSBA_OK;
 }
 
 int lsba_get_stats(lsba_handle h, lsba_stats* out) {

@@ -23,14 +23,17 @@ MODIFICATIONS = {"fom": 0, "gmres": 1}
 
 EXPORTED = ("lsba_default_options", "lsba_create", "lsba_set_options", "lsba_solve",
             "lsba_solve_host", "lsba_get_stats", "lsba_get_history", "lsba_status_string",
-            "lsba_destroy", "lsba_spmm", "lsba_gram", "lsba_combine")
+            "lsba_destroy", "lsba_spmm", "lsba_gram", "lsba_combine", "lsba_get_profile",
+            "lsba_reset_profile")
+KERNEL_CLASSES = ("spmm", "gram", "update", "small")
 
 
 class Options(C.Structure):
     _fields_ = [("modification", C.c_int32), ("max_restarts", C.c_int32),
                 ("adaptive_restart", C.c_int32), ("verify_true_residual", C.c_int32),
                 ("record_history", C.c_int32), ("inject_flag_cycle", C.c_int32),
-                ("inject_flag_relation", C.c_int32), ("reserved", C.c_int32 * 8)]
+                ("inject_flag_relation", C.c_int32), ("profile", C.c_int32),
+                ("reserved", C.c_int32 * 7)]
 
 
 class Stats(C.Structure):
@@ -82,6 +85,8 @@ def load(path: str = LIB_PATH):
     lib.lsba_spmm.argtypes = [vp, C.POINTER(CSRDesc), vp, vp, i32]
     lib.lsba_gram.argtypes = [vp, vp, i32, vp, i32, i64, i32, vp]
     lib.lsba_combine.argtypes = [vp, vp, i32, i64, i32, vp, vp, vp]
+    lib.lsba_get_profile.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_int64), i32]
+    lib.lsba_reset_profile.argtypes = [vp]
     for name in EXPORTED:
         if name not in ("lsba_default_options", "lsba_status_string"):
             getattr(lib, name).restype = C.c_int
@@ -205,6 +210,15 @@ class Solver:
         s = Stats()
         _check(self.lib.lsba_get_stats(self.h, C.byref(s)))
         return {f: getattr(s, f) for f, _ in Stats._fields_}
+
+    def profile(self) -> dict:
+        ms = (C.c_double * 4)()
+        cnt = (C.c_int64 * 4)()
+        _check(self.lib.lsba_get_profile(self.h, ms, cnt, 4))
+        return {k: (ms[i], cnt[i]) for i, k in enumerate(KERNEL_CLASSES)}
+
+    def reset_profile(self):
+        _check(self.lib.lsba_reset_profile(self.h))
 
     def history(self) -> dict:
         hs = History()
