@@ -186,6 +186,35 @@ int lsba_gram(lsba_handle h, const double* d_L, int a, const double* d_R, int b,
 int lsba_combine(lsba_handle h, const double* d_in, int nin, int64_t n, int s,
                  const double* d_C, const double* d_T, double* d_out);
 
+/* ---- allocation-free variant ------------------------------------------------
+ * The paper has no counterpart to this entry point; it exists for callers that
+ * cannot allocate device memory: code running while a CUDA graph is captured
+ * (cudaMalloc/cudaFree are not allowed there), serving loops that must not
+ * pay for an allocation or the synchronisation cudaFree implies, and hosts
+ * that fix the device memory footprint at start-up.
+ *
+ * lsba_gram_noalloc computes the same G = [L_1..L_a]^T [R_1..R_b] as lsba_gram
+ * (same arguments and layouts) without a handle and without allocating: no
+ * cudaMalloc, cudaFree or allocating library routine is called.  Its partial
+ * sums live in a fixed array in the library's device memory of
+ * LSBA_GRAM_NOALLOC_SCRATCH_DOUBLES doubles (512 KiB), which every GPU that loads
+ * the library holds until the process exits.
+ *   - Limit: (a*s)*(b*s) <= LSBA_GRAM_NOALLOC_SCRATCH_DOUBLES, otherwise
+ *     LSBA_INVALID_ARG is returned and nothing is launched; when the usual
+ *     number of row partitions would not fit, fewer are used.
+ *   - Device: the current CUDA device.  The first call on a device looks up the
+ *     array's device address (cudaGetSymbolAddress) and caches it; make that
+ *     first call before any stream capture.
+ *   - Ordering: enqueued on cuda_stream (NULL = legacy default stream); the
+ *     call returns without waiting.  Every call shares the one array and
+ *     overwrites all of it that it reads, so no clearing is needed, but calls
+ *     whose kernels overlap on the GPU (different streams, or different host
+ *     threads) race on it and must be serialised by the caller.
+ * Returns LSBA_OK, LSBA_INVALID_ARG or LSBA_CUDA_ERROR. */
+#define LSBA_GRAM_NOALLOC_SCRATCH_DOUBLES (1 << 16)
+int lsba_gram_noalloc(const double* d_L, int a, const double* d_R, int b, int64_t n, int s,
+                      double* d_G, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "liblsba.so")
-SOURCES = ["engine.cu", "kernels_big.cu", "kernels_small.cu"]
+SOURCES = ["engine.cu", "kernels_big.cu", "kernels_small.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -24,7 +24,7 @@ MODIFICATIONS = {"fom": 0, "gmres": 1}
 EXPORTED = ("lsba_default_options", "lsba_create", "lsba_set_options", "lsba_solve",
             "lsba_solve_host", "lsba_get_stats", "lsba_get_history", "lsba_status_string",
             "lsba_destroy", "lsba_spmm", "lsba_gram", "lsba_combine", "lsba_get_profile",
-            "lsba_reset_profile")
+            "lsba_reset_profile", "lsba_gram_noalloc")
 KERNEL_CLASSES = ("spmm", "gram", "update", "small")
 
 
@@ -87,6 +87,7 @@ def load(path: str = LIB_PATH):
     lib.lsba_combine.argtypes = [vp, vp, i32, i64, i32, vp, vp, vp]
     lib.lsba_get_profile.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_int64), i32]
     lib.lsba_reset_profile.argtypes = [vp]
+    lib.lsba_gram_noalloc.argtypes = [vp, i32, vp, i32, i64, i32, vp, vp]
     for name in EXPORTED:
         if name not in ("lsba_default_options", "lsba_status_string"):
             getattr(lib, name).restype = C.c_int
