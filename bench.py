@@ -38,6 +38,9 @@ WORKLOAD = "lapl512_s8"
 M = 20
 SKELETON = "bcgsi_ls"
 FP64_PEAK_TFLOPS = 1.25   # nominal FP64 (DFMA) rate of GB300; the probe measured 1.00
+# Double-float: one FP64-accurate FMA = 13 FP32-pipe instructions (df.cuh), so the
+# ALU peak in FP64-equivalent flops is 152 SMs x 128 FP32 lanes x 2.07 GHz / 13 x 2.
+DF_PEAK_TFLOPS = 152 * 128 * 2.07e9 / 13 * 2 / 1e12
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 
 
@@ -265,11 +268,18 @@ def main():
     dom_launches = prof[dom][1] / args.steps
     achieved_tflops = fl[dom] / (dom_ms_per_step * 1e-3) / 1e12
     achieved_gbs = by[dom] / (dom_ms_per_step * 1e-3) / 1e9
+    is_df = st0["precision"] == 1
+    peak = DF_PEAK_TFLOPS if is_df else FP64_PEAK_TFLOPS
+    suffix = "_df" if is_df else ""
     roofline = {
-        "kernel": {"gram": "k_gram+k_gram_reduce", "update": "k_update", "spmm": "k_spmm"}[dom],
-        "bound": "alu", "achieved": achieved_tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-        "frac": achieved_tflops / FP64_PEAK_TFLOPS, "traffic": None,
-        "peak_source": "nominal FP64 DFMA rate (1.25 TFLOP/s); the FP64 probe measured 1.00",
+        "kernel": {"gram": f"k_gram{suffix}+k_gram_reduce{suffix}",
+                   "update": ("k_coef_df+k_update_df" if is_df else "k_update"),
+                   "spmm": f"k_spmm{suffix}"}[dom],
+        "bound": "alu", "achieved": achieved_tflops, "peak": peak, "unit": "TFLOP/s",
+        "frac": achieved_tflops / peak, "traffic": None,
+        "peak_source": ("derived: double-float FMA = 13 FP32 ops; 152 SMs x 128 lanes x 2.07 GHz"
+                        " / 13 x 2 flop (FP64-equivalent)") if is_df else
+                       "nominal FP64 DFMA rate (1.25 TFLOP/s); the FP64 probe measured 1.00",
         "launches_per_step": dom_launches,
         "algorithmic_bytes_per_launch": by[dom] / max(dom_launches, 1),
         "algorithmic_flops_per_launch": fl[dom] / max(dom_launches, 1),
@@ -280,6 +290,25 @@ def main():
                    "share": prof[k][0] / max(sum(v[0] for v in prof.values()), 1e-12)}
                for k in prof}
     gpu_launches = int(sum(v[1] for v in prof.values()))
+
+    # The same steps with native FP64 (DFMA) Gram/update/SpMM kernels.
+    sv64 = lsba.Solver(dev, modification="gmres", max_restarts=0, verify_true_residual=0,
+                       precision="fp64")
+    for _ in range(2):
+        sv64.solve(dA, dB, dX, M, 1e-30, SKELETON)
+    k64 = max(1, min(args.steps, 3))
+    torch.cuda.synchronize(dev)
+    f0 = torch.cuda.Event(enable_timing=True)
+    f1 = torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    for _ in range(k64):
+        sv64.solve(dA, dB, dX, M, 1e-30, SKELETON)
+    f1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms64 = f0.elapsed_time(f1) / k64
+    fp64_plain = {"value": step_bytes / (ms64 * 1e-3) / 1e9, "unit": "GB/s", "ms_per_step": ms64,
+                  "speedup_of_value": ms64 / ms_step}
+    sv64.close()
 
     # End to end through the C ABI with host buffers (copies inside the timed region).
     e2e_steps = min(args.steps, 3)
@@ -334,7 +363,9 @@ def main():
         line = {
             "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64 (double-float: hi+lo FP32 pairs, compensated products on the FP32 pipes)"
+                     if st0["precision"] == 1 else "f64",
             "data": "synthetic (seeded numpy inputs shaped like the paper's lapl_2d)",
             "config": {"workload": f"{WORKLOAD}: 2D 5-point Laplacian 512x512 (n=262144), B n x 8 "
                                    f"N(0,1), BGMRES(m={M}), BCGSI+LS, one restart cycle per step",
@@ -344,6 +375,7 @@ def main():
                        "algorithmic_bytes_per_step": step_bytes},
             "roofline": roofline, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": gpu_launches, "clocks": clocks, "time_to_tol": time_to_tol,
+            "fp64_plain": fp64_plain,
         }
         print(json.dumps(line))
     if pg:

@@ -84,8 +84,21 @@ typedef struct {
                                     inject_flag_cycle (1-based); -1 disables            */
   int32_t profile;               /* 1: time every kernel launch with CUDA events on the
                                     handle's stream (lsba_get_profile)                  */
-  int32_t reserved[7];
+  int32_t precision;             /* arithmetic of the SpMM, Gram and update passes:
+                                    LSBA_PREC_DF: double-float (hi + lo FP32 pairs, 48
+                                    significand bits, 8 bytes per entry) on the FP32
+                                    pipes; LSBA_PREC_FP64: native FP64 (DFMA);
+                                    LSBA_PREC_AUTO (default): DF for BCGSI+LS and
+                                    BMGS-CWY/ICWY, FP64 for BCGS and BCGS-PIP, whose
+                                    O(eps) kappa^2 loss of orthogonality (Table 2)
+                                    amplifies the 2^-48 representation error.  The
+                                    small s x s / ks x s kernels are FP64 in all modes.
+                                    DF needs 8*(2(m+3)+3)s^2 bytes of shared memory
+                                    <= 200 KB; larger (m, s) run in FP64.            */
+  int32_t reserved[6];
 } lsba_options;
+
+enum { LSBA_PREC_FP64 = 0, LSBA_PREC_DF = 1, LSBA_PREC_AUTO = 2 };
 
 /* Counters and outcome of the last lsba_solve. */
 typedef struct {
@@ -100,6 +113,8 @@ typedef struct {
   double relres_est;       /* last residual estimate ||[M;-H] c C||_F / ||B||_F  */
   double relres_true;      /* ||B - A X||_F / ||B||_F (NaN if not computed)       */
   double solve_ms;         /* wall time of lsba_solve                            */
+  int32_t precision;       /* precision the solve ran in (LSBA_PREC_*)           */
+  int32_t pad;
 } lsba_stats;
 
 /* Host-side copies kept by the handle when record_history = 1; valid until the

@@ -62,6 +62,14 @@ struct lsba_ctx {
   std::vector<cudaEvent_t> ev;
   std::vector<int> ev_class;
   size_t ev_used = 0;
+  // double-float mode buffers
+  int df = 0;
+  float2* A_df = nullptr;      // CSR values as hi + lo pairs
+  size_t A_df_cap = 0;
+  double* Bdf = nullptr;       // n x s float2 (as raw 8-byte words)
+  double* Xdf = nullptr;
+  float2* cdf = nullptr;       // converted update coefficients
+  size_t cdf_cap = 0;
   double prof_ms[LSBA_K_NCLASS] = {0, 0, 0, 0};
   int64_t prof_n[LSBA_K_NCLASS] = {0, 0, 0, 0};
 };
@@ -114,6 +122,12 @@ static void free_ws(lsba_ctx* h) {
   cudaFree(h->Gbuf);
   cudaFree(h->small);
   cudaFree(h->ismall);
+  cudaFree(h->Bdf);
+  cudaFree(h->Xdf);
+  cudaFree(h->cdf);
+  h->Bdf = h->Xdf = nullptr;
+  h->cdf = nullptr;
+  h->cdf_cap = 0;
   h->basis = h->Wb = h->Ub = h->partials = h->Gbuf = h->small = nullptr;
   h->ismall = nullptr;
   h->cap_n = 0;
@@ -129,6 +143,9 @@ static size_t max_partials(int64_t n, int s, int mmax, int sms, size_t* qmax_out
       size_t v = (size_t)p.grid_x * p.q;
       if (v > best) best = v;
       if ((size_t)p.q > qmax) qmax = p.q;
+      GramPlan pd = plan_gram_df(n, s, a, b, sms);
+      v = (size_t)pd.grid_x * pd.q;
+      if (v > best) best = v;
     }
   *qmax_out = qmax;
   return best;
@@ -177,6 +194,14 @@ static int ensure_ws(lsba_ctx* h, int64_t n, int s, int m) {
     return LSBA_OUT_OF_MEMORY;
   }
   h->ismall_cap = 2 * hist_cap + 2 * (m + 4);
+  h->cdf_cap = coef_df_count(m + 3, s, true);
+  if (cudaMalloc(&h->Bdf, sizeof(double) * blk) != cudaSuccess ||
+      cudaMalloc(&h->Xdf, sizeof(double) * blk) != cudaSuccess ||
+      cudaMalloc(&h->cdf, sizeof(float2) * h->cdf_cap) != cudaSuccess) {
+    cudaGetLastError();
+    free_ws(h);
+    return LSBA_OUT_OF_MEMORY;
+  }
   if (cudaMalloc(&h->ismall, sizeof(int) * h->ismall_cap) != cudaSuccess) {
     cudaGetLastError();
     free_ws(h);
@@ -255,28 +280,63 @@ static int pull_ctl(lsba_ctx* h) {
 enum { SK_BCGS = 0, SK_PIP = 1, SK_LS = 2, SK_ICWY = 3, SK_CWY = 4 };
 static bool lagged(int skel) { return skel == SK_LS || skel == SK_ICWY || skel == SK_CWY; }
 
+// Precision dispatch of the three bandwidth-shaped passes (profiled).  In the
+// double-float mode every block vector buffer holds float2 (hi, lo) pairs.
+static void do_gram(lsba_ctx* h, const BlockPtrs& L, int a, const BlockPtrs& R, int b, int64_t n,
+                    int s, const Ctl* ctl, int guard) {
+  prof_begin(h, LSBA_K_GRAM);
+  if (h->df) {
+    GramPlan p = plan_gram_df(n, s, a, b, h->num_sms);
+    launch_gram_df(h->stream, p, L, a, R, b, n, s, (float2*)h->partials, h->Gbuf, ctl, guard);
+  } else {
+    GramPlan p = plan_gram(n, s, a, b, h->num_sms);
+    launch_gram(h->stream, p, L, a, R, b, n, s, h->partials, h->Gbuf, ctl, guard);
+  }
+  prof_end(h);
+}
+
+static void do_spmm(lsba_ctx* h, const lsba_csr* A, const double* V, double* W, int s,
+                    const Ctl* ctl, int guard) {
+  prof_begin(h, LSBA_K_SPMM);
+  if (h->df)
+    launch_spmm_df(h->stream, A->n, A->d_rowptr, A->d_colidx, h->A_df, (const float2*)V,
+                   (float2*)W, s, ctl, guard);
+  else
+    launch_spmm(h->stream, A->n, A->d_rowptr, A->d_colidx, A->d_vals, V, W, s, ctl, guard);
+  prof_end(h);
+}
+
+static void do_update(lsba_ctx* h, const BlockPtrs& in, int nin, int64_t n, int s, double* out1,
+                      const double* coef1, const double* tri1, double* out2, const double* coef2,
+                      const double* chain, const double* tri2, const Ctl* ctl, int step) {
+  prof_begin(h, LSBA_K_UPDATE);
+  if (h->df)
+    launch_update_df(h->stream, in, nin, n, s, (float2*)out1, coef1, tri1, (float2*)out2, coef2,
+                     chain, tri2, h->cdf, ctl, step, h->num_sms);
+  else
+    launch_update(h->stream, in, nin, n, s, out1, coef1, tri1, out2, coef2, chain, tri2, ctl, step);
+  prof_end(h);
+}
+
 // Enqueue the CholQR of R_start and every loop iteration of one cycle.
 static void enqueue_cycle(lsba_ctx* h, const lsba_csr* A, const double* Rstart, int64_t n, int s,
                           int m_cur, int start_flags) {
   cudaStream_t st = h->stream;
   const SmallWs& w = h->ws;
   const int skel = w.skel;
+  Ctl* ctl = h->d_ctl;
   BlockPtrs one;
   memset(&one, 0, sizeof(one));
   one.p[0] = Rstart;
-  {
-    GramPlan p = plan_gram(n, s, 1, 1, h->num_sms);
-    PROF(LSBA_K_GRAM, launch_gram(st, p, one, 1, one, 1, n, s, h->partials, h->Gbuf, h->d_ctl, 0));
-  }
+  do_gram(h, one, 1, one, 1, n, s, ctl, 0);
   PROF(LSBA_K_SMALL, launch_small_start(st, w, start_flags));
-  PROF(LSBA_K_UPDATE, launch_update(st, one, 1, n, s, h->basis, w.coef1, w.tri1, nullptr, nullptr, nullptr, nullptr,
-                h->d_ctl, 0));
+  do_update(h, one, 1, n, s, h->basis, w.coef1, w.tri1, nullptr, nullptr, nullptr, nullptr, ctl, 0);
   const int kmax = lagged(skel) ? m_cur + 1 : m_cur;
   const size_t blk = (size_t)n * s;
   for (int k = 1; k <= kmax; ++k) {
     if (skel == SK_PIP || skel == SK_BCGS) {
       const double* Vk = h->basis + (size_t)(k - 1) * blk;
-      PROF(LSBA_K_SPMM, launch_spmm(st, n, A->d_rowptr, A->d_colidx, A->d_vals, Vk, h->Wb, s, h->d_ctl, 1));
+      do_spmm(h, A, Vk, h->Wb, s, ctl, 1);
       BlockPtrs L = basis_list(h, n, s, k);
       BlockPtrs R;
       memset(&R, 0, sizeof(R));
@@ -286,38 +346,33 @@ static void enqueue_cycle(lsba_ctx* h, const lsba_csr* A, const double* Rstart, 
       double* Vnext = h->basis + (size_t)k * blk;
       if (skel == SK_PIP) {
         L.p[k] = h->Wb;
-        GramPlan p = plan_gram(n, s, k + 1, 1, h->num_sms);
-        PROF(LSBA_K_GRAM, launch_gram(st, p, L, k + 1, R, 1, n, s, h->partials, h->Gbuf, h->d_ctl, 1));
+        do_gram(h, L, k + 1, R, 1, n, s, ctl, 1);
         PROF(LSBA_K_SMALL, launch_small_step(st, w, k, 0));
-        PROF(LSBA_K_UPDATE, launch_update(st, in, k + 1, n, s, Vnext, w.coef1, w.tri1, nullptr, nullptr, nullptr,
-                      nullptr, h->d_ctl, k));
+        do_update(h, in, k + 1, n, s, Vnext, w.coef1, w.tri1, nullptr, nullptr, nullptr, nullptr,
+                  ctl, k);
       } else {
-        GramPlan p = plan_gram(n, s, k, 1, h->num_sms);
-        PROF(LSBA_K_GRAM, launch_gram(st, p, L, k, R, 1, n, s, h->partials, h->Gbuf, h->d_ctl, 1));
+        do_gram(h, L, k, R, 1, n, s, ctl, 1);
         PROF(LSBA_K_SMALL, launch_small_step(st, w, k, 0));
-        PROF(LSBA_K_UPDATE, launch_update(st, in, k + 1, n, s, h->Wb, w.coef1, nullptr, nullptr, nullptr, nullptr,
-                      nullptr, h->d_ctl, k));
-        GramPlan p2 = plan_gram(n, s, 1, 1, h->num_sms);
-        PROF(LSBA_K_GRAM, launch_gram(st, p2, R, 1, R, 1, n, s, h->partials, h->Gbuf, h->d_ctl, 1));
+        do_update(h, in, k + 1, n, s, h->Wb, w.coef1, nullptr, nullptr, nullptr, nullptr, nullptr,
+                  ctl, k);
+        do_gram(h, R, 1, R, 1, n, s, ctl, 1);
         PROF(LSBA_K_SMALL, launch_small_step(st, w, k, 1));
-        PROF(LSBA_K_UPDATE, launch_update(st, R, 1, n, s, Vnext, w.coef1, w.tri1, nullptr, nullptr, nullptr, nullptr,
-                      h->d_ctl, k));
+        do_update(h, R, 1, n, s, Vnext, w.coef1, w.tri1, nullptr, nullptr, nullptr, nullptr, ctl, k);
       }
     } else {
       const double* U = (k == 1) ? h->basis : h->Ub;
-      PROF(LSBA_K_SPMM, launch_spmm(st, n, A->d_rowptr, A->d_colidx, A->d_vals, U, h->Wb, s, h->d_ctl, 1));
+      do_spmm(h, A, U, h->Wb, s, ctl, 1);
       if (k == 1) {
         BlockPtrs L = basis_list(h, n, s, 1);
         BlockPtrs R;
         memset(&R, 0, sizeof(R));
         R.p[0] = h->Wb;
-        GramPlan p = plan_gram(n, s, 1, 1, h->num_sms);
-        PROF(LSBA_K_GRAM, launch_gram(st, p, L, 1, R, 1, n, s, h->partials, h->Gbuf, h->d_ctl, 1));
+        do_gram(h, L, 1, R, 1, n, s, ctl, 1);
         PROF(LSBA_K_SMALL, launch_small_step(st, w, 1, 0));
         BlockPtrs in = basis_list(h, n, s, 1);
         in.p[1] = h->Wb;
-        PROF(LSBA_K_UPDATE, launch_update(st, in, 2, n, s, h->Ub, w.coef1, nullptr, nullptr, nullptr, nullptr, nullptr,
-                      h->d_ctl, 1));
+        do_update(h, in, 2, n, s, h->Ub, w.coef1, nullptr, nullptr, nullptr, nullptr, nullptr, ctl,
+                  1);
       } else {
         BlockPtrs L = basis_list(h, n, s, k - 1);
         L.p[k - 1] = h->Ub;
@@ -325,18 +380,35 @@ static void enqueue_cycle(lsba_ctx* h, const lsba_csr* A, const double* Rstart, 
         memset(&R, 0, sizeof(R));
         R.p[0] = h->Ub;
         R.p[1] = h->Wb;
-        GramPlan p = plan_gram(n, s, k, 2, h->num_sms);
-        PROF(LSBA_K_GRAM, launch_gram(st, p, L, k, R, 2, n, s, h->partials, h->Gbuf, h->d_ctl, 1));
+        do_gram(h, L, k, R, 2, n, s, ctl, 1);
         PROF(LSBA_K_SMALL, launch_small_step(st, w, k, 0));
         BlockPtrs in = basis_list(h, n, s, k - 1);
         in.p[k - 1] = h->Ub;
         in.p[k] = h->Wb;
         double* Vk = h->basis + (size_t)(k - 1) * blk;
-        PROF(LSBA_K_UPDATE, launch_update(st, in, k + 1, n, s, Vk, w.coef1, w.tri1, h->Ub, w.coef2, w.chain,
-                      skel == SK_LS ? w.tri2 : nullptr, h->d_ctl, k));
+        do_update(h, in, k + 1, n, s, Vk, w.coef1, w.tri1, h->Ub, w.coef2, w.chain,
+                  skel == SK_LS ? w.tri2 : nullptr, ctl, k);
       }
     }
   }
+}
+
+// ||B - A X||_F / ||B||_F into ctl->relres_true (X, B in the solve's precision).
+static void enqueue_true_residual(lsba_ctx* h, const lsba_csr* A, const double* Bw, const double* Xw,
+                                  int64_t n, int s) {
+  cudaStream_t st = h->stream;
+  do_spmm(h, A, Xw, h->Wb, s, nullptr, 0);
+  prof_begin(h, LSBA_K_UPDATE);
+  if (h->df)
+    launch_sub_df(st, n * s, (const float2*)Bw, (const float2*)h->Wb, (float2*)h->Ub);
+  else
+    launch_axpby(st, n, s, Bw, h->Wb, h->Ub);
+  prof_end(h);
+  BlockPtrs one;
+  memset(&one, 0, sizeof(one));
+  one.p[0] = h->Ub;
+  do_gram(h, one, 1, one, 1, n, s, nullptr, 0);
+  PROF(LSBA_K_SMALL, launch_true_relres(st, h->Gbuf, s, h->d_ctl));
 }
 
 extern "C" {
@@ -351,6 +423,8 @@ void lsba_default_options(lsba_options* o) {
   o->record_history = 0;
   o->inject_flag_cycle = -1;
   o->inject_flag_relation = -1;
+  o->profile = 0;
+  o->precision = LSBA_PREC_AUTO;
 }
 
 const char* lsba_status_string(int st) {
@@ -413,6 +487,7 @@ int lsba_destroy(lsba_handle h) {
   cudaFree(h->hA_vals);
   cudaFree(h->hB);
   cudaFree(h->hX);
+  cudaFree(h->A_df);
   for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
   delete h;
   return LSBA_OK;
@@ -450,7 +525,30 @@ static int solve_impl(lsba_handle h, const lsba_csr* A, const double* d_B, doubl
   w.modification = h->opt.modification == LSBA_FOM ? 0 : 1;
   cudaStream_t st = h->stream;
   const size_t blk = (size_t)n * s;
-  CK(cudaMemsetAsync(d_X, 0, sizeof(double) * blk, st));
+  // Precision: double-float unless its update coefficients do not fit shared memory.
+  const bool want_df = h->opt.precision == LSBA_PREC_DF ||
+                       (h->opt.precision == LSBA_PREC_AUTO && lagged(skel));
+  h->df = (want_df && update_df_smem(m + 3, s, true) <= 200 * 1024) ? 1 : 0;
+  const double* Bw = d_B;   // B and X in the working precision
+  double* Xw = d_X;
+  if (h->df) {
+    if ((size_t)A->nnz > h->A_df_cap) {
+      cudaFree(h->A_df);
+      h->A_df = nullptr;
+      h->A_df_cap = 0;
+      if (cudaMalloc(&h->A_df, sizeof(float2) * (A->nnz > 0 ? A->nnz : 1)) != cudaSuccess) {
+        cudaGetLastError();
+        return h->stats.status = LSBA_OUT_OF_MEMORY;
+      }
+      h->A_df_cap = A->nnz;
+    }
+    PROF(LSBA_K_UPDATE, launch_to_df(st, A->nnz, A->d_vals, h->A_df));
+    PROF(LSBA_K_UPDATE, launch_to_df(st, n * s, d_B, (float2*)h->Bdf));
+    Bw = h->Bdf;
+    Xw = h->Xdf;
+  }
+  CK(cudaMemsetAsync(Xw, 0, sizeof(double) * blk, st));
+  h->stats.precision = h->df ? LSBA_PREC_DF : LSBA_PREC_FP64;
   Ctl* c = h->h_ctl;
   const int hist_cap = c->hist_cap, gram_cap = c->gram_hist_cap;
   memset(c, 0, sizeof(Ctl));
@@ -475,7 +573,7 @@ static int solve_impl(lsba_handle h, const lsba_csr* A, const double* d_B, doubl
   const int vper = (skel == SK_LS) ? 4 : (skel == SK_PIP || lagged(skel)) ? 3 : 2;
   const int vcyc = lagged(skel) ? 1 : 0;
   int m_cur = m;
-  const double* Rstart = d_B;
+  const double* Rstart = Bw;
   int start_flags = 3;
   int status = LSBA_NOT_CONVERGED;
   lsba_stats& S = h->stats;
@@ -538,9 +636,9 @@ static int solve_impl(lsba_handle h, const lsba_csr* A, const double* d_B, doubl
     PROF(LSBA_K_SMALL, launch_small_end(st, w));
     {
       BlockPtrs in = basis_list(h, n, s, j + 1);
-      in.p[j + 1] = d_X;
-      PROF(LSBA_K_UPDATE, launch_update(st, in, j + 2, n, s, d_X, w.coef1, nullptr, h->Ub, w.coef2, nullptr, nullptr,
-                    h->d_ctl, LSBA_END_STEP));
+      in.p[j + 1] = Xw;
+      do_update(h, in, j + 2, n, s, Xw, w.coef1, nullptr, h->Ub, w.coef2, nullptr, nullptr,
+                h->d_ctl, LSBA_END_STEP);
     }
     CK(cudaGetLastError());
     if (c->flagged && !h->opt.adaptive_restart) {
@@ -550,14 +648,7 @@ static int solve_impl(lsba_handle h, const lsba_csr* A, const double* d_B, doubl
     if (c->converged) {
       if (h->opt.verify_true_residual) {
         // R = B - A X into Ub; ||R||_F / ||B||_F from its Gram.
-        PROF(LSBA_K_SPMM, launch_spmm(st, n, A->d_rowptr, A->d_colidx, A->d_vals, d_X, h->Wb, s, nullptr, 0));
-        PROF(LSBA_K_UPDATE, launch_axpby(st, n, s, d_B, h->Wb, h->Ub));
-        BlockPtrs one;
-        memset(&one, 0, sizeof(one));
-        one.p[0] = h->Ub;
-        GramPlan p = plan_gram(n, s, 1, 1, h->num_sms);
-        PROF(LSBA_K_GRAM, launch_gram(st, p, one, 1, one, 1, n, s, h->partials, h->Gbuf, nullptr, 0));
-        PROF(LSBA_K_SMALL, launch_true_relres(st, h->Gbuf, s, h->d_ctl));
+        enqueue_true_residual(h, A, Bw, Xw, n, s);
         if ((rc = pull_ctl(h)) != LSBA_OK) return S.status = rc;
         S.relres_true = c->relres_true;
         have_true = true;
@@ -578,17 +669,11 @@ static int solve_impl(lsba_handle h, const lsba_csr* A, const double* d_B, doubl
   S.status = status;
   // True residual of the returned X.
   if (!have_true && status != LSBA_INVALID_ARG) {
-    PROF(LSBA_K_SPMM, launch_spmm(st, n, A->d_rowptr, A->d_colidx, A->d_vals, d_X, h->Wb, s, nullptr, 0));
-    PROF(LSBA_K_UPDATE, launch_axpby(st, n, s, d_B, h->Wb, h->Ub));
-    BlockPtrs one;
-    memset(&one, 0, sizeof(one));
-    one.p[0] = h->Ub;
-    GramPlan p = plan_gram(n, s, 1, 1, h->num_sms);
-    PROF(LSBA_K_GRAM, launch_gram(st, p, one, 1, one, 1, n, s, h->partials, h->Gbuf, nullptr, 0));
-    PROF(LSBA_K_SMALL, launch_true_relres(st, h->Gbuf, s, h->d_ctl));
+    enqueue_true_residual(h, A, Bw, Xw, n, s);
     if ((rc = pull_ctl(h)) != LSBA_OK) return S.status = rc;
     S.relres_true = c->relres_true;
   }
+  if (h->df) PROF(LSBA_K_UPDATE, launch_from_df(st, n * s, (const float2*)Xw, d_X));
   CK(cudaStreamSynchronize(st));
   if (h->opt.record_history) {
     const int ne = c->n_hist;

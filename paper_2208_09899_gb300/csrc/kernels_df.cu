@@ -1,0 +1,471 @@
+// Double-float (FP64-accurate, FP32-pipe) versions of the bandwidth-shaped
+// kernels of one block Arnoldi step.  GB300 executes FP64 at 1/72 of its FP32
+// rate, which leaves the FP64 Gram and update kernels 10-20x below the HBM
+// roofline; here every block vector is stored as hi + lo FP32 pairs (8 bytes
+// per entry, the same footprint as FP64) and every product-sum runs as a
+// compensated double-float accumulation (df.cuh) on the FP32 pipes.
+//
+//   k_spmm_df    W = A V                           (the paper's matvec, Sec. 2.1)
+//   k_gram_df    [L_1..L_a]^T [R_1..R_b], one pass (the sync point of Alg. 3
+//                line 4, Alg. 6 line 10, Alg. 7 line 10), register-tiled 4x4
+//   k_update_df  out = (sum_i in_i C_i (+ out1 chain)) T^{-1}, two outputs in
+//                one pass (Alg. 3 line 6, Alg. 6 lines 17-18, Alg. 7 lines 16-17)
+// The Gram result and everything after it (the small kernels) are FP64.
+#include "df.cuh"
+#include "lsba_internal.cuh"
+
+namespace lsba {
+
+static __device__ __forceinline__ int ctl_active_df(const Ctl* c) {
+  return *(volatile const int*)&c->active;
+}
+
+static inline int next_pow2_df(int s) {
+  int p = 1;
+  while (p < s) p <<= 1;
+  return p;
+}
+
+// ----------------------------------------------------------------- conversions
+__global__ void k_to_df(int64_t count, const double* __restrict__ in, float2* __restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < count) out[i] = df_from_double(in[i]);
+}
+__global__ void k_from_df(int64_t count, const float2* __restrict__ in, double* __restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < count) out[i] = df_to_double(in[i]);
+}
+// R = B - W (double-float)
+__global__ void k_sub_df(int64_t count, const float2* __restrict__ B, const float2* __restrict__ W,
+                         float2* __restrict__ R) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < count) {
+    dfacc a{B[i].x, B[i].y};
+    const float2 w = W[i];
+    df_add_to(a, make_float2(-w.x, -w.y));
+    R[i] = df_value(a);
+  }
+}
+
+void launch_to_df(cudaStream_t st, int64_t count, const double* in, float2* out) {
+  if (count > 0) k_to_df<<<(unsigned)((count + 255) / 256), 256, 0, st>>>(count, in, out);
+}
+void launch_from_df(cudaStream_t st, int64_t count, const float2* in, double* out) {
+  if (count > 0) k_from_df<<<(unsigned)((count + 255) / 256), 256, 0, st>>>(count, in, out);
+}
+void launch_sub_df(cudaStream_t st, int64_t count, const float2* B, const float2* W, float2* R) {
+  if (count > 0) k_sub_df<<<(unsigned)((count + 255) / 256), 256, 0, st>>>(count, B, W, R);
+}
+
+// ----------------------------------------------------------------- SpMM
+__global__ void __launch_bounds__(256) k_spmm_df(int64_t n, const int32_t* __restrict__ rowptr,
+                                                 const int32_t* __restrict__ colidx,
+                                                 const float2* __restrict__ vals,
+                                                 const float2* __restrict__ V,
+                                                 float2* __restrict__ W, int s, int S2,
+                                                 const Ctl* ctl, int guard) {
+  if (guard && !ctl_active_df(ctl)) return;
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t row = idx / S2;
+  const int c = (int)(idx % S2);
+  if (row >= n || c >= s) return;
+  const int p0 = rowptr[row], p1 = rowptr[row + 1];
+  dfacc acc{0.f, 0.f};
+  for (int p = p0; p < p1; ++p) df_fma(acc, vals[p], V[(int64_t)colidx[p] * s + c]);
+  W[row * s + c] = df_value(acc);
+}
+
+void launch_spmm_df(cudaStream_t st, int64_t n, const int32_t* rowptr, const int32_t* colidx,
+                    const float2* vals, const float2* V, float2* W, int s, const Ctl* ctl,
+                    int guard) {
+  const int S2 = next_pow2_df(s);
+  const int64_t threads = n * S2;
+  if (threads == 0) return;
+  k_spmm_df<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(n, rowptr, colidx, vals, V, W, s,
+                                                                S2, ctl, guard);
+}
+
+// ----------------------------------------------------------------- Gram
+// Shared-memory chunk layout: [block][row][sp] with sp = s rounded up to 4 (the
+// padding columns are zero).  The output, in the padded index space
+// (a sp) x (b sp), is cut into 4x4 thread tiles; a CTA owns up to 256 tiles
+// (blockIdx.y) and a contiguous row range (blockIdx.x).  When it owns fewer
+// than 256 tiles, groups of threads split the chunk's rows and are summed in
+// shared memory at the end.  Per-CTA partials are double-float, reduced in
+// CTA order by k_gram_reduce_df into FP64.
+#define GDF_THREADS 256
+
+struct GramDfArgs {
+  BlockPtrs L;
+  BlockPtrs R;
+  int a, b, s, sp, rc;
+  int64_t n, rows_per_cta;
+  int q;          // a*s*b*s (unpadded outputs)
+  int ntj;        // tiles along the padded column dimension (b*sp/4)
+  int ntile;      // total tiles
+  float2* partials;
+  const Ctl* ctl;
+  int guard;
+};
+
+__global__ void __launch_bounds__(GDF_THREADS) k_gram_df(const __grid_constant__ GramDfArgs g) {
+  if (g.guard && !ctl_active_df(g.ctl)) return;
+  extern __shared__ float2 smf[];
+  const int s = g.s, sp = g.sp, rc = g.rc, a = g.a, b = g.b;
+  const int nblk = a + b;
+  const int tile_base = blockIdx.y * GDF_THREADS;
+  const int cnt = min(GDF_THREADS, g.ntile - tile_base);
+  const int groups = GDF_THREADS / cnt;
+  const int grp = threadIdx.x / cnt;
+  const int tl = threadIdx.x % cnt;
+  const bool active = grp < groups;
+  const int T = tile_base + tl;
+  const int it = T / g.ntj, jt = T % g.ntj;
+  // Element (blk, r, col) of the chunk lives at smf[(blk * rc + r) * sp + col].
+  const int li = it * 4;                    // padded L index: block li/sp, column li%sp
+  const int lofs = (li / sp) * rc * sp + (li % sp);
+  const int rj = jt * 4;
+  const int rofs = (a + rj / sp) * rc * sp + (rj % sp);
+
+  dfacc acc[4][4];
+#pragma unroll
+  for (int x = 0; x < 4; ++x)
+#pragma unroll
+    for (int y = 0; y < 4; ++y) acc[x][y] = dfacc{0.f, 0.f};
+
+  const int64_t r_begin = (int64_t)blockIdx.x * g.rows_per_cta;
+  const int64_t r_end = min(g.n, r_begin + g.rows_per_cta);
+  // Zero the padding columns once (never overwritten by the chunk loads).
+  if (sp != s) {
+    for (int idx = threadIdx.x; idx < nblk * rc * (sp - s); idx += GDF_THREADS) {
+      const int pc = idx % (sp - s), br = idx / (sp - s);
+      smf[br * sp + s + pc] = make_float2(0.f, 0.f);
+    }
+  }
+  for (int64_t r0 = r_begin; r0 < r_end; r0 += rc) {
+    const int rows = (int)min((int64_t)rc, r_end - r0);
+    const int per = rows * s;
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < nblk * per; idx += GDF_THREADS) {
+      const int blk = idx / per, off = idx - blk * per;
+      const int r = off / s, c = off - r * s;
+      const float2* src = (const float2*)(blk < a ? g.L.p[blk] : g.R.p[blk - a]);
+      smf[(blk * rc + r) * sp + c] = src[r0 * s + off];
+    }
+    __syncthreads();
+    if (active) {
+      for (int r = grp; r < rows; r += groups) {
+        const float4* lp = (const float4*)(smf + lofs + r * sp);
+        const float4* rp = (const float4*)(smf + rofs + r * sp);
+        const float4 l01 = lp[0], l23 = lp[1], r01 = rp[0], r23 = rp[1];
+        const float2 lv[4] = {make_float2(l01.x, l01.y), make_float2(l01.z, l01.w),
+                              make_float2(l23.x, l23.y), make_float2(l23.z, l23.w)};
+        const float2 rv[4] = {make_float2(r01.x, r01.y), make_float2(r01.z, r01.w),
+                              make_float2(r23.x, r23.y), make_float2(r23.z, r23.w)};
+#pragma unroll
+        for (int x = 0; x < 4; ++x)
+#pragma unroll
+          for (int y = 0; y < 4; ++y) df_fma(acc[x][y], lv[x], rv[y]);
+      }
+#pragma unroll
+      for (int x = 0; x < 4; ++x)
+#pragma unroll
+        for (int y = 0; y < 4; ++y) df_renorm(acc[x][y]);
+    }
+  }
+  // Sum the row groups (shared memory), then write this CTA's partials.
+  if (groups > 1) {
+    __syncthreads();
+    float2* red = smf;  // [groups][cnt][16]
+    if (active) {
+#pragma unroll
+      for (int x = 0; x < 4; ++x)
+#pragma unroll
+        for (int y = 0; y < 4; ++y)
+          red[((size_t)grp * cnt + tl) * 16 + x * 4 + y] = make_float2(acc[x][y].s, acc[x][y].c);
+    }
+    __syncthreads();
+    if (grp == 0) {
+      for (int g2 = 1; g2 < groups; ++g2) {
+#pragma unroll
+        for (int x = 0; x < 4; ++x)
+#pragma unroll
+          for (int y = 0; y < 4; ++y) {
+            const float2 v = red[((size_t)g2 * cnt + tl) * 16 + x * 4 + y];
+            df_add_to(acc[x][y], make_float2(v.x, 0.f));
+            df_add_to(acc[x][y], make_float2(v.y, 0.f));
+          }
+      }
+    }
+  }
+  if (grp == 0) {
+    const int bs = b * s;
+#pragma unroll
+    for (int x = 0; x < 4; ++x) {
+      const int pi = li + x;               // padded row index
+      const int i = (pi / sp) * s + (pi % sp);
+      if (pi % sp >= s || pi >= a * sp) continue;
+#pragma unroll
+      for (int y = 0; y < 4; ++y) {
+        const int pj = rj + y;
+        if (pj % sp >= s || pj >= b * sp) continue;
+        const int j = (pj / sp) * s + (pj % sp);
+        const float2 v = df_value(acc[x][y]);
+        g.partials[(int64_t)blockIdx.x * g.q + (int64_t)i * bs + j] = v;
+      }
+    }
+  }
+}
+
+__global__ void k_gram_reduce_df(const float2* __restrict__ partials, int nparts, int q,
+                                 double* __restrict__ G, const Ctl* ctl, int guard) {
+  if (guard && !ctl_active_df(ctl)) return;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= q) return;
+  dfacc acc{0.f, 0.f};
+  for (int x = 0; x < nparts; ++x) df_add_to(acc, partials[(int64_t)x * q + e]);
+  G[e] = dfacc_to_double(acc);
+}
+
+GramPlan plan_gram_df(int64_t n, int s, int a, int b, int num_sms) {
+  GramPlan p;
+  const int sp = (s + 3) & ~3;
+  p.q = a * s * b * s;
+  const int ntile = (a * sp / 4) * (b * sp / 4);
+  p.tile = GDF_THREADS;
+  p.grid_y = (ntile + GDF_THREADS - 1) / GDF_THREADS;
+  const size_t row_bytes = (size_t)(a + b) * sp * sizeof(float2);
+  int rc = (int)((80 * 1024) / row_bytes);
+  if (rc > 128) rc = 128;
+  if (rc < 1) rc = 1;
+  p.rows_per_chunk = rc;
+  size_t red_bytes = (size_t)GDF_THREADS * 16 * sizeof(float2);
+  p.smem = row_bytes * rc > red_bytes ? row_bytes * rc : red_bytes;
+  int gx = (2 * num_sms + p.grid_y - 1) / p.grid_y;
+  const int64_t max_gx = (n + rc - 1) / rc;
+  if (gx > max_gx) gx = (int)max_gx;
+  if (gx < 1) gx = 1;
+  int64_t rpc = (n + gx - 1) / gx;
+  rpc = ((rpc + rc - 1) / rc) * rc;
+  if (rpc < rc) rpc = rc;
+  gx = (int)((n + rpc - 1) / rpc);
+  if (gx < 1) gx = 1;
+  p.grid_x = gx;
+  p.rows_per_cta = rpc;
+  return p;
+}
+
+void launch_gram_df(cudaStream_t st, const GramPlan& p, const BlockPtrs& L, int a,
+                    const BlockPtrs& R, int b, int64_t n, int s, float2* partials, double* G,
+                    const Ctl* ctl, int guard) {
+  GramDfArgs g;
+  g.L = L;
+  g.R = R;
+  g.a = a;
+  g.b = b;
+  g.s = s;
+  g.sp = (s + 3) & ~3;
+  g.rc = p.rows_per_chunk;
+  g.n = n;
+  g.rows_per_cta = p.rows_per_cta;
+  g.q = p.q;
+  g.ntj = b * g.sp / 4;
+  g.ntile = (a * g.sp / 4) * g.ntj;
+  g.partials = partials;
+  g.ctl = ctl;
+  g.guard = guard;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(k_gram_df, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr_set = true;
+  }
+  dim3 grid(p.grid_x, p.grid_y);
+  k_gram_df<<<grid, GDF_THREADS, p.smem, st>>>(g);
+  k_gram_reduce_df<<<(p.q + 255) / 256, 256, 0, st>>>(partials, p.grid_x, p.q, G, ctl, guard);
+}
+
+// ----------------------------------------------------------------- Update
+// The small kernels produce the update coefficients in FP64; k_coef_df
+// converts them once per step with many CTAs (FP64->FP32 conversions run on
+// the slow FP64 pipe), into the layout
+//   [c1: nin*s*s][c2: nin*s*s if two][chain: s*s][t1: s*s][t2: s*s][r1: s][r2: s]
+// (r = reciprocal diagonals of the triangular factors).  k_update_df runs a
+// persistent grid; each CTA copies the converted coefficients to shared memory
+// and walks row groups.  A row's s entries belong to a group of S2 lanes of one
+// warp; input values are exchanged by shuffles.
+__host__ __device__ size_t coef_df_count(int nin, int s, bool two) {
+  const size_t ss = (size_t)s * s;
+  return (size_t)nin * ss * (two ? 2 : 1) + 3 * ss + 2 * (size_t)s;
+}
+
+struct CoefDfArgs {
+  const double* coef1;
+  const double* coef2;
+  const double* chain;
+  const double* tri1;
+  const double* tri2;
+  int nin, s, two;
+  float2* out;
+  const Ctl* ctl;
+  int step;
+};
+
+__global__ void k_coef_df(const __grid_constant__ CoefDfArgs a) {
+  if (a.step >= 0 && *(volatile const int*)&a.ctl->update_step != a.step) return;
+  const int s = a.s, ss = s * s;
+  const int n1 = a.nin * ss, n2 = a.two ? n1 : 0;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  int o = e;
+  if (o < n1) { a.out[e] = df_from_double(a.coef1[o]); return; }
+  o -= n1;
+  if (o < n2) { a.out[e] = df_from_double(a.coef2[o]); return; }
+  o -= n2;
+  if (o < ss) { a.out[e] = (a.two && a.chain) ? df_from_double(a.chain[o]) : make_float2(0.f, 0.f); return; }
+  o -= ss;
+  if (o < ss) { a.out[e] = a.tri1 ? df_from_double(a.tri1[o]) : make_float2(0.f, 0.f); return; }
+  o -= ss;
+  if (o < ss) { a.out[e] = (a.two && a.tri2) ? df_from_double(a.tri2[o]) : make_float2(0.f, 0.f); return; }
+  o -= ss;
+  if (o < s) { a.out[e] = a.tri1 ? df_from_double(1.0 / a.tri1[o * s + o]) : make_float2(0.f, 0.f); return; }
+  o -= s;
+  if (o < s) { a.out[e] = (a.two && a.tri2) ? df_from_double(1.0 / a.tri2[o * s + o]) : make_float2(0.f, 0.f); }
+}
+
+struct UpdDfArgs {
+  BlockPtrs in;
+  int nin, s, S2;
+  int64_t n;
+  float2* out1;
+  float2* out2;
+  const float2* cdf;
+  int has_tri1, has_chain, has_tri2;
+  const Ctl* ctl;
+  int step;
+};
+
+__device__ __forceinline__ float2 shfl_f2(float2 v, int src, int width) {
+  return make_float2(__shfl_sync(0xffffffffu, v.x, src, width),
+                     __shfl_sync(0xffffffffu, v.y, src, width));
+}
+
+// Right-multiply the row held by the lane group by T^{-1} (upper triangular):
+// forward substitution over the columns in double-float.
+__device__ __forceinline__ float2 row_trsm_df(dfacc t, const float2* T, const float2* rinv, int c,
+                                              int s, int S2) {
+  const float2 rc = c < s ? rinv[c] : make_float2(0.f, 0.f);
+  for (int q = 0; q < s; ++q) {
+    const float2 vq = shfl_f2(df_mul(df_value(t), rc), q, S2);
+    if (c == q) {
+      t.s = vq.x;
+      t.c = vq.y;
+    } else if (c > q && c < s) {
+      df_fms(t, vq, T[q * s + c]);
+    }
+  }
+  return df_value(t);
+}
+
+__global__ void __launch_bounds__(256) k_update_df(const __grid_constant__ UpdDfArgs u) {
+  if (u.step >= 0 && *(volatile const int*)&u.ctl->update_step != u.step) return;
+  extern __shared__ float2 cs[];
+  const int s = u.s, S2 = u.S2, nin = u.nin;
+  const int ss = s * s;
+  const bool two = u.out2 != nullptr;
+  const int total = (int)coef_df_count(nin, s, two);
+  for (int e = threadIdx.x; e < total; e += blockDim.x) cs[e] = u.cdf[e];
+  __syncthreads();
+  const float2* c1 = cs;
+  const float2* c2 = c1 + (size_t)nin * ss;
+  const float2* ch = c2 + (two ? (size_t)nin * ss : 0);
+  const float2* t1 = ch + ss;
+  const float2* t2 = t1 + ss;
+  const float2* r1 = t2 + ss;
+  const float2* r2 = r1 + s;
+  const int c = threadIdx.x % S2;
+  const int rows_per_cta = blockDim.x / S2;
+  for (int64_t row0 = (int64_t)blockIdx.x * rows_per_cta; row0 < u.n;
+       row0 += (int64_t)gridDim.x * rows_per_cta) {
+    const int64_t row = row0 + threadIdx.x / S2;
+    const bool live = (row < u.n) && (c < s);
+    dfacc a1{0.f, 0.f}, a2{0.f, 0.f};
+    for (int bk = 0; bk < nin; ++bk) {
+      const float2 v = live ? ((const float2*)u.in.p[bk])[row * s + c] : make_float2(0.f, 0.f);
+      const float2* k1 = c1 + (size_t)bk * ss;
+      const float2* k2 = c2 + (size_t)bk * ss;
+      for (int q = 0; q < s; ++q) {
+        const float2 x = shfl_f2(v, q, S2);
+        if (c < s) {
+          df_fma(a1, x, k1[q * s + c]);
+          if (two) df_fma(a2, x, k2[q * s + c]);
+        }
+      }
+    }
+    const float2 o1 = u.has_tri1 ? row_trsm_df(a1, t1, r1, c, s, S2) : df_value(a1);
+    float2 o2 = make_float2(0.f, 0.f);
+    if (two) {
+      if (u.has_chain) {
+        for (int q = 0; q < s; ++q) {
+          const float2 x = shfl_f2(o1, q, S2);
+          if (c < s) df_fma(a2, x, ch[q * s + c]);
+        }
+      }
+      o2 = u.has_tri2 ? row_trsm_df(a2, t2, r2, c, s, S2) : df_value(a2);
+    }
+    __syncwarp();
+    if (live) {
+      u.out1[row * s + c] = o1;
+      if (two) u.out2[row * s + c] = o2;
+    }
+  }
+}
+
+size_t update_df_smem(int nin, int s, bool two) { return sizeof(float2) * coef_df_count(nin, s, two); }
+
+void launch_update_df(cudaStream_t st, const BlockPtrs& in, int nin, int64_t n, int s, float2* out1,
+                      const double* coef1, const double* tri1, float2* out2, const double* coef2,
+                      const double* chain, const double* tri2, float2* cdf, const Ctl* ctl,
+                      int step, int num_sms) {
+  const bool two = out2 != nullptr;
+  CoefDfArgs ca;
+  ca.coef1 = coef1;
+  ca.coef2 = coef2;
+  ca.chain = chain;
+  ca.tri1 = tri1;
+  ca.tri2 = tri2;
+  ca.nin = nin;
+  ca.s = s;
+  ca.two = two ? 1 : 0;
+  ca.out = cdf;
+  ca.ctl = ctl;
+  ca.step = step;
+  const int total = (int)coef_df_count(nin, s, two);
+  k_coef_df<<<(total + 127) / 128, 128, 0, st>>>(ca);
+  UpdDfArgs u;
+  u.in = in;
+  u.nin = nin;
+  u.s = s;
+  u.S2 = next_pow2_df(s);
+  u.n = n;
+  u.out1 = out1;
+  u.out2 = out2;
+  u.cdf = cdf;
+  u.has_tri1 = tri1 != nullptr;
+  u.has_chain = two && chain != nullptr;
+  u.has_tri2 = two && tri2 != nullptr;
+  u.ctl = ctl;
+  u.step = step;
+  const size_t smem = update_df_smem(nin, s, two);
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(k_update_df, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr_set = true;
+  }
+  const int rows_per_cta = 256 / u.S2;
+  const int64_t need = (n + rows_per_cta - 1) / rows_per_cta;
+  int64_t grid = 4LL * num_sms;
+  if (grid > need) grid = need;
+  if (grid < 1) grid = 1;
+  k_update_df<<<(unsigned)grid, 256, smem, st>>>(u);
+}
+
+}  // namespace lsba

@@ -106,6 +106,23 @@ void launch_update(cudaStream_t st, const BlockPtrs& in, int nin, int64_t n, int
                    double* out2, const double* coef2, const double* chain, const double* tri2,
                    const Ctl* ctl, int step);
 
+// ---- double-float (FP64-accurate, FP32-pipe) variants; block vectors are float2 (hi, lo) ----
+void launch_to_df(cudaStream_t st, int64_t count, const double* in, float2* out);
+void launch_from_df(cudaStream_t st, int64_t count, const float2* in, double* out);
+void launch_sub_df(cudaStream_t st, int64_t count, const float2* B, const float2* W, float2* R);
+void launch_spmm_df(cudaStream_t st, int64_t n, const int32_t* rowptr, const int32_t* colidx,
+                    const float2* vals, const float2* V, float2* W, int s, const Ctl* ctl, int guard);
+GramPlan plan_gram_df(int64_t n, int s, int a, int b, int num_sms);
+void launch_gram_df(cudaStream_t st, const GramPlan& p, const BlockPtrs& L, int a,
+                    const BlockPtrs& R, int b, int64_t n, int s, float2* partials, double* G,
+                    const Ctl* ctl, int guard);
+__host__ __device__ size_t coef_df_count(int nin, int s, bool two);
+size_t update_df_smem(int nin, int s, bool two);
+void launch_update_df(cudaStream_t st, const BlockPtrs& in, int nin, int64_t n, int s, float2* out1,
+                      const double* coef1, const double* tri1, float2* out2, const double* coef2,
+                      const double* chain, const double* tri2, float2* cdf, const Ctl* ctl,
+                      int step, int num_sms);
+
 // Small single-CTA kernels (skeleton logic, Cholesky, least squares, estimate).
 void launch_small_start(cudaStream_t st, const SmallWs& w, int flags);
 void launch_true_relres(cudaStream_t st, const double* G, int s, Ctl* ctl);

@@ -20,6 +20,7 @@ LSBA_OK, LSBA_NOT_CONVERGED, LSBA_BREAKDOWN, LSBA_INVALID_ARG = 0, 1, 2, 3
 LSBA_OUT_OF_MEMORY, LSBA_CUDA_ERROR, LSBA_DEVICE_TIMEOUT = 4, 5, 6
 SKELETONS = {"bcgs": 0, "bcgs_pip": 1, "bcgsi_ls": 2, "bmgs_icwy": 3, "bmgs_cwy": 4}
 MODIFICATIONS = {"fom": 0, "gmres": 1}
+PRECISIONS = {"fp64": 0, "df": 1, "auto": 2}
 
 EXPORTED = ("lsba_default_options", "lsba_create", "lsba_set_options", "lsba_solve",
             "lsba_solve_host", "lsba_get_stats", "lsba_get_history", "lsba_status_string",
@@ -33,14 +34,15 @@ class Options(C.Structure):
                 ("adaptive_restart", C.c_int32), ("verify_true_residual", C.c_int32),
                 ("record_history", C.c_int32), ("inject_flag_cycle", C.c_int32),
                 ("inject_flag_relation", C.c_int32), ("profile", C.c_int32),
-                ("reserved", C.c_int32 * 7)]
+                ("precision", C.c_int32), ("reserved", C.c_int32 * 6)]
 
 
 class Stats(C.Structure):
     _fields_ = [("status", C.c_int32), ("cycles", C.c_int32), ("steps", C.c_int32),
                 ("a_calls", C.c_int32), ("syncs", C.c_int32), ("v_apps", C.c_int32),
                 ("flags", C.c_int32), ("m_final", C.c_int32), ("relres_est", C.c_double),
-                ("relres_true", C.c_double), ("solve_ms", C.c_double)]
+                ("relres_true", C.c_double), ("solve_ms", C.c_double),
+                ("precision", C.c_int32), ("pad", C.c_int32)]
 
 
 class History(C.Structure):
@@ -166,6 +168,8 @@ class Solver:
         for k, v in opts.items():
             if k == "modification" and isinstance(v, str):
                 v = MODIFICATIONS[v]
+            if k == "precision" and isinstance(v, str):
+                v = PRECISIONS[v]
             if isinstance(v, bool):
                 v = int(v)
             setattr(self.opt, k, v)
