@@ -62,6 +62,9 @@ struct lsba_ctx {
   std::vector<cudaEvent_t> ev;
   std::vector<int> ev_class;
   size_t ev_used = 0;
+  // side stream for the off-critical-path small kernel, and its events
+  cudaStream_t side = nullptr;
+  std::vector<cudaEvent_t> ev_main, ev_side;
   // double-float mode buffers
   int df = 0;
   float2* A_df = nullptr;      // CSR values as hi + lo pairs
@@ -75,7 +78,7 @@ struct lsba_ctx {
 };
 
 // Record the start event of a launch of kernel class `cls` (no-op unless profiling).
-static void prof_begin(lsba_ctx* h, int cls) {
+static void prof_begin(lsba_ctx* h, int cls, cudaStream_t st) {
   if (!h->opt.profile) return;
   if (h->ev_used + 2 > h->ev.size()) {
     for (int i = 0; i < 2; ++i) {
@@ -86,13 +89,15 @@ static void prof_begin(lsba_ctx* h, int cls) {
     h->ev_class.resize(h->ev.size() / 2);
   }
   h->ev_class[h->ev_used / 2] = cls;
-  cudaEventRecord(h->ev[h->ev_used], h->stream);
+  cudaEventRecord(h->ev[h->ev_used], st);
 }
-static void prof_end(lsba_ctx* h) {
+static void prof_begin(lsba_ctx* h, int cls) { prof_begin(h, cls, h->stream); }
+static void prof_end(lsba_ctx* h, cudaStream_t st) {
   if (!h->opt.profile) return;
-  cudaEventRecord(h->ev[h->ev_used + 1], h->stream);
+  cudaEventRecord(h->ev[h->ev_used + 1], st);
   h->ev_used += 2;
 }
+static void prof_end(lsba_ctx* h) { prof_end(h, h->stream); }
 // Accumulate the recorded pairs (the stream must be synchronized).
 static void prof_collect(lsba_ctx* h) {
   for (size_t i = 0; i + 1 < h->ev_used; i += 2) {
@@ -183,7 +188,8 @@ static int ensure_ws(lsba_ctx* h, int64_t n, int s, int m) {
                otau = take((size_t)(m + 1) * s), og = take((size_t)ldH * s), oTf = take(ss),
                ogf = take(ss), ocf = take(ss), ouf = take((size_t)ldH * s), oC = take(ss),
                oBc = take(ss), oXi = take((size_t)ldH * s), oMv = take((size_t)ldH * s),
-               owk = take((size_t)6 * ldH * s + 16 * ss), ohe = take(hist_cap),
+               owk = take((size_t)6 * ldH * s + 16 * ss), osz = take((size_t)ldH * s),
+               osy = take((size_t)ldH * s), osr = take(ss), ohe = take(hist_cap),
                ogh = take(gram_hist_cap);
   h->small_cap = off;
   if (cudaMalloc(&h->small, sizeof(double) * off) != cudaSuccess ||
@@ -237,6 +243,9 @@ static int ensure_ws(lsba_ctx* h, int64_t n, int s, int m) {
   w.Xi = b + oXi;
   w.Mvec = b + oMv;
   w.work = b + owk;
+  w.saveZP = b + osz;
+  w.saveY = b + osy;
+  w.saveR = b + osr;
   w.hist_est = b + ohe;
   w.gram_hist = b + ogh;
   w.hist_cycle = h->ismall;
@@ -245,6 +254,27 @@ static int ensure_ws(lsba_ctx* h, int64_t n, int s, int m) {
   w.ctl = h->d_ctl;
   h->h_ctl->hist_cap = (int)hist_cap;
   h->h_ctl->gram_hist_cap = (int)gram_hist_cap;
+  if (!h->side) {
+    int lo = 0, hi = 0;
+    cudaDeviceGetStreamPriorityRange(&lo, &hi);
+    if (cudaStreamCreateWithPriority(&h->side, cudaStreamNonBlocking, hi) != cudaSuccess) {
+      cudaGetLastError();
+      h->side = nullptr;
+      free_ws(h);
+      return LSBA_CUDA_ERROR;
+    }
+  }
+  while ((int)h->ev_main.size() < m + 3) {
+    cudaEvent_t a, b;
+    if (cudaEventCreateWithFlags(&a, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b, cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      free_ws(h);
+      return LSBA_CUDA_ERROR;
+    }
+    h->ev_main.push_back(a);
+    h->ev_side.push_back(b);
+  }
   h->cap_n = n;
   h->cap_s = s;
   h->cap_m = m;
@@ -318,6 +348,21 @@ static void do_update(lsba_ctx* h, const BlockPtrs& in, int nin, int64_t n, int 
   prof_end(h);
 }
 
+// After the small kernel of loop iteration k: run its side kernel on the side
+// stream (it overlaps the next iteration's SpMM and Gram).  The next small
+// kernel, and the end of the batch, wait for it.
+static void enqueue_side(lsba_ctx* h, int k) {
+  cudaEventRecord(h->ev_main[k], h->stream);
+  cudaStreamWaitEvent(h->side, h->ev_main[k], 0);
+  prof_begin(h, LSBA_K_SMALL, h->side);
+  launch_small_side(h->side, h->ws, k);
+  prof_end(h, h->side);
+  cudaEventRecord(h->ev_side[k], h->side);
+}
+static void wait_side(lsba_ctx* h, int k) {
+  if (k >= 1) cudaStreamWaitEvent(h->stream, h->ev_side[k], 0);
+}
+
 // Enqueue the CholQR of R_start and every loop iteration of one cycle.
 static void enqueue_cycle(lsba_ctx* h, const lsba_csr* A, const double* Rstart, int64_t n, int s,
                           int m_cur, int start_flags) {
@@ -347,16 +392,20 @@ static void enqueue_cycle(lsba_ctx* h, const lsba_csr* A, const double* Rstart, 
       if (skel == SK_PIP) {
         L.p[k] = h->Wb;
         do_gram(h, L, k + 1, R, 1, n, s, ctl, 1);
+        wait_side(h, k - 1);
         PROF(LSBA_K_SMALL, launch_small_step(st, w, k, 0));
+        enqueue_side(h, k);
         do_update(h, in, k + 1, n, s, Vnext, w.coef1, w.tri1, nullptr, nullptr, nullptr, nullptr,
                   ctl, k);
       } else {
         do_gram(h, L, k, R, 1, n, s, ctl, 1);
+        wait_side(h, k - 1);
         PROF(LSBA_K_SMALL, launch_small_step(st, w, k, 0));
         do_update(h, in, k + 1, n, s, h->Wb, w.coef1, nullptr, nullptr, nullptr, nullptr, nullptr,
                   ctl, k);
         do_gram(h, R, 1, R, 1, n, s, ctl, 1);
         PROF(LSBA_K_SMALL, launch_small_step(st, w, k, 1));
+        enqueue_side(h, k);
         do_update(h, R, 1, n, s, Vnext, w.coef1, w.tri1, nullptr, nullptr, nullptr, nullptr, ctl, k);
       }
     } else {
@@ -381,7 +430,9 @@ static void enqueue_cycle(lsba_ctx* h, const lsba_csr* A, const double* Rstart, 
         R.p[0] = h->Ub;
         R.p[1] = h->Wb;
         do_gram(h, L, k, R, 2, n, s, ctl, 1);
+        wait_side(h, k - 1);
         PROF(LSBA_K_SMALL, launch_small_step(st, w, k, 0));
+        enqueue_side(h, k);
         BlockPtrs in = basis_list(h, n, s, k - 1);
         in.p[k - 1] = h->Ub;
         in.p[k] = h->Wb;
@@ -391,6 +442,7 @@ static void enqueue_cycle(lsba_ctx* h, const lsba_csr* A, const double* Rstart, 
       }
     }
   }
+  wait_side(h, kmax);
 }
 
 // ||B - A X||_F / ||B||_F into ctl->relres_true (X, B in the solve's precision).
@@ -489,6 +541,9 @@ int lsba_destroy(lsba_handle h) {
   cudaFree(h->hX);
   cudaFree(h->A_df);
   for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
+  for (cudaEvent_t e : h->ev_main) cudaEventDestroy(e);
+  for (cudaEvent_t e : h->ev_side) cudaEventDestroy(e);
+  if (h->side) cudaStreamDestroy(h->side);
   delete h;
   return LSBA_OK;
 }
@@ -557,6 +612,7 @@ static int solve_impl(lsba_handle h, const lsba_csr* A, const double* d_B, doubl
   c->tol = tol;
   c->record = h->opt.record_history ? 1 : 0;
   c->update_step = -1;
+  c->side_step = -1;
   h->h_est.clear();
   h->h_est_cycle.clear();
   h->h_est_j.clear();

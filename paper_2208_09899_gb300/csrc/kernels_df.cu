@@ -146,11 +146,22 @@ __global__ void __launch_bounds__(GDF_THREADS) k_gram_df(const __grid_constant__
     const int rows = (int)min((int64_t)rc, r_end - r0);
     const int per = rows * s;
     __syncthreads();
-    for (int idx = threadIdx.x; idx < nblk * per; idx += GDF_THREADS) {
-      const int blk = idx / per, off = idx - blk * per;
-      const int r = off / s, c = off - r * s;
-      const float2* src = (const float2*)(blk < a ? g.L.p[blk] : g.R.p[blk - a]);
-      smf[(blk * rc + r) * sp + c] = src[r0 * s + off];
+    if (sp == s) {
+      // Each block's chunk is contiguous in global and in shared memory.
+      const int per4 = per >> 1;  // float4 = two entries (s is a multiple of 4)
+      for (int blk = 0; blk < nblk; ++blk) {
+        const float4* src = (const float4*)((const float2*)(blk < a ? g.L.p[blk] : g.R.p[blk - a]) +
+                                            r0 * s);
+        float4* dst = (float4*)(smf + (size_t)blk * rc * sp);
+        for (int i = threadIdx.x; i < per4; i += GDF_THREADS) dst[i] = src[i];
+      }
+    } else {
+      for (int idx = threadIdx.x; idx < nblk * per; idx += GDF_THREADS) {
+        const int blk = idx / per, off = idx - blk * per;
+        const int r = off / s, c = off - r * s;
+        const float2* src = (const float2*)(blk < a ? g.L.p[blk] : g.R.p[blk - a]);
+        smf[(blk * rc + r) * sp + c] = src[r0 * s + off];
+      }
     }
     __syncthreads();
     if (active) {
@@ -419,6 +430,95 @@ __global__ void __launch_bounds__(256) k_update_df(const __grid_constant__ UpdDf
   }
 }
 
+// One thread per row (s = 4, 8, 16): the row of every input block is loaded
+// with 16-byte loads into registers, the coefficients (identical for all rows)
+// are broadcast from shared memory, and both outputs accumulate in registers.
+template <int S, bool TWO>
+__global__ void __launch_bounds__(256) k_update_df_row(const __grid_constant__ UpdDfArgs u) {
+  if (u.step >= 0 && *(volatile const int*)&u.ctl->update_step != u.step) return;
+  extern __shared__ float2 cs[];
+  const int nin = u.nin;
+  constexpr int SS = S * S;
+  const int total = (int)coef_df_count(nin, S, TWO);
+  for (int e = threadIdx.x; e < total; e += blockDim.x) cs[e] = u.cdf[e];
+  __syncthreads();
+  const float2* c1 = cs;
+  const float2* c2 = c1 + (size_t)nin * SS;
+  const float2* ch = c2 + (TWO ? (size_t)nin * SS : 0);
+  const float2* t1 = ch + SS;
+  const float2* t2 = t1 + SS;
+  const float2* r1 = t2 + SS;
+  const float2* r2 = r1 + S;
+  for (int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; row < u.n;
+       row += (int64_t)gridDim.x * blockDim.x) {
+    dfacc a1[S], a2[S];
+#pragma unroll
+    for (int c = 0; c < S; ++c) {
+      a1[c] = dfacc{0.f, 0.f};
+      a2[c] = dfacc{0.f, 0.f};
+    }
+    for (int bk = 0; bk < nin; ++bk) {
+      float2 v[S];
+      const float4* src = (const float4*)((const float2*)u.in.p[bk] + row * S);
+#pragma unroll
+      for (int i = 0; i < S / 2; ++i) {
+        const float4 t = src[i];
+        v[2 * i] = make_float2(t.x, t.y);
+        v[2 * i + 1] = make_float2(t.z, t.w);
+      }
+      const float2* k1 = c1 + (size_t)bk * SS;
+      const float2* k2 = c2 + (size_t)bk * SS;
+#pragma unroll
+      for (int q = 0; q < S; ++q) {
+#pragma unroll
+        for (int c = 0; c < S; ++c) {
+          df_fma(a1[c], v[q], k1[q * S + c]);
+          if (TWO) df_fma(a2[c], v[q], k2[q * S + c]);
+        }
+      }
+    }
+    float2 o1[S];
+    if (u.has_tri1) {
+      // o1 = a1 T1^{-1}: forward substitution over the columns.
+#pragma unroll
+      for (int c = 0; c < S; ++c) {
+#pragma unroll
+        for (int q = 0; q < c; ++q) df_fms(a1[c], o1[q], t1[q * S + c]);
+        o1[c] = df_mul(df_value(a1[c]), r1[c]);
+      }
+    } else {
+#pragma unroll
+      for (int c = 0; c < S; ++c) o1[c] = df_value(a1[c]);
+    }
+    float4* d1 = (float4*)(u.out1 + row * S);
+#pragma unroll
+    for (int i = 0; i < S / 2; ++i) d1[i] = make_float4(o1[2 * i].x, o1[2 * i].y, o1[2 * i + 1].x, o1[2 * i + 1].y);
+    if (TWO) {
+      if (u.has_chain) {
+#pragma unroll
+        for (int q = 0; q < S; ++q)
+#pragma unroll
+          for (int c = 0; c < S; ++c) df_fma(a2[c], o1[q], ch[q * S + c]);
+      }
+      float2 o2[S];
+      if (u.has_tri2) {
+#pragma unroll
+        for (int c = 0; c < S; ++c) {
+#pragma unroll
+          for (int q = 0; q < c; ++q) df_fms(a2[c], o2[q], t2[q * S + c]);
+          o2[c] = df_mul(df_value(a2[c]), r2[c]);
+        }
+      } else {
+#pragma unroll
+        for (int c = 0; c < S; ++c) o2[c] = df_value(a2[c]);
+      }
+      float4* d2 = (float4*)(u.out2 + row * S);
+#pragma unroll
+      for (int i = 0; i < S / 2; ++i) d2[i] = make_float4(o2[2 * i].x, o2[2 * i].y, o2[2 * i + 1].x, o2[2 * i + 1].y);
+    }
+  }
+}
+
 size_t update_df_smem(int nin, int s, bool two) { return sizeof(float2) * coef_df_count(nin, s, two); }
 
 void launch_update_df(cudaStream_t st, const BlockPtrs& in, int nin, int64_t n, int s, float2* out1,
@@ -458,7 +558,27 @@ void launch_update_df(cudaStream_t st, const BlockPtrs& in, int nin, int64_t n, 
   static bool attr_set = false;
   if (!attr_set) {
     cudaFuncSetAttribute(k_update_df, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_update_df_row<4, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_update_df_row<4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_update_df_row<8, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_update_df_row<8, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_update_df_row<16, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_update_df_row<16, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     attr_set = true;
+  }
+  if (s == 4 || s == 8 || s == 16) {
+    int64_t need = (n + 255) / 256;
+    int64_t grid = 4LL * num_sms;
+    if (grid > need) grid = need;
+    if (grid < 1) grid = 1;
+#define LAUNCH_ROW(SV)                                                        \
+    if (two) k_update_df_row<SV, true><<<(unsigned)grid, 256, smem, st>>>(u); \
+    else k_update_df_row<SV, false><<<(unsigned)grid, 256, smem, st>>>(u);
+    if (s == 4) { LAUNCH_ROW(4) }
+    else if (s == 8) { LAUNCH_ROW(8) }
+    else { LAUNCH_ROW(16) }
+#undef LAUNCH_ROW
+    return;
   }
   const int rows_per_cta = 256 / u.S2;
   const int64_t need = (n + rows_per_cta - 1) / rows_per_cta;

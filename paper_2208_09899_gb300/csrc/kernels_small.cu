@@ -544,8 +544,12 @@ __device__ void step_pip(const SmallWs& w, int k, Shared& sh) {
   put_coef(w.coef1, k, s, nullptr, 0, 1.0);
   put_tri(w.tri1, sh.R, s);
   __syncthreads();
-  if (threadIdx.x == 0) w.ctl->update_step = k;
-  relation_complete(w, k, sh);
+  if (threadIdx.x == 0) {
+    w.ctl->update_step = k;
+    w.ctl->side_step = k;
+    w.ctl->side_rel = k;
+    w.ctl->side_J = 0;
+  }
 }
 
 __device__ void step_bcgs(const SmallWs& w, int k, int phase, Shared& sh) {
@@ -578,8 +582,12 @@ __device__ void step_bcgs(const SmallWs& w, int k, int phase, Shared& sh) {
   put_coef(w.coef1, 0, s, nullptr, 0, 1.0);
   put_tri(w.tri1, sh.R, s);
   __syncthreads();
-  if (threadIdx.x == 0) w.ctl->update_step = k;
-  relation_complete(w, k, sh);
+  if (threadIdx.x == 0) {
+    w.ctl->update_step = k;
+    w.ctl->side_step = k;
+    w.ctl->side_rel = k;
+    w.ctl->side_J = 0;
+  }
 }
 
 // Lagged skeletons, iteration k = 1: H_{1,1} = <U, W> (= J), U <- W - V_1 H_{1,1}.
@@ -678,8 +686,12 @@ __device__ void step_cwy(const SmallWs& w, int k, bool inverse, Shared& sh) {
   put_coef(w.chain, 0, s, ZP + k1s, ks, -1.0);
   put_tri(w.tri1, sh.R, s);
   __syncthreads();
-  if (threadIdx.x == 0) w.ctl->update_step = k;
-  relation_complete(w, k - 1, sh);
+  if (threadIdx.x == 0) {
+    w.ctl->update_step = k;
+    w.ctl->side_step = k;
+    w.ctl->side_rel = k - 1;
+    w.ctl->side_J = 0;
+  }
 }
 
 // BCGSI+LS iteration k >= 2 (Alg. 7).  Inputs [V_1..V_{k-1}, U, W]; out1 = V_k, out2 = U.
@@ -724,13 +736,16 @@ __device__ void step_ls(const SmallWs& w, int k, Shared& sh) {
   }
   __syncthreads();
   cta_trsm_left_T(sh.R, s, ZP + k1s, ks, s);
-  // J = ([Z; P] - H_{1:k,1:k-1} Y) R^{-1}.  Y as a (k-1)s x s col-major matrix is
-  // G^T-indexed: Y(i,c) = G[i*cols + c]  -> pass as op(B) with tb = true, ldb = cols.
-  cta_gemm(ks, s, k1s, -1.0, w.H, ldH, false, G, cols, true, 0.0, tmp, ks);
-  for (int e = threadIdx.x; e < ks * s; e += NT) tmp[e] += ZP[e];
-  __syncthreads();
-  cta_trsm_right(tmp, ks, ks, sh.R, s);
-  cta_copy(w.J, ldH, tmp, ks, ks, s);
+  // J = ([Z; P] - H_{1:k,1:k-1} Y) R^{-1} is needed only by the next iteration:
+  // keep [Z; P], Y and R for the side kernel, which computes it off the
+  // critical path.
+  for (int e = threadIdx.x; e < ks * s; e += NT) w.saveZP[e] = ZP[e];
+  for (int e = threadIdx.x; e < k1s * s; e += NT) {
+    const int i = e % k1s, c = e / k1s;
+    w.saveY[i + c * k1s] = G[i * cols + c];
+  }
+  for (int e = threadIdx.x; e < s * s; e += NT) w.saveR[e] = sh.R[e];
+  (void)tmp;
   // out1 = V_k = (U - V_{1:k-1} Y) R^{-1};  out2 = (W - V_{1:k-1} Z - V_k P) R^{-1}
   for (int b = 0; b < k - 1; ++b) {
     double* c1 = w.coef1 + (size_t)b * s * s;
@@ -749,8 +764,12 @@ __device__ void step_ls(const SmallWs& w, int k, Shared& sh) {
   put_tri(w.tri1, sh.R, s);
   put_tri(w.tri2, sh.R, s);
   __syncthreads();
-  if (threadIdx.x == 0) w.ctl->update_step = k;
-  relation_complete(w, k - 1, sh);
+  if (threadIdx.x == 0) {
+    w.ctl->update_step = k;
+    w.ctl->side_step = k;
+    w.ctl->side_rel = k - 1;
+    w.ctl->side_J = 1;
+  }
 }
 
 __global__ void __launch_bounds__(NT) k_small_step(SmallWs w, int k, int phase) {
@@ -758,6 +777,7 @@ __global__ void __launch_bounds__(NT) k_small_step(SmallWs w, int k, int phase) 
   if (!*(volatile int*)&w.ctl->active) return;
   if (threadIdx.x == 0) {
     w.ctl->update_step = -1;
+    w.ctl->side_step = -1;
     w.ctl->k = k;
   }
   __syncthreads();
@@ -774,6 +794,41 @@ __global__ void __launch_bounds__(NT) k_small_step(SmallWs w, int k, int phase) 
       else step_ls(w, k, sh);
       break;
   }
+}
+
+// ---------------------------------------------------------------- side kernel
+// Work of loop iteration k that the next iteration's bandwidth kernels do not
+// wait for, run on a second stream while they execute:
+//   * BCGSI+LS: J = ([Z; P] - H_{1:k,1:k-1} Y) R^{-1} (Alg. 7 line 15), read only by
+//     iteration k+1's small kernel.  H_{1:k,1:k-1} is block upper Hessenberg, so
+//     row block i only meets column blocks >= i-1.
+//   * the relation that iteration k completed: incremental least squares,
+//     residual estimate (Eq. (9)), convergence and the basis-size limit.
+__global__ void __launch_bounds__(NT) k_small_side(SmallWs w, int k) {
+  __shared__ Shared sh;
+  Ctl* ctl = w.ctl;
+  if (*(volatile int*)&ctl->side_step != k) return;
+  const int s = w.s, ldH = w.ldH;
+  if (ctl->side_J) {
+    const int ks = k * s, k1s = (k - 1) * s;
+    double* tmp = w.work + 4 * (size_t)w.ldH * s;   // ks x s (clear of the relation scratch)
+    for (int e = threadIdx.x; e < ks * s; e += NT) {
+      const int r = e % ks, c = e / ks;
+      const int q0 = max(0, (r / s - 1) * s);
+      double a0 = 0.0, a1 = 0.0;
+      int q = q0;
+      for (; q + 1 < k1s; q += 2) {
+        a0 = fma(w.H[r + (size_t)q * ldH], w.saveY[q + c * k1s], a0);
+        a1 = fma(w.H[r + (size_t)(q + 1) * ldH], w.saveY[q + 1 + c * k1s], a1);
+      }
+      if (q < k1s) a0 = fma(w.H[r + (size_t)q * ldH], w.saveY[q + c * k1s], a0);
+      tmp[r + c * ks] = w.saveZP[r + c * ks] - (a0 + a1);
+    }
+    cta_copy(sh.R, s, w.saveR, s, s, s);
+    cta_trsm_right(tmp, ks, ks, sh.R, s);
+    cta_copy(w.J, ldH, tmp, ks, ks, s);
+  }
+  relation_complete(w, ctl->side_rel, sh);
 }
 
 // ---------------------------------------------------------------- cycle end
@@ -879,6 +934,9 @@ void launch_true_relres(cudaStream_t st, const double* G, int s, Ctl* ctl) {
 }
 void launch_small_step(cudaStream_t st, const SmallWs& w, int k, int phase) {
   k_small_step<<<1, NT, 0, st>>>(w, k, phase);
+}
+void launch_small_side(cudaStream_t st, const SmallWs& w, int k) {
+  k_small_side<<<1, NT, 0, st>>>(w, k);
 }
 void launch_small_end(cudaStream_t st, const SmallWs& w) {
   k_small_end<<<1, NT, 0, st>>>(w);

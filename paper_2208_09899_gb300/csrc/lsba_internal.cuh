@@ -38,6 +38,10 @@ struct Ctl {
   double normB;        // ||B||_F
   double tol;
   double relres_true;
+  int side_step;       // loop index whose side kernel must run (-1: none)
+  int side_rel;        // relation the side kernel completes
+  int side_J;          // side kernel also forms J (BCGSI+LS)
+  int pad2;
 };
 
 // Pointers of up to LSBA_MAXB blocks (each n x s, row-major, FP64).
@@ -72,7 +76,10 @@ struct SmallWs {
   double* Bcyc;        // s x s col-major: CholQR factor of the cycle's start block
   double* Xi;          // (m+1)s x s col-major
   double* Mvec;        // (m+1)s x s col-major
-  double* work;        // scratch, >= 4*(m+2)s*s + 8*s*s doubles
+  double* work;        // scratch, >= 6*(m+2)s*s + 16*s*s doubles
+  double* saveZP;      // BCGSI+LS: [Z; P] of the last iteration, (m+1)s x s
+  double* saveY;       // BCGSI+LS: Y of the last iteration, (m+1)s x s
+  double* saveR;       // BCGSI+LS: R = H_{k,k-1} of the last iteration, s x s
   double* hist_est;    // [hist_cap]
   int* hist_cycle;
   int* hist_j;
@@ -127,6 +134,7 @@ void launch_update_df(cudaStream_t st, const BlockPtrs& in, int nin, int64_t n, 
 void launch_small_start(cudaStream_t st, const SmallWs& w, int flags);
 void launch_true_relres(cudaStream_t st, const double* G, int s, Ctl* ctl);
 void launch_small_step(cudaStream_t st, const SmallWs& w, int k, int phase);
+void launch_small_side(cudaStream_t st, const SmallWs& w, int k);
 void launch_small_end(cudaStream_t st, const SmallWs& w);
 
 }  // namespace lsba
