@@ -317,7 +317,8 @@ static void do_gram(lsba_ctx* h, const BlockPtrs& L, int a, const BlockPtrs& R, 
   prof_begin(h, LSBA_K_GRAM);
   if (h->df) {
     GramPlan p = plan_gram_df(n, s, a, b, h->num_sms);
-    launch_gram_df(h->stream, p, L, a, R, b, n, s, (float2*)h->partials, h->Gbuf, ctl, guard);
+    launch_gram_df(h->stream, p, L, a, R, b, n, s, (float2*)h->partials, h->Gbuf, ctl, guard,
+                   &h->d_ctl->error);
   } else {
     GramPlan p = plan_gram(n, s, a, b, h->num_sms);
     launch_gram(h->stream, p, L, a, R, b, n, s, h->partials, h->Gbuf, ctl, guard);
@@ -649,6 +650,7 @@ static int solve_impl(lsba_handle h, const lsba_csr* A, const double* d_B, doubl
     enqueue_cycle(h, A, Rstart, n, s, m_cur, start_flags);
     CK(cudaGetLastError());
     if ((rc = pull_ctl(h)) != LSBA_OK) return S.status = rc;
+    if (c->error) return S.status = LSBA_DEVICE_TIMEOUT;
     S.syncs += 1;
     if (c->start_flag) {
       status = (cycle == 1) ? LSBA_BREAKDOWN : LSBA_NOT_CONVERGED;

@@ -228,6 +228,195 @@ __global__ void __launch_bounds__(GDF_THREADS) k_gram_df(const __grid_constant__
   }
 }
 
+// ---- Gram with asynchronous bulk copies (s a multiple of 4) ----------------
+// The same computation as k_gram_df, but each chunk of rows is brought into
+// shared memory by one-dimensional bulk copies (cp.async.bulk, the TMA engine)
+// that complete on an mbarrier, two chunks in flight: the copy of chunk c+2
+// overlaps the arithmetic on chunk c+1.  Every wait on an mbarrier is bounded;
+// on a timeout the CTA records an error in *err, waits (bounded) for its own
+// copies, and returns.
+#define TMA_WAIT_LIMIT (1u << 22)
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, unsigned bytes,
+                                              uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}" : "=r"(ok) : "r"(smem_addr(bar)), "r"(parity) : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity) {
+  for (unsigned it = 0; it < TMA_WAIT_LIMIT; ++it)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
+struct GramTmaArgs {
+  BlockPtrs L;
+  BlockPtrs R;
+  int a, b, s, rc;
+  int64_t n, rows_per_cta;
+  int q, ntj, ntile;
+  unsigned stage_elems;   // float2 per stage = (a+b) * rc * s
+  float2* partials;
+  const Ctl* ctl;
+  int guard;
+  int* err;
+};
+
+__global__ void __launch_bounds__(GDF_THREADS) k_gram_df_tma(const __grid_constant__ GramTmaArgs g) {
+  if (g.guard && !ctl_active_df(g.ctl)) return;
+  extern __shared__ __align__(128) unsigned char smraw[];
+  uint64_t* bars = (uint64_t*)smraw;
+  float2* stage0 = (float2*)(smraw + 128);
+  float2* stage1 = stage0 + g.stage_elems;
+  const int s = g.s, rc = g.rc, a = g.a, b = g.b;
+  const int nblk = a + b;
+  const int tile_base = blockIdx.y * GDF_THREADS;
+  const int cnt = min(GDF_THREADS, g.ntile - tile_base);
+  const int groups = GDF_THREADS / cnt;
+  const int grp = threadIdx.x / cnt;
+  const int tl = threadIdx.x % cnt;
+  const bool active = grp < groups;
+  const int T = tile_base + tl;
+  const int it = T / g.ntj, jt = T % g.ntj;
+  const int li = it * 4, rj = jt * 4;
+  const int lofs = (li / s) * rc * s + (li % s);
+  const int rofs = (a + rj / s) * rc * s + (rj % s);
+  const int64_t r_begin = (int64_t)blockIdx.x * g.rows_per_cta;
+  const int64_t r_end = min(g.n, r_begin + g.rows_per_cta);
+  const int nchunks = r_end > r_begin ? (int)((r_end - r_begin + rc - 1) / rc) : 0;
+
+  if (threadIdx.x == 0) {
+    mbar_init(&bars[0], 1);
+    mbar_init(&bars[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  auto issue = [&](int c, int st) {
+    const int64_t r0 = r_begin + (int64_t)c * rc;
+    const int rows = (int)min((int64_t)rc, r_end - r0);
+    const unsigned bytes = (unsigned)(rows * s * sizeof(float2));
+    float2* dst = st ? stage1 : stage0;
+    mbar_expect_tx(&bars[st], bytes * nblk);
+    for (int blk = 0; blk < nblk; ++blk) {
+      const float2* src = (const float2*)(blk < a ? g.L.p[blk] : g.R.p[blk - a]) + r0 * s;
+      bulk_copy_g2s(dst + (size_t)blk * rc * s, src, bytes, &bars[st]);
+    }
+  };
+  if (threadIdx.x == 0) {
+    if (nchunks > 0) issue(0, 0);
+    if (nchunks > 1) issue(1, 1);
+  }
+
+  dfacc acc[4][4];
+#pragma unroll
+  for (int x = 0; x < 4; ++x)
+#pragma unroll
+    for (int y = 0; y < 4; ++y) acc[x][y] = dfacc{0.f, 0.f};
+
+  bool failed = false;
+  for (int c = 0; c < nchunks; ++c) {
+    const int st = c & 1;
+    const unsigned parity = (unsigned)((c >> 1) & 1);
+    const bool ok = mbar_wait_bounded(&bars[st], parity);
+    if (__syncthreads_or(!ok)) {
+      failed = true;
+      break;
+    }
+    const float2* buf = st ? stage1 : stage0;
+    const int rows = (int)min((int64_t)rc, r_end - (r_begin + (int64_t)c * rc));
+    if (active) {
+      for (int r = grp; r < rows; r += groups) {
+        const float4* lp = (const float4*)(buf + lofs + r * s);
+        const float4* rp = (const float4*)(buf + rofs + r * s);
+        const float4 l01 = lp[0], l23 = lp[1], r01 = rp[0], r23 = rp[1];
+        const float2 lv[4] = {make_float2(l01.x, l01.y), make_float2(l01.z, l01.w),
+                              make_float2(l23.x, l23.y), make_float2(l23.z, l23.w)};
+        const float2 rv[4] = {make_float2(r01.x, r01.y), make_float2(r01.z, r01.w),
+                              make_float2(r23.x, r23.y), make_float2(r23.z, r23.w)};
+#pragma unroll
+        for (int x = 0; x < 4; ++x)
+#pragma unroll
+          for (int y = 0; y < 4; ++y) df_fma(acc[x][y], lv[x], rv[y]);
+      }
+#pragma unroll
+      for (int x = 0; x < 4; ++x)
+#pragma unroll
+        for (int y = 0; y < 4; ++y) df_renorm(acc[x][y]);
+    }
+    __syncthreads();  // every thread is done reading this stage
+    if (threadIdx.x == 0 && c + 2 < nchunks) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      issue(c + 2, st);
+    }
+  }
+  if (failed) {
+    if (threadIdx.x == 0) {
+      if (g.err) atomicExch(g.err, 1);
+      // Let this CTA's copies in flight land before the shared memory goes away.
+      for (int c2 = 0; c2 < 2; ++c2) mbar_wait_bounded(&bars[c2], 0), mbar_wait_bounded(&bars[c2], 1);
+    }
+    __syncthreads();
+    return;
+  }
+  if (groups > 1) {
+    __syncthreads();
+    float2* red = stage0;  // [groups][cnt][16], all copies have landed
+    if (active) {
+#pragma unroll
+      for (int x = 0; x < 4; ++x)
+#pragma unroll
+        for (int y = 0; y < 4; ++y)
+          red[((size_t)grp * cnt + tl) * 16 + x * 4 + y] = make_float2(acc[x][y].s, acc[x][y].c);
+    }
+    __syncthreads();
+    if (grp == 0) {
+      for (int g2 = 1; g2 < groups; ++g2) {
+#pragma unroll
+        for (int x = 0; x < 4; ++x)
+#pragma unroll
+          for (int y = 0; y < 4; ++y) {
+            const float2 v = red[((size_t)g2 * cnt + tl) * 16 + x * 4 + y];
+            df_add_to(acc[x][y], make_float2(v.x, 0.f));
+            df_add_to(acc[x][y], make_float2(v.y, 0.f));
+          }
+      }
+    }
+  }
+  if (grp == 0) {
+    const int bs = b * s;
+#pragma unroll
+    for (int x = 0; x < 4; ++x) {
+      const int i = li + x;
+#pragma unroll
+      for (int y = 0; y < 4; ++y) {
+        const int j = rj + y;
+        g.partials[(int64_t)blockIdx.x * g.q + (int64_t)i * bs + j] = df_value(acc[x][y]);
+      }
+    }
+  }
+}
+
 __global__ void k_gram_reduce_df(const float2* __restrict__ partials, int nparts, int q,
                                  double* __restrict__ G, const Ctl* ctl, int guard) {
   if (guard && !ctl_active_df(ctl)) return;
@@ -246,13 +435,26 @@ GramPlan plan_gram_df(int64_t n, int s, int a, int b, int num_sms) {
   p.tile = GDF_THREADS;
   p.grid_y = (ntile + GDF_THREADS - 1) / GDF_THREADS;
   const size_t row_bytes = (size_t)(a + b) * sp * sizeof(float2);
-  int rc = (int)((80 * 1024) / row_bytes);
-  if (rc > 128) rc = 128;
-  if (rc < 1) rc = 1;
+  const size_t red_bytes = (size_t)GDF_THREADS * 16 * sizeof(float2);
+  int rc;
+  int ctas_per_sm;
+  if (sp == s) {
+    // Two pipeline stages of <= 32 KB each: three CTAs per SM.
+    rc = (int)((32 * 1024) / row_bytes);
+    if (rc > 128) rc = 128;
+    if (rc < 1) rc = 1;
+    const size_t stages = 128 + 2 * row_bytes * rc;
+    p.smem = stages > 128 + red_bytes ? stages : 128 + red_bytes;
+    ctas_per_sm = 3;
+  } else {
+    rc = (int)((80 * 1024) / row_bytes);
+    if (rc > 128) rc = 128;
+    if (rc < 1) rc = 1;
+    p.smem = row_bytes * rc > red_bytes ? row_bytes * rc : red_bytes;
+    ctas_per_sm = 2;
+  }
   p.rows_per_chunk = rc;
-  size_t red_bytes = (size_t)GDF_THREADS * 16 * sizeof(float2);
-  p.smem = row_bytes * rc > red_bytes ? row_bytes * rc : red_bytes;
-  int gx = (2 * num_sms + p.grid_y - 1) / p.grid_y;
+  int gx = (ctas_per_sm * num_sms + p.grid_y - 1) / p.grid_y;
   const int64_t max_gx = (n + rc - 1) / rc;
   if (gx > max_gx) gx = (int)max_gx;
   if (gx < 1) gx = 1;
@@ -268,30 +470,53 @@ GramPlan plan_gram_df(int64_t n, int s, int a, int b, int num_sms) {
 
 void launch_gram_df(cudaStream_t st, const GramPlan& p, const BlockPtrs& L, int a,
                     const BlockPtrs& R, int b, int64_t n, int s, float2* partials, double* G,
-                    const Ctl* ctl, int guard) {
-  GramDfArgs g;
-  g.L = L;
-  g.R = R;
-  g.a = a;
-  g.b = b;
-  g.s = s;
-  g.sp = (s + 3) & ~3;
-  g.rc = p.rows_per_chunk;
-  g.n = n;
-  g.rows_per_cta = p.rows_per_cta;
-  g.q = p.q;
-  g.ntj = b * g.sp / 4;
-  g.ntile = (a * g.sp / 4) * g.ntj;
-  g.partials = partials;
-  g.ctl = ctl;
-  g.guard = guard;
+                    const Ctl* ctl, int guard, int* err) {
   static bool attr_set = false;
   if (!attr_set) {
     cudaFuncSetAttribute(k_gram_df, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_gram_df_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     attr_set = true;
   }
   dim3 grid(p.grid_x, p.grid_y);
-  k_gram_df<<<grid, GDF_THREADS, p.smem, st>>>(g);
+  const int sp = (s + 3) & ~3;
+  if (sp == s) {
+    GramTmaArgs g;
+    g.L = L;
+    g.R = R;
+    g.a = a;
+    g.b = b;
+    g.s = s;
+    g.rc = p.rows_per_chunk;
+    g.n = n;
+    g.rows_per_cta = p.rows_per_cta;
+    g.q = p.q;
+    g.ntj = b * s / 4;
+    g.ntile = (a * s / 4) * g.ntj;
+    g.stage_elems = (unsigned)((a + b) * p.rows_per_chunk * s);
+    g.partials = partials;
+    g.ctl = ctl;
+    g.guard = guard;
+    g.err = err;
+    k_gram_df_tma<<<grid, GDF_THREADS, p.smem, st>>>(g);
+  } else {
+    GramDfArgs g;
+    g.L = L;
+    g.R = R;
+    g.a = a;
+    g.b = b;
+    g.s = s;
+    g.sp = sp;
+    g.rc = p.rows_per_chunk;
+    g.n = n;
+    g.rows_per_cta = p.rows_per_cta;
+    g.q = p.q;
+    g.ntj = b * g.sp / 4;
+    g.ntile = (a * g.sp / 4) * g.ntj;
+    g.partials = partials;
+    g.ctl = ctl;
+    g.guard = guard;
+    k_gram_df<<<grid, GDF_THREADS, p.smem, st>>>(g);
+  }
   k_gram_reduce_df<<<(p.q + 255) / 256, 256, 0, st>>>(partials, p.grid_x, p.q, G, ctl, guard);
 }
 

@@ -725,7 +725,6 @@ __device__ void step_ls(const SmallWs& w, int k, Shared& sh) {
   // P = R^{-T} (P~ - Y^T Z):  sh.B = Y^T Z  (Y^T as col-major (s x k1s) from G, Z likewise)
   cta_gemm(s, s, k1s, 1.0, G, cols, false, G + s, cols, true, 0.0, sh.B, s);
   double* ZP = w.work;                // ks x s, ld ks
-  double* tmp = w.work + ks * s;      // ks x s
   for (int e = threadIdx.x; e < s * s; e += NT) {
     const int a = e % s, c = e / s;
     ZP[k1s + a + c * ks] = G[(k1s + a) * cols + s + c] - sh.B[a + c * s];
@@ -745,7 +744,6 @@ __device__ void step_ls(const SmallWs& w, int k, Shared& sh) {
     w.saveY[i + c * k1s] = G[i * cols + c];
   }
   for (int e = threadIdx.x; e < s * s; e += NT) w.saveR[e] = sh.R[e];
-  (void)tmp;
   // out1 = V_k = (U - V_{1:k-1} Y) R^{-1};  out2 = (W - V_{1:k-1} Z - V_k P) R^{-1}
   for (int b = 0; b < k - 1; ++b) {
     double* c1 = w.coef1 + (size_t)b * s * s;

@@ -41,7 +41,7 @@ struct Ctl {
   int side_step;       // loop index whose side kernel must run (-1: none)
   int side_rel;        // relation the side kernel completes
   int side_J;          // side kernel also forms J (BCGSI+LS)
-  int pad2;
+  int error;           // a bounded device wait gave up (LSBA_DEVICE_TIMEOUT)
 };
 
 // Pointers of up to LSBA_MAXB blocks (each n x s, row-major, FP64).
@@ -122,7 +122,7 @@ void launch_spmm_df(cudaStream_t st, int64_t n, const int32_t* rowptr, const int
 GramPlan plan_gram_df(int64_t n, int s, int a, int b, int num_sms);
 void launch_gram_df(cudaStream_t st, const GramPlan& p, const BlockPtrs& L, int a,
                     const BlockPtrs& R, int b, int64_t n, int s, float2* partials, double* G,
-                    const Ctl* ctl, int guard);
+                    const Ctl* ctl, int guard, int* err);
 __host__ __device__ size_t coef_df_count(int nin, int s, bool two);
 size_t update_df_smem(int nin, int s, bool two);
 void launch_update_df(cudaStream_t st, const BlockPtrs& in, int nin, int64_t n, int s, float2* out1,
