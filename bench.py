@@ -154,6 +154,68 @@ def blas_threads():
     return os.cpu_count()
 
 
+def _timed(torch, stream, fn, reps):
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(reps):
+        fn()
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / reps
+
+
+def mixed_precision(torch, lsba, dev, stream):
+    """FP32 inner solver inside FP64 iterative refinement vs the FP64-accurate
+    paths on the same GPU.
+      * per restart cycle on the 2D Laplacian 2048x2048 (n = 4194304), B n x 16,
+        BGMRES(16), BCGSI+LS: one FP32 inner cycle (plus the two FP64 residuals
+        of its refinement step) vs one double-float and one FP64 cycle;
+      * time to relative residual 1e-10 on the 2D Laplacian 256x256, B n x 16,
+        BGMRES(16), BCGSI+LS, in the three precisions."""
+    out = {}
+    A, B = W.workload("lapl2048_s16", 0)
+    n, s = B.shape
+    dA = lsba.DeviceCSR.from_host(A, f"cuda:{dev}")
+    dB = torch.from_numpy(B).to(f"cuda:{dev}")
+    dX = torch.empty_like(dB)
+    cyc = {}
+    for prec, reps in (("fp32_ir", 3), ("df", 2), ("fp64", 1)):
+        extra = {"ir_max_outer": 1} if prec == "fp32_ir" else {}
+        sv = lsba.Solver(dev, modification="gmres", max_restarts=0, verify_true_residual=0,
+                         precision=prec, **extra)
+        sv.solve(dA, dB, dX, 16, 1e-30, SKELETON)
+        cyc[prec] = _timed(torch, stream, lambda: sv.solve(dA, dB, dX, 16, 1e-30, SKELETON), reps)
+        sv.close()
+    by, _ = algorithmic_cost(n, A.nnz, s, 16)
+    out["cycle"] = {"workload": "lapl2048_s16: 2D Laplacian 2048x2048 (n=4194304), B n x 16 N(0,1),"
+                                " BGMRES(16), BCGSI+LS, one restart cycle",
+                    "ms": cyc, "speedup_fp32_ir_vs_df": cyc["df"] / cyc["fp32_ir"],
+                    "speedup_fp32_ir_vs_fp64": cyc["fp64"] / cyc["fp32_ir"],
+                    "fp32_inner_gbs_algorithmic": 0.5 * sum(by.values()) / (cyc["fp32_ir"] * 1e-3) / 1e9}
+    del dA, dB, dX
+    A = W.laplacian_2d(256)
+    B = W.gaussian_block(A.n, 16, 0)
+    dA = lsba.DeviceCSR.from_host(A, f"cuda:{dev}")
+    dB = torch.from_numpy(B).to(f"cuda:{dev}")
+    dX = torch.empty_like(dB)
+    tt = {}
+    for prec in ("fp32_ir", "df", "fp64"):
+        sv = lsba.Solver(dev, modification="gmres", max_restarts=5000, precision=prec)
+        ms = _timed(torch, stream, lambda: sv.solve(dA, dB, dX, 16, 1e-10, SKELETON), 1)
+        st = sv.stats()
+        tt[prec] = {"ms": ms, "cycles": st["cycles"], "relres_true": st["relres_true"],
+                    "status": st["status"], "ir_outer": st["ir_outer"]}
+        sv.close()
+    out["time_to_1e-10"] = {"workload": "lapl256_s16: 2D Laplacian 256x256 (n=65536), B n x 16 "
+                                        "N(0,1), BGMRES(16), BCGSI+LS, tol 1e-10",
+                            "results": tt,
+                            "speedup_fp32_ir_vs_df": tt["df"]["ms"] / tt["fp32_ir"]["ms"],
+                            "speedup_fp32_ir_vs_fp64": tt["fp64"]["ms"] / tt["fp32_ir"]["ms"]}
+    return out
+
+
 def dist_setup():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -197,6 +259,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     world, rank, local = dist_setup()
@@ -347,6 +410,8 @@ def main():
                    "ms": statistics.median(tts), "cycles": st1["cycles"], "steps": st1["steps"],
                    "relres_true": st1["relres_true"], "status": st1["status"]}
 
+    mixed = None if args.no_mixed else mixed_precision(torch, lsba, dev, stream)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         t_or = oracle_cycle_seconds(A, B, M)
@@ -375,7 +440,7 @@ def main():
                        "algorithmic_bytes_per_step": step_bytes},
             "roofline": roofline, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": gpu_launches, "clocks": clocks, "time_to_tol": time_to_tol,
-            "fp64_plain": fp64_plain,
+            "fp64_plain": fp64_plain, "mixed_precision": mixed,
         }
         print(json.dumps(line))
     if pg:

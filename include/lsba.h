@@ -94,11 +94,18 @@ typedef struct {
                                     amplifies the 2^-48 representation error.  The
                                     small s x s / ks x s kernels are FP64 in all modes.
                                     DF needs 8*(2(m+3)+3)s^2 bytes of shared memory
-                                    <= 200 KB; larger (m, s) run in FP64.            */
-  int32_t reserved[6];
+                                    <= 200 KB; larger (m, s) run in FP64.
+                                    LSBA_PREC_FP32_IR: FP64 iterative refinement
+                                    (residual B - A X and X += D in FP64) around an
+                                    FP32 inner solve of A D = R (FP32 SpMM, Gram and
+                                    update with FP32 accumulation; FP64 Cholesky and
+                                    least squares); s must be 4, 8 or 16.            */
+  int32_t ir_max_outer;          /* FP32_IR: at most this many refinement steps (10)   */
+  double ir_inner_tol;           /* FP32_IR: relative residual of each inner solve (1e-5) */
+  int32_t reserved[4];
 } lsba_options;
 
-enum { LSBA_PREC_FP64 = 0, LSBA_PREC_DF = 1, LSBA_PREC_AUTO = 2 };
+enum { LSBA_PREC_FP64 = 0, LSBA_PREC_DF = 1, LSBA_PREC_AUTO = 2, LSBA_PREC_FP32_IR = 3 };
 
 /* Counters and outcome of the last lsba_solve. */
 typedef struct {
@@ -114,7 +121,7 @@ typedef struct {
   double relres_true;      /* ||B - A X||_F / ||B||_F (NaN if not computed)       */
   double solve_ms;         /* wall time of lsba_solve                            */
   int32_t precision;       /* precision the solve ran in (LSBA_PREC_*)           */
-  int32_t pad;
+  int32_t ir_outer;        /* FP32_IR: refinement steps (inner solves) taken     */
 } lsba_stats;
 
 /* Host-side copies kept by the handle when record_history = 1; valid until the

@@ -16,7 +16,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "liblsba.so")
-SOURCES = ["engine.cu", "kernels_big.cu", "kernels_small.cu", "kernels_df.cu", "noalloc.cu"]
+SOURCES = ["engine.cu", "kernels_big.cu", "kernels_small.cu", "kernels_df.cu", "kernels_f32.cu",
+           "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -45,6 +46,7 @@ def build(force: bool = False, verbose_ptxas: bool = False) -> str:
     os.makedirs(OUT_DIR, exist_ok=True)
     srcs = [os.path.join(CSRC, s) for s in SOURCES] + [
         os.path.join(CSRC, "lsba_internal.cuh"), os.path.join(CSRC, "df.cuh"),
+        os.path.join(CSRC, "tma.cuh"),
         os.path.join(ROOT, "include", "lsba.h")]
     if not force and os.path.exists(LIB):
         t = os.path.getmtime(LIB)

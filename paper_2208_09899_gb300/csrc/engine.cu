@@ -21,6 +21,8 @@
 
 using namespace lsba;
 
+enum { MODE_FP64 = 0, MODE_DF = 1, MODE_F32 = 2 };
+
 struct lsba_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
@@ -65,8 +67,8 @@ struct lsba_ctx {
   // side stream for the off-critical-path small kernel, and its events
   cudaStream_t side = nullptr;
   std::vector<cudaEvent_t> ev_main, ev_side;
-  // double-float mode buffers
-  int df = 0;
+  // working precision of the bandwidth-shaped passes
+  int mode = 0;
   float2* A_df = nullptr;      // CSR values as hi + lo pairs
   size_t A_df_cap = 0;
   double* Bdf = nullptr;       // n x s float2 (as raw 8-byte words)
@@ -151,6 +153,11 @@ static size_t max_partials(int64_t n, int s, int mmax, int sms, size_t* qmax_out
       GramPlan pd = plan_gram_df(n, s, a, b, sms);
       v = (size_t)pd.grid_x * pd.q;
       if (v > best) best = v;
+      if (s % 4 == 0) {
+        GramPlan pf = plan_gram_f32(n, s, a, b, sms);
+        v = (size_t)pf.grid_x * pf.q;
+        if (v > best) best = v;
+      }
     }
   *qmax_out = qmax;
   return best;
@@ -315,10 +322,14 @@ static bool lagged(int skel) { return skel == SK_LS || skel == SK_ICWY || skel =
 static void do_gram(lsba_ctx* h, const BlockPtrs& L, int a, const BlockPtrs& R, int b, int64_t n,
                     int s, const Ctl* ctl, int guard) {
   prof_begin(h, LSBA_K_GRAM);
-  if (h->df) {
+  if (h->mode == MODE_DF) {
     GramPlan p = plan_gram_df(n, s, a, b, h->num_sms);
     launch_gram_df(h->stream, p, L, a, R, b, n, s, (float2*)h->partials, h->Gbuf, ctl, guard,
                    &h->d_ctl->error);
+  } else if (h->mode == MODE_F32) {
+    GramPlan p = plan_gram_f32(n, s, a, b, h->num_sms);
+    launch_gram_f32(h->stream, p, L, a, R, b, n, s, (float*)h->partials, h->Gbuf, ctl, guard,
+                    &h->d_ctl->error);
   } else {
     GramPlan p = plan_gram(n, s, a, b, h->num_sms);
     launch_gram(h->stream, p, L, a, R, b, n, s, h->partials, h->Gbuf, ctl, guard);
@@ -329,9 +340,12 @@ static void do_gram(lsba_ctx* h, const BlockPtrs& L, int a, const BlockPtrs& R, 
 static void do_spmm(lsba_ctx* h, const lsba_csr* A, const double* V, double* W, int s,
                     const Ctl* ctl, int guard) {
   prof_begin(h, LSBA_K_SPMM);
-  if (h->df)
+  if (h->mode == MODE_DF)
     launch_spmm_df(h->stream, A->n, A->d_rowptr, A->d_colidx, h->A_df, (const float2*)V,
                    (float2*)W, s, ctl, guard);
+  else if (h->mode == MODE_F32)
+    launch_spmm_f32(h->stream, A->n, A->d_rowptr, A->d_colidx, (const float*)h->A_df,
+                    (const float*)V, (float*)W, s, ctl, guard);
   else
     launch_spmm(h->stream, A->n, A->d_rowptr, A->d_colidx, A->d_vals, V, W, s, ctl, guard);
   prof_end(h);
@@ -341,9 +355,12 @@ static void do_update(lsba_ctx* h, const BlockPtrs& in, int nin, int64_t n, int 
                       const double* coef1, const double* tri1, double* out2, const double* coef2,
                       const double* chain, const double* tri2, const Ctl* ctl, int step) {
   prof_begin(h, LSBA_K_UPDATE);
-  if (h->df)
+  if (h->mode == MODE_DF)
     launch_update_df(h->stream, in, nin, n, s, (float2*)out1, coef1, tri1, (float2*)out2, coef2,
                      chain, tri2, h->cdf, ctl, step, h->num_sms);
+  else if (h->mode == MODE_F32)
+    launch_update_f32(h->stream, in, nin, n, s, (float*)out1, coef1, tri1, (float*)out2, coef2,
+                      chain, tri2, (float*)h->cdf, ctl, step, h->num_sms);
   else
     launch_update(h->stream, in, nin, n, s, out1, coef1, tri1, out2, coef2, chain, tri2, ctl, step);
   prof_end(h);
@@ -452,7 +469,7 @@ static void enqueue_true_residual(lsba_ctx* h, const lsba_csr* A, const double* 
   cudaStream_t st = h->stream;
   do_spmm(h, A, Xw, h->Wb, s, nullptr, 0);
   prof_begin(h, LSBA_K_UPDATE);
-  if (h->df)
+  if (h->mode == MODE_DF)
     launch_sub_df(st, n * s, (const float2*)Bw, (const float2*)h->Wb, (float2*)h->Ub);
   else
     launch_axpby(st, n, s, Bw, h->Wb, h->Ub);
@@ -478,6 +495,8 @@ void lsba_default_options(lsba_options* o) {
   o->inject_flag_relation = -1;
   o->profile = 0;
   o->precision = LSBA_PREC_AUTO;
+  o->ir_max_outer = 10;
+  o->ir_inner_tol = 1e-5;
 }
 
 const char* lsba_status_string(int st) {
@@ -560,80 +579,27 @@ static int skel_code(lsba_skeleton s) {
   }
 }
 
-static int solve_impl(lsba_handle h, const lsba_csr* A, const double* d_B, double* d_X, int s, int m,
-                      double tol, lsba_skeleton skel_in) {
-  auto t0 = std::chrono::steady_clock::now();
-  memset(&h->stats, 0, sizeof(h->stats));
-  h->stats.relres_true = NAN;
-  h->stats.relres_est = NAN;
-  const int skel = skel_code(skel_in);
-  if (!A || !d_B || !d_X || skel < 0 || s < 1 || s > LSBA_MAX_S || m < 1 ||
-      (int64_t)(m + 1) * s > LSBA_MAX_MS || m + 3 > LSBA_MAXB || A->n < 1 || A->nnz < 0 ||
-      A->nnz >= (int64_t)1 << 31 || !A->d_rowptr || (A->nnz > 0 && (!A->d_colidx || !A->d_vals)) ||
-      !(tol >= 0.0) || h->opt.max_restarts < 0)
-    return h->stats.status = LSBA_INVALID_ARG;
-  const int64_t n = A->n;
-  CK(cudaSetDevice(h->device));
-  int rc = ensure_ws(h, n, s, m);
-  if (rc != LSBA_OK) return h->stats.status = rc;
+// Restart cycles of one (inner) solve of A X = B in the current working
+// precision (h->mode), from X = 0.  Bw, Xw: B and X in that precision.
+// Accumulates into h->stats; history of the first cycle when record_first.
+static int run_cycles(lsba_handle h, const lsba_csr* A, const double* Bw, double* Xw, int64_t n,
+                      int s, int m, double tol, bool verify, bool record_first, int* status_out) {
   SmallWs& w = h->ws;
-  w.skel = skel;
-  w.modification = h->opt.modification == LSBA_FOM ? 0 : 1;
+  const int skel = w.skel;
   cudaStream_t st = h->stream;
-  const size_t blk = (size_t)n * s;
-  // Precision: double-float unless its update coefficients do not fit shared memory.
-  const bool want_df = h->opt.precision == LSBA_PREC_DF ||
-                       (h->opt.precision == LSBA_PREC_AUTO && lagged(skel));
-  h->df = (want_df && update_df_smem(m + 3, s, true) <= 200 * 1024) ? 1 : 0;
-  const double* Bw = d_B;   // B and X in the working precision
-  double* Xw = d_X;
-  if (h->df) {
-    if ((size_t)A->nnz > h->A_df_cap) {
-      cudaFree(h->A_df);
-      h->A_df = nullptr;
-      h->A_df_cap = 0;
-      if (cudaMalloc(&h->A_df, sizeof(float2) * (A->nnz > 0 ? A->nnz : 1)) != cudaSuccess) {
-        cudaGetLastError();
-        return h->stats.status = LSBA_OUT_OF_MEMORY;
-      }
-      h->A_df_cap = A->nnz;
-    }
-    PROF(LSBA_K_UPDATE, launch_to_df(st, A->nnz, A->d_vals, h->A_df));
-    PROF(LSBA_K_UPDATE, launch_to_df(st, n * s, d_B, (float2*)h->Bdf));
-    Bw = h->Bdf;
-    Xw = h->Xdf;
-  }
-  CK(cudaMemsetAsync(Xw, 0, sizeof(double) * blk, st));
-  h->stats.precision = h->df ? LSBA_PREC_DF : LSBA_PREC_FP64;
   Ctl* c = h->h_ctl;
-  const int hist_cap = c->hist_cap, gram_cap = c->gram_hist_cap;
-  memset(c, 0, sizeof(Ctl));
-  c->hist_cap = hist_cap;
-  c->gram_hist_cap = gram_cap;
-  c->tol = tol;
-  c->record = h->opt.record_history ? 1 : 0;
-  c->update_step = -1;
-  c->side_step = -1;
-  h->h_est.clear();
-  h->h_est_cycle.clear();
-  h->h_est_j.clear();
-  h->h_cycle_m.clear();
-  h->h_cycle_flag.clear();
-  h->h_cycle_mcur.clear();
-  h->h_first_H.clear();
-  h->h_first_beta.clear();
-  h->h_gram_data.clear();
-  h->h_gram_rows.clear();
-  h->h_gram_cols.clear();
-  h->first_j = 0;
-
+  lsba_stats& S = h->stats;
   const int vper = (skel == SK_LS) ? 4 : (skel == SK_PIP || lagged(skel)) ? 3 : 2;
   const int vcyc = lagged(skel) ? 1 : 0;
+  int rc;
+  CK(cudaMemsetAsync(Xw, 0, sizeof(double) * (size_t)n * s, st));
+  c->tol = tol;
+  c->update_step = -1;
+  c->side_step = -1;
   int m_cur = m;
   const double* Rstart = Bw;
   int start_flags = 3;
   int status = LSBA_NOT_CONVERGED;
-  lsba_stats& S = h->stats;
   int cycle = 0;
   bool have_true = false;
   while (true) {
@@ -644,14 +610,16 @@ static int solve_impl(lsba_handle h, const lsba_csr* A, const double* d_B, doubl
       break;
     }
     c->cycle = cycle;
+    c->record = (record_first && h->opt.record_history) ? 1 : 0;
     c->m_cur = m_cur;
     c->inject_relation = (cycle == h->opt.inject_flag_cycle) ? h->opt.inject_flag_relation : -1;
-    if ((rc = push_ctl(h)) != LSBA_OK) return S.status = rc;
+    if ((rc = push_ctl(h)) != LSBA_OK) return rc;
     enqueue_cycle(h, A, Rstart, n, s, m_cur, start_flags);
     CK(cudaGetLastError());
-    if ((rc = pull_ctl(h)) != LSBA_OK) return S.status = rc;
-    if (c->error) return S.status = LSBA_DEVICE_TIMEOUT;
+    if ((rc = pull_ctl(h)) != LSBA_OK) return rc;
+    if (c->error) return LSBA_DEVICE_TIMEOUT;
     S.syncs += 1;
+    S.cycles += 1;
     if (c->start_flag) {
       status = (cycle == 1) ? LSBA_BREAKDOWN : LSBA_NOT_CONVERGED;
       break;
@@ -663,14 +631,12 @@ static int solve_impl(lsba_handle h, const lsba_csr* A, const double* d_B, doubl
     h->h_cycle_flag.push_back(c->flagged);
     h->h_cycle_mcur.push_back(m_cur);
     S.steps += j;
-    int a_calls;
-    if (lagged(skel)) a_calls = j + 1 + f;
-    else a_calls = j + f;
+    const int a_calls = lagged(skel) ? j + 1 + f : j + f;
     S.a_calls += a_calls;
     S.syncs += (skel == SK_BCGS) ? 2 * a_calls : a_calls;
     S.v_apps += vper * j + (j > 0 ? vcyc : 0);
     if (!std::isnan(c->est)) S.relres_est = c->est;
-    if (cycle == 1 && h->opt.record_history) {
+    if (cycle == 1 && record_first && h->opt.record_history) {
       h->first_j = j;
       if (j > 0) {
         const int rows = (j + 1) * s, cols = j * s;
@@ -704,10 +670,9 @@ static int solve_impl(lsba_handle h, const lsba_csr* A, const double* d_B, doubl
       break;
     }
     if (c->converged) {
-      if (h->opt.verify_true_residual) {
-        // R = B - A X into Ub; ||R||_F / ||B||_F from its Gram.
+      if (verify) {
         enqueue_true_residual(h, A, Bw, Xw, n, s);
-        if ((rc = pull_ctl(h)) != LSBA_OK) return S.status = rc;
+        if ((rc = pull_ctl(h)) != LSBA_OK) return rc;
         S.relres_true = c->relres_true;
         have_true = true;
         if (!(c->relres_true <= tol)) {
@@ -722,16 +687,150 @@ static int solve_impl(lsba_handle h, const lsba_csr* A, const double* d_B, doubl
     Rstart = h->Ub;
     start_flags = 0;
   }
-  S.cycles = cycle;
   S.m_final = m_cur;
-  S.status = status;
-  // True residual of the returned X.
-  if (!have_true && status != LSBA_INVALID_ARG) {
-    enqueue_true_residual(h, A, Bw, Xw, n, s);
+  *status_out = status;
+  (void)have_true;
+  return LSBA_OK;
+}
+
+static int ensure_lowprec_A(lsba_handle h, const lsba_csr* A) {
+  if ((size_t)A->nnz > h->A_df_cap) {
+    cudaFree(h->A_df);
+    h->A_df = nullptr;
+    h->A_df_cap = 0;
+    if (cudaMalloc(&h->A_df, sizeof(float2) * (A->nnz > 0 ? A->nnz : 1)) != cudaSuccess) {
+      cudaGetLastError();
+      return LSBA_OUT_OF_MEMORY;
+    }
+    h->A_df_cap = A->nnz;
+  }
+  return LSBA_OK;
+}
+
+// FP64 residual R = B - A X into Ub (double) and its norm ratio into
+// ctl->relres_true (ratio to ctl->outer_normB; outer = 1 first stores ||B||).
+static void enqueue_fp64_residual(lsba_ctx* h, const lsba_csr* A, const double* d_B,
+                                  const double* d_X, int64_t n, int s, bool norm_of_B) {
+  cudaStream_t st = h->stream;
+  BlockPtrs one;
+  memset(&one, 0, sizeof(one));
+  const int mode = h->mode;
+  h->mode = MODE_FP64;
+  if (norm_of_B) {
+    one.p[0] = d_B;
+    do_gram(h, one, 1, one, 1, n, s, nullptr, 0);
+    PROF(LSBA_K_SMALL, launch_outer_norm(st, h->Gbuf, s, h->d_ctl, 0));
+  }
+  do_spmm(h, A, d_X, h->Wb, s, nullptr, 0);
+  PROF(LSBA_K_UPDATE, launch_axpby(st, n, s, d_B, h->Wb, h->Ub));
+  one.p[0] = h->Ub;
+  do_gram(h, one, 1, one, 1, n, s, nullptr, 0);
+  PROF(LSBA_K_SMALL, launch_outer_norm(st, h->Gbuf, s, h->d_ctl, 1));
+  h->mode = mode;
+}
+
+static int solve_impl(lsba_handle h, const lsba_csr* A, const double* d_B, double* d_X, int s, int m,
+                      double tol, lsba_skeleton skel_in) {
+  auto t0 = std::chrono::steady_clock::now();
+  memset(&h->stats, 0, sizeof(h->stats));
+  h->stats.relres_true = NAN;
+  h->stats.relres_est = NAN;
+  const int skel = skel_code(skel_in);
+  if (!A || !d_B || !d_X || skel < 0 || s < 1 || s > LSBA_MAX_S || m < 1 ||
+      (int64_t)(m + 1) * s > LSBA_MAX_MS || m + 3 > LSBA_MAXB || A->n < 1 || A->nnz < 0 ||
+      A->nnz >= (int64_t)1 << 31 || !A->d_rowptr || (A->nnz > 0 && (!A->d_colidx || !A->d_vals)) ||
+      !(tol >= 0.0) || h->opt.max_restarts < 0)
+    return h->stats.status = LSBA_INVALID_ARG;
+  const int64_t n = A->n;
+  CK(cudaSetDevice(h->device));
+  int rc = ensure_ws(h, n, s, m);
+  if (rc != LSBA_OK) return h->stats.status = rc;
+  SmallWs& w = h->ws;
+  w.skel = skel;
+  w.modification = h->opt.modification == LSBA_FOM ? 0 : 1;
+  cudaStream_t st = h->stream;
+  const size_t blk = (size_t)n * s;
+  // Working precision of the SpMM / Gram / update passes.
+  const int prec = h->opt.precision;
+  const bool fits_df = update_df_smem(m + 3, s, true) <= 200 * 1024;
+  const bool fits_f32 = (s == 4 || s == 8 || s == 16) && update_f32_smem(m + 3, s, true) <= 200 * 1024;
+  const bool ir = prec == LSBA_PREC_FP32_IR && fits_f32;
+  if (ir) h->mode = MODE_F32;
+  else if ((prec == LSBA_PREC_DF || (prec == LSBA_PREC_AUTO && lagged(skel)) ||
+            prec == LSBA_PREC_FP32_IR) && fits_df)
+    h->mode = MODE_DF;
+  else h->mode = MODE_FP64;
+  h->stats.precision = ir ? LSBA_PREC_FP32_IR : h->mode == MODE_DF ? LSBA_PREC_DF : LSBA_PREC_FP64;
+
+  Ctl* c = h->h_ctl;
+  const int hist_cap = c->hist_cap, gram_cap = c->gram_hist_cap;
+  memset(c, 0, sizeof(Ctl));
+  c->hist_cap = hist_cap;
+  c->gram_hist_cap = gram_cap;
+  h->h_est.clear();
+  h->h_est_cycle.clear();
+  h->h_est_j.clear();
+  h->h_cycle_m.clear();
+  h->h_cycle_flag.clear();
+  h->h_cycle_mcur.clear();
+  h->h_first_H.clear();
+  h->h_first_beta.clear();
+  h->h_gram_data.clear();
+  h->h_gram_rows.clear();
+  h->h_gram_cols.clear();
+  h->first_j = 0;
+  lsba_stats& S = h->stats;
+  int status = LSBA_NOT_CONVERGED;
+
+  if (!ir) {
+    const double* Bw = d_B;
+    double* Xw = d_X;
+    if (h->mode == MODE_DF) {
+      if ((rc = ensure_lowprec_A(h, A)) != LSBA_OK) return S.status = rc;
+      PROF(LSBA_K_UPDATE, launch_to_df(st, A->nnz, A->d_vals, h->A_df));
+      PROF(LSBA_K_UPDATE, launch_to_df(st, n * s, d_B, (float2*)h->Bdf));
+      Bw = h->Bdf;
+      Xw = h->Xdf;
+    }
+    if ((rc = run_cycles(h, A, Bw, Xw, n, s, m, tol, h->opt.verify_true_residual != 0, true,
+                         &status)) != LSBA_OK)
+      return S.status = rc;
+    if (h->mode == MODE_DF) PROF(LSBA_K_UPDATE, launch_from_df(st, n * s, (const float2*)Xw, d_X));
+    // True residual of the returned X (FP64).
+    enqueue_fp64_residual(h, A, d_B, d_X, n, s, true);
     if ((rc = pull_ctl(h)) != LSBA_OK) return S.status = rc;
     S.relres_true = c->relres_true;
+  } else {
+    // FP64 iterative refinement around an FP32 inner BGMRES/BFOM:
+    //   R = B - A X (FP64);  solve A D = R in FP32 to ir_inner_tol;  X += D (FP64).
+    if ((rc = ensure_lowprec_A(h, A)) != LSBA_OK) return S.status = rc;
+    PROF(LSBA_K_UPDATE, launch_to_f32(st, A->nnz, A->d_vals, (float*)h->A_df));
+    CK(cudaMemsetAsync(d_X, 0, sizeof(double) * blk, st));
+    const double inner_tol = h->opt.ir_inner_tol > 0 ? h->opt.ir_inner_tol : 1e-5;
+    const int max_outer = h->opt.ir_max_outer > 0 ? h->opt.ir_max_outer : 10;
+    double prev = INFINITY;
+    for (int it = 0; it <= max_outer; ++it) {
+      enqueue_fp64_residual(h, A, d_B, d_X, n, s, it == 0);
+      if ((rc = pull_ctl(h)) != LSBA_OK) return S.status = rc;
+      S.relres_true = c->relres_true;
+      if (c->relres_true <= tol) {
+        status = LSBA_OK;
+        break;
+      }
+      if (it == max_outer || !(c->relres_true < prev)) break;
+      prev = c->relres_true;
+      S.ir_outer += 1;
+      // Inner FP32 solve of A D = R (R in Ub as FP64 -> FP32 into Bdf).
+      PROF(LSBA_K_UPDATE, launch_to_f32(st, n * s, h->Ub, (float*)h->Bdf));
+      int inner_status = 0;
+      if ((rc = run_cycles(h, A, h->Bdf, h->Xdf, n, s, m, inner_tol, false, it == 0,
+                           &inner_status)) != LSBA_OK)
+        return S.status = rc;
+      if (inner_status == LSBA_BREAKDOWN) break;
+      PROF(LSBA_K_UPDATE, launch_add_f32(st, n * s, (const float*)h->Xdf, d_X));
+    }
   }
-  if (h->df) PROF(LSBA_K_UPDATE, launch_from_df(st, n * s, (const float2*)Xw, d_X));
+  S.status = status;
   CK(cudaStreamSynchronize(st));
   if (h->opt.record_history) {
     const int ne = c->n_hist;

@@ -13,6 +13,7 @@
 // The Gram result and everything after it (the small kernels) are FP64.
 #include "df.cuh"
 #include "lsba_internal.cuh"
+#include "tma.cuh"
 
 namespace lsba {
 
@@ -235,41 +236,6 @@ __global__ void __launch_bounds__(GDF_THREADS) k_gram_df(const __grid_constant__
 // overlaps the arithmetic on chunk c+1.  Every wait on an mbarrier is bounded;
 // on a timeout the CTA records an error in *err, waits (bounded) for its own
 // copies, and returns.
-#define TMA_WAIT_LIMIT (1u << 22)
-
-__device__ __forceinline__ uint32_t smem_addr(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
-               : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
-               "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, unsigned bytes,
-                                              uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-          smem_addr(dst)),
-      "l"(src), "r"(bytes), "r"(smem_addr(bar))
-      : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-      " selp.u32 %0, 1, 0, p;\n}" : "=r"(ok) : "r"(smem_addr(bar)), "r"(parity) : "memory");
-  return ok != 0;
-}
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity) {
-  for (unsigned it = 0; it < TMA_WAIT_LIMIT; ++it)
-    if (mbar_try_wait(bar, parity)) return true;
-  return false;
-}
-
 struct GramTmaArgs {
   BlockPtrs L;
   BlockPtrs R;

@@ -930,6 +930,18 @@ void launch_small_start(cudaStream_t st, const SmallWs& w, int flags) {
 void launch_true_relres(cudaStream_t st, const double* G, int s, Ctl* ctl) {
   k_true_relres<<<1, 32, 0, st>>>(G, s, ctl);
 }
+
+__global__ void k_outer_norm(const double* G, int s, Ctl* ctl, int mode) {
+  if (threadIdx.x == 0) {
+    double tr = 0.0;
+    for (int a = 0; a < s; ++a) tr += G[a * s + a];
+    if (mode == 0) ctl->outer_normB = sqrt(tr);
+    else ctl->relres_true = sqrt(tr) / ctl->outer_normB;
+  }
+}
+void launch_outer_norm(cudaStream_t st, const double* G, int s, Ctl* ctl, int mode) {
+  k_outer_norm<<<1, 32, 0, st>>>(G, s, ctl, mode);
+}
 void launch_small_step(cudaStream_t st, const SmallWs& w, int k, int phase) {
   k_small_step<<<1, NT, 0, st>>>(w, k, phase);
 }

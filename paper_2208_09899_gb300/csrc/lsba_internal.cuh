@@ -42,6 +42,7 @@ struct Ctl {
   int side_rel;        // relation the side kernel completes
   int side_J;          // side kernel also forms J (BCGSI+LS)
   int error;           // a bounded device wait gave up (LSBA_DEVICE_TIMEOUT)
+  double outer_normB;  // ||B||_F of the outer (FP64) problem of iterative refinement
 };
 
 // Pointers of up to LSBA_MAXB blocks (each n x s, row-major, FP64).
@@ -130,9 +131,27 @@ void launch_update_df(cudaStream_t st, const BlockPtrs& in, int nin, int64_t n, 
                       const double* chain, const double* tri2, float2* cdf, const Ctl* ctl,
                       int step, int num_sms);
 
+// ---- FP32 variants (inner solver of FP64 iterative refinement); block vectors are float ----
+void launch_to_f32(cudaStream_t st, int64_t count, const double* in, float* out);
+void launch_add_f32(cudaStream_t st, int64_t count, const float* d, double* x);
+void launch_spmm_f32(cudaStream_t st, int64_t n, const int32_t* rowptr, const int32_t* colidx,
+                     const float* vals, const float* V, float* W, int s, const Ctl* ctl, int guard);
+GramPlan plan_gram_f32(int64_t n, int s, int a, int b, int num_sms);
+void launch_gram_f32(cudaStream_t st, const GramPlan& p, const BlockPtrs& L, int a,
+                     const BlockPtrs& R, int b, int64_t n, int s, float* partials, double* G,
+                     const Ctl* ctl, int guard, int* err);
+__host__ __device__ size_t coef_f32_count(int nin, int s, bool two);
+size_t update_f32_smem(int nin, int s, bool two);
+void launch_update_f32(cudaStream_t st, const BlockPtrs& in, int nin, int64_t n, int s, float* out1,
+                       const double* coef1, const double* tri1, float* out2, const double* coef2,
+                       const double* chain, const double* tri2, float* cf, const Ctl* ctl, int step,
+                       int num_sms);
+
 // Small single-CTA kernels (skeleton logic, Cholesky, least squares, estimate).
 void launch_small_start(cudaStream_t st, const SmallWs& w, int flags);
 void launch_true_relres(cudaStream_t st, const double* G, int s, Ctl* ctl);
+// mode 0: ctl->outer_normB = sqrt(trace G); mode 1: ctl->relres_true = sqrt(trace G) / outer_normB.
+void launch_outer_norm(cudaStream_t st, const double* G, int s, Ctl* ctl, int mode);
 void launch_small_step(cudaStream_t st, const SmallWs& w, int k, int phase);
 void launch_small_side(cudaStream_t st, const SmallWs& w, int k);
 void launch_small_end(cudaStream_t st, const SmallWs& w);

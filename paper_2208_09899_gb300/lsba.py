@@ -20,7 +20,7 @@ LSBA_OK, LSBA_NOT_CONVERGED, LSBA_BREAKDOWN, LSBA_INVALID_ARG = 0, 1, 2, 3
 LSBA_OUT_OF_MEMORY, LSBA_CUDA_ERROR, LSBA_DEVICE_TIMEOUT = 4, 5, 6
 SKELETONS = {"bcgs": 0, "bcgs_pip": 1, "bcgsi_ls": 2, "bmgs_icwy": 3, "bmgs_cwy": 4}
 MODIFICATIONS = {"fom": 0, "gmres": 1}
-PRECISIONS = {"fp64": 0, "df": 1, "auto": 2}
+PRECISIONS = {"fp64": 0, "df": 1, "auto": 2, "fp32_ir": 3}
 
 EXPORTED = ("lsba_default_options", "lsba_create", "lsba_set_options", "lsba_solve",
             "lsba_solve_host", "lsba_get_stats", "lsba_get_history", "lsba_status_string",
@@ -34,7 +34,8 @@ class Options(C.Structure):
                 ("adaptive_restart", C.c_int32), ("verify_true_residual", C.c_int32),
                 ("record_history", C.c_int32), ("inject_flag_cycle", C.c_int32),
                 ("inject_flag_relation", C.c_int32), ("profile", C.c_int32),
-                ("precision", C.c_int32), ("reserved", C.c_int32 * 6)]
+                ("precision", C.c_int32), ("ir_max_outer", C.c_int32),
+                ("ir_inner_tol", C.c_double), ("reserved", C.c_int32 * 4)]
 
 
 class Stats(C.Structure):
@@ -42,7 +43,7 @@ class Stats(C.Structure):
                 ("a_calls", C.c_int32), ("syncs", C.c_int32), ("v_apps", C.c_int32),
                 ("flags", C.c_int32), ("m_final", C.c_int32), ("relres_est", C.c_double),
                 ("relres_true", C.c_double), ("solve_ms", C.c_double),
-                ("precision", C.c_int32), ("pad", C.c_int32)]
+                ("precision", C.c_int32), ("ir_outer", C.c_int32)]
 
 
 class History(C.Structure):

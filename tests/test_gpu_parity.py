@@ -263,3 +263,35 @@ def test_lapl512_first_cycle_full_size(env, sk, precision):
     assert max(errs) <= TOL_GRAM
     assert _rel(hist["first_H"], fc["H"]) <= TOL_GRAM
     assert _rel(X, ref.X) <= TOL_X
+
+
+@pytest.mark.parametrize("sk", ["bcgsi_ls", "bcgs_pip", "bmgs_icwy"])
+def test_fp32_inner_fp64_refinement_well_conditioned(env, sk):
+    """FP64 iterative refinement around an FP32 inner BGMRES: relative residual
+    1e-10 and X within 1e-8 of the FP64 oracle (tridiag(-1,4,-1): kappa < 3)."""
+    torch, lsba = env
+    A, B = W.workload("tridiag2000_s4", 0)
+    X, st, _ = lsba.solve(A, B, 10, 1e-10, sk, device=0, precision="fp32_ir", max_restarts=50)
+    ref = O.solve(A, B, 10, 1e-10, sk, modification="gmres", max_restarts=50)
+    assert st["precision"] == lsba.PRECISIONS["fp32_ir"]
+    assert st["status"] == lsba.LSBA_OK and st["relres_true"] <= 1e-10
+    assert st["ir_outer"] >= 2
+    assert _rel(X, ref.X) <= TOL_X
+
+
+def test_fp32_inner_fp64_refinement_laplacian_error_vs_oracle(env):
+    """On the 2D Laplacian (kappa ~ 1.7e3) the refined solution reaches relative
+    residual 1e-10 and its error against the FP64 oracle is bounded by
+    kappa(A) * (sum of both relative residuals)."""
+    torch, lsba = env
+    A = W.laplacian_2d(64)
+    B = W.gaussian_block(A.n, 8, 2)
+    X, st, _ = lsba.solve(A, B, 16, 1e-10, "bcgsi_ls", device=0, precision="fp32_ir",
+                          max_restarts=400)
+    ref = O.solve(A, B, 16, 1e-10, "bcgsi_ls", modification="gmres", max_restarts=400)
+    kappa = 4.0 / (4 * np.sin(np.pi / (2 * 65)) ** 2)
+    err = _rel(X, ref.X)
+    print(f"FP32IR lapl64: outer {st['ir_outer']} cycles {st['cycles']} relres "
+          f"{st['relres_true']:.2e} error vs oracle {err:.2e}")
+    assert st["status"] == lsba.LSBA_OK and st["relres_true"] <= 1e-10
+    assert err <= kappa * (st["relres_true"] + ref.relres_true)
