@@ -192,7 +192,8 @@ static int ensure_ws(lsba_ctx* h, int64_t n, int s, int m) {
                oJ = take((size_t)ldH * s), oc1 = take((size_t)(m + 4) * ss),
                oc2 = take((size_t)(m + 4) * ss), och = take(ss), ot1 = take(ss), ot2 = take(ss),
                oRb = take((size_t)ldR * ldR), orf = take((size_t)(m + 1) * 2 * ss),
-               otau = take((size_t)(m + 1) * s), og = take((size_t)ldH * s), oTf = take(ss),
+               otau = take((size_t)(m + 1) * s), otw = take((size_t)(m + 1) * ss),
+               og = take((size_t)ldH * s), oTf = take(ss),
                ogf = take(ss), ocf = take(ss), ouf = take((size_t)ldH * s), oC = take(ss),
                oBc = take(ss), oXi = take((size_t)ldH * s), oMv = take((size_t)ldH * s),
                owk = take((size_t)6 * ldH * s + 16 * ss), osz = take((size_t)ldH * s),
@@ -240,6 +241,7 @@ static int ensure_ws(lsba_ctx* h, int64_t n, int s, int m) {
   w.Rbar = b + oRb;
   w.refl = b + orf;
   w.tau = b + otau;
+  w.Twy = b + otw;
   w.g = b + og;
   w.Tfom = b + oTf;
   w.gfom = b + ogf;
@@ -601,7 +603,6 @@ static int run_cycles(lsba_handle h, const lsba_csr* A, const double* Bw, double
   int start_flags = 3;
   int status = LSBA_NOT_CONVERGED;
   int cycle = 0;
-  bool have_true = false;
   while (true) {
     ++cycle;
     if (cycle > h->opt.max_restarts + 1) {
@@ -674,7 +675,6 @@ static int run_cycles(lsba_handle h, const lsba_csr* A, const double* Bw, double
         enqueue_true_residual(h, A, Bw, Xw, n, s);
         if ((rc = pull_ctl(h)) != LSBA_OK) return rc;
         S.relres_true = c->relres_true;
-        have_true = true;
         if (!(c->relres_true <= tol)) {
           Rstart = h->Ub;
           start_flags = 2;
@@ -689,7 +689,6 @@ static int run_cycles(lsba_handle h, const lsba_csr* A, const double* Bw, double
   }
   S.m_final = m_cur;
   *status_out = status;
-  (void)have_true;
   return LSBA_OK;
 }
 

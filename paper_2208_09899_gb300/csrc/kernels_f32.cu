@@ -1,8 +1,9 @@
 // FP32 kernels of the inner solver of FP64 iterative refinement (mixed
 // precision).  Block vectors are FP32 (4 bytes per entry); the SpMM, the
 // one-pass Gram and the basis update multiply and accumulate in FP32 on the
-// FP32 pipes.  The per-CTA Gram partials are summed across CTAs in FP64 (in CTA
-// order) and every small s x s / ks x s computation after the Gram (Cholesky,
+// FP32 pipes.  The per-CTA Gram partials are summed across CTAs in CTA order
+// with compensated (TwoSum) FP32 arithmetic and converted to FP64; every small
+// s x s / ks x s computation after the Gram (Cholesky,
 // Hessenberg least squares, estimate) stays FP64, as do the outer residual
 // B - A X and the solution update X += D.
 //
@@ -195,9 +196,16 @@ __global__ void k_gram_reduce_f32(const float* __restrict__ partials, int nparts
   if (guard && !ctl_on(ctl)) return;
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= q) return;
-  double v = 0.0;
-  for (int x = 0; x < nparts; ++x) v += (double)partials[(int64_t)x * q + e];
-  G[e] = v;
+  // Compensated (TwoSum) FP32 accumulation in CTA order; one FP64 conversion.
+  float sum = 0.f, comp = 0.f;
+  for (int x = 0; x < nparts; ++x) {
+    const float p = partials[(int64_t)x * q + e];
+    const float t = __fadd_rn(sum, p);
+    const float bb = __fsub_rn(t, sum);
+    comp = __fadd_rn(comp, __fadd_rn(__fsub_rn(sum, __fsub_rn(t, bb)), __fsub_rn(p, bb)));
+    sum = t;
+  }
+  G[e] = (double)sum + (double)comp;
 }
 
 GramPlan plan_gram_f32(int64_t n, int s, int a, int b, int num_sms) {

@@ -61,6 +61,51 @@ __device__ void cta_gemm(int M, int N, int K, double alpha, const double* A, int
   __syncthreads();
 }
 
+// Dynamic shared-memory arena of every small kernel (doubles).
+#define SMALL_ARENA_DOUBLES (12 * 1024)
+extern __shared__ double small_arena[];
+
+// The same product with op(A) and op(B) first staged in shared memory by one
+// coalesced, parallel load (the small kernels' operands sit in L2; staging
+// turns K dependent L2 round trips per thread into one).  Falls back to
+// cta_gemm when the panels do not fit the arena.
+__device__ void cta_gemm_s(int M, int N, int K, double alpha, const double* A, int lda, bool ta,
+                           const double* B, int ldb, bool tb, double beta, double* C, int ldc) {
+  if ((size_t)M * K + (size_t)K * N > SMALL_ARENA_DOUBLES || K == 0) {
+    cta_gemm(M, N, K, alpha, A, lda, ta, B, ldb, tb, beta, C, ldc);
+    return;
+  }
+  double* As = small_arena;          // M x K, col-major (ld M)
+  double* Bs = small_arena + M * K;  // K x N, col-major (ld K)
+  for (int e = threadIdx.x; e < M * K; e += NT) {
+    int i, q;
+    if (ta) { q = e % K; i = e / K; } else { i = e % M; q = e / M; }
+    As[i + q * M] = ta ? A[q + i * lda] : A[i + q * lda];
+  }
+  for (int e = threadIdx.x; e < K * N; e += NT) {
+    int q, j;
+    if (tb) { j = e % N; q = e / N; } else { q = e % K; j = e / K; }
+    Bs[q + j * K] = tb ? B[j + q * ldb] : B[q + j * ldb];
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < M * N; e += NT) {
+    const int i = e % M, j = e / M;
+    const double* bj = Bs + j * K;
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    int q = 0;
+    for (; q + 3 < K; q += 4) {
+      a0 = fma(As[i + q * M], bj[q], a0);
+      a1 = fma(As[i + (q + 1) * M], bj[q + 1], a1);
+      a2 = fma(As[i + (q + 2) * M], bj[q + 2], a2);
+      a3 = fma(As[i + (q + 3) * M], bj[q + 3], a3);
+    }
+    for (; q < K; ++q) a0 = fma(As[i + q * M], bj[q], a0);
+    const double v = (a0 + a1) + (a2 + a3);
+    C[i + j * ldc] = alpha * v + (beta == 0.0 ? 0.0 : beta * C[i + j * ldc]);
+  }
+  __syncthreads();
+}
+
 __device__ void cta_copy(double* dst, int ldd, const double* src, int lds, int rows, int cols,
                          double alpha = 1.0) {
   for (int e = threadIdx.x; e < rows * cols; e += NT) {
@@ -74,6 +119,13 @@ __device__ void cta_copy(double* dst, int ldd, const double* src, int lds, int r
 // matrix whose upper triangle is read from S (col-major, lds).  Returns 1 (the
 // NaN-flag) if an upper entry is non-finite or a pivot is <= 0 or non-finite.
 __device__ int cta_chol(const double* S, int lds, int s, double* R, int* sflag) {
+  // Right-looking: pivot p reads the updated row p of the working matrix (in
+  // R's lower-left free space is not used: the work copy lives in the strict
+  // upper triangle of R itself and row p is finalised in place).  Each pivot
+  // takes one reciprocal square root (computed redundantly by every thread)
+  // and one barrier: the row-p scaling and the trailing update of rows > p use
+  // the unscaled row p, so they need no barrier between them.
+  __shared__ double wrk[LSBA_MAX_S * LSBA_MAX_S];
   if (threadIdx.x == 0) *sflag = 0;
   __syncthreads();
   for (int e = threadIdx.x; e < s * s; e += NT) {
@@ -83,25 +135,22 @@ __device__ int cta_chol(const double* S, int lds, int s, double* R, int* sflag) 
       v = S[a + c * lds];
       if (!isfinite(v)) *sflag = 1;
     }
-    R[a + c * s] = v;
+    wrk[a + c * s] = v;
+    R[a + c * s] = 0.0;
   }
   __syncthreads();
   if (*sflag) return 1;
   for (int p = 0; p < s; ++p) {
-    if (threadIdx.x == 0) {
-      const double d = R[p + p * s];
-      if (!(d > 0.0) || !isfinite(d)) *sflag = 1;
-      else R[p + p * s] = sqrt(d);
-    }
-    __syncthreads();
-    if (*sflag) return 1;
-    const double rpp = R[p + p * s];
-    for (int c = p + 1 + threadIdx.x; c < s; c += NT) R[p + c * s] = R[p + c * s] / rpp;
-    __syncthreads();
-    const int nt = s - p - 1;
+    const double d = wrk[p + p * s];
+    if (!(d > 0.0) || !isfinite(d)) return 1;   // uniform: every thread reads the same d
+    const double ri = rsqrt(d);
+    const double id = ri * ri;
+    const int nt = s - p;                        // row p (c >= p) and rows a in (p, c]
     for (int e = threadIdx.x; e < nt * nt; e += NT) {
-      const int a = p + 1 + e % nt, c = p + 1 + e / nt;
-      if (a <= c) R[a + c * s] = fma(-R[p + a * s], R[p + c * s], R[a + c * s]);
+      const int a = p + e % nt, c = p + e / nt;
+      if (a > c) continue;
+      if (a == p) R[p + c * s] = (c == p) ? d * ri : wrk[p + c * s] * ri;
+      else wrk[a + c * s] = fma(-wrk[p + a * s] * id, wrk[p + c * s], wrk[a + c * s]);
     }
     __syncthreads();
   }
@@ -123,16 +172,24 @@ __device__ void cta_trsm_right(double* X, int ldx, int rows, const double* R, in
   }
 }
 
-// Y (s x cols, ldy) <- R^{-T} Y, R upper s x s col-major (ld s).
+// Y (s x cols, ldy) <- R^{-T} Y, R upper s x s col-major (ld s): forward
+// substitution with R^T, one row per step (two barriers per row).
 __device__ void cta_trsm_left_T(const double* R, int s, double* Y, int ldy, int cols) {
+  __shared__ double rowq[64];
+  __shared__ double rdiag[LSBA_MAX_S];
+  for (int q = threadIdx.x; q < s; q += NT) rdiag[q] = 1.0 / R[q + q * s];
+  __syncthreads();
   for (int q = 0; q < s; ++q) {
-    const double rq = R[q + q * s];
-    for (int c = threadIdx.x; c < cols; c += NT) Y[q + c * ldy] = Y[q + c * ldy] / rq;
+    for (int c = threadIdx.x; c < cols; c += NT) {
+      const double v = Y[q + c * ldy] * rdiag[q];
+      Y[q + c * ldy] = v;
+      rowq[c] = v;
+    }
     __syncthreads();
     const int nr = s - q - 1;
     for (int e = threadIdx.x; e < nr * cols; e += NT) {
       const int r = q + 1 + e % nr, c = e / nr;
-      Y[r + c * ldy] = fma(-R[q + r * s], Y[q + c * ldy], Y[r + c * ldy]);
+      Y[r + c * ldy] = fma(-R[q + r * s], rowq[c], Y[r + c * ldy]);
     }
     __syncthreads();
   }
@@ -222,11 +279,11 @@ __device__ int warp_lu_solve(const double* Tin, const double* Bin, int s, double
       }
       __syncwarp();
       if (*sflag) break;
-      const double d = sT[p + p * s];
+      const double dinv = 1.0 / sT[p + p * s];
       // lane c updates column c of T (c > p) and of X.
       if (lane < s) {
         for (int i = p + 1; i < s; ++i) {
-          const double l = sT[i + p * s] / d;
+          const double l = sT[i + p * s] * dinv;
           if (lane > p) sT[i + lane * s] = fma(-l, sT[p + lane * s], sT[i + lane * s]);
           X[i + lane * s] = fma(-l, X[p + lane * s], X[i + lane * s]);
         }
@@ -237,7 +294,7 @@ __device__ int warp_lu_solve(const double* Tin, const double* Bin, int s, double
       for (int i = s - 1; i >= 0; --i) {
         double v = X[i + lane * s];
         for (int q = i + 1; q < s; ++q) v = fma(-sT[i + q * s], X[q + lane * s], v);
-        v = v / sT[i + i * s];
+        v = v * (1.0 / sT[i + i * s]);
         if (!isfinite(v)) *sflag = 1;
         X[i + lane * s] = v;
       }
@@ -289,12 +346,16 @@ __device__ void house_qr(double* X, int ldx, int r0, int s, double* v, double* t
       const double a1 = (lane + 32 >= l + 1 && lane + 32 < h) ? xl[lane + 32] : 0.0;
       const double xn2 = warp_sum(fma(a0, a0, a1 * a1));
       if (lane == 0) {
+        // beta = -sign(alpha) ||x||, tau = (beta - alpha) / beta = 1 + |alpha| / ||x||,
+        // v = x / (alpha - beta) below the leading 1: one rsqrt and one division.
         const double alpha = xl[l];
         double t = 0.0, beta = alpha, scale = 0.0;
         if (xn2 > 0.0) {
-          const double nrm = sqrt(fma(alpha, alpha, xn2));
+          const double n2 = fma(alpha, alpha, xn2);
+          const double rn = rsqrt(n2);
+          const double nrm = n2 * rn;
           beta = alpha >= 0.0 ? -nrm : nrm;
-          t = (beta - alpha) / beta;
+          t = fma(fabs(alpha), rn, 1.0);
           scale = 1.0 / (alpha - beta);
         }
         sh[0] = t;
@@ -334,6 +395,37 @@ __device__ void house_qr(double* X, int ldx, int r0, int s, double* v, double* t
     }
     __syncthreads();
   }
+}
+
+// Compact WY form of reflector set i: H_0 H_1 ... H_{s-1} = I - V T V^T with T
+// upper triangular (Schreiber and Van Loan's construction):
+//   T(l,l) = tau_l,  T(0:l, l) = -tau_l T(0:l, 0:l) (V(:, 0:l)^T v_l).
+// vtv: s x s scratch (global), T: s x s col-major.
+__device__ void build_wy_T(const double* v, const double* tau, int s, double* T, double* vtv) {
+  const int h = 2 * s;
+  cta_gemm_s(s, s, h, 1.0, v, h, true, v, h, false, 0.0, vtv, s);
+  for (int e = threadIdx.x; e < s * s; e += NT) T[e] = 0.0;
+  __syncthreads();
+  for (int l = 0; l < s; ++l) {
+    const double tl = tau[l];
+    for (int i = threadIdx.x; i < l; i += NT) {
+      double acc = 0.0;
+      for (int q = i; q < l; ++q) acc = fma(T[i + q * s], vtv[q + l * s], acc);
+      T[i + l * s] = -tl * acc;
+    }
+    if (threadIdx.x == 0) T[l + l * s] = tl;
+    __syncthreads();
+  }
+}
+
+// X(r0:r0+2s, 0:ncols) <- Q^T X (transpose = 1) or Q X (transpose = 0) with
+// Q = I - V T V^T: three small products, three barriers.  w1, w2: s x ncols scratch.
+__device__ void apply_set_wy(const double* v, const double* T, int s, double* X, int ldx, int r0,
+                             int ncols, int transpose, double* w1, double* w2) {
+  const int h = 2 * s;
+  cta_gemm_s(s, ncols, h, 1.0, v, h, true, X + r0, ldx, false, 0.0, w1, s);
+  cta_gemm_s(s, ncols, s, 1.0, T, s, transpose != 0, w1, s, false, 0.0, w2, s);
+  cta_gemm_s(h, ncols, s, -1.0, v, h, false, w2, s, false, 1.0, X + r0, ldx);
 }
 
 // ||X C||_F for s x s X (col-major, ldx) and C (col-major ld s).
@@ -413,9 +505,11 @@ __device__ void relation_complete(const SmallWs& w, int j, Shared& sh) {
   double* col = w.work;                   // (j+1)s x s, ld = ldH
   const double* Hj = w.H + (size_t)(j - 1) * s * ldH;
   cta_copy(col, ldH, Hj, ldH, (j + 1) * s, s);
+  double* w1 = w.work + (size_t)2 * w.ldH * s;   // s x s scratch (clear of col and of J's)
+  double* w2 = w1 + (size_t)s * s;
   for (int i = 1; i < j; ++i)
-    apply_set(w.refl + (size_t)(i - 1) * 2 * s * s, w.tau + (i - 1) * s, s, col, ldH, (i - 1) * s,
-              s, 1);
+    apply_set_wy(w.refl + (size_t)(i - 1) * 2 * s * s, w.Twy + (size_t)(i - 1) * s * s, s, col,
+                 ldH, (i - 1) * s, s, 1, w1, w2);
   // BFOM pieces (before reflector set j).
   cta_copy(w.Tfom, s, col + (j - 1) * s, ldH, s, s);
   cta_copy(w.ufom, ldH, col, ldH, (j - 1) * s, s);
@@ -424,14 +518,17 @@ __device__ void relation_complete(const SmallWs& w, int j, Shared& sh) {
   if (w.modification == 0) sing = warp_lu_solve(w.Tfom, w.gfom, s, w.cfom, sh.A, &sh.piv, &sh.flag2);
   // Reflector set j and the R factor's block column j.
   house_qr(col, ldH, (j - 1) * s, s, w.refl + (size_t)(j - 1) * 2 * s * s, w.tau + (j - 1) * s, sh.red);
+  build_wy_T(w.refl + (size_t)(j - 1) * 2 * s * s, w.tau + (j - 1) * s, s,
+             w.Twy + (size_t)(j - 1) * s * s, w1);
   cta_copy(w.Rbar + (size_t)(j - 1) * s * ldR, ldR, col, ldH, j * s, s);
-  apply_set(w.refl + (size_t)(j - 1) * 2 * s * s, w.tau + (j - 1) * s, s, w.g, ldg, (j - 1) * s, s, 1);
+  apply_set_wy(w.refl + (size_t)(j - 1) * 2 * s * s, w.Twy + (size_t)(j - 1) * s * s, s, w.g, ldg,
+               (j - 1) * s, s, 1, w1, w2);
   double est;
   if (w.modification == 1) {
     est = cta_norm_prod(w.g + j * s, ldg, w.Cfac, s, sh.red) / ctl->normB;
   } else if (!sing) {
     // ||H_{j+1,j} c C||_F
-    cta_gemm(s, s, s, 1.0, w.H + j * s + (size_t)(j - 1) * s * ldH, ldH, false, w.cfom, s, false, 0.0,
+    cta_gemm_s(s, s, s, 1.0, w.H + j * s + (size_t)(j - 1) * s * ldH, ldH, false, w.cfom, s, false, 0.0,
              sh.B, s);
     est = cta_norm_prod(sh.B, s, w.Cfac, s, sh.red) / ctl->normB;
   } else {
@@ -519,7 +616,7 @@ __device__ void step_pip(const SmallWs& w, int k, Shared& sh) {
   const double* G = w.G;  // ((k+1)s x s) row-major: element (i, c) at G[i*s + c]
   record_gram(w, G, (k + 1) * s, s);
   // S = Omega - Hc^T Hc ; Hc(i,c) = G[i*s+c] is, as a col-major matrix, Hc^T with ld s.
-  cta_gemm(s, s, ks, -1.0, G, s, false, G, s, true, 0.0, sh.A, s);
+  cta_gemm_s(s, s, ks, -1.0, G, s, false, G, s, true, 0.0, sh.A, s);
   for (int e = threadIdx.x; e < s * s; e += NT) {
     const int a = e % s, c = e / s;
     sh.A[a + c * s] += G[(ks + a) * s + c];
@@ -701,7 +798,7 @@ __device__ void step_ls(const SmallWs& w, int k, Shared& sh) {
   const double* G = w.G;
   record_gram(w, G, ks, cols);
   // Omega = Omega~ - Y^T Y.  Y(i,c) = G[i*cols + c] is Y^T col-major with ld cols.
-  cta_gemm(s, s, k1s, -1.0, G, cols, false, G, cols, true, 0.0, sh.A, s);
+  cta_gemm_s(s, s, k1s, -1.0, G, cols, false, G, cols, true, 0.0, sh.A, s);
   for (int e = threadIdx.x; e < s * s; e += NT) {
     const int a = e % s, c = e / s;
     sh.A[a + c * s] += G[(k1s + a) * cols + c];
@@ -723,7 +820,7 @@ __device__ void step_ls(const SmallWs& w, int k, Shared& sh) {
     Hkm1[i + c * ldH] = w.J[i + c * ldH] + G[i * cols + c];
   }
   // P = R^{-T} (P~ - Y^T Z):  sh.B = Y^T Z  (Y^T as col-major (s x k1s) from G, Z likewise)
-  cta_gemm(s, s, k1s, 1.0, G, cols, false, G + s, cols, true, 0.0, sh.B, s);
+  cta_gemm_s(s, s, k1s, 1.0, G, cols, false, G + s, cols, true, 0.0, sh.B, s);
   double* ZP = w.work;                // ks x s, ld ks
   for (int e = threadIdx.x; e < s * s; e += NT) {
     const int a = e % s, c = e / s;
@@ -806,27 +903,83 @@ __global__ void __launch_bounds__(NT) k_small_side(SmallWs w, int k) {
   __shared__ Shared sh;
   Ctl* ctl = w.ctl;
   if (*(volatile int*)&ctl->side_step != k) return;
-  const int s = w.s, ldH = w.ldH;
-  if (ctl->side_J) {
-    const int ks = k * s, k1s = (k - 1) * s;
-    double* tmp = w.work + 4 * (size_t)w.ldH * s;   // ks x s (clear of the relation scratch)
-    for (int e = threadIdx.x; e < ks * s; e += NT) {
-      const int r = e % ks, c = e / ks;
-      const int q0 = max(0, (r / s - 1) * s);
-      double a0 = 0.0, a1 = 0.0;
-      int q = q0;
-      for (; q + 1 < k1s; q += 2) {
-        a0 = fma(w.H[r + (size_t)q * ldH], w.saveY[q + c * k1s], a0);
-        a1 = fma(w.H[r + (size_t)(q + 1) * ldH], w.saveY[q + 1 + c * k1s], a1);
-      }
-      if (q < k1s) a0 = fma(w.H[r + (size_t)q * ldH], w.saveY[q + c * k1s], a0);
-      tmp[r + c * ks] = w.saveZP[r + c * ks] - (a0 + a1);
-    }
-    cta_copy(sh.R, s, w.saveR, s, s, s);
-    cta_trsm_right(tmp, ks, ks, sh.R, s);
-    cta_copy(w.J, ldH, tmp, ks, ks, s);
-  }
   relation_complete(w, ctl->side_rel, sh);
+}
+
+// BCGSI+LS: J = ([Z; P] - H_{1:k,1:k-1} Y) R^{-1} (Alg. 7 line 15), needed only by
+// the next iteration's small kernel.  Spread over many CTAs (the FP64 pipes of
+// several SMs): one lane group of S2 lanes per row of J; H_{1:k,1:k-1} is block
+// upper Hessenberg, so row block i only meets column blocks >= i-1; the row is
+// then multiplied by R^{-1} by forward substitution across the lane group.
+__global__ void __launch_bounds__(64) k_side_J(SmallWs w, int k, int S2) {
+  Ctl* ctl = w.ctl;
+  if (*(volatile int*)&ctl->side_step != k || !ctl->side_J) return;
+  extern __shared__ double jsm[];
+  const int s = w.s, ldH = w.ldH, ks = k * s, k1s = (k - 1) * s;
+  const int rows = blockDim.x / S2;                 // rows of J in this CTA
+  const int r0 = blockIdx.x * rows;
+  double* Ys = jsm;                                 // k1s x s
+  double* Hs = jsm + (size_t)k1s * s;               // rows x k1s
+  for (int e = threadIdx.x; e < k1s * s; e += blockDim.x) Ys[e] = w.saveY[e];
+  for (int e = threadIdx.x; e < rows * k1s; e += blockDim.x) {
+    const int rr = e % rows, q = e / rows;
+    Hs[rr + q * rows] = (r0 + rr < ks) ? w.H[(r0 + rr) + (size_t)q * ldH] : 0.0;
+  }
+  __syncthreads();
+  const int rl = threadIdx.x / S2, c = threadIdx.x % S2;
+  const int r = r0 + rl;
+  const bool live = r < ks && c < s;
+  double t = 0.0;
+  if (live) {
+    const int q0 = max(0, (r / s - 1) * s);
+    const double* Yc = Ys + (size_t)c * k1s;
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    int q = q0;
+    for (; q + 3 < k1s; q += 4) {
+      a0 = fma(Hs[rl + q * rows], Yc[q], a0);
+      a1 = fma(Hs[rl + (q + 1) * rows], Yc[q + 1], a1);
+      a2 = fma(Hs[rl + (q + 2) * rows], Yc[q + 2], a2);
+      a3 = fma(Hs[rl + (q + 3) * rows], Yc[q + 3], a3);
+    }
+    for (; q < k1s; ++q) a0 = fma(Hs[rl + q * rows], Yc[q], a0);
+    t = w.saveZP[r + c * ks] - ((a0 + a1) + (a2 + a3));
+  }
+  const double rinv = (c < s) ? 1.0 / w.saveR[c + c * s] : 0.0;
+  for (int q = 0; q < s; ++q) {
+    const double vq = __shfl_sync(0xffffffffu, t * rinv, q, S2);
+    if (c == q) t = vq;
+    else if (c > q && c < s) t = fma(-vq, w.saveR[q + c * s], t);
+  }
+  if (live) w.J[r + c * ldH] = t;
+}
+
+// The same product without shared-memory staging, for Y too large to stage.
+__global__ void __launch_bounds__(256) k_side_J_glob(SmallWs w, int k, int S2) {
+  Ctl* ctl = w.ctl;
+  if (*(volatile int*)&ctl->side_step != k || !ctl->side_J) return;
+  const int s = w.s, ldH = w.ldH, ks = k * s, k1s = (k - 1) * s;
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  const int r = idx / S2, c = idx % S2;
+  const bool live = r < ks && c < s;
+  double t = 0.0;
+  if (live) {
+    const int q0 = max(0, (r / s - 1) * s);
+    double a0 = 0.0, a1 = 0.0;
+    int q = q0;
+    for (; q + 1 < k1s; q += 2) {
+      a0 = fma(w.H[r + (size_t)q * ldH], w.saveY[q + (size_t)c * k1s], a0);
+      a1 = fma(w.H[r + (size_t)(q + 1) * ldH], w.saveY[q + 1 + (size_t)c * k1s], a1);
+    }
+    if (q < k1s) a0 = fma(w.H[r + (size_t)q * ldH], w.saveY[q + (size_t)c * k1s], a0);
+    t = w.saveZP[r + c * ks] - (a0 + a1);
+  }
+  const double rinv = (c < s) ? 1.0 / w.saveR[c + c * s] : 0.0;
+  for (int q = 0; q < s; ++q) {
+    const double vq = __shfl_sync(0xffffffffu, t * rinv, q, S2);
+    if (c == q) t = vq;
+    else if (c > q && c < s) t = fma(-vq, w.saveR[q + c * s], t);
+  }
+  if (live) w.J[r + c * ldH] = t;
 }
 
 // ---------------------------------------------------------------- cycle end
@@ -853,34 +1006,42 @@ __global__ void __launch_bounds__(NT) k_small_end(SmallWs w) {
     cta_copy(Xi + (j - 1) * s, ldH, w.cfom, s, s, s);
     cta_copy(Xi, ldH, w.g, ldg, (j - 1) * s, s);
     // g_{1:j-1} - u c
-    cta_gemm((j - 1) * s, s, s, -1.0, w.ufom, ldH, false, w.cfom, s, false, 1.0, Xi, ldH);
+    cta_gemm_s((j - 1) * s, s, s, -1.0, w.ufom, ldH, false, w.cfom, s, false, 1.0, Xi, ldH);
   }
   // Block back substitution with Rbar (BGMRES: blocks 1..j; BFOM: blocks 1..j-1).
+  // The inverses of the upper-triangular diagonal blocks are formed first, all
+  // blocks at once (one thread per block column: back substitution for R_ii x = e_c),
+  // so that each block step is two small products.
   const int top = (w.modification == 1) ? j : j - 1;
+  double* Rinv = w.work + (size_t)4 * w.ldH * s;  // top blocks of s x s (clear of Ylast/XiC/w1/w2)
+  for (int e = threadIdx.x; e < top * s; e += NT) {
+    const int i = e / s, c = e % s;  // block i (0-based), column c
+    const double* Rii = w.Rbar + (size_t)i * s + (size_t)i * s * ldR;
+    double* Ri = Rinv + (size_t)i * s * s;
+    for (int r = s - 1; r >= 0; --r) {
+      double acc = (r == c) ? 1.0 : 0.0;
+      if (r < c) {
+        for (int p2 = r + 1; p2 <= c; ++p2) acc = fma(-Rii[r + (size_t)p2 * ldR], Ri[p2 + c * s], acc);
+      }
+      Ri[r + c * s] = (r <= c) ? acc / Rii[r + (size_t)r * ldR] : 0.0;
+    }
+  }
+  __syncthreads();
   for (int i = top; i >= 1; --i) {
     double* Xii = Xi + (i - 1) * s;
     const int rest = top - i;  // blocks i+1..top already known
     if (rest > 0)
-      cta_gemm(s, s, rest * s, -1.0, w.Rbar + (i - 1) * s + (size_t)i * s * ldR, ldR, false,
+      cta_gemm_s(s, s, rest * s, -1.0, w.Rbar + (i - 1) * s + (size_t)i * s * ldR, ldR, false,
                Xi + i * s, ldH, false, 1.0, Xii, ldH);
-    // Xii <- Rbar_ii^{-1} Xii  (upper triangular): copy Rbar_ii, solve column by column.
-    cta_copy(sh.R, s, w.Rbar + (i - 1) * s + (size_t)(i - 1) * s * ldR, ldR, s, s);
-    for (int q = s - 1; q >= 0; --q) {
-      for (int c = threadIdx.x; c < s; c += NT) Xii[q + c * ldH] = Xii[q + c * ldH] / sh.R[q + q * s];
-      __syncthreads();
-      for (int e = threadIdx.x; e < q * s; e += NT) {
-        const int r = e % q, c = e / q;
-        Xii[r + c * ldH] = fma(-sh.R[r + q * s], Xii[q + c * ldH], Xii[r + c * ldH]);
-      }
-      __syncthreads();
-    }
+    cta_gemm_s(s, s, s, 1.0, Rinv + (size_t)(i - 1) * s * s, s, false, Xii, ldH, false, 0.0, sh.B, s);
+    cta_copy(Xii, ldH, sh.B, s, s, s);
   }
   // c = Xi_j (s x s) -> sh.A
   cta_copy(sh.A, s, Xi + (j - 1) * s, ldH, s, s);
   // M (BGMRES): Q_{1..j-1} [0; T^{-T} S], S = H_{j+1,j}^T H_{j+1,j}
   const double* Hsub = w.H + js + (size_t)(j - 1) * s * ldH;
   if (w.modification == 1) {
-    cta_gemm(s, s, s, 1.0, Hsub, ldH, true, Hsub, ldH, false, 0.0, sh.B, s);
+    cta_gemm_s(s, s, s, 1.0, Hsub, ldH, true, Hsub, ldH, false, 0.0, sh.B, s);
     // T^{-T} S: solve T^T Y = S  -> LU solve with T^T.
     for (int e = threadIdx.x; e < s * s; e += NT) {
       const int a = e % s, c = e / s;
@@ -894,12 +1055,15 @@ __global__ void __launch_bounds__(NT) k_small_end(SmallWs w) {
       Mv[r + c * ldH] = (r >= (j - 1) * s) ? Ylast[(r - (j - 1) * s) + c * s] : 0.0;
     }
     __syncthreads();
+    double* w1 = w.work + (size_t)2 * w.ldH * s + 2 * (size_t)s * s;
+    double* w2 = w1 + (size_t)s * s;
     for (int i = j - 1; i >= 1; --i)
-      apply_set(w.refl + (size_t)(i - 1) * 2 * s * s, w.tau + (i - 1) * s, s, Mv, ldH, (i - 1) * s, s, 0);
+      apply_set_wy(w.refl + (size_t)(i - 1) * 2 * s * s, w.Twy + (size_t)(i - 1) * s * s, s, Mv,
+                   ldH, (i - 1) * s, s, 0, w1, w2);
   }
   // Coefficients.  Xi C -> coef1 blocks 0..j-1; coef1 block j = 0; block j+1 (X) = I.
   double* XiC = w.work + 2 * s * s;  // js x s, ld js
-  cta_gemm(js, s, s, 1.0, Xi, ldH, false, w.Cfac, s, false, 0.0, XiC, js);
+  cta_gemm_s(js, s, s, 1.0, Xi, ldH, false, w.Cfac, s, false, 0.0, XiC, js);
   for (int b = 0; b < j; ++b) {
     put_coef(w.coef1, b, s, XiC + b * s, js, 1.0);
     if (w.modification == 1) put_coef(w.coef2, b, s, Mv + b * s, ldH, 1.0);
@@ -910,7 +1074,7 @@ __global__ void __launch_bounds__(NT) k_small_end(SmallWs w) {
   put_coef(w.coef1, j + 1, s, nullptr, 0, 1.0);
   put_zero_coef(w.coef2, j + 1, s);
   // C <- c C
-  cta_gemm(s, s, s, 1.0, sh.A, s, false, w.Cfac, s, false, 0.0, sh.B, s);
+  cta_gemm_s(s, s, s, 1.0, sh.A, s, false, w.Cfac, s, false, 0.0, sh.B, s);
   cta_copy(w.Cfac, s, sh.B, s, s, s);
   if (threadIdx.x == 0) ctl->update_step = LSBA_END_STEP;
 }
@@ -924,8 +1088,20 @@ __global__ void k_true_relres(const double* G, int s, Ctl* ctl) {
   }
 }
 
+static void small_attrs() {
+  static bool done = false;
+  if (done) return;
+  const int bytes = SMALL_ARENA_DOUBLES * sizeof(double);
+  cudaFuncSetAttribute(k_small_start, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  cudaFuncSetAttribute(k_small_step, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  cudaFuncSetAttribute(k_small_side, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  cudaFuncSetAttribute(k_small_end, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  done = true;
+}
+
 void launch_small_start(cudaStream_t st, const SmallWs& w, int flags) {
-  k_small_start<<<1, NT, 0, st>>>(w, flags);
+  small_attrs();
+  k_small_start<<<1, NT, SMALL_ARENA_DOUBLES * sizeof(double), st>>>(w, flags);
 }
 void launch_true_relres(cudaStream_t st, const double* G, int s, Ctl* ctl) {
   k_true_relres<<<1, 32, 0, st>>>(G, s, ctl);
@@ -943,13 +1119,31 @@ void launch_outer_norm(cudaStream_t st, const double* G, int s, Ctl* ctl, int mo
   k_outer_norm<<<1, 32, 0, st>>>(G, s, ctl, mode);
 }
 void launch_small_step(cudaStream_t st, const SmallWs& w, int k, int phase) {
-  k_small_step<<<1, NT, 0, st>>>(w, k, phase);
+  k_small_step<<<1, NT, SMALL_ARENA_DOUBLES * sizeof(double), st>>>(w, k, phase);
 }
 void launch_small_side(cudaStream_t st, const SmallWs& w, int k) {
-  k_small_side<<<1, NT, 0, st>>>(w, k);
+  if (w.skel == SK_LS && k >= 2) {
+    int S2 = 1;
+    while (S2 < w.s) S2 <<= 1;
+    const int rows = 64 / S2 > 0 ? 64 / S2 : 1;
+    const int ctas = (k * w.s + rows - 1) / rows;
+    const size_t smem = sizeof(double) * ((size_t)(k - 1) * w.s * w.s + (size_t)rows * (k - 1) * w.s);
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(k_side_J, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+      attr = true;
+    }
+    if (smem <= 200 * 1024) {
+      k_side_J<<<ctas, 64, smem, st>>>(w, k, S2);
+    } else {
+      const int threads = k * w.s * S2;
+      k_side_J_glob<<<(threads + 255) / 256, 256, 0, st>>>(w, k, S2);
+    }
+  }
+  k_small_side<<<1, NT, SMALL_ARENA_DOUBLES * sizeof(double), st>>>(w, k);
 }
 void launch_small_end(cudaStream_t st, const SmallWs& w) {
-  k_small_end<<<1, NT, 0, st>>>(w);
+  k_small_end<<<1, NT, SMALL_ARENA_DOUBLES * sizeof(double), st>>>(w);
 }
 
 }  // namespace lsba

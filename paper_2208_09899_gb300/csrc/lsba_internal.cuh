@@ -68,6 +68,7 @@ struct SmallWs {
   double* Rbar;        // QR of the block Hessenberg: R factor, ldR x ldR col-major
   double* refl;        // Householder vectors per block column: [(m+1)][2s x s] col-major
   double* tau;         // [(m+1)][s]
+  double* Twy;         // compact WY factor per reflector set: [(m+1)][s x s] col-major
   double* g;           // transformed right-hand side E_1 Beta, (m+2)s x s col-major, ld (m+2)s
   double* Tfom;        // s x s col-major: last block of H_j's last column after j-1 reflector sets
   double* gfom;        // s x s: g block j before reflector set j
