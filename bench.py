@@ -91,6 +91,25 @@ def algorithmic_cost(n, nnz, s, m, skeleton=SKELETON):
     return by, fl
 
 
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "roofline_traffic.json")
+
+
+def captured_traffic(kernel_key, bytes_per_launch):
+    """DRAM bytes per launch of the dominant kernel from the committed ncu
+    capture (profiles/roofline_traffic.json), scaled from the captured launch to
+    the average launch by algorithmic bytes; None if absent or if the kernel's
+    source file changed since the capture."""
+    import hashlib
+    try:
+        rec = json.load(open(TRAFFIC_FILE))[kernel_key]
+        src = open(os.path.join(ROOT, "paper_2208_09899_gb300", "csrc", rec["source"]), "rb").read()
+        if hashlib.sha256(src).hexdigest() != rec["source_sha256"]:
+            return None
+        return rec["dram_bytes"] * bytes_per_launch / rec["algorithmic_bytes"]
+    except Exception:
+        return None
+
+
 def sample_clocks_start(path):
     try:
         f = open(path, "w")
@@ -98,7 +117,7 @@ def sample_clocks_start(path):
             ["nvidia-smi", "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,"
              "clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
-             "clocks_event_reasons.sw_power_cap", "--format=csv,noheader,nounits", "-lms", "200"],
+             "clocks_event_reasons.sw_power_cap", "--format=csv,noheader,nounits", "-lms", "50"],
             stdout=f, stderr=subprocess.DEVNULL)
         return p, f
     except Exception:
@@ -290,6 +309,8 @@ def main():
     def step():
         sv.solve(dA, dB, dX, M, 1e-30, SKELETON)
 
+    clk_path = os.path.join(tempfile.gettempdir(), f"lsba_clocks_{os.getpid()}.csv")
+    proc, fh = sample_clocks_start(clk_path)
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize(dev)
@@ -297,8 +318,6 @@ def main():
     assert st0["cycles"] == 1 and st0["steps"] == M, st0
     sv.reset_profile()
 
-    clk_path = os.path.join(tempfile.gettempdir(), f"lsba_clocks_{os.getpid()}.csv")
-    proc, fh = sample_clocks_start(clk_path)
     if pg:
         pg.barrier()
     torch.cuda.synchronize(dev)
@@ -339,7 +358,8 @@ def main():
                    "update": ("k_coef_df+k_update_df" if is_df else "k_update"),
                    "spmm": f"k_spmm{suffix}"}[dom],
         "bound": "alu", "achieved": achieved_tflops, "peak": peak, "unit": "TFLOP/s",
-        "frac": achieved_tflops / peak, "traffic": None,
+        "frac": achieved_tflops / peak,
+        "traffic": captured_traffic(dom + ("_df" if is_df else ""), by[dom] / max(dom_launches, 1)),
         "peak_source": ("derived: double-float FMA = 13 FP32 ops; 152 SMs x 128 lanes x 2.07 GHz"
                         " / 13 x 2 flop (FP64-equivalent)") if is_df else
                        "nominal FP64 DFMA rate (1.25 TFLOP/s); the FP64 probe measured 1.00",
