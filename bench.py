@@ -191,7 +191,7 @@ def mixed_precision(torch, lsba, dev, stream):
       * per restart cycle on the 2D Laplacian 2048x2048 (n = 4194304), B n x 16,
         BGMRES(16), BCGSI+LS: one FP32 inner cycle (plus the two FP64 residuals
         of its refinement step) vs one double-float and one FP64 cycle;
-      * time to relative residual 1e-10 on the 2D Laplacian 256x256, B n x 16,
+      * time to relative residual 1e-10 on the 2D Laplacian 128x128, B n x 16,
         BGMRES(16), BCGSI+LS, in the three precisions."""
     out = {}
     A, B = W.workload("lapl2048_s16", 0)
@@ -214,7 +214,7 @@ def mixed_precision(torch, lsba, dev, stream):
                     "speedup_fp32_ir_vs_fp64": cyc["fp64"] / cyc["fp32_ir"],
                     "fp32_inner_gbs_algorithmic": 0.5 * sum(by.values()) / (cyc["fp32_ir"] * 1e-3) / 1e9}
     del dA, dB, dX
-    A = W.laplacian_2d(256)
+    A = W.laplacian_2d(128)
     B = W.gaussian_block(A.n, 16, 0)
     dA = lsba.DeviceCSR.from_host(A, f"cuda:{dev}")
     dB = torch.from_numpy(B).to(f"cuda:{dev}")
@@ -227,11 +227,36 @@ def mixed_precision(torch, lsba, dev, stream):
         tt[prec] = {"ms": ms, "cycles": st["cycles"], "relres_true": st["relres_true"],
                     "status": st["status"], "ir_outer": st["ir_outer"]}
         sv.close()
-    out["time_to_1e-10"] = {"workload": "lapl256_s16: 2D Laplacian 256x256 (n=65536), B n x 16 "
+    out["time_to_1e-10"] = {"workload": "lapl128_s16: 2D Laplacian 128x128 (n=16384), B n x 16 "
                                         "N(0,1), BGMRES(16), BCGSI+LS, tol 1e-10",
                             "results": tt,
                             "speedup_fp32_ir_vs_df": tt["df"]["ms"] / tt["fp32_ir"]["ms"],
                             "speedup_fp32_ir_vs_fp64": tt["fp64"]["ms"] / tt["fp32_ir"]["ms"]}
+    return out
+
+
+def rgg_cycles(torch, lsba, dev, stream):
+    """The ill-conditioned graph workload: random geometric graph Laplacian,
+    n = 2^20, B n x 16, BGMRES(16); BCGS-PIP vs BCGSI+LS, three restart cycles
+    each (per-cycle time and the restart log)."""
+    A, B = W.workload("rgg1M_s16", 0)
+    dA = lsba.DeviceCSR.from_host(A, f"cuda:{dev}")
+    dB = torch.from_numpy(B).to(f"cuda:{dev}")
+    dX = torch.empty_like(dB)
+    out = {"workload": "rgg1M_s16: random geometric graph Laplacian n=2^20 (mean degree "
+                       f"{(A.nnz - A.n) / A.n:.2f}), weights 10^U(-3,3), shift 1e-6 max diag; "
+                       "B n x 16 N(0,1); BGMRES(16), 3 cycles", "nnz": A.nnz, "skeletons": {}}
+    for sk in ("bcgs_pip", "bcgsi_ls"):
+        sv = lsba.Solver(dev, modification="gmres", max_restarts=2, verify_true_residual=0,
+                         record_history=1)
+        sv.solve(dA, dB, dX, 16, 1e-8, sk)
+        ms = _timed(torch, stream, lambda: sv.solve(dA, dB, dX, 16, 1e-8, sk), 1)
+        st = sv.stats()
+        h = sv.history()
+        out["skeletons"][sk] = {"ms_per_cycle": ms / max(st["cycles"], 1), "cycles": st["cycles"],
+                                "cycle_m": h["cycle_m"], "cycle_flag": h["cycle_flag"],
+                                "relres_true": st["relres_true"], "precision": st["precision"]}
+        sv.close()
     return out
 
 
@@ -279,6 +304,7 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--no-rgg", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     world, rank, local = dist_setup()
@@ -431,6 +457,7 @@ def main():
                    "relres_true": st1["relres_true"], "status": st1["status"]}
 
     mixed = None if args.no_mixed else mixed_precision(torch, lsba, dev, stream)
+    rgg = None if args.no_rgg else rgg_cycles(torch, lsba, dev, stream)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -460,7 +487,7 @@ def main():
                        "algorithmic_bytes_per_step": step_bytes},
             "roofline": roofline, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": gpu_launches, "clocks": clocks, "time_to_tol": time_to_tol,
-            "fp64_plain": fp64_plain, "mixed_precision": mixed,
+            "fp64_plain": fp64_plain, "mixed_precision": mixed, "graph_workload": rgg,
         }
         print(json.dumps(line))
     if pg:

@@ -98,7 +98,8 @@ def test_combine_matches_oracle(env, s, nin, n, tri):
     assert _rel(dO.cpu().numpy(), ref) <= 1e-13
 
 
-def _compare_solve(lsba, A, B, m, tol, sk, mod, max_restarts=50, first_cycle_tol=TOL_GRAM, **kw):
+def _compare_solve(lsba, A, B, m, tol, sk, mod, max_restarts=50, first_cycle_tol=TOL_GRAM,
+                   x_tol=TOL_X, **kw):
     X, st, hist = lsba.solve(A, B, m, tol, sk, device=0, modification=mod,
                              max_restarts=max_restarts, record_history=True, **kw)
     inject = []
@@ -137,7 +138,7 @@ def _compare_solve(lsba, A, B, m, tol, sk, mod, max_restarts=50, first_cycle_tol
     ok = np.isfinite(est_ref)
     assert np.allclose(hist["est"][ok], est_ref[ok], rtol=1e-6, atol=0)
     # Final X and residuals.
-    assert _rel(X, ref.X) <= TOL_X
+    assert _rel(X, ref.X) <= x_tol
     if ref.status == O.OK:
         assert st["relres_true"] <= tol and ref.relres_true <= tol
     return X, st, hist, ref
@@ -295,3 +296,20 @@ def test_fp32_inner_fp64_refinement_laplacian_error_vs_oracle(env):
           f"{st['relres_true']:.2e} error vs oracle {err:.2e}")
     assert st["status"] == lsba.LSBA_OK and st["relres_true"] <= 1e-10
     assert err <= kappa * (st["relres_true"] + ref.relres_true)
+
+
+@pytest.mark.parametrize("sk", ["bcgs_pip", "bcgsi_ls"])
+def test_rgg_graph_laplacian_restart_log(env, sk):
+    """Random geometric graph Laplacian (log-uniform weights 1e-3..1e3, shift
+    1e-6 max diag), n = 2^14, B n x 16, BGMRES(16): three unconverged cycles with
+    the oracle's restart log and first-cycle Gram/Hessenberg within 1e-11.  The
+    1e-8 bound on X applies to converged solves; the iterate after three
+    unconverged cycles on this matrix carries rounding differences amplified by
+    its conditioning (measured 1.2e-8 for BCGSI+LS in double-float, 5.9e-8 for
+    BCGS-PIP), so it is checked at 1e-6."""
+    torch, lsba = env
+    A = W.rgg_laplacian(1 << 14, 0)
+    B = W.gaussian_block(A.n, 16, 1000)
+    X, st, hist, ref = _compare_solve(lsba, A, B, 16, 1e-8, sk, "gmres", max_restarts=2,
+                                      x_tol=1e-6)
+    assert st["status"] == lsba.LSBA_NOT_CONVERGED and st["cycles"] == 3
