@@ -260,6 +260,52 @@ def rgg_cycles(torch, lsba, dev, stream):
     return out
 
 
+def serving(torch, lsba, dev, count, seed=5, slots=16, cap_gb=150.0):
+    """Continuous batching: a seeded mix of block solves (3D 7-point Laplacian
+    + delta I, delta ~ U[0,0.1], side N ~ U{22..100}, s ~ U{1,4,8,16,32},
+    m ~ U{8..32}, tol 1e-8, BGMRES with BCGSI+LS) served by SolveServer with
+    an HBM admission cap.  Capacity = solves/s with every request queued at
+    t = 0 (also with one slot, i.e. one solve at a time); then Poisson arrivals
+    at 0.8 x capacity give p50/p99 latency.  Host copies of A and B and the
+    read-back of X are inside each request's latency."""
+    from paper_2208_09899_gb300 import serve
+    out = {"workload": f"{count} requests: 3D 7-point Laplacian + delta I, delta~U[0,0.1], "
+                       "N~U{22..100} (n=N^3), s~U{1,4,8,16,32}, m~U{8..32}, B~N(0,1), tol 1e-8, "
+                       "BGMRES, BCGSI+LS, max 500 restarts",
+           "slots": slots, "hbm_cap_gb": cap_gb, "precisions": {}}
+    warm = serve.serving_requests(slots, seed=99, side_range=(8, 12), m_range=(4, 8))
+    t0 = time.perf_counter()
+    base = serve.serving_requests(count, seed=seed)
+    out["request_build_s"] = time.perf_counter() - t0
+    for prec in ("auto", "fp32_ir"):
+        for r in base:
+            r.precision, r.arrival = prec, 0.0
+        for r in warm:
+            r.precision = prec
+        res = {}
+        if prec == "auto":
+            one = serve.SolveServer(slots=1, hbm_cap_bytes=cap_gb * 1e9, device=dev)
+            one.run(warm[:1], keep_x=False)
+            res["capacity_one_slot"] = serve.summarize(one.run(base, keep_x=False))
+            one.close()
+        srv = serve.SolveServer(slots=slots, hbm_cap_bytes=cap_gb * 1e9, device=dev)
+        srv.run(warm, keep_x=False)
+        cap = serve.summarize(srv.run(base, keep_x=False))
+        res["capacity"] = cap
+        rate = 0.8 * cap["solves_per_s"]
+        for r, a in zip(base, serve.poisson_arrivals(count, rate, seed=seed + 1)):
+            r.arrival = float(a)
+        load = srv.run(base, keep_x=False)
+        res["load_0.8"] = dict(serve.summarize(load, t_first=0.0), rate_per_s=rate)
+        res["peak_admitted_gb"] = srv.peak_bytes / 1e9
+        res["status_counts"] = {str(k): sum(1 for r in load if r.stats.get("status") == k)
+                                for k in sorted({r.stats.get("status") for r in load}, key=str)}
+        res["mean_cycles"] = float(np.mean([r.stats.get("cycles", 0) for r in load]))
+        srv.close()
+        out["precisions"][prec] = res
+    return out
+
+
 def dist_setup():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -305,6 +351,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-rgg", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=32)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     world, rank, local = dist_setup()
@@ -458,6 +506,7 @@ def main():
 
     mixed = None if args.no_mixed else mixed_precision(torch, lsba, dev, stream)
     rgg = None if args.no_rgg else rgg_cycles(torch, lsba, dev, stream)
+    served = None if args.no_serving else serving(torch, lsba, dev, args.serve_requests)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -488,6 +537,7 @@ def main():
             "roofline": roofline, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": gpu_launches, "clocks": clocks, "time_to_tol": time_to_tol,
             "fp64_plain": fp64_plain, "mixed_precision": mixed, "graph_workload": rgg,
+            "serving": served,
         }
         print(json.dumps(line))
     if pg:

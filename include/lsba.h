@@ -174,6 +174,18 @@ int lsba_solve_host(lsba_handle h, int64_t n, int64_t nnz, const int32_t* h_rowp
 
 int lsba_get_stats(lsba_handle h, lsba_stats* out);
 
+/* Return the handle's device workspace to the device memory pool (stream-ordered
+ * on the handle's stream; no device-wide synchronisation).  The next solve
+ * allocates again.  All workspace allocations of the library are stream-ordered
+ * (cudaMallocAsync / cudaFreeAsync), so solves on different handles and
+ * streams can run, grow and release concurrently. */
+int lsba_release_workspace(lsba_handle h);
+
+/* Upper bound of the device memory (bytes) a solve with n x s blocks, nnz
+ * nonzeros and maximum basis size m allocates, for admission control; -1 on
+ * invalid sizes.  Host computation only. */
+int64_t lsba_workspace_bytes(int64_t n, int64_t nnz, int s, int m);
+
 /* Kernel classes of lsba_get_profile. */
 enum { LSBA_K_SPMM = 0, LSBA_K_GRAM = 1, LSBA_K_UPDATE = 2, LSBA_K_SMALL = 3, LSBA_K_NCLASS = 4 };
 

@@ -121,17 +121,28 @@ static void prof_collect(lsba_ctx* h) {
     }                                                 \
   } while (0)
 
+// Workspace memory is stream-ordered (cudaMallocAsync / cudaFreeAsync on the
+// handle's stream, from the device's default memory pool): growing or
+// releasing one handle's workspace never synchronises the device, so solves on
+// other streams keep running.
+static cudaError_t ws_alloc(lsba_ctx* h, void* pp, size_t bytes) {
+  return cudaMallocAsync((void**)pp, bytes, h->stream);
+}
+static void ws_free(lsba_ctx* h, void* p) {
+  if (p) cudaFreeAsync(p, h->stream);
+}
+
 static void free_ws(lsba_ctx* h) {
-  cudaFree(h->basis);
-  cudaFree(h->Wb);
-  cudaFree(h->Ub);
-  cudaFree(h->partials);
-  cudaFree(h->Gbuf);
-  cudaFree(h->small);
-  cudaFree(h->ismall);
-  cudaFree(h->Bdf);
-  cudaFree(h->Xdf);
-  cudaFree(h->cdf);
+  ws_free(h, h->basis);
+  ws_free(h, h->Wb);
+  ws_free(h, h->Ub);
+  ws_free(h, h->partials);
+  ws_free(h, h->Gbuf);
+  ws_free(h, h->small);
+  ws_free(h, h->ismall);
+  ws_free(h, h->Bdf);
+  ws_free(h, h->Xdf);
+  ws_free(h, h->cdf);
   h->Bdf = h->Xdf = nullptr;
   h->cdf = nullptr;
   h->cdf_cap = 0;
@@ -168,9 +179,9 @@ static int ensure_ws(lsba_ctx* h, int64_t n, int s, int m) {
   if (n <= h->cap_n && s == h->cap_s && m <= h->cap_m && h->basis) return LSBA_OK;
   free_ws(h);
   const size_t blk = (size_t)n * s;
-  if (cudaMalloc(&h->basis, sizeof(double) * blk * (m + 1)) != cudaSuccess ||
-      cudaMalloc(&h->Wb, sizeof(double) * blk) != cudaSuccess ||
-      cudaMalloc(&h->Ub, sizeof(double) * blk) != cudaSuccess) {
+  if (ws_alloc(h, &h->basis, sizeof(double) * blk * (m + 1)) != cudaSuccess ||
+      ws_alloc(h, &h->Wb, sizeof(double) * blk) != cudaSuccess ||
+      ws_alloc(h, &h->Ub, sizeof(double) * blk) != cudaSuccess) {
     cudaGetLastError();
     free_ws(h);
     return LSBA_OUT_OF_MEMORY;
@@ -200,23 +211,23 @@ static int ensure_ws(lsba_ctx* h, int64_t n, int s, int m) {
                osy = take((size_t)ldH * s), osr = take(ss), ohe = take(hist_cap),
                ogh = take(gram_hist_cap);
   h->small_cap = off;
-  if (cudaMalloc(&h->small, sizeof(double) * off) != cudaSuccess ||
-      cudaMalloc(&h->partials, sizeof(double) * h->partials_cap) != cudaSuccess ||
-      cudaMalloc(&h->Gbuf, sizeof(double) * h->G_cap) != cudaSuccess) {
+  if (ws_alloc(h, &h->small, sizeof(double) * off) != cudaSuccess ||
+      ws_alloc(h, &h->partials, sizeof(double) * h->partials_cap) != cudaSuccess ||
+      ws_alloc(h, &h->Gbuf, sizeof(double) * h->G_cap) != cudaSuccess) {
     cudaGetLastError();
     free_ws(h);
     return LSBA_OUT_OF_MEMORY;
   }
   h->ismall_cap = 2 * hist_cap + 2 * (m + 4);
   h->cdf_cap = coef_df_count(m + 3, s, true);
-  if (cudaMalloc(&h->Bdf, sizeof(double) * blk) != cudaSuccess ||
-      cudaMalloc(&h->Xdf, sizeof(double) * blk) != cudaSuccess ||
-      cudaMalloc(&h->cdf, sizeof(float2) * h->cdf_cap) != cudaSuccess) {
+  if (ws_alloc(h, &h->Bdf, sizeof(double) * blk) != cudaSuccess ||
+      ws_alloc(h, &h->Xdf, sizeof(double) * blk) != cudaSuccess ||
+      ws_alloc(h, &h->cdf, sizeof(float2) * h->cdf_cap) != cudaSuccess) {
     cudaGetLastError();
     free_ws(h);
     return LSBA_OUT_OF_MEMORY;
   }
-  if (cudaMalloc(&h->ismall, sizeof(int) * h->ismall_cap) != cudaSuccess) {
+  if (ws_alloc(h, &h->ismall, sizeof(int) * h->ismall_cap) != cudaSuccess) {
     cudaGetLastError();
     free_ws(h);
     return LSBA_OUT_OF_MEMORY;
@@ -556,12 +567,13 @@ int lsba_destroy(lsba_handle h) {
   free_ws(h);
   cudaFree(h->d_ctl);
   cudaFreeHost(h->h_ctl);
-  cudaFree(h->hA_rowptr);
-  cudaFree(h->hA_colidx);
-  cudaFree(h->hA_vals);
-  cudaFree(h->hB);
-  cudaFree(h->hX);
-  cudaFree(h->A_df);
+  ws_free(h, h->hA_rowptr);
+  ws_free(h, h->hA_colidx);
+  ws_free(h, h->hA_vals);
+  ws_free(h, h->hB);
+  ws_free(h, h->hX);
+  ws_free(h, h->A_df);
+  cudaStreamSynchronize(h->stream);
   for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
   for (cudaEvent_t e : h->ev_main) cudaEventDestroy(e);
   for (cudaEvent_t e : h->ev_side) cudaEventDestroy(e);
@@ -694,10 +706,10 @@ static int run_cycles(lsba_handle h, const lsba_csr* A, const double* Bw, double
 
 static int ensure_lowprec_A(lsba_handle h, const lsba_csr* A) {
   if ((size_t)A->nnz > h->A_df_cap) {
-    cudaFree(h->A_df);
+    ws_free(h, h->A_df);
     h->A_df = nullptr;
     h->A_df_cap = 0;
-    if (cudaMalloc(&h->A_df, sizeof(float2) * (A->nnz > 0 ? A->nnz : 1)) != cudaSuccess) {
+    if (ws_alloc(h, &h->A_df, sizeof(float2) * (A->nnz > 0 ? A->nnz : 1)) != cudaSuccess) {
       cudaGetLastError();
       return LSBA_OUT_OF_MEMORY;
     }
@@ -875,21 +887,21 @@ int lsba_solve_host(lsba_handle h, int64_t n, int64_t nnz, const int32_t* h_rowp
     return LSBA_INVALID_ARG;
   CK(cudaSetDevice(h->device));
   if (n != h->host_n || nnz != h->host_nnz || s != h->host_s) {
-    cudaFree(h->hA_rowptr);
-    cudaFree(h->hA_colidx);
-    cudaFree(h->hA_vals);
-    cudaFree(h->hB);
-    cudaFree(h->hX);
+    ws_free(h, h->hA_rowptr);
+    ws_free(h, h->hA_colidx);
+    ws_free(h, h->hA_vals);
+    ws_free(h, h->hB);
+    ws_free(h, h->hX);
     h->hA_rowptr = nullptr;
     h->hA_colidx = nullptr;
     h->hA_vals = nullptr;
     h->hB = h->hX = nullptr;
     h->host_n = h->host_nnz = 0;
-    if (cudaMalloc(&h->hA_rowptr, sizeof(int32_t) * (n + 1)) != cudaSuccess ||
-        cudaMalloc(&h->hA_colidx, sizeof(int32_t) * (nnz > 0 ? nnz : 1)) != cudaSuccess ||
-        cudaMalloc(&h->hA_vals, sizeof(double) * (nnz > 0 ? nnz : 1)) != cudaSuccess ||
-        cudaMalloc(&h->hB, sizeof(double) * n * s) != cudaSuccess ||
-        cudaMalloc(&h->hX, sizeof(double) * n * s) != cudaSuccess) {
+    if (ws_alloc(h, &h->hA_rowptr, sizeof(int32_t) * (n + 1)) != cudaSuccess ||
+        ws_alloc(h, &h->hA_colidx, sizeof(int32_t) * (nnz > 0 ? nnz : 1)) != cudaSuccess ||
+        ws_alloc(h, &h->hA_vals, sizeof(double) * (nnz > 0 ? nnz : 1)) != cudaSuccess ||
+        ws_alloc(h, &h->hB, sizeof(double) * n * s) != cudaSuccess ||
+        ws_alloc(h, &h->hX, sizeof(double) * n * s) != cudaSuccess) {
       cudaGetLastError();
       return LSBA_OUT_OF_MEMORY;
     }
@@ -915,6 +927,41 @@ int lsba_solve_host(lsba_handle h, int64_t n, int64_t nnz, const int32_t* h_rowp
   CK(cudaMemcpyAsync(h_X, h->hX, sizeof(double) * n * s, cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   return rc;
+}
+
+int lsba_release_workspace(lsba_handle h) {
+  if (!h) return LSBA_INVALID_ARG;
+  CK(cudaSetDevice(h->device));
+  free_ws(h);
+  ws_free(h, h->A_df);
+  h->A_df = nullptr;
+  h->A_df_cap = 0;
+  ws_free(h, h->hA_rowptr);
+  ws_free(h, h->hA_colidx);
+  ws_free(h, h->hA_vals);
+  ws_free(h, h->hB);
+  ws_free(h, h->hX);
+  h->hA_rowptr = h->hA_colidx = nullptr;
+  h->hA_vals = h->hB = h->hX = nullptr;
+  h->host_n = h->host_nnz = 0;
+  h->host_s = 0;
+  CK(cudaGetLastError());
+  return LSBA_OK;
+}
+
+int64_t lsba_workspace_bytes(int64_t n, int64_t nnz, int s, int m) {
+  if (n < 1 || s < 1 || s > LSBA_MAX_S || m < 1 || nnz < 0) return -1;
+  const int64_t blk = n * s * (int64_t)sizeof(double);
+  const int64_t ldH = (int64_t)(m + 2) * s, ss = (int64_t)s * s;
+  int64_t bytes = blk * (m + 1) + 4 * blk;                 // basis, W, U, B and X copies
+  bytes += (int64_t)sizeof(float2) * (nnz > 0 ? nnz : 1);  // low-precision A values
+  int64_t smalld = ldH * (m + 1) * s + ldH * ldH + ldH * s * 14 + 2 * (m + 4) * ss +
+                   (int64_t)(m + 1) * (m + 1) * ss + (int64_t)(m + 1) * 3 * ss + 32 * ss +
+                   (int64_t)(m + 3) * (m + 3) * 2 * ss;
+  bytes += smalld * (int64_t)sizeof(double);
+  const int64_t q = ldH * 2 * s;
+  bytes += (int64_t)sizeof(double) * q * (3 * 152 + 64);   // Gram partials (upper bound)
+  return bytes;
 }
 
 int lsba_get_profile(lsba_handle h, double* ms, int64_t* launches, int nclass) {
@@ -985,10 +1032,10 @@ int lsba_gram(lsba_handle h, const double* d_L, int a, const double* d_R, int b,
   GramPlan p = plan_gram(n, s, a, b, h->num_sms);
   const size_t need = (size_t)p.grid_x * p.q;
   if (need > h->partials_cap) {
-    cudaFree(h->partials);
+    ws_free(h, h->partials);
     h->partials = nullptr;
     h->partials_cap = 0;
-    if (cudaMalloc(&h->partials, sizeof(double) * need) != cudaSuccess) {
+    if (ws_alloc(h, &h->partials, sizeof(double) * need) != cudaSuccess) {
       cudaGetLastError();
       return LSBA_OUT_OF_MEMORY;
     }

@@ -183,11 +183,10 @@ void launch_gram(cudaStream_t st, const GramPlan& p, const BlockPtrs& L, int a, 
   g.partials = partials;
   g.ctl = ctl;
   g.guard = guard;
-  static bool attr_set = false;
-  if (!attr_set) {
+  static std::atomic<unsigned long long> attr_done{0};
+  once_per_device(attr_done, [] {
     cudaFuncSetAttribute(k_gram, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    attr_set = true;
-  }
+  });
   dim3 grid(p.grid_x, p.grid_y);
   k_gram<<<grid, GRAM_THREADS, p.smem, st>>>(g);
   k_gram_reduce<<<(p.q + 255) / 256, 256, 0, st>>>(partials, p.grid_x, p.q, G, ctl, guard);

@@ -437,12 +437,11 @@ GramPlan plan_gram_df(int64_t n, int s, int a, int b, int num_sms) {
 void launch_gram_df(cudaStream_t st, const GramPlan& p, const BlockPtrs& L, int a,
                     const BlockPtrs& R, int b, int64_t n, int s, float2* partials, double* G,
                     const Ctl* ctl, int guard, int* err) {
-  static bool attr_set = false;
-  if (!attr_set) {
+  static std::atomic<unsigned long long> attr_done{0};
+  once_per_device(attr_done, [] {
     cudaFuncSetAttribute(k_gram_df, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(k_gram_df_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    attr_set = true;
-  }
+  });
   dim3 grid(p.grid_x, p.grid_y);
   const int sp = (s + 3) & ~3;
   if (sp == s) {
@@ -746,8 +745,8 @@ void launch_update_df(cudaStream_t st, const BlockPtrs& in, int nin, int64_t n, 
   u.ctl = ctl;
   u.step = step;
   const size_t smem = update_df_smem(nin, s, two);
-  static bool attr_set = false;
-  if (!attr_set) {
+  static std::atomic<unsigned long long> attr_done{0};
+  once_per_device(attr_done, [] {
     cudaFuncSetAttribute(k_update_df, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(k_update_df_row<4, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(k_update_df_row<4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
@@ -755,8 +754,7 @@ void launch_update_df(cudaStream_t st, const BlockPtrs& in, int nin, int64_t n, 
     cudaFuncSetAttribute(k_update_df_row<8, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(k_update_df_row<16, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(k_update_df_row<16, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    attr_set = true;
-  }
+  });
   if (s == 4 || s == 8 || s == 16) {
     int64_t need = (n + 255) / 256;
     int64_t grid = 4LL * num_sms;

@@ -239,11 +239,10 @@ GramPlan plan_gram_f32(int64_t n, int s, int a, int b, int num_sms) {
 void launch_gram_f32(cudaStream_t st, const GramPlan& p, const BlockPtrs& L, int a,
                      const BlockPtrs& R, int b, int64_t n, int s, float* partials, double* G,
                      const Ctl* ctl, int guard, int* err) {
-  static bool attr_set = false;
-  if (!attr_set) {
+  static std::atomic<unsigned long long> attr_done{0};
+  once_per_device(attr_done, [] {
     cudaFuncSetAttribute(k_gram_f32_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    attr_set = true;
-  }
+  });
   GramF32Args g;
   g.L = L;
   g.R = R;
@@ -425,16 +424,15 @@ void launch_update_f32(cudaStream_t st, const BlockPtrs& in, int nin, int64_t n,
   u.ctl = ctl;
   u.step = step;
   const size_t smem = update_f32_smem(nin, s, two);
-  static bool attr_set = false;
-  if (!attr_set) {
+  static std::atomic<unsigned long long> attr_done{0};
+  once_per_device(attr_done, [] {
     cudaFuncSetAttribute(k_update_f32<4, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(k_update_f32<4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(k_update_f32<8, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(k_update_f32<8, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(k_update_f32<16, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(k_update_f32<16, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    attr_set = true;
-  }
+  });
   int64_t need = (n + 255) / 256;
   int64_t grid = 4LL * num_sms;
   if (grid > need) grid = need;

@@ -1089,14 +1089,14 @@ __global__ void k_true_relres(const double* G, int s, Ctl* ctl) {
 }
 
 static void small_attrs() {
-  static bool done = false;
-  if (done) return;
-  const int bytes = SMALL_ARENA_DOUBLES * sizeof(double);
-  cudaFuncSetAttribute(k_small_start, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  cudaFuncSetAttribute(k_small_step, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  cudaFuncSetAttribute(k_small_side, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  cudaFuncSetAttribute(k_small_end, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  done = true;
+  static std::atomic<unsigned long long> attr_done{0};
+  once_per_device(attr_done, [] {
+    const int bytes = SMALL_ARENA_DOUBLES * sizeof(double);
+    cudaFuncSetAttribute(k_small_start, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaFuncSetAttribute(k_small_step, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaFuncSetAttribute(k_small_side, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaFuncSetAttribute(k_small_end, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  });
 }
 
 void launch_small_start(cudaStream_t st, const SmallWs& w, int flags) {
@@ -1128,11 +1128,10 @@ void launch_small_side(cudaStream_t st, const SmallWs& w, int k) {
     const int rows = 64 / S2 > 0 ? 64 / S2 : 1;
     const int ctas = (k * w.s + rows - 1) / rows;
     const size_t smem = sizeof(double) * ((size_t)(k - 1) * w.s * w.s + (size_t)rows * (k - 1) * w.s);
-    static bool attr = false;
-    if (!attr) {
+    static std::atomic<unsigned long long> attr_done{0};
+    once_per_device(attr_done, [] {
       cudaFuncSetAttribute(k_side_J, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-      attr = true;
-    }
+    });
     if (smem <= 200 * 1024) {
       k_side_J<<<ctas, 64, smem, st>>>(w, k, S2);
     } else {

@@ -1,6 +1,7 @@
 // Internal declarations shared by the CUDA translation units of the solver.
 // Not part of the public C ABI (include/lsba.h).
 #pragma once
+#include <atomic>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -11,6 +12,21 @@
 #define LSBA_END_STEP (1 << 20)   // update_step value that enables the cycle-end pass
 
 namespace lsba {
+
+// Runs f() once per device for the calling thread's current device.  Kernel
+// attributes (the dynamic shared-memory opt-in) belong to a device, and solver
+// handles on several host threads may launch the first kernels concurrently:
+// the bit is published only after f() has returned, and two threads that both
+// run f() set the same attributes.
+template <class F>
+inline void once_per_device(std::atomic<unsigned long long>& done, F&& f) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const unsigned long long bit = 1ull << (dev & 63);
+  if (done.load(std::memory_order_acquire) & bit) return;
+  f();
+  done.fetch_or(bit, std::memory_order_release);
+}
 
 // Device-side control record of one solve.  Written by the small (single-CTA)
 // kernels, read by every launch of the step so that a cycle that has ended

@@ -25,7 +25,8 @@ PRECISIONS = {"fp64": 0, "df": 1, "auto": 2, "fp32_ir": 3}
 EXPORTED = ("lsba_default_options", "lsba_create", "lsba_set_options", "lsba_solve",
             "lsba_solve_host", "lsba_get_stats", "lsba_get_history", "lsba_status_string",
             "lsba_destroy", "lsba_spmm", "lsba_gram", "lsba_combine", "lsba_get_profile",
-            "lsba_reset_profile", "lsba_gram_noalloc")
+            "lsba_reset_profile", "lsba_gram_noalloc", "lsba_release_workspace",
+            "lsba_workspace_bytes")
 KERNEL_CLASSES = ("spmm", "gram", "update", "small")
 
 
@@ -91,11 +92,19 @@ def load(path: str = LIB_PATH):
     lib.lsba_get_profile.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_int64), i32]
     lib.lsba_reset_profile.argtypes = [vp]
     lib.lsba_gram_noalloc.argtypes = [vp, i32, vp, i32, i64, i32, vp, vp]
+    lib.lsba_release_workspace.argtypes = [vp]
+    lib.lsba_workspace_bytes.argtypes = [i64, i64, i32, i32]
     for name in EXPORTED:
         if name not in ("lsba_default_options", "lsba_status_string"):
             getattr(lib, name).restype = C.c_int
+    lib.lsba_workspace_bytes.restype = C.c_int64
     _lib = lib
     return lib
+
+
+def workspace_bytes(n: int, nnz: int, s: int, m: int) -> int:
+    """Upper bound of the device memory one solve allocates (admission control)."""
+    return int(load().lsba_workspace_bytes(n, nnz, s, m))
 
 
 def status_string(code: int) -> str:
@@ -222,6 +231,9 @@ class Solver:
         cnt = (C.c_int64 * 4)()
         _check(self.lib.lsba_get_profile(self.h, ms, cnt, 4))
         return {k: (ms[i], cnt[i]) for i, k in enumerate(KERNEL_CLASSES)}
+
+    def release_workspace(self):
+        _check(self.lib.lsba_release_workspace(self.h))
 
     def reset_profile(self):
         _check(self.lib.lsba_reset_profile(self.h))

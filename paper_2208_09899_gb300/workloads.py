@@ -111,23 +111,21 @@ def laplacian_2d(nx: int, ny: int | None = None) -> CSR:
 
 
 def laplacian_3d(N: int, shift: float = 0.0) -> CSR:
-    """7-point Dirichlet Laplacian on an N^3 grid (stencil 6, -1 x 6) + shift*I."""
+    """7-point Dirichlet Laplacian on an N^3 grid (stencil 6, -1 x 6) + shift*I,
+    lexicographic ordering i = (z*N + y)*N + x.  Built row by row in column
+    order (offsets -N^2, -N, -1, 0, +1, +N, +N^2), no sort needed."""
     n = N ** 3
-    idx = np.arange(n).reshape(N, N, N)
-    rows = [idx.ravel()]
-    cols = [idx.ravel()]
-    vals = [np.full(n, 6.0 + shift)]
-    sl = slice(1, None), slice(None, -1)
-    for ax in range(3):
-        for a_sl, b_sl in ((sl[0], sl[1]), (sl[1], sl[0])):
-            ia = [slice(None)] * 3
-            ib = [slice(None)] * 3
-            ia[ax], ib[ax] = a_sl, b_sl
-            a, b = idx[tuple(ia)], idx[tuple(ib)]
-            rows.append(a.ravel())
-            cols.append(b.ravel())
-            vals.append(np.full(a.size, -1.0))
-    return _from_coo(n, np.concatenate(rows), np.concatenate(cols), np.concatenate(vals))
+    i = np.arange(n, dtype=np.int64)
+    x, y, z = i % N, (i // N) % N, i // (N * N)
+    offs = (-N * N, -N, -1, 0, 1, N, N * N)
+    ok = (z > 0, y > 0, x > 0, np.ones(n, bool), x < N - 1, y < N - 1, z < N - 1)
+    cols = np.stack([i + o for o in offs], axis=1)
+    mask = np.stack(ok, axis=1)
+    vals = np.where(np.arange(7) == 3, 6.0 + shift, -1.0)
+    vals = np.broadcast_to(vals, (n, 7))
+    rowptr = np.zeros(n + 1, dtype=np.int32)
+    np.cumsum(mask.sum(axis=1), out=rowptr[1:])
+    return CSR(n, rowptr, cols[mask].astype(np.int32), np.ascontiguousarray(vals[mask]))
 
 
 def rgg_laplacian(n: int, seed: int = 0, avg_degree: float = 6.0,
