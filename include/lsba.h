@@ -93,8 +93,7 @@ typedef struct {
                                     O(eps) kappa^2 loss of orthogonality (Table 2)
                                     amplifies the 2^-48 representation error.  The
                                     small s x s / ks x s kernels are FP64 in all modes.
-                                    DF needs 8*(2(m+3)+3)s^2 bytes of shared memory
-                                    <= 200 KB; larger (m, s) run in FP64.
+                                    DF takes every s <= 32 and m.
                                     LSBA_PREC_FP32_IR: FP64 iterative refinement
                                     (residual B - A X and X += D in FP64) around an
                                     FP32 inner solve of A D = R (FP32 SpMM, Gram and
@@ -181,9 +180,12 @@ int lsba_get_stats(lsba_handle h, lsba_stats* out);
  * streams can run, grow and release concurrently. */
 int lsba_release_workspace(lsba_handle h);
 
-/* Upper bound of the device memory (bytes) a solve with n x s blocks, nnz
- * nonzeros and maximum basis size m allocates, for admission control; -1 on
- * invalid sizes.  Host computation only. */
+/* Upper bound of the device memory (bytes) lsba_solve with n x s blocks, nnz
+ * nonzeros and basis size m allocates on the current device, for admission
+ * control (lsba_solve_host adds its own copies of A, B and X); -1 on invalid
+ * sizes.  Host computation only; with no device visible it assumes 256 SMs,
+ * which bounds the Gram partial sums of any current part.  The restart
+ * history of lsba_get_history keeps at most 4096 cycles. */
 int64_t lsba_workspace_bytes(int64_t n, int64_t nnz, int s, int m);
 
 /* Kernel classes of lsba_get_profile. */

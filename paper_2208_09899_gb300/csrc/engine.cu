@@ -174,6 +174,60 @@ static size_t max_partials(int64_t n, int s, int mmax, int sms, size_t* qmax_out
   return best;
 }
 
+// Offsets (in doubles, 256-byte aligned) of the small matrices of one handle
+// in its single small-matrix allocation.  The restart history holds at most
+// LSBA_HIST_RESTARTS cycles.
+#define LSBA_HIST_RESTARTS 4096
+struct SmallLayout {
+  size_t oH, oT, oJ, oc1, oc2, och, ot1, ot2, oRb, orf, otau, otw, og, oTf, ogf, ocf, ouf, oC,
+      oBc, oXi, oMv, owk, osz, osy, osr, ohe, ogh;
+  size_t hist_cap, gram_hist_cap, total;
+};
+
+static SmallLayout small_layout(int s, int m, int max_restarts) {
+  SmallLayout L;
+  const size_t ldH = (size_t)(m + 2) * s, ldR = (size_t)(m + 1) * s;
+  const size_t ss = (size_t)s * s;
+  const int restarts = max_restarts < LSBA_HIST_RESTARTS ? max_restarts : LSBA_HIST_RESTARTS;
+  L.hist_cap = (size_t)(restarts + 3) * (m + 2) + 16;
+  L.gram_hist_cap = (size_t)(m + 3) * (m + 3) * 2 * ss + 64;
+  size_t off = 0;
+  auto take = [&](size_t count) {
+    size_t o = off;
+    off += (count + 31) & ~(size_t)31;
+    return o;
+  };
+  L.oH = take(ldH * (m + 1) * s);
+  L.oT = take(ldH * ldH);
+  L.oJ = take(ldH * s);
+  L.oc1 = take((size_t)(m + 4) * ss);
+  L.oc2 = take((size_t)(m + 4) * ss);
+  L.och = take(ss);
+  L.ot1 = take(ss);
+  L.ot2 = take(ss);
+  L.oRb = take(ldR * ldR);
+  L.orf = take((size_t)(m + 1) * 2 * ss);
+  L.otau = take((size_t)(m + 1) * s);
+  L.otw = take((size_t)(m + 1) * ss);
+  L.og = take(ldH * s);
+  L.oTf = take(ss);
+  L.ogf = take(ss);
+  L.ocf = take(ss);
+  L.ouf = take(ldH * s);
+  L.oC = take(ss);
+  L.oBc = take(ss);
+  L.oXi = take(ldH * s);
+  L.oMv = take(ldH * s);
+  L.owk = take(6 * ldH * s + 16 * ss);
+  L.osz = take(ldH * s);
+  L.osy = take(ldH * s);
+  L.osr = take(ss);
+  L.ohe = take(L.hist_cap);
+  L.ogh = take(L.gram_hist_cap);
+  L.total = off;
+  return L;
+}
+
 // Allocate (or grow) the workspace for n x s blocks and basis size m.
 static int ensure_ws(lsba_ctx* h, int64_t n, int s, int m) {
   if (n <= h->cap_n && s == h->cap_s && m <= h->cap_m && h->basis) return LSBA_OK;
@@ -190,26 +244,14 @@ static int ensure_ws(lsba_ctx* h, int64_t n, int s, int m) {
   h->partials_cap = max_partials(n, s, m, h->num_sms, &qmax);
   h->G_cap = qmax;
   const int ldH = (m + 2) * s, ldR = (m + 1) * s;
-  const size_t ss = (size_t)s * s;
-  const size_t hist_cap = (size_t)(h->opt.max_restarts + 3) * (m + 2) + 16;
-  const size_t gram_hist_cap = (size_t)(m + 3) * (m + 3) * 2 * ss + 64;
-  size_t off = 0;
-  auto take = [&](size_t count) {
-    size_t o = off;
-    off += (count + 31) & ~(size_t)31;
-    return o;
-  };
-  const size_t oH = take((size_t)ldH * (m + 1) * s), oT = take((size_t)ldH * ldH),
-               oJ = take((size_t)ldH * s), oc1 = take((size_t)(m + 4) * ss),
-               oc2 = take((size_t)(m + 4) * ss), och = take(ss), ot1 = take(ss), ot2 = take(ss),
-               oRb = take((size_t)ldR * ldR), orf = take((size_t)(m + 1) * 2 * ss),
-               otau = take((size_t)(m + 1) * s), otw = take((size_t)(m + 1) * ss),
-               og = take((size_t)ldH * s), oTf = take(ss),
-               ogf = take(ss), ocf = take(ss), ouf = take((size_t)ldH * s), oC = take(ss),
-               oBc = take(ss), oXi = take((size_t)ldH * s), oMv = take((size_t)ldH * s),
-               owk = take((size_t)6 * ldH * s + 16 * ss), osz = take((size_t)ldH * s),
-               osy = take((size_t)ldH * s), osr = take(ss), ohe = take(hist_cap),
-               ogh = take(gram_hist_cap);
+  const SmallLayout L = small_layout(s, m, h->opt.max_restarts);
+  const size_t hist_cap = L.hist_cap, gram_hist_cap = L.gram_hist_cap;
+  const size_t oH = L.oH, oT = L.oT, oJ = L.oJ, oc1 = L.oc1, oc2 = L.oc2, och = L.och, ot1 = L.ot1,
+               ot2 = L.ot2, oRb = L.oRb, orf = L.orf, otau = L.otau, otw = L.otw, og = L.og,
+               oTf = L.oTf, ogf = L.ogf, ocf = L.ocf, ouf = L.ouf, oC = L.oC, oBc = L.oBc,
+               oXi = L.oXi, oMv = L.oMv, owk = L.owk, osz = L.osz, osy = L.osy, osr = L.osr,
+               ohe = L.ohe, ogh = L.ogh;
+  const size_t off = L.total;
   h->small_cap = off;
   if (ws_alloc(h, &h->small, sizeof(double) * off) != cudaSuccess ||
       ws_alloc(h, &h->partials, sizeof(double) * h->partials_cap) != cudaSuccess ||
@@ -763,12 +805,14 @@ static int solve_impl(lsba_handle h, const lsba_csr* A, const double* d_B, doubl
   const size_t blk = (size_t)n * s;
   // Working precision of the SpMM / Gram / update passes.
   const int prec = h->opt.precision;
-  const bool fits_df = update_df_smem(m + 3, s, true) <= 200 * 1024;
+  // The double-float kernels take every s (coefficient sets too large for
+  // shared memory are read from global memory); the FP32 inner solver has
+  // row kernels for s = 4, 8, 16 only and otherwise runs in double-float.
   const bool fits_f32 = (s == 4 || s == 8 || s == 16) && update_f32_smem(m + 3, s, true) <= 200 * 1024;
   const bool ir = prec == LSBA_PREC_FP32_IR && fits_f32;
   if (ir) h->mode = MODE_F32;
-  else if ((prec == LSBA_PREC_DF || (prec == LSBA_PREC_AUTO && lagged(skel)) ||
-            prec == LSBA_PREC_FP32_IR) && fits_df)
+  else if (prec == LSBA_PREC_DF || prec == LSBA_PREC_FP32_IR ||
+           (prec == LSBA_PREC_AUTO && lagged(skel)))
     h->mode = MODE_DF;
   else h->mode = MODE_FP64;
   h->stats.precision = ir ? LSBA_PREC_FP32_IR : h->mode == MODE_DF ? LSBA_PREC_DF : LSBA_PREC_FP64;
@@ -951,16 +995,28 @@ int lsba_release_workspace(lsba_handle h) {
 
 int64_t lsba_workspace_bytes(int64_t n, int64_t nnz, int s, int m) {
   if (n < 1 || s < 1 || s > LSBA_MAX_S || m < 1 || nnz < 0) return -1;
+  // Every allocation of ensure_ws / ensure_lowprec_A at the largest settings:
+  // basis (m+1 blocks), W, U, the low-precision B and X copies, the
+  // low-precision matrix values, the small matrices with a full restart
+  // history, the Gram partials of the largest plan, the converted update
+  // coefficients and the integer history arrays.
+  int num_sms = 0, dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      num_sms < 1) {
+    cudaGetLastError();
+    num_sms = 256;  // no device visible: a bound above any current part
+  }
   const int64_t blk = n * s * (int64_t)sizeof(double);
-  const int64_t ldH = (int64_t)(m + 2) * s, ss = (int64_t)s * s;
-  int64_t bytes = blk * (m + 1) + 4 * blk;                 // basis, W, U, B and X copies
-  bytes += (int64_t)sizeof(float2) * (nnz > 0 ? nnz : 1);  // low-precision A values
-  int64_t smalld = ldH * (m + 1) * s + ldH * ldH + ldH * s * 14 + 2 * (m + 4) * ss +
-                   (int64_t)(m + 1) * (m + 1) * ss + (int64_t)(m + 1) * 3 * ss + 32 * ss +
-                   (int64_t)(m + 3) * (m + 3) * 2 * ss;
-  bytes += smalld * (int64_t)sizeof(double);
-  const int64_t q = ldH * 2 * s;
-  bytes += (int64_t)sizeof(double) * q * (3 * 152 + 64);   // Gram partials (upper bound)
+  int64_t bytes = blk * (m + 5);
+  bytes += (int64_t)sizeof(float2) * (nnz > 0 ? nnz : 1);
+  const SmallLayout L = small_layout(s, m, LSBA_HIST_RESTARTS);
+  bytes += (int64_t)(L.total * sizeof(double));
+  size_t qmax = 0;
+  const size_t partials = max_partials(n, s, m, num_sms, &qmax);
+  bytes += (int64_t)((partials + qmax) * sizeof(double));
+  bytes += (int64_t)(coef_df_count(m + 3, s, true) * sizeof(float2));
+  bytes += (int64_t)((2 * L.hist_cap + 2 * (m + 4)) * sizeof(int));
   return bytes;
 }
 

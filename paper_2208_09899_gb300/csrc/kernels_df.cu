@@ -242,7 +242,7 @@ struct GramTmaArgs {
   int a, b, s, rc;
   int64_t n, rows_per_cta;
   int q, ntj, ntile;
-  unsigned stage_elems;   // float2 per stage = (a+b) * rc * s
+  unsigned stage_elems;   // float2 per stage = (nl_max + b) * rc * s
   float2* partials;
   const Ctl* ctl;
   int guard;
@@ -255,8 +255,7 @@ __global__ void __launch_bounds__(GDF_THREADS) k_gram_df_tma(const __grid_consta
   uint64_t* bars = (uint64_t*)smraw;
   float2* stage0 = (float2*)(smraw + 128);
   float2* stage1 = stage0 + g.stage_elems;
-  const int s = g.s, rc = g.rc, a = g.a, b = g.b;
-  const int nblk = a + b;
+  const int s = g.s, rc = g.rc, b = g.b;
   const int tile_base = blockIdx.y * GDF_THREADS;
   const int cnt = min(GDF_THREADS, g.ntile - tile_base);
   const int groups = GDF_THREADS / cnt;
@@ -266,8 +265,12 @@ __global__ void __launch_bounds__(GDF_THREADS) k_gram_df_tma(const __grid_consta
   const int T = tile_base + tl;
   const int it = T / g.ntj, jt = T % g.ntj;
   const int li = it * 4, rj = jt * 4;
-  const int lofs = (li / s) * rc * s + (li % s);
-  const int rofs = (a + rj / s) * rc * s + (rj % s);
+  // Only the left blocks this tile group reads are copied: [lb0, lb0 + nl).
+  int lb0, nl;
+  gram_tile_blocks(tile_base, cnt, g.ntj, s, &lb0, &nl);
+  const int nblk = nl + b;
+  const int lofs = (li / s - lb0) * rc * s + (li % s);
+  const int rofs = (nl + rj / s) * rc * s + (rj % s);
   const int64_t r_begin = (int64_t)blockIdx.x * g.rows_per_cta;
   const int64_t r_end = min(g.n, r_begin + g.rows_per_cta);
   const int nchunks = r_end > r_begin ? (int)((r_end - r_begin + rc - 1) / rc) : 0;
@@ -285,7 +288,7 @@ __global__ void __launch_bounds__(GDF_THREADS) k_gram_df_tma(const __grid_consta
     float2* dst = st ? stage1 : stage0;
     mbar_expect_tx(&bars[st], bytes * nblk);
     for (int blk = 0; blk < nblk; ++blk) {
-      const float2* src = (const float2*)(blk < a ? g.L.p[blk] : g.R.p[blk - a]) + r0 * s;
+      const float2* src = (const float2*)(blk < nl ? g.L.p[lb0 + blk] : g.R.p[blk - nl]) + r0 * s;
       bulk_copy_g2s(dst + (size_t)blk * rc * s, src, bytes, &bars[st]);
     }
   };
@@ -404,12 +407,23 @@ GramPlan plan_gram_df(int64_t n, int s, int a, int b, int num_sms) {
   const size_t red_bytes = (size_t)GDF_THREADS * 16 * sizeof(float2);
   int rc;
   int ctas_per_sm;
+  p.nl_max = a;
   if (sp == s) {
+    // A tile group copies only the left blocks its tiles read.
+    p.nl_max = 0;
+    for (int y = 0; y < p.grid_y; ++y) {
+      const int base = y * GDF_THREADS;
+      const int cnt = ntile - base < GDF_THREADS ? ntile - base : GDF_THREADS;
+      int first, count;
+      gram_tile_blocks(base, cnt, b * s / 4, s, &first, &count);
+      if (count > p.nl_max) p.nl_max = count;
+    }
+    const size_t row_bytes_g = (size_t)(p.nl_max + b) * s * sizeof(float2);
     // Two pipeline stages of <= 32 KB each: three CTAs per SM.
-    rc = (int)((32 * 1024) / row_bytes);
+    rc = (int)((32 * 1024) / row_bytes_g);
     if (rc > 128) rc = 128;
     if (rc < 1) rc = 1;
-    const size_t stages = 128 + 2 * row_bytes * rc;
+    const size_t stages = 128 + 2 * row_bytes_g * rc;
     p.smem = stages > 128 + red_bytes ? stages : 128 + red_bytes;
     ctas_per_sm = 3;
   } else {
@@ -457,7 +471,7 @@ void launch_gram_df(cudaStream_t st, const GramPlan& p, const BlockPtrs& L, int 
     g.q = p.q;
     g.ntj = b * s / 4;
     g.ntile = (a * s / 4) * g.ntj;
-    g.stage_elems = (unsigned)((a + b) * p.rows_per_chunk * s);
+    g.stage_elems = (unsigned)((p.nl_max + b) * p.rows_per_chunk * s);
     g.partials = partials;
     g.ctl = ctl;
     g.guard = guard;
@@ -540,6 +554,7 @@ struct UpdDfArgs {
   float2* out2;
   const float2* cdf;
   int has_tri1, has_chain, has_tri2;
+  int staged;          // coefficients copied to shared memory (else read from cdf)
   const Ctl* ctl;
   int step;
 };
@@ -572,10 +587,16 @@ __global__ void __launch_bounds__(256) k_update_df(const __grid_constant__ UpdDf
   const int s = u.s, S2 = u.S2, nin = u.nin;
   const int ss = s * s;
   const bool two = u.out2 != nullptr;
-  const int total = (int)coef_df_count(nin, s, two);
-  for (int e = threadIdx.x; e < total; e += blockDim.x) cs[e] = u.cdf[e];
-  __syncthreads();
-  const float2* c1 = cs;
+  // Coefficients that fit are staged in shared memory; larger sets (s = 32
+  // with a long basis) are read from global memory, where every CTA reuses
+  // the same few KB per input block through L1.
+  const float2* c1 = u.cdf;
+  if (u.staged) {
+    const int total = (int)coef_df_count(nin, s, two);
+    for (int e = threadIdx.x; e < total; e += blockDim.x) cs[e] = u.cdf[e];
+    __syncthreads();
+    c1 = cs;
+  }
   const float2* c2 = c1 + (size_t)nin * ss;
   const float2* ch = c2 + (two ? (size_t)nin * ss : 0);
   const float2* t1 = ch + ss;
@@ -709,7 +730,142 @@ __global__ void __launch_bounds__(256) k_update_df_row(const __grid_constant__ U
   }
 }
 
+// s = 32: a pair of adjacent lanes per row, each owning 16 columns of both
+// outputs (64 accumulator registers per lane).  Both lanes read the row's 32
+// input values (one L1 transaction serves the pair); the coefficients come
+// from global memory through L1 (every CTA reads the same 16 KB per input
+// block).  The triangular solves run column by column: the lane that owns
+// column q finishes it and hands it to its partner by a shuffle.
+template <bool TWO>
+__global__ void __launch_bounds__(256, 1) k_update_df_w32(const __grid_constant__ UpdDfArgs u) {
+  if (u.step >= 0 && *(volatile const int*)&u.ctl->update_step != u.step) return;
+  constexpr int S = 32, CG = 16, SS = S * S;
+  const int nin = u.nin;
+  const float2* c1 = u.cdf;
+  const float2* c2 = c1 + (size_t)nin * SS;
+  const float2* ch = c2 + (TWO ? (size_t)nin * SS : 0);
+  const float2* t1 = ch + SS;
+  const float2* t2 = t1 + SS;
+  const float2* r1 = t2 + SS;
+  const float2* r2 = r1 + S;
+  const int half = threadIdx.x & 1;
+  const int c0 = half * CG;
+  const unsigned pair = 3u << (threadIdx.x & 30);
+  const int64_t stride = ((int64_t)gridDim.x * blockDim.x) >> 1;
+  for (int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 1; row < u.n; row += stride) {
+    dfacc a1[CG], a2[CG];
+#pragma unroll
+    for (int c = 0; c < CG; ++c) {
+      a1[c] = dfacc{0.f, 0.f};
+      a2[c] = dfacc{0.f, 0.f};
+    }
+    // Eight input values (a quarter row) per iteration; the next quarter is
+    // loaded before the arithmetic on the current one.
+    const int iters = nin * 4;
+    float4 nxt[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) nxt[i] = ((const float4*)((const float2*)u.in.p[0] + row * S))[i];
+#pragma unroll 1
+    for (int itr = 0; itr < iters; ++itr) {
+      const int bk = itr >> 2, qb = (itr & 3) * 8;
+      float2 v[8];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        v[2 * i] = make_float2(nxt[i].x, nxt[i].y);
+        v[2 * i + 1] = make_float2(nxt[i].z, nxt[i].w);
+      }
+      if (itr + 1 < iters) {
+        const int bn = (itr + 1) >> 2, qn = ((itr + 1) & 3) * 8;
+        const float4* src = (const float4*)((const float2*)u.in.p[bn] + row * S + qn);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) nxt[i] = src[i];
+      }
+      const float2* k1 = c1 + (size_t)bk * SS + c0;
+      const float2* k2 = c2 + (size_t)bk * SS + c0;
+#pragma unroll
+      for (int qq = 0; qq < 8; ++qq) {
+        const float4* kr1 = (const float4*)(k1 + (qb + qq) * S);
+        const float4* kr2 = (const float4*)(k2 + (qb + qq) * S);
+#pragma unroll
+        for (int c = 0; c < CG; c += 2) {
+          const float4 k = __ldg(kr1 + c / 2);
+          df_fma(a1[c], v[qq], make_float2(k.x, k.y));
+          df_fma(a1[c + 1], v[qq], make_float2(k.z, k.w));
+          if (TWO) {
+            const float4 kk = __ldg(kr2 + c / 2);
+            df_fma(a2[c], v[qq], make_float2(kk.x, kk.y));
+            df_fma(a2[c + 1], v[qq], make_float2(kk.z, kk.w));
+          }
+        }
+      }
+    }
+    // out1 = a1 T1^{-1}; the finished column values overwrite a1 (s = hi, c = lo).
+    if (u.has_tri1) {
+#pragma unroll
+      for (int q = 0; q < S; ++q) {
+        if (half == q / CG) {
+          const float2 o = df_mul(df_value(a1[q % CG]), __ldg(r1 + q));
+          a1[q % CG] = dfacc{o.x, o.y};
+        }
+        const float2 oq = make_float2(__shfl_sync(pair, a1[q % CG].s, q / CG, 2),
+                                      __shfl_sync(pair, a1[q % CG].c, q / CG, 2));
+#pragma unroll
+        for (int c = 0; c < CG; ++c)
+          if (c0 + c > q) df_fms(a1[c], oq, __ldg(t1 + q * S + c0 + c));
+      }
+    } else {
+#pragma unroll
+      for (int c = 0; c < CG; ++c) {
+        const float2 o = df_value(a1[c]);
+        a1[c] = dfacc{o.x, o.y};
+      }
+    }
+    float4* d1 = (float4*)(u.out1 + row * S + c0);
+#pragma unroll
+    for (int i = 0; i < CG / 2; ++i)
+      d1[i] = make_float4(a1[2 * i].s, a1[2 * i].c, a1[2 * i + 1].s, a1[2 * i + 1].c);
+    if (TWO) {
+      if (u.has_chain) {
+#pragma unroll
+        for (int q = 0; q < S; ++q) {
+          const float2 oq = make_float2(__shfl_sync(pair, a1[q % CG].s, q / CG, 2),
+                                        __shfl_sync(pair, a1[q % CG].c, q / CG, 2));
+#pragma unroll
+          for (int c = 0; c < CG; ++c) df_fma(a2[c], oq, __ldg(ch + q * S + c0 + c));
+        }
+      }
+      if (u.has_tri2) {
+#pragma unroll
+        for (int q = 0; q < S; ++q) {
+          if (half == q / CG) {
+            const float2 o = df_mul(df_value(a2[q % CG]), __ldg(r2 + q));
+            a2[q % CG] = dfacc{o.x, o.y};
+          }
+          const float2 oq = make_float2(__shfl_sync(pair, a2[q % CG].s, q / CG, 2),
+                                        __shfl_sync(pair, a2[q % CG].c, q / CG, 2));
+#pragma unroll
+          for (int c = 0; c < CG; ++c)
+            if (c0 + c > q) df_fms(a2[c], oq, __ldg(t2 + q * S + c0 + c));
+        }
+      } else {
+#pragma unroll
+        for (int c = 0; c < CG; ++c) {
+          const float2 o = df_value(a2[c]);
+          a2[c] = dfacc{o.x, o.y};
+        }
+      }
+      float4* d2 = (float4*)(u.out2 + row * S + c0);
+#pragma unroll
+      for (int i = 0; i < CG / 2; ++i)
+        d2[i] = make_float4(a2[2 * i].s, a2[2 * i].c, a2[2 * i + 1].s, a2[2 * i + 1].c);
+    }
+  }
+}
+
 size_t update_df_smem(int nin, int s, bool two) { return sizeof(float2) * coef_df_count(nin, s, two); }
+
+// Largest coefficient set staged in shared memory by the update kernels.
+static constexpr size_t UPDATE_DF_SMEM_MAX = 200 * 1024;
 
 void launch_update_df(cudaStream_t st, const BlockPtrs& in, int nin, int64_t n, int s, float2* out1,
                       const double* coef1, const double* tri1, float2* out2, const double* coef2,
@@ -744,7 +900,9 @@ void launch_update_df(cudaStream_t st, const BlockPtrs& in, int nin, int64_t n, 
   u.has_tri2 = two && tri2 != nullptr;
   u.ctl = ctl;
   u.step = step;
-  const size_t smem = update_df_smem(nin, s, two);
+  const size_t smem_all = update_df_smem(nin, s, two);
+  u.staged = smem_all <= UPDATE_DF_SMEM_MAX ? 1 : 0;
+  const size_t smem = u.staged ? smem_all : 0;
   static std::atomic<unsigned long long> attr_done{0};
   once_per_device(attr_done, [] {
     cudaFuncSetAttribute(k_update_df, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
@@ -755,7 +913,7 @@ void launch_update_df(cudaStream_t st, const BlockPtrs& in, int nin, int64_t n, 
     cudaFuncSetAttribute(k_update_df_row<16, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(k_update_df_row<16, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   });
-  if (s == 4 || s == 8 || s == 16) {
+  if (u.staged && (s == 4 || s == 8 || s == 16)) {
     int64_t need = (n + 255) / 256;
     int64_t grid = 4LL * num_sms;
     if (grid > need) grid = need;
@@ -767,6 +925,15 @@ void launch_update_df(cudaStream_t st, const BlockPtrs& in, int nin, int64_t n, 
     else if (s == 8) { LAUNCH_ROW(8) }
     else { LAUNCH_ROW(16) }
 #undef LAUNCH_ROW
+    return;
+  }
+  if (s == 32) {
+    const int64_t need = (n + 127) / 128;
+    int64_t grid = 4LL * num_sms;
+    if (grid > need) grid = need;
+    if (grid < 1) grid = 1;
+    if (two) k_update_df_w32<true><<<(unsigned)grid, 256, 0, st>>>(u);
+    else k_update_df_w32<false><<<(unsigned)grid, 256, 0, st>>>(u);
     return;
   }
   const int rows_per_cta = 256 / u.S2;

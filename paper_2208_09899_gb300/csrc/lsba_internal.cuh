@@ -119,7 +119,19 @@ struct GramPlan {
   size_t smem;
   int rows_per_chunk;
   int64_t rows_per_cta;
+  int nl_max;     // bulk-copy Gram kernels: most left blocks one tile group reads
 };
+
+// Left blocks [first, first + count) that the output tiles tile_base ..
+// tile_base + cnt - 1 of a bulk-copy Gram kernel read (tiles are 4 x 4, row
+// tile it = T / ntj covers left columns 4 it .. 4 it + 3 of one block, s a
+// multiple of 4).
+__host__ __device__ inline void gram_tile_blocks(int tile_base, int cnt, int ntj, int s,
+                                                 int* first, int* count) {
+  const int it_lo = tile_base / ntj, it_hi = (tile_base + cnt - 1) / ntj;
+  *first = (4 * it_lo) / s;
+  *count = (4 * it_hi) / s - *first + 1;
+}
 GramPlan plan_gram(int64_t n, int s, int a, int b, int num_sms);
 void launch_gram(cudaStream_t st, const GramPlan& p, const BlockPtrs& L, int a, const BlockPtrs& R,
                  int b, int64_t n, int s, double* partials, double* G, const Ctl* ctl, int guard);

@@ -176,6 +176,23 @@ def test_odd_block_sizes(env, s):
     _compare_solve(lsba, A, B, 6, 1e-10, "bcgsi_ls", "gmres", max_restarts=300)
 
 
+@pytest.mark.parametrize("s,sk,precision,expect", [
+    (32, "bcgsi_ls", "df", "df"), (31, "bcgsi_ls", "df", "df"), (24, "bcgsi_ls", "df", "df"),
+    (32, "bmgs_icwy", "auto", "df"), (32, "bmgs_cwy", "df", "df"), (32, "bcgs_pip", "auto", "fp64"),
+    (32, "bcgs", "fp64", "fp64")])
+def test_wide_blocks(env, s, sk, precision, expect):
+    """s = 24, 31, 32 with m = 14 on the 64 x 60 Laplacian (n = 3840; the
+    basis holds 15 s <= 480 columns): the double-float update coefficients of
+    s = 31, 32 (17 blocks of s x s, two outputs) exceed shared memory and are
+    read from global memory; s = 24 stages them."""
+    torch, lsba = env
+    A = W.laplacian_2d(64, 60)
+    B = W.gaussian_block(A.n, s, 21)
+    _, st, _, _ = _compare_solve(lsba, A, B, 14, 1e-10, sk, "gmres", max_restarts=100,
+                                 precision=precision)
+    assert st["precision"] == lsba.PRECISIONS[expect]
+
+
 @pytest.mark.parametrize("sk", ["bcgs_pip", "bcgsi_ls", "bmgs_icwy", "bcgs"])
 def test_adaptive_restart_injected_flag(env, sk):
     torch, lsba = env
