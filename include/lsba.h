@@ -101,7 +101,14 @@ typedef struct {
                                     least squares); s must be 4, 8 or 16.            */
   int32_t ir_max_outer;          /* FP32_IR: at most this many refinement steps (10)   */
   double ir_inner_tol;           /* FP32_IR: relative residual of each inner solve (1e-5) */
-  int32_t reserved[4];
+  int32_t cuda_graphs;           /* 1 (default): a restart cycle whose launch sequence
+                                    (matrix, block buffers, basis size, start mode,
+                                    skeleton, precision, workspace) is seen a second
+                                    time is captured into a CUDA graph, and later
+                                    occurrences replay it (same kernels, same
+                                    results); 0: every launch is issued directly.
+                                    Off while profile = 1.                            */
+  int32_t reserved[3];
 } lsba_options;
 
 enum { LSBA_PREC_FP64 = 0, LSBA_PREC_DF = 1, LSBA_PREC_AUTO = 2, LSBA_PREC_FP32_IR = 3 };
@@ -146,9 +153,12 @@ typedef struct {
 /* Fill *opt with the defaults. */
 void lsba_default_options(lsba_options* opt);
 
-/* Create a solver handle on `device`, ordered on `cuda_stream` (a cudaStream_t;
- * NULL = the legacy default stream).  opt may be NULL (defaults).  The handle
- * owns its workspace, allocated on first use and grown on demand. */
+/* Create a solver handle on `device`, ordered on `cuda_stream` (a cudaStream_t).
+ * NULL: the handle creates a blocking stream of its own, which the legacy
+ * default stream orders implicitly against its own work (the same ordering as
+ * launching on the legacy default stream, which cannot be captured into a
+ * graph).  opt may be NULL (defaults).  The handle owns its workspace,
+ * allocated on first use and grown on demand. */
 int lsba_create(lsba_handle* out, int device, void* cuda_stream, const lsba_options* opt);
 
 /* Replace the handle's options. */

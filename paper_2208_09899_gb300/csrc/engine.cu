@@ -77,7 +77,34 @@ struct lsba_ctx {
   size_t cdf_cap = 0;
   double prof_ms[LSBA_K_NCLASS] = {0, 0, 0, 0};
   int64_t prof_n[LSBA_K_NCLASS] = {0, 0, 0, 0};
+  // captured restart cycles (see run_cycle_body)
+  uint64_t ws_gen = 1;         // bumped whenever workspace buffers move
+  std::vector<struct CycleGraph> graphs;
+  uint64_t graph_clock = 0;
+  std::vector<uint8_t> side_recorded;  // side events recorded in the current cycle
+  bool own_stream = false;     // stream created by the handle (caller passed NULL)
 };
+
+// The launch sequence of one restart cycle is fixed by these values; a cycle
+// graph is reused only when all of them match.
+struct CycleKey {
+  const void* rowptr;
+  const void* colidx;
+  const void* vals;
+  const void* a_lowprec;
+  const double* rstart;
+  int64_t n;
+  int s, m_cur, start_flags, skel, modification, mode;
+  uint64_t ws_gen;
+  bool operator==(const CycleKey& o) const { return memcmp(this, &o, sizeof(*this)) == 0; }
+};
+struct CycleGraph {
+  CycleKey key;
+  cudaGraphExec_t exec;   // null until the key is seen a second time
+  uint64_t last_use;
+  bool failed;            // capture failed: issue this cycle directly
+};
+static const size_t LSBA_MAX_CYCLE_GRAPHS = 8;
 
 // Record the start event of a launch of kernel class `cls` (no-op unless profiling).
 static void prof_begin(lsba_ctx* h, int cls, cudaStream_t st) {
@@ -132,7 +159,15 @@ static void ws_free(lsba_ctx* h, void* p) {
   if (p) cudaFreeAsync(p, h->stream);
 }
 
+static void clear_graphs(lsba_ctx* h) {
+  for (auto& g : h->graphs)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+  h->graphs.clear();
+}
+
 static void free_ws(lsba_ctx* h) {
+  clear_graphs(h);
+  ++h->ws_gen;
   ws_free(h, h->basis);
   ws_free(h, h->Wb);
   ws_free(h, h->Ub);
@@ -431,9 +466,11 @@ static void enqueue_side(lsba_ctx* h, int k) {
   launch_small_side(h->side, h->ws, k);
   prof_end(h, h->side);
   cudaEventRecord(h->ev_side[k], h->side);
+  h->side_recorded[k] = 1;
 }
+// Join the side kernel of iteration k (if this cycle launched one).
 static void wait_side(lsba_ctx* h, int k) {
-  if (k >= 1) cudaStreamWaitEvent(h->stream, h->ev_side[k], 0);
+  if (k >= 1 && h->side_recorded[k]) cudaStreamWaitEvent(h->stream, h->ev_side[k], 0);
 }
 
 // Enqueue the CholQR of R_start and every loop iteration of one cycle.
@@ -443,6 +480,7 @@ static void enqueue_cycle(lsba_ctx* h, const lsba_csr* A, const double* Rstart, 
   const SmallWs& w = h->ws;
   const int skel = w.skel;
   Ctl* ctl = h->d_ctl;
+  h->side_recorded.assign(h->ev_side.size(), 0);
   BlockPtrs one;
   memset(&one, 0, sizeof(one));
   one.p[0] = Rstart;
@@ -552,6 +590,7 @@ void lsba_default_options(lsba_options* o) {
   o->precision = LSBA_PREC_AUTO;
   o->ir_max_outer = 10;
   o->ir_inner_tol = 1e-5;
+  o->cuda_graphs = 1;
 }
 
 const char* lsba_status_string(int st) {
@@ -578,6 +617,17 @@ int lsba_create(lsba_handle* out, int device, void* cuda_stream, const lsba_opti
   if (!h) return LSBA_OUT_OF_MEMORY;
   h->device = device;
   h->stream = (cudaStream_t)cuda_stream;
+  if (!h->stream) {
+    // The legacy default stream cannot be captured into a graph: run on a
+    // blocking stream of the handle's own, which the legacy default stream
+    // orders implicitly against its own work (same ordering for the caller).
+    if (cudaStreamCreate(&h->stream) != cudaSuccess) {
+      cudaGetLastError();
+      delete h;
+      return LSBA_CUDA_ERROR;
+    }
+    h->own_stream = true;
+  }
   if (opt) h->opt = *opt;
   else lsba_default_options(&h->opt);
   cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, device);
@@ -585,6 +635,7 @@ int lsba_create(lsba_handle* out, int device, void* cuda_stream, const lsba_opti
       cudaMallocHost(&h->h_ctl, sizeof(Ctl)) != cudaSuccess) {
     cudaGetLastError();
     cudaFree(h->d_ctl);
+    if (h->own_stream) cudaStreamDestroy(h->stream);
     delete h;
     return LSBA_OUT_OF_MEMORY;
   }
@@ -620,6 +671,7 @@ int lsba_destroy(lsba_handle h) {
   for (cudaEvent_t e : h->ev_main) cudaEventDestroy(e);
   for (cudaEvent_t e : h->ev_side) cudaEventDestroy(e);
   if (h->side) cudaStreamDestroy(h->side);
+  if (h->own_stream) cudaStreamDestroy(h->stream);
   delete h;
   return LSBA_OK;
 }
@@ -633,6 +685,81 @@ static int skel_code(lsba_skeleton s) {
     case LSBA_BMGS_CWY: return SK_CWY;
     default: return -1;
   }
+}
+
+// One restart cycle: control record to the device, the cycle's launches, the
+// control record back, one host synchronisation.  With options.cuda_graphs the
+// sequence is captured into a CUDA graph the second time its key is seen
+// (stream capture in thread-local mode, so solves on other host threads are
+// not disturbed) and replayed from then on; the copies of the pinned control
+// record are part of the graph and read/write it when the graph runs.
+static int run_cycle_body(lsba_handle h, const lsba_csr* A, const double* Rstart, int64_t n,
+                          int s, int m_cur, int start_flags) {
+  cudaStream_t st = h->stream;
+  CycleGraph* g = nullptr;
+  if (h->opt.cuda_graphs && !h->opt.profile) {
+    CycleKey key;
+    memset(&key, 0, sizeof(key));
+    key.rowptr = A->d_rowptr;
+    key.colidx = A->d_colidx;
+    key.vals = A->d_vals;
+    key.a_lowprec = h->mode == MODE_FP64 ? nullptr : h->A_df;
+    key.rstart = Rstart;
+    key.n = n;
+    key.s = s;
+    key.m_cur = m_cur;
+    key.start_flags = start_flags;
+    key.skel = h->ws.skel;
+    key.modification = h->ws.modification;
+    key.mode = h->mode;
+    key.ws_gen = h->ws_gen;
+    for (auto& e : h->graphs)
+      if (e.key == key) g = &e;
+    if (!g) {
+      if (h->graphs.size() >= LSBA_MAX_CYCLE_GRAPHS) {
+        size_t old = 0;
+        for (size_t i = 1; i < h->graphs.size(); ++i)
+          if (h->graphs[i].last_use < h->graphs[old].last_use) old = i;
+        if (h->graphs[old].exec) cudaGraphExecDestroy(h->graphs[old].exec);
+        h->graphs.erase(h->graphs.begin() + old);
+      }
+      h->graphs.push_back(CycleGraph{key, nullptr, ++h->graph_clock, false});
+      g = nullptr;  // first sighting: issue directly
+    } else {
+      g->last_use = ++h->graph_clock;
+      if (!g->exec && !g->failed) {
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+          cudaMemcpyAsync(h->d_ctl, h->h_ctl, sizeof(Ctl), cudaMemcpyHostToDevice, st);
+          enqueue_cycle(h, A, Rstart, n, s, m_cur, start_flags);
+          cudaMemcpyAsync(h->h_ctl, h->d_ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st);
+          e = cudaStreamEndCapture(st, &graph);
+        }
+        cudaGraphExec_t exec = nullptr;
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+          cudaGetLastError();
+          if (exec) cudaGraphExecDestroy(exec);
+          g->failed = true;
+        } else {
+          g->exec = exec;
+        }
+      }
+      if (g->failed) g = nullptr;
+    }
+  }
+  if (g && g->exec) {
+    CK(cudaGraphLaunch(g->exec, st));
+    CK(cudaStreamSynchronize(st));
+    return LSBA_OK;
+  }
+  int rc;
+  if ((rc = push_ctl(h)) != LSBA_OK) return rc;
+  enqueue_cycle(h, A, Rstart, n, s, m_cur, start_flags);
+  CK(cudaGetLastError());
+  return pull_ctl(h);
 }
 
 // Restart cycles of one (inner) solve of A X = B in the current working
@@ -668,10 +795,7 @@ static int run_cycles(lsba_handle h, const lsba_csr* A, const double* Bw, double
     c->record = (record_first && h->opt.record_history) ? 1 : 0;
     c->m_cur = m_cur;
     c->inject_relation = (cycle == h->opt.inject_flag_cycle) ? h->opt.inject_flag_relation : -1;
-    if ((rc = push_ctl(h)) != LSBA_OK) return rc;
-    enqueue_cycle(h, A, Rstart, n, s, m_cur, start_flags);
-    CK(cudaGetLastError());
-    if ((rc = pull_ctl(h)) != LSBA_OK) return rc;
+    if ((rc = run_cycle_body(h, A, Rstart, n, s, m_cur, start_flags)) != LSBA_OK) return rc;
     if (c->error) return LSBA_DEVICE_TIMEOUT;
     S.syncs += 1;
     S.cycles += 1;

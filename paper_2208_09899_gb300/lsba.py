@@ -36,7 +36,8 @@ class Options(C.Structure):
                 ("record_history", C.c_int32), ("inject_flag_cycle", C.c_int32),
                 ("inject_flag_relation", C.c_int32), ("profile", C.c_int32),
                 ("precision", C.c_int32), ("ir_max_outer", C.c_int32),
-                ("ir_inner_tol", C.c_double), ("reserved", C.c_int32 * 4)]
+                ("ir_inner_tol", C.c_double), ("cuda_graphs", C.c_int32),
+                ("reserved", C.c_int32 * 3)]
 
 
 class Stats(C.Structure):

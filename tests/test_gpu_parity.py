@@ -330,3 +330,37 @@ def test_rgg_graph_laplacian_restart_log(env, sk):
     X, st, hist, ref = _compare_solve(lsba, A, B, 16, 1e-8, sk, "gmres", max_restarts=2,
                                       x_tol=1e-6)
     assert st["status"] == lsba.LSBA_NOT_CONVERGED and st["cycles"] == 3
+
+
+@pytest.mark.parametrize("sk,precision", [("bcgsi_ls", "df"), ("bcgs_pip", "fp64"),
+                                          ("bcgs", "auto"), ("bmgs_icwy", "fp32_ir")])
+def test_cuda_graph_replay_is_bitwise_identical(env, sk, precision):
+    """Restart cycles captured into CUDA graphs (second sighting) and replayed
+    (third and later) give the same bits, counters and restart log as direct
+    launches."""
+    torch, lsba = env
+    A = W.laplacian_2d(40, 37)
+    B = W.gaussian_block(A.n, 4, 5)
+    dA = lsba.DeviceCSR.from_host(A)
+    dB = torch.from_numpy(B).cuda()
+    opts = dict(modification="gmres", max_restarts=200, precision=precision, record_history=1)
+    ref_sv = lsba.Solver(0, cuda_graphs=0, **opts)
+    dX = torch.empty_like(dB)
+    ref_sv.solve(dA, dB, dX, 8, 1e-10, sk)
+    torch.cuda.synchronize()
+    X0, st0, h0 = dX.cpu().numpy(), ref_sv.stats(), ref_sv.history()
+    ref_sv.close()
+    assert st0["cycles"] >= 3
+    sv = lsba.Solver(0, cuda_graphs=1, **opts)
+    for _ in range(3):
+        dX.zero_()
+        sv.solve(dA, dB, dX, 8, 1e-10, sk)
+        torch.cuda.synchronize()
+        st, h = sv.stats(), sv.history()
+        assert np.array_equal(dX.cpu().numpy(), X0)
+        for key in ("status", "cycles", "steps", "a_calls", "syncs", "v_apps", "flags", "m_final"):
+            assert st[key] == st0[key], key
+        assert st["relres_true"] == st0["relres_true"]
+        assert h["cycle_m"] == h0["cycle_m"] and h["cycle_flag"] == h0["cycle_flag"]
+        assert np.array_equal(h["est"], h0["est"])
+    sv.close()
