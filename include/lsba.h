@@ -108,7 +108,13 @@ typedef struct {
                                     occurrences replay it (same kernels, same
                                     results); 0: every launch is issued directly.
                                     Off while profile = 1.                            */
-  int32_t reserved[3];
+  int32_t tensor_cores;          /* 1 (default): the double-float Gram passes whose
+                                    shape the tensor-core digit kernel runs faster
+                                    (b s = 16 and a s >= 160, a s + b s <= 256) use
+                                    it (exact digit products, 48-bit accuracy); 2:
+                                    every pass whose shape it allows; 0: FP32-pipe
+                                    kernels only.                                      */
+  int32_t reserved[2];
 } lsba_options;
 
 enum { LSBA_PREC_FP64 = 0, LSBA_PREC_DF = 1, LSBA_PREC_AUTO = 2, LSBA_PREC_FP32_IR = 3 };
@@ -224,6 +230,18 @@ int lsba_spmm(lsba_handle h, const lsba_csr* A, const double* d_V, double* d_W, 
  * Summation order is fixed: the result is bitwise reproducible run to run. */
 int lsba_gram(lsba_handle h, const double* d_L, int a, const double* d_R, int b,
               int64_t n, int s, double* d_G);
+
+/* The same G as lsba_gram, computed by the double-float Gram kernels of the
+ * solver (the block inner product of every skeleton, Sec. 2): L and R are
+ * converted to hi + lo FP32 pairs on the device, G is returned in FP64.
+ * tensor_cores = 1 selects the tensor-core digit kernel wherever its shape
+ * allows (s % 4 == 0, b s <= 16, (a + b) s <= 256), 0 the FP32-pipe kernel.
+ * b <= 2.
+ * Temporary copies are allocated stream-ordered on the handle's stream and
+ * released before return.  LSBA_DEVICE_TIMEOUT if a kernel's bounded wait
+ * gave up. */
+int lsba_gram_df(lsba_handle h, const double* d_L, int a, const double* d_R, int b, int64_t n,
+                 int s, double* d_G, int tensor_cores);
 
 /* Block combination (the basis update of Alg. 3 line 6 / Alg. 7 lines 16-17):
  *   out[r,:] = ( sum_i in_i[r,:] * C_i ) * T^{-1}

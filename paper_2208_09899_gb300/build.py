@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "liblsba.so")
 SOURCES = ["engine.cu", "kernels_big.cu", "kernels_small.cu", "kernels_df.cu", "kernels_f32.cu",
-           "noalloc.cu"]
+           "kernels_tc.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -46,7 +46,7 @@ def build(force: bool = False, verbose_ptxas: bool = False) -> str:
     os.makedirs(OUT_DIR, exist_ok=True)
     srcs = [os.path.join(CSRC, s) for s in SOURCES] + [
         os.path.join(CSRC, "lsba_internal.cuh"), os.path.join(CSRC, "df.cuh"),
-        os.path.join(CSRC, "tma.cuh"),
+        os.path.join(CSRC, "tma.cuh"), os.path.join(CSRC, "tc.cuh"),
         os.path.join(ROOT, "include", "lsba.h")]
     if not force and os.path.exists(LIB):
         t = os.path.getmtime(LIB)

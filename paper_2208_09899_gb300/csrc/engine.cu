@@ -94,7 +94,7 @@ struct CycleKey {
   const void* a_lowprec;
   const double* rstart;
   int64_t n;
-  int s, m_cur, start_flags, skel, modification, mode;
+  int s, m_cur, start_flags, skel, modification, mode, tensor_cores;
   uint64_t ws_gen;
   bool operator==(const CycleKey& o) const { return memcmp(this, &o, sizeof(*this)) == 0; }
 };
@@ -196,9 +196,11 @@ static size_t max_partials(int64_t n, int s, int mmax, int sms, size_t* qmax_out
       size_t v = (size_t)p.grid_x * p.q;
       if (v > best) best = v;
       if ((size_t)p.q > qmax) qmax = p.q;
-      GramPlan pd = plan_gram_df(n, s, a, b, sms);
-      v = (size_t)pd.grid_x * pd.q;
-      if (v > best) best = v;
+      for (int tc = 0; tc < 3; tc += 2) {
+        GramPlan pd = plan_gram_df(n, s, a, b, sms, tc);
+        v = (size_t)pd.grid_x * pd.q;
+        if (v > best) best = v;
+      }
       if (s % 4 == 0) {
         GramPlan pf = plan_gram_f32(n, s, a, b, sms);
         v = (size_t)pf.grid_x * pf.q;
@@ -413,7 +415,7 @@ static void do_gram(lsba_ctx* h, const BlockPtrs& L, int a, const BlockPtrs& R, 
                     int s, const Ctl* ctl, int guard) {
   prof_begin(h, LSBA_K_GRAM);
   if (h->mode == MODE_DF) {
-    GramPlan p = plan_gram_df(n, s, a, b, h->num_sms);
+    GramPlan p = plan_gram_df(n, s, a, b, h->num_sms, h->opt.tensor_cores);
     launch_gram_df(h->stream, p, L, a, R, b, n, s, (float2*)h->partials, h->Gbuf, ctl, guard,
                    &h->d_ctl->error);
   } else if (h->mode == MODE_F32) {
@@ -591,6 +593,7 @@ void lsba_default_options(lsba_options* o) {
   o->ir_max_outer = 10;
   o->ir_inner_tol = 1e-5;
   o->cuda_graphs = 1;
+  o->tensor_cores = 1;
 }
 
 const char* lsba_status_string(int st) {
@@ -712,6 +715,7 @@ static int run_cycle_body(lsba_handle h, const lsba_csr* A, const double* Rstart
     key.skel = h->ws.skel;
     key.modification = h->ws.modification;
     key.mode = h->mode;
+    key.tensor_cores = h->opt.tensor_cores;
     key.ws_gen = h->ws_gen;
     for (auto& e : h->graphs)
       if (e.key == key) g = &e;
@@ -1230,6 +1234,53 @@ int lsba_gram(lsba_handle h, const double* d_L, int a, const double* d_R, int b,
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(h->stream));
   return LSBA_OK;
+}
+
+int lsba_gram_df(lsba_handle h, const double* d_L, int a, const double* d_R, int b, int64_t n,
+                 int s, double* d_G, int tensor_cores) {
+  if (!h || !d_L || !d_R || !d_G || a < 1 || b < 1 || b > 2 || s < 1 || s > LSBA_MAX_S || n < 1 ||
+      a + b > LSBA_MAXB || (int64_t)a * s > LSBA_MAX_MS)
+    return LSBA_INVALID_ARG;
+  CK(cudaSetDevice(h->device));
+  cudaStream_t st = h->stream;
+  GramPlan p = plan_gram_df(n, s, a, b, h->num_sms, tensor_cores ? 2 : 0);
+  const size_t need = (size_t)p.grid_x * p.q;
+  if (need > h->partials_cap) {
+    ws_free(h, h->partials);
+    h->partials = nullptr;
+    h->partials_cap = 0;
+    if (ws_alloc(h, &h->partials, sizeof(double) * need) != cudaSuccess) {
+      cudaGetLastError();
+      return LSBA_OUT_OF_MEMORY;
+    }
+    h->partials_cap = need;
+  }
+  float2 *Ldf = nullptr, *Rdf = nullptr;
+  const size_t la = (size_t)a * n * s, lb = (size_t)b * n * s;
+  if (ws_alloc(h, &Ldf, sizeof(float2) * la) != cudaSuccess ||
+      ws_alloc(h, &Rdf, sizeof(float2) * lb) != cudaSuccess) {
+    cudaGetLastError();
+    ws_free(h, Ldf);
+    ws_free(h, Rdf);
+    return LSBA_OUT_OF_MEMORY;
+  }
+  launch_to_df(st, (int64_t)la, d_L, Ldf);
+  launch_to_df(st, (int64_t)lb, d_R, Rdf);
+  BlockPtrs L, R;
+  memset(&L, 0, sizeof(L));
+  memset(&R, 0, sizeof(R));
+  for (int i = 0; i < a; ++i) L.p[i] = (const double*)(Ldf + (size_t)i * n * s);
+  for (int i = 0; i < b; ++i) R.p[i] = (const double*)(Rdf + (size_t)i * n * s);
+  CK(cudaMemsetAsync(&h->d_ctl->error, 0, sizeof(int), st));
+  launch_gram_df(st, p, L, a, R, b, n, s, (float2*)h->partials, d_G, nullptr, 0, &h->d_ctl->error);
+  CK(cudaGetLastError());
+  int err = 0;
+  CK(cudaMemcpyAsync(&h->h_ctl->error, &h->d_ctl->error, sizeof(int), cudaMemcpyDeviceToHost, st));
+  ws_free(h, Ldf);
+  ws_free(h, Rdf);
+  CK(cudaStreamSynchronize(st));
+  err = h->h_ctl->error;
+  return err ? LSBA_DEVICE_TIMEOUT : LSBA_OK;
 }
 
 int lsba_combine(lsba_handle h, const double* d_in, int nin, int64_t n, int s, const double* d_C,

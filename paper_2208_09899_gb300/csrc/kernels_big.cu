@@ -144,7 +144,7 @@ __global__ void k_gram_reduce(const double* __restrict__ partials, int nparts, i
 }
 
 GramPlan plan_gram(int64_t n, int s, int a, int b, int num_sms) {
-  GramPlan p;
+  GramPlan p{};
   p.q = a * s * b * s;
   p.tile = GRAM_THREADS * GRAM_EPT;
   p.grid_y = (p.q + p.tile - 1) / p.tile;

@@ -396,8 +396,15 @@ __global__ void k_gram_reduce_df(const float2* __restrict__ partials, int nparts
   G[e] = dfacc_to_double(acc);
 }
 
-GramPlan plan_gram_df(int64_t n, int s, int a, int b, int num_sms) {
-  GramPlan p;
+GramPlan plan_gram_df(int64_t n, int s, int a, int b, int num_sms, int tensor_cores) {
+  if ((tensor_cores == 2 && gram_tc_eligible(s, a, b)) ||
+      (tensor_cores == 1 && gram_tc_profitable(s, a, b))) {
+    GramPlan t = plan_gram_tc(n, s, a, b, num_sms);
+    t.tc = 1;
+    return t;
+  }
+  GramPlan p{};
+  p.tc = 0;
   const int sp = (s + 3) & ~3;
   p.q = a * s * b * s;
   const int ntile = (a * sp / 4) * (b * sp / 4);
@@ -456,6 +463,11 @@ void launch_gram_df(cudaStream_t st, const GramPlan& p, const BlockPtrs& L, int 
     cudaFuncSetAttribute(k_gram_df, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(k_gram_df_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   });
+  if (p.tc) {
+    launch_gram_tc(st, p, L, a, R, b, n, s, partials, ctl, guard, err);
+    k_gram_reduce_df<<<(p.q + 255) / 256, 256, 0, st>>>(partials, p.grid_x, p.q, G, ctl, guard);
+    return;
+  }
   dim3 grid(p.grid_x, p.grid_y);
   const int sp = (s + 3) & ~3;
   if (sp == s) {

@@ -209,7 +209,7 @@ __global__ void k_gram_reduce_f32(const float* __restrict__ partials, int nparts
 }
 
 GramPlan plan_gram_f32(int64_t n, int s, int a, int b, int num_sms) {
-  GramPlan p;
+  GramPlan p{};
   p.q = a * s * b * s;
   const int ntile = (a * s / 4) * (b * s / 4);
   p.tile = GF_THREADS;

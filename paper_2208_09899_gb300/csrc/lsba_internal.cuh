@@ -120,6 +120,7 @@ struct GramPlan {
   int rows_per_chunk;
   int64_t rows_per_cta;
   int nl_max;     // bulk-copy Gram kernels: most left blocks one tile group reads
+  int tc;         // double-float Gram on the tensor cores (k_gram_df_tc)
 };
 
 // Left blocks [first, first + count) that the output tiles tile_base ..
@@ -149,7 +150,17 @@ void launch_from_df(cudaStream_t st, int64_t count, const float2* in, double* ou
 void launch_sub_df(cudaStream_t st, int64_t count, const float2* B, const float2* W, float2* R);
 void launch_spmm_df(cudaStream_t st, int64_t n, const int32_t* rowptr, const int32_t* colidx,
                     const float2* vals, const float2* V, float2* W, int s, const Ctl* ctl, int guard);
-GramPlan plan_gram_df(int64_t n, int s, int a, int b, int num_sms);
+// tensor_cores: 0 FP32-pipe kernels only; 1 the tensor-core kernel where it
+// measured faster (gram_tc_profitable); 2 wherever its shape allows.
+GramPlan plan_gram_df(int64_t n, int s, int a, int b, int num_sms, int tensor_cores = 1);
+// Tensor-core double-float Gram (kernels_tc.cu): shapes with s % 4 == 0,
+// b s <= 16 and a s + b s <= 256.
+bool gram_tc_eligible(int s, int a, int b);
+bool gram_tc_profitable(int s, int a, int b);
+GramPlan plan_gram_tc(int64_t n, int s, int a, int b, int num_sms);
+void launch_gram_tc(cudaStream_t st, const GramPlan& p, const BlockPtrs& L, int a,
+                    const BlockPtrs& R, int b, int64_t n, int s, float2* partials,
+                    const Ctl* ctl, int guard, int* err);
 void launch_gram_df(cudaStream_t st, const GramPlan& p, const BlockPtrs& L, int a,
                     const BlockPtrs& R, int b, int64_t n, int s, float2* partials, double* G,
                     const Ctl* ctl, int guard, int* err);

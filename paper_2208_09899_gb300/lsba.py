@@ -26,7 +26,7 @@ EXPORTED = ("lsba_default_options", "lsba_create", "lsba_set_options", "lsba_sol
             "lsba_solve_host", "lsba_get_stats", "lsba_get_history", "lsba_status_string",
             "lsba_destroy", "lsba_spmm", "lsba_gram", "lsba_combine", "lsba_get_profile",
             "lsba_reset_profile", "lsba_gram_noalloc", "lsba_release_workspace",
-            "lsba_workspace_bytes")
+            "lsba_workspace_bytes", "lsba_gram_df")
 KERNEL_CLASSES = ("spmm", "gram", "update", "small")
 
 
@@ -37,7 +37,7 @@ class Options(C.Structure):
                 ("inject_flag_relation", C.c_int32), ("profile", C.c_int32),
                 ("precision", C.c_int32), ("ir_max_outer", C.c_int32),
                 ("ir_inner_tol", C.c_double), ("cuda_graphs", C.c_int32),
-                ("reserved", C.c_int32 * 3)]
+                ("tensor_cores", C.c_int32), ("reserved", C.c_int32 * 2)]
 
 
 class Stats(C.Structure):
@@ -95,6 +95,7 @@ def load(path: str = LIB_PATH):
     lib.lsba_gram_noalloc.argtypes = [vp, i32, vp, i32, i64, i32, vp, vp]
     lib.lsba_release_workspace.argtypes = [vp]
     lib.lsba_workspace_bytes.argtypes = [i64, i64, i32, i32]
+    lib.lsba_gram_df.argtypes = [vp, vp, i32, vp, i32, i64, i32, vp, i32]
     for name in EXPORTED:
         if name not in ("lsba_default_options", "lsba_status_string"):
             getattr(lib, name).restype = C.c_int
@@ -285,6 +286,13 @@ class Solver:
         b = R.shape[0]
         _check(self.lib.lsba_gram(self.h, C.c_void_p(_ptr(L)), a, C.c_void_p(_ptr(R)), b, n, s,
                                   C.c_void_p(_ptr(G))))
+
+    def gram_df(self, L, R, G, tensor_cores: bool = True):
+        """Double-float Gram kernels: L (a, n, s), R (b, n, s) CUDA FP64 -> G (a*s, b*s)."""
+        a, n, s = L.shape
+        b = R.shape[0]
+        _check(self.lib.lsba_gram_df(self.h, C.c_void_p(_ptr(L)), a, C.c_void_p(_ptr(R)), b, n, s,
+                                     C.c_void_p(_ptr(G)), int(tensor_cores)))
 
     def combine(self, inputs, coef, tri, out):
         """inputs: (nin, n, s); coef: (nin*s, s); tri: (s, s) upper or None; out: (n, s)."""

@@ -79,6 +79,37 @@ def test_gram_matches_oracle_and_is_reproducible(env, s, a, b, n):
     assert np.array_equal(G1, dG.cpu().numpy())
 
 
+@pytest.mark.parametrize("tc", [True, False])
+@pytest.mark.parametrize("s,a,b,n", [(8, 21, 2, 70001), (8, 1, 1, 1000), (4, 3, 2, 1000),
+                                     (8, 30, 2, 5003), (16, 8, 1, 40003), (4, 60, 2, 2049),
+                                     (8, 21, 2, 31), (8, 16, 1, 4096)])
+def test_gram_df_kernels_match_oracle(env, s, a, b, n, tc):
+    """Double-float Gram kernels (tensor-core digit kernel and FP32-pipe kernel)
+    against the FP64 oracle product, entry by entry relative to |L|^T |R|: a
+    double-float value carries 48 significand bits (the FP32-pipe kernel's
+    error is a few 2^-48 |x||y| per product), and the digit kernel represents
+    each value to 2^-48 of its column's maximum over 32 rows.  Bound:
+    64 * 2^-48 |L|^T |R|.  Both kernels are bitwise reproducible."""
+    torch, lsba = env
+    rng = np.random.default_rng(a * 1000 + s + n)
+    L = rng.standard_normal((a, n, s))
+    R = rng.standard_normal((b, n, s))
+    sv = lsba.Solver(0)
+    dL, dR = torch.from_numpy(L).cuda(), torch.from_numpy(R).cuda()
+    dG = torch.empty((a * s, b * s), dtype=torch.float64, device="cuda")
+    sv.gram_df(dL, dR, dG, tensor_cores=tc)
+    G1 = dG.cpu().numpy()
+    Lh, Rh = np.hstack(list(L)), np.hstack(list(R))
+    ref = O.inner(Lh, Rh)
+    scale = O.inner(np.abs(Lh), np.abs(Rh))
+    err = np.max(np.abs(G1 - ref) / scale)
+    print(f"GRAMDF s={s} a={a} b={b} n={n} tc={tc} err/(|L|^T|R|)={err:.2e} "
+          f"normwise={_rel(G1, ref):.2e}")
+    assert err <= 64 * 2.0 ** -48
+    sv.gram_df(dL, dR, dG, tensor_cores=tc)
+    assert np.array_equal(G1, dG.cpu().numpy())
+
+
 @pytest.mark.parametrize("s,nin,n,tri", [(4, 3, 1001, True), (8, 22, 9999, True),
                                          (16, 18, 4097, False), (3, 2, 17, True), (32, 4, 300, True)])
 def test_combine_matches_oracle(env, s, nin, n, tri):
@@ -364,3 +395,16 @@ def test_cuda_graph_replay_is_bitwise_identical(env, sk, precision):
         assert h["cycle_m"] == h0["cycle_m"] and h["cycle_flag"] == h0["cycle_flag"]
         assert np.array_equal(h["est"], h0["est"])
     sv.close()
+
+
+@pytest.mark.parametrize("sk,s,m", [("bcgsi_ls", 4, 8), ("bcgsi_ls", 8, 12), ("bmgs_icwy", 8, 10),
+                                    ("bmgs_cwy", 4, 8)])
+def test_tensor_core_gram_in_solves(env, sk, s, m):
+    """Double-float solves with every eligible Gram on the tensor-core digit
+    kernel (tensor_cores = 2): same restart log and counters as the oracle,
+    first-cycle Gram outputs and Hessenberg within 1e-11, and X within 1e-8."""
+    torch, lsba = env
+    A = W.laplacian_2d(48, 41)
+    B = W.gaussian_block(A.n, s, 31)
+    _compare_solve(lsba, A, B, m, 1e-10, sk, "gmres", max_restarts=200, precision="df",
+                   tensor_cores=2)
