@@ -260,6 +260,35 @@ def rgg_cycles(torch, lsba, dev, stream):
     return out
 
 
+def gram_kernels(torch, lsba, dev, n=262144, s=8, b=2, reps=5):
+    """Double-float Gram kernels alone (CUDA events around each launch):
+    the tensor-core digit kernel vs the FP32-pipe kernel, L = a blocks and
+    R = b blocks of n x s N(0,1) values, device time per launch."""
+    rng = np.random.default_rng(0)
+    amax = 30
+    dL = torch.from_numpy(rng.standard_normal((amax, n, s))).to(f"cuda:{dev}")
+    dR = torch.from_numpy(rng.standard_normal((b, n, s))).to(f"cuda:{dev}")
+    sv = lsba.Solver(dev, profile=1)
+    out = {"workload": f"G = L^T R, L: a blocks, R: {b} blocks of n={n} x s={s} N(0,1); "
+                       "us per Gram launch (digit kernel with its reduction; FP32-pipe kernel "
+                       "with its reduction)", "a": {}}
+    for a in (4, 8, 12, 16, 21, 25, 30):
+        L = dL[:a].contiguous()
+        dG = torch.empty((a * s, b * s), dtype=torch.float64, device=f"cuda:{dev}")
+        row = {}
+        for tc in (True, False):
+            sv.gram_df(L, dR, dG, tensor_cores=tc)
+            sv.reset_profile()
+            for _ in range(reps):
+                sv.gram_df(L, dR, dG, tensor_cores=tc)
+            ms, cnt = sv.profile()["gram"]
+            row["tensor_core_us" if tc else "fp32_pipe_us"] = ms / max(cnt, 1) * 1e3
+        row["speedup"] = row["fp32_pipe_us"] / row["tensor_core_us"]
+        out["a"][str(a)] = row
+    sv.close()
+    return out
+
+
 def serving(torch, lsba, dev, count, seed=5, slots=16, cap_gb=150.0):
     """Continuous batching: a seeded mix of block solves (3D 7-point Laplacian
     + delta I, delta ~ U[0,0.1], side N ~ U{22..100}, s ~ U{1,4,8,16,32},
@@ -352,6 +381,7 @@ def main():
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-rgg", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-gram-kernels", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=32)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -428,7 +458,8 @@ def main():
     peak = DF_PEAK_TFLOPS if is_df else FP64_PEAK_TFLOPS
     suffix = "_df" if is_df else ""
     roofline = {
-        "kernel": {"gram": f"k_gram{suffix}+k_gram_reduce{suffix}",
+        "kernel": {"gram": ("k_gram_df_tma (k_gram_df_tc where a s >= 160) + k_gram_reduce_df" if is_df
+                            else "k_gram + k_gram_reduce"),
                    "update": ("k_coef_df+k_update_df" if is_df else "k_update"),
                    "spmm": f"k_spmm{suffix}"}[dom],
         "bound": "alu", "achieved": achieved_tflops, "peak": peak, "unit": "TFLOP/s",
@@ -524,6 +555,7 @@ def main():
     mixed = None if args.no_mixed else mixed_precision(torch, lsba, dev, stream)
     rgg = None if args.no_rgg else rgg_cycles(torch, lsba, dev, stream)
     served = None if args.no_serving else serving(torch, lsba, dev, args.serve_requests)
+    gk = None if args.no_gram_kernels else gram_kernels(torch, lsba, dev)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -554,7 +586,7 @@ def main():
             "roofline": roofline, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": gpu_launches, "clocks": clocks, "time_to_tol": time_to_tol,
             "fp64_plain": fp64_plain, "mixed_precision": mixed, "graph_workload": rgg,
-            "serving": served,
+            "serving": served, "gram_kernels": gk,
         }
         print(json.dumps(line))
     if pg:

@@ -239,7 +239,8 @@ int lsba_gram(lsba_handle h, const double* d_L, int a, const double* d_R, int b,
  * b <= 2.
  * Temporary copies are allocated stream-ordered on the handle's stream and
  * released before return.  LSBA_DEVICE_TIMEOUT if a kernel's bounded wait
- * gave up. */
+ * gave up.  With options.profile = 1 the Gram kernels' device time (without
+ * the conversions) is added to the LSBA_K_GRAM class of lsba_get_profile. */
 int lsba_gram_df(lsba_handle h, const double* d_L, int a, const double* d_R, int b, int64_t n,
                  int s, double* d_G, int tensor_cores);
 

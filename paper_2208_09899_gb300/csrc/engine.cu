@@ -1272,13 +1272,16 @@ int lsba_gram_df(lsba_handle h, const double* d_L, int a, const double* d_R, int
   for (int i = 0; i < a; ++i) L.p[i] = (const double*)(Ldf + (size_t)i * n * s);
   for (int i = 0; i < b; ++i) R.p[i] = (const double*)(Rdf + (size_t)i * n * s);
   CK(cudaMemsetAsync(&h->d_ctl->error, 0, sizeof(int), st));
+  prof_begin(h, LSBA_K_GRAM);
   launch_gram_df(st, p, L, a, R, b, n, s, (float2*)h->partials, d_G, nullptr, 0, &h->d_ctl->error);
+  prof_end(h);
   CK(cudaGetLastError());
   int err = 0;
   CK(cudaMemcpyAsync(&h->h_ctl->error, &h->d_ctl->error, sizeof(int), cudaMemcpyDeviceToHost, st));
   ws_free(h, Ldf);
   ws_free(h, Rdf);
   CK(cudaStreamSynchronize(st));
+  prof_collect(h);
   err = h->h_ctl->error;
   return err ? LSBA_DEVICE_TIMEOUT : LSBA_OK;
 }

@@ -396,10 +396,9 @@ bool gram_tc_eligible(int s, int a, int b) {
 }
 
 // Where the digit kernel measured faster than the FP32-pipe kernel on GB300
-// (n = 2^18, both kernels timed alone): with all 16 R columns and at least
-// 160 L columns (s = 8, b = 2, a >= 20: 1.4-1.7x).  Its cost per chunk is
-// nearly independent of the column count up to there, while the FP32-pipe
-// kernel's grows with a b s^2.
+// (n = 2^18, both kernels timed alone, s = 8, b = 2): a s >= 160 (one thread
+// per column; 1.4-1.7x for a = 20..30).  Its cost per chunk depends little on
+// the column count there, while the FP32-pipe kernel's grows with a b s^2.
 bool gram_tc_profitable(int s, int a, int b) {
   return gram_tc_eligible(s, a, b) && b * s == GTC_NP && a * s >= 160;
 }
