@@ -275,9 +275,16 @@ __global__ void __launch_bounds__(GDF_THREADS) k_gram_df_tma(const __grid_consta
   const int64_t r_end = min(g.n, r_begin + g.rows_per_cta);
   const int nchunks = r_end > r_begin ? (int)((r_end - r_begin + rc - 1) / rc) : 0;
 
+  // bars[0..1]: stage full (copies landed); bars[2..3]: stage empty (every
+  // warp has finished reading it).  Only the copy-issuing thread waits for a
+  // stage to drain, so warps are not held in step by a CTA-wide barrier.
+  uint64_t* empty = bars + 2;
+  const int lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
     mbar_init(&bars[0], 1);
     mbar_init(&bars[1], 1);
+    mbar_init(&empty[0], GDF_THREADS / 32);
+    mbar_init(&empty[1], GDF_THREADS / 32);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
@@ -307,11 +314,9 @@ __global__ void __launch_bounds__(GDF_THREADS) k_gram_df_tma(const __grid_consta
   for (int c = 0; c < nchunks; ++c) {
     const int st = c & 1;
     const unsigned parity = (unsigned)((c >> 1) & 1);
-    const bool ok = mbar_wait_bounded(&bars[st], parity);
-    if (__syncthreads_or(!ok)) {
-      failed = true;
-      break;
-    }
+    if (!failed && !mbar_wait_bounded(&bars[st], parity)) failed = true;
+    failed = __any_sync(0xffffffffu, failed);
+    if (failed) break;
     const float2* buf = st ? stage1 : stage0;
     const int rows = (int)min((int64_t)rc, r_end - (r_begin + (int64_t)c * rc));
     if (active) {
@@ -333,13 +338,18 @@ __global__ void __launch_bounds__(GDF_THREADS) k_gram_df_tma(const __grid_consta
 #pragma unroll
         for (int y = 0; y < 4; ++y) df_renorm(acc[x][y]);
     }
-    __syncthreads();  // every thread is done reading this stage
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty[st]);  // this warp is done reading the stage
     if (threadIdx.x == 0 && c + 2 < nchunks) {
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      issue(c + 2, st);
+      if (mbar_wait_bounded(&empty[st], parity)) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        issue(c + 2, st);
+      } else {
+        failed = true;
+      }
     }
   }
-  if (failed) {
+  if (__syncthreads_or(failed)) {
     if (threadIdx.x == 0) {
       if (g.err) atomicExch(g.err, 1);
       // Let this CTA's copies in flight land before the shared memory goes away.
@@ -386,14 +396,30 @@ __global__ void __launch_bounds__(GDF_THREADS) k_gram_df_tma(const __grid_consta
   }
 }
 
-__global__ void k_gram_reduce_df(const float2* __restrict__ partials, int nparts, int q,
-                                 double* __restrict__ G, const Ctl* ctl, int guard) {
+// 32 outputs per CTA; the 8 warps sum fixed eighths of the partials (warp y:
+// partials [y P/8, (y+1) P/8) in order), then warp 0 adds the eight sums in
+// order: a fixed summation order for a given plan.
+__global__ void __launch_bounds__(256) k_gram_reduce_df(const float2* __restrict__ partials,
+                                                        int nparts, int q, double* __restrict__ G,
+                                                        const Ctl* ctl, int guard) {
   if (guard && !ctl_active_df(ctl)) return;
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= q) return;
+  __shared__ float2 part[8][32];
+  const int ox = threadIdx.x & 31, gy = threadIdx.x >> 5;
+  const int e = blockIdx.x * 32 + ox;
   dfacc acc{0.f, 0.f};
-  for (int x = 0; x < nparts; ++x) df_add_to(acc, partials[(int64_t)x * q + e]);
-  G[e] = dfacc_to_double(acc);
+  if (e < q) {
+    const int per = (nparts + 7) / 8;
+    const int x0 = gy * per, x1 = min(nparts, x0 + per);
+    for (int x = x0; x < x1; ++x) df_add_to(acc, partials[(int64_t)x * q + e]);
+  }
+  part[gy][ox] = df_value(acc);
+  __syncthreads();
+  if (gy == 0 && e < q) {
+    dfacc t{0.f, 0.f};
+#pragma unroll
+    for (int y = 0; y < 8; ++y) df_add_to(t, part[y][ox]);
+    G[e] = dfacc_to_double(t);
+  }
 }
 
 GramPlan plan_gram_df(int64_t n, int s, int a, int b, int num_sms, int tensor_cores) {
@@ -465,7 +491,7 @@ void launch_gram_df(cudaStream_t st, const GramPlan& p, const BlockPtrs& L, int 
   });
   if (p.tc) {
     launch_gram_tc(st, p, L, a, R, b, n, s, partials, ctl, guard, err);
-    k_gram_reduce_df<<<(p.q + 255) / 256, 256, 0, st>>>(partials, p.grid_x, p.q, G, ctl, guard);
+    k_gram_reduce_df<<<(p.q + 31) / 32, 256, 0, st>>>(partials, p.grid_x, p.q, G, ctl, guard);
     return;
   }
   dim3 grid(p.grid_x, p.grid_y);
@@ -508,7 +534,7 @@ void launch_gram_df(cudaStream_t st, const GramPlan& p, const BlockPtrs& L, int 
     g.guard = guard;
     k_gram_df<<<grid, GDF_THREADS, p.smem, st>>>(g);
   }
-  k_gram_reduce_df<<<(p.q + 255) / 256, 256, 0, st>>>(partials, p.grid_x, p.q, G, ctl, guard);
+  k_gram_reduce_df<<<(p.q + 31) / 32, 256, 0, st>>>(partials, p.grid_x, p.q, G, ctl, guard);
 }
 
 // ----------------------------------------------------------------- Update
