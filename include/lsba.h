@@ -235,8 +235,11 @@ int lsba_gram(lsba_handle h, const double* d_L, int a, const double* d_R, int b,
  * solver (the block inner product of every skeleton, Sec. 2): L and R are
  * converted to hi + lo FP32 pairs on the device, G is returned in FP64.
  * tensor_cores = 1 selects the tensor-core digit kernel wherever its shape
- * allows (s % 4 == 0, b s <= 16, (a + b) s <= 256), 0 the FP32-pipe kernel.
- * b <= 2.
+ * allows (s % 4 == 0, b s <= 16, (a + b) s <= 256), 0 the FP32-pipe kernel,
+ * 3 the tensor-core kernel on stored digit planes that the solver uses for a
+ * lagged skeleton's basis (s = 8, b = 2, 2 <= a, a s <= 168): L_1..L_{a-1}
+ * are split into digit planes first and R_1 stands for L_a, so the result is
+ * [L_1..L_{a-1}, R_1]^T [R_1, R_2].  b <= 2.
  * Temporary copies are allocated stream-ordered on the handle's stream and
  * released before return.  LSBA_DEVICE_TIMEOUT if a kernel's bounded wait
  * gave up.  With options.profile = 1 the Gram kernels' device time (without

@@ -75,6 +75,11 @@ struct lsba_ctx {
   double* Xdf = nullptr;
   float2* cdf = nullptr;       // converted update coefficients
   size_t cdf_cap = 0;
+  // stored digit planes of the basis (tensor-core Gram, s = 8): block i at
+  // dig + i * digit_block_bytes(n, s), exponents at dexp + i * digit_exp_count(n, s)
+  unsigned char* dig = nullptr;
+  int* dexp = nullptr;
+  bool use_tcs = false;
   double prof_ms[LSBA_K_NCLASS] = {0, 0, 0, 0};
   int64_t prof_n[LSBA_K_NCLASS] = {0, 0, 0, 0};
   // captured restart cycles (see run_cycle_body)
@@ -168,6 +173,10 @@ static void clear_graphs(lsba_ctx* h) {
 static void free_ws(lsba_ctx* h) {
   clear_graphs(h);
   ++h->ws_gen;
+  ws_free(h, h->dig);
+  ws_free(h, h->dexp);
+  h->dig = nullptr;
+  h->dexp = nullptr;
   ws_free(h, h->basis);
   ws_free(h, h->Wb);
   ws_free(h, h->Ub);
@@ -199,6 +208,11 @@ static size_t max_partials(int64_t n, int s, int mmax, int sms, size_t* qmax_out
       for (int tc = 0; tc < 3; tc += 2) {
         GramPlan pd = plan_gram_df(n, s, a, b, sms, tc);
         v = (size_t)pd.grid_x * pd.q;
+        if (v > best) best = v;
+      }
+      if (gram_tcs_eligible(s, a, b)) {
+        GramPlan pt = plan_gram_tcs(n, s, a, b, sms);
+        v = (size_t)pt.grid_x * pt.q;
         if (v > best) best = v;
       }
       if (s % 4 == 0) {
@@ -380,6 +394,23 @@ static int ensure_ws(lsba_ctx* h, int64_t n, int s, int m) {
   return LSBA_OK;
 }
 
+// Digit planes for the m + 1 basis blocks (allocated on first use, within the
+// workspace's capacity n <= cap_n, m <= cap_m).
+static int ensure_digits(lsba_ctx* h) {
+  if (h->dig) return LSBA_OK;
+  const size_t nb = (size_t)h->cap_m + 1;
+  if (ws_alloc(h, &h->dig, nb * digit_block_bytes(h->cap_n, h->cap_s)) != cudaSuccess ||
+      ws_alloc(h, &h->dexp, sizeof(int) * nb * digit_exp_count(h->cap_n, h->cap_s)) != cudaSuccess) {
+    cudaGetLastError();
+    ws_free(h, h->dig);
+    ws_free(h, h->dexp);
+    h->dig = nullptr;
+    h->dexp = nullptr;
+    return LSBA_OUT_OF_MEMORY;
+  }
+  return LSBA_OK;
+}
+
 static BlockPtrs basis_list(const lsba_ctx* h, int64_t n, int s, int count) {
   BlockPtrs p;
   memset(&p, 0, sizeof(p));
@@ -458,6 +489,24 @@ static void do_update(lsba_ctx* h, const BlockPtrs& in, int nin, int64_t n, int 
   prof_end(h);
 }
 
+// The Gram of a lagged skeleton's iteration k >= 2 on the stored digit planes:
+// [V_1..V_{k-1}, U]^T [U, W].
+static void do_gram_tcs(lsba_ctx* h, int k, int64_t n, int s, const Ctl* ctl) {
+  prof_begin(h, LSBA_K_GRAM);
+  GramPlan p = plan_gram_tcs(n, s, k, 2, h->num_sms);
+  launch_gram_tcs(h->stream, p, h->dig, h->dexp, n, s, k, (const float2*)h->Ub,
+                  (const float2*)h->Wb, (float2*)h->partials, h->Gbuf, ctl, 1, &h->d_ctl->error);
+  prof_end(h);
+}
+// Digit planes of basis block i, written by the update of iteration `step`.
+static void split_basis(lsba_ctx* h, int i, int64_t n, int s, const Ctl* ctl, int step) {
+  prof_begin(h, LSBA_K_UPDATE);
+  launch_split_digits(h->stream, (const float2*)(h->basis + (size_t)i * n * s), n, s,
+                      h->dig + (size_t)i * digit_block_bytes(n, s),
+                      h->dexp + (size_t)i * digit_exp_count(n, s), ctl, step, h->num_sms);
+  prof_end(h);
+}
+
 // After the small kernel of loop iteration k: run its side kernel on the side
 // stream (it overlaps the next iteration's SpMM and Gram).  The next small
 // kernel, and the end of the batch, wait for it.
@@ -489,6 +538,7 @@ static void enqueue_cycle(lsba_ctx* h, const lsba_csr* A, const double* Rstart, 
   do_gram(h, one, 1, one, 1, n, s, ctl, 0);
   PROF(LSBA_K_SMALL, launch_small_start(st, w, start_flags));
   do_update(h, one, 1, n, s, h->basis, w.coef1, w.tri1, nullptr, nullptr, nullptr, nullptr, ctl, 0);
+  if (h->use_tcs) split_basis(h, 0, n, s, ctl, 0);
   const int kmax = lagged(skel) ? m_cur + 1 : m_cur;
   const size_t blk = (size_t)n * s;
   for (int k = 1; k <= kmax; ++k) {
@@ -542,7 +592,8 @@ static void enqueue_cycle(lsba_ctx* h, const lsba_csr* A, const double* Rstart, 
         memset(&R, 0, sizeof(R));
         R.p[0] = h->Ub;
         R.p[1] = h->Wb;
-        do_gram(h, L, k, R, 2, n, s, ctl, 1);
+        if (h->use_tcs && gram_tcs_eligible(s, k, 2)) do_gram_tcs(h, k, n, s, ctl);
+        else do_gram(h, L, k, R, 2, n, s, ctl, 1);
         wait_side(h, k - 1);
         PROF(LSBA_K_SMALL, launch_small_step(st, w, k, 0));
         enqueue_side(h, k);
@@ -552,6 +603,7 @@ static void enqueue_cycle(lsba_ctx* h, const lsba_csr* A, const double* Rstart, 
         double* Vk = h->basis + (size_t)(k - 1) * blk;
         do_update(h, in, k + 1, n, s, Vk, w.coef1, w.tri1, h->Ub, w.coef2, w.chain,
                   skel == SK_LS ? w.tri2 : nullptr, ctl, k);
+        if (h->use_tcs) split_basis(h, k - 1, n, s, ctl, k);
       }
     }
   }
@@ -944,6 +996,9 @@ static int solve_impl(lsba_handle h, const lsba_csr* A, const double* d_B, doubl
     h->mode = MODE_DF;
   else h->mode = MODE_FP64;
   h->stats.precision = ir ? LSBA_PREC_FP32_IR : h->mode == MODE_DF ? LSBA_PREC_DF : LSBA_PREC_FP64;
+  // Tensor-core Gram on stored digit planes: double-float lagged skeletons, s = 8.
+  h->use_tcs = h->mode == MODE_DF && s == 8 && h->opt.tensor_cores != 0 && lagged(skel);
+  if (h->use_tcs && ensure_digits(h) != LSBA_OK) h->use_tcs = false;
 
   Ctl* c = h->h_ctl;
   const int hist_cap = c->hist_cap, gram_cap = c->gram_hist_cap;
@@ -1145,6 +1200,8 @@ int64_t lsba_workspace_bytes(int64_t n, int64_t nnz, int s, int m) {
   bytes += (int64_t)((partials + qmax) * sizeof(double));
   bytes += (int64_t)(coef_df_count(m + 3, s, true) * sizeof(float2));
   bytes += (int64_t)((2 * L.hist_cap + 2 * (m + 4)) * sizeof(int));
+  if (s == 8)  // stored digit planes of the basis (tensor-core Gram)
+    bytes += (int64_t)((m + 1) * (digit_block_bytes(n, s) + sizeof(int) * digit_exp_count(n, s)));
   return bytes;
 }
 
@@ -1243,7 +1300,10 @@ int lsba_gram_df(lsba_handle h, const double* d_L, int a, const double* d_R, int
     return LSBA_INVALID_ARG;
   CK(cudaSetDevice(h->device));
   cudaStream_t st = h->stream;
-  GramPlan p = plan_gram_df(n, s, a, b, h->num_sms, tensor_cores ? 2 : 0);
+  const bool stored = tensor_cores == 3;
+  if (stored && !gram_tcs_eligible(s, a, b)) return LSBA_INVALID_ARG;
+  GramPlan p = stored ? plan_gram_tcs(n, s, a, b, h->num_sms)
+                      : plan_gram_df(n, s, a, b, h->num_sms, tensor_cores ? 2 : 0);
   const size_t need = (size_t)p.grid_x * p.q;
   if (need > h->partials_cap) {
     ws_free(h, h->partials);
@@ -1272,14 +1332,39 @@ int lsba_gram_df(lsba_handle h, const double* d_L, int a, const double* d_R, int
   for (int i = 0; i < a; ++i) L.p[i] = (const double*)(Ldf + (size_t)i * n * s);
   for (int i = 0; i < b; ++i) R.p[i] = (const double*)(Rdf + (size_t)i * n * s);
   CK(cudaMemsetAsync(&h->d_ctl->error, 0, sizeof(int), st));
+  unsigned char* dig = nullptr;
+  int* dexp = nullptr;
+  if (stored) {
+    // Digit planes of L_1..L_{a-1}, as the solver keeps them for its basis;
+    // the kernel splits R_1 (standing for L_a = U) and R_2 itself.
+    const size_t db = digit_block_bytes(n, s), de = digit_exp_count(n, s);
+    if (ws_alloc(h, &dig, db * (a - 1)) != cudaSuccess ||
+        ws_alloc(h, &dexp, sizeof(int) * de * (a - 1)) != cudaSuccess) {
+      cudaGetLastError();
+      ws_free(h, dig);
+      ws_free(h, dexp);
+      ws_free(h, Ldf);
+      ws_free(h, Rdf);
+      return LSBA_OUT_OF_MEMORY;
+    }
+    for (int i = 0; i < a - 1; ++i)
+      launch_split_digits(st, Ldf + (size_t)i * n * s, n, s, dig + i * db, dexp + i * de, h->d_ctl,
+                          -1, h->num_sms);
+  }
   prof_begin(h, LSBA_K_GRAM);
-  launch_gram_df(st, p, L, a, R, b, n, s, (float2*)h->partials, d_G, nullptr, 0, &h->d_ctl->error);
+  if (stored)
+    launch_gram_tcs(st, p, dig, dexp, n, s, a, Rdf, Rdf + (size_t)n * s, (float2*)h->partials, d_G,
+                    nullptr, 0, &h->d_ctl->error);
+  else
+    launch_gram_df(st, p, L, a, R, b, n, s, (float2*)h->partials, d_G, nullptr, 0, &h->d_ctl->error);
   prof_end(h);
   CK(cudaGetLastError());
   int err = 0;
   CK(cudaMemcpyAsync(&h->h_ctl->error, &h->d_ctl->error, sizeof(int), cudaMemcpyDeviceToHost, st));
   ws_free(h, Ldf);
   ws_free(h, Rdf);
+  ws_free(h, dig);
+  ws_free(h, dexp);
   CK(cudaStreamSynchronize(st));
   prof_collect(h);
   err = h->h_ctl->error;

@@ -422,6 +422,11 @@ __global__ void __launch_bounds__(256) k_gram_reduce_df(const float2* __restrict
   }
 }
 
+void launch_gram_reduce_df(cudaStream_t st, const float2* partials, int nparts, int q, double* G,
+                           const Ctl* ctl, int guard) {
+  k_gram_reduce_df<<<(q + 31) / 32, 256, 0, st>>>(partials, nparts, q, G, ctl, guard);
+}
+
 GramPlan plan_gram_df(int64_t n, int s, int a, int b, int num_sms, int tensor_cores) {
   if ((tensor_cores == 2 && gram_tc_eligible(s, a, b)) ||
       (tensor_cores == 1 && gram_tc_profitable(s, a, b))) {

@@ -157,6 +157,20 @@ GramPlan plan_gram_df(int64_t n, int s, int a, int b, int num_sms, int tensor_co
 // b s <= 16 and a s + b s <= 256.
 bool gram_tc_eligible(int s, int a, int b);
 bool gram_tc_profitable(int s, int a, int b);
+void launch_gram_reduce_df(cudaStream_t st, const float2* partials, int nparts, int q, double* G,
+                           const Ctl* ctl, int guard);
+// Stored digit planes of basis blocks (kernels_tc.cu): bytes and exponent
+// count of one n x s block (s % 8 == 0), the split kernel, and the Gram of
+// [V_1..V_{a-1} (stored), U] x [U, W] (s = 8, b = 2, a s <= 168).
+size_t digit_block_bytes(int64_t n, int s);
+size_t digit_exp_count(int64_t n, int s);
+void launch_split_digits(cudaStream_t st, const float2* V, int64_t n, int s, unsigned char* dig,
+                         int* dexp, const Ctl* ctl, int step, int num_sms);
+bool gram_tcs_eligible(int s, int a, int b);
+GramPlan plan_gram_tcs(int64_t n, int s, int a, int b, int num_sms);
+void launch_gram_tcs(cudaStream_t st, const GramPlan& p, const unsigned char* dig,
+                     const int* dexp, int64_t n, int s, int a, const float2* U, const float2* W,
+                     float2* partials, double* G, const Ctl* ctl, int guard, int* err);
 GramPlan plan_gram_tc(int64_t n, int s, int a, int b, int num_sms);
 void launch_gram_tc(cudaStream_t st, const GramPlan& p, const BlockPtrs& L, int a,
                     const BlockPtrs& R, int b, int64_t n, int s, float2* partials,

@@ -287,12 +287,15 @@ class Solver:
         _check(self.lib.lsba_gram(self.h, C.c_void_p(_ptr(L)), a, C.c_void_p(_ptr(R)), b, n, s,
                                   C.c_void_p(_ptr(G))))
 
-    def gram_df(self, L, R, G, tensor_cores: bool = True):
-        """Double-float Gram kernels: L (a, n, s), R (b, n, s) CUDA FP64 -> G (a*s, b*s)."""
+    def gram_df(self, L, R, G, tensor_cores=True):
+        """Double-float Gram kernels: L (a, n, s), R (b, n, s) CUDA FP64 -> G (a*s, b*s).
+        tensor_cores: False (FP32-pipe kernel), True (tensor-core digit kernel), or
+        "stored" (the basis kernel: L_1..L_{a-1} as stored digit planes, R_1 for L_a)."""
         a, n, s = L.shape
         b = R.shape[0]
+        mode = 3 if tensor_cores == "stored" else int(bool(tensor_cores))
         _check(self.lib.lsba_gram_df(self.h, C.c_void_p(_ptr(L)), a, C.c_void_p(_ptr(R)), b, n, s,
-                                     C.c_void_p(_ptr(G)), int(tensor_cores)))
+                                     C.c_void_p(_ptr(G)), mode))
 
     def combine(self, inputs, coef, tri, out):
         """inputs: (nin, n, s); coef: (nin*s, s); tri: (s, s) upper or None; out: (n, s)."""

@@ -110,6 +110,33 @@ def test_gram_df_kernels_match_oracle(env, s, a, b, n, tc):
     assert np.array_equal(G1, dG.cpu().numpy())
 
 
+@pytest.mark.parametrize("a,n", [(2, 1000), (9, 70001), (16, 4099), (17, 262147), (21, 70001),
+                                 (21, 31)])
+def test_gram_stored_digits_matches_oracle(env, a, n):
+    """The basis Gram of the lagged skeletons on stored digit planes (s = 8):
+    [L_1..L_{a-1}, U]^T [U, W] with L_1..L_{a-1} split by the split kernel and
+    U, W split inside the Gram; same entry-wise bound as the other
+    double-float Gram kernels, bitwise reproducible."""
+    torch, lsba = env
+    s = 8
+    rng = np.random.default_rng(a * 7 + n)
+    L = rng.standard_normal((a, n, s)) * np.exp(rng.uniform(-3, 3, size=(a, 1, s)))
+    W = rng.standard_normal((n, s)) * 5.0
+    R = np.stack([L[-1], W])
+    sv = lsba.Solver(0)
+    dL, dR = torch.from_numpy(L).cuda(), torch.from_numpy(R).cuda()
+    dG = torch.empty((a * s, 2 * s), dtype=torch.float64, device="cuda")
+    sv.gram_df(dL, dR, dG, tensor_cores="stored")
+    G1 = dG.cpu().numpy()
+    Lh, Rh = np.hstack(list(L)), np.hstack(list(R))
+    ref = O.inner(Lh, Rh)
+    err = np.max(np.abs(G1 - ref) / O.inner(np.abs(Lh), np.abs(Rh)))
+    print(f"GRAMTCS a={a} n={n} err/(|L|^T|R|)={err:.2e} normwise={_rel(G1, ref):.2e}")
+    assert err <= 64 * 2.0 ** -48
+    sv.gram_df(dL, dR, dG, tensor_cores="stored")
+    assert np.array_equal(G1, dG.cpu().numpy())
+
+
 @pytest.mark.parametrize("s,nin,n,tri", [(4, 3, 1001, True), (8, 22, 9999, True),
                                          (16, 18, 4097, False), (3, 2, 17, True), (32, 4, 300, True)])
 def test_combine_matches_oracle(env, s, nin, n, tri):
