@@ -601,8 +601,17 @@ static void enqueue_cycle(lsba_ctx* h, const lsba_csr* A, const double* Rstart, 
         in.p[k - 1] = h->Ub;
         in.p[k] = h->Wb;
         double* Vk = h->basis + (size_t)(k - 1) * blk;
-        do_update(h, in, k + 1, n, s, Vk, w.coef1, w.tri1, h->Ub, w.coef2, w.chain,
-                  skel == SK_LS ? w.tri2 : nullptr, ctl, k);
+        if (h->use_tcs && update_tcs_eligible(s, k + 1, true)) {
+          prof_begin(h, LSBA_K_UPDATE);
+          launch_update_tcs(st, h->dig, h->dexp, k - 1, (const float2*)h->Ub,
+                            (const float2*)h->Wb, n, (float2*)Vk, (float2*)h->Ub, w.coef1, w.tri1,
+                            w.coef2, w.chain, skel == SK_LS ? w.tri2 : nullptr, h->cdf, ctl, k,
+                            &h->d_ctl->error, h->num_sms);
+          prof_end(h);
+        } else {
+          do_update(h, in, k + 1, n, s, Vk, w.coef1, w.tri1, h->Ub, w.coef2, w.chain,
+                    skel == SK_LS ? w.tri2 : nullptr, ctl, k);
+        }
         if (h->use_tcs) split_basis(h, k - 1, n, s, ctl, k);
       }
     }

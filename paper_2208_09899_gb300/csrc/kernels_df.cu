@@ -910,6 +910,25 @@ size_t update_df_smem(int nin, int s, bool two) { return sizeof(float2) * coef_d
 // Largest coefficient set staged in shared memory by the update kernels.
 static constexpr size_t UPDATE_DF_SMEM_MAX = 200 * 1024;
 
+void launch_coef_df(cudaStream_t st, int nin, int s, bool two, const double* coef1,
+                    const double* coef2, const double* chain, const double* tri1,
+                    const double* tri2, float2* cdf, const Ctl* ctl, int step) {
+  CoefDfArgs ca;
+  ca.coef1 = coef1;
+  ca.coef2 = coef2;
+  ca.chain = chain;
+  ca.tri1 = tri1;
+  ca.tri2 = tri2;
+  ca.nin = nin;
+  ca.s = s;
+  ca.two = two ? 1 : 0;
+  ca.out = cdf;
+  ca.ctl = ctl;
+  ca.step = step;
+  const int total = (int)coef_df_count(nin, s, two);
+  k_coef_df<<<(total + 127) / 128, 128, 0, st>>>(ca);
+}
+
 void launch_update_df(cudaStream_t st, const BlockPtrs& in, int nin, int64_t n, int s, float2* out1,
                       const double* coef1, const double* tri1, float2* out2, const double* coef2,
                       const double* chain, const double* tri2, float2* cdf, const Ctl* ctl,

@@ -492,17 +492,21 @@ void launch_gram_tc(cudaStream_t st, const GramPlan& p, const BlockPtrs& L, int 
 // groups of 8 columns, group g at byte (c (s/8) + g) 3072; inside a group,
 // digit t at t 512, rows 16 j.. of the chunk (slab j) at j 256, rows 8 kc..
 // of the slab at kc 128, column (col % 8) at 16 (col % 8), row (row % 8) at
-// 2 (row % 8).  As the A operand this is the no-swizzle K-major layout with
-// LBO = 128 (rows) and SBO = 3072 (next 8 columns).  Exponents: int32
-// [chunk][s].
+// 2 (row % 8).  As the Gram's A operand this is the no-swizzle K-major layout
+// with LBO = 128 (rows) and SBO = 3072 (next 8 columns).  Exponents: int32
+// [chunk][s], each the exponent of the column's maximum over the chunk's
+// 128-row tile (chunks 4 t .. 4 t + 3).
 // ============================================================================
 #define DIG_GROUP 3072
 
 size_t digit_block_bytes(int64_t n, int s) { return (size_t)((n + 31) / 32) * (s / 8) * DIG_GROUP; }
 size_t digit_exp_count(int64_t n, int s) { return (size_t)((n + 31) / 32) * s; }
 
-// One warp per (chunk, group of 8 columns); lane = row of the chunk.  The
-// warp assembles the group's 3 KB in shared memory and stores it with
+// One warp per (128-row tile, group of 8 columns); lane = row within each of
+// the tile's four 32-row chunks.  A column's exponent is taken over the whole
+// 128-row tile (so that the tensor-core update, whose MMA tile is 128 rows,
+// sees one exponent per column) and stored for each of the four chunks.  The
+// warp assembles each chunk's 3 KB in shared memory and stores it with
 // 16-byte writes.  Runs iff step < 0 or ctl->update_step == step (the same
 // condition as the update that wrote the block).
 __global__ void __launch_bounds__(256) k_split_digits(const float2* __restrict__ V, int64_t n, int s,
@@ -513,49 +517,57 @@ __global__ void __launch_bounds__(256) k_split_digits(const float2* __restrict__
   __shared__ __align__(16) unsigned char st[8][DIG_GROUP];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int groups = s / 8;
-  const int64_t nch = (n + 31) / 32, ntask = nch * groups;
+  const int64_t nch = (n + 31) / 32, ntile = (n + 127) / 128, ntask = ntile * groups;
   unsigned char* my = st[warp];
   for (int64_t task = (int64_t)blockIdx.x * 8 + warp; task < ntask; task += (int64_t)gridDim.x * 8) {
-    const int64_t c = task / groups;
+    const int64_t tile = task / groups;
     const int g = (int)(task % groups);
-    const int64_t row = c * 32 + lane;
-    float2 x[8];
+    float2 x[4][8];
 #pragma unroll
-    for (int i = 0; i < 8; ++i) x[i] = row < n ? V[row * s + g * 8 + i] : make_float2(0.f, 0.f);
+    for (int q = 0; q < 4; ++q) {
+      const int64_t row = tile * 128 + q * 32 + lane;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) x[q][i] = row < n ? V[row * s + g * 8 + i] : make_float2(0.f, 0.f);
+    }
     int e[8];
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
-      float amax = fabsf(x[i].x);
+      float amax = fmaxf(fmaxf(fabsf(x[0][i].x), fabsf(x[1][i].x)), fmaxf(fabsf(x[2][i].x), fabsf(x[3][i].x)));
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
       e[i] = amax > 0.f ? ((__float_as_int(amax) >> 23) & 255) - 126 : 0;
       e[i] = max(e[i], -119);
     }
-#pragma unroll
-    for (int i = 0; i < 8; ++i)
-      if (lane == i) dexp[c * s + g * 8 + i] = e[i];
     const uint32_t rofs = (uint32_t)(lane >> 4) * 256 + (uint32_t)((lane >> 3) & 1) * 128 +
                           (uint32_t)(lane & 7) * 2;
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      float d[6];
-      gtc_digits(x[i], gtc_pow2(7 - e[i]), d);
+    for (int q = 0; q < 4; ++q) {
+      const int64_t c = tile * 4 + q;   // 32-row chunk
+      if (c >= nch) break;              // uniform across the warp
 #pragma unroll
-      for (int t = 0; t < 6; ++t)
-        *reinterpret_cast<__nv_bfloat16*>(my + t * 512 + rofs + i * 16) = __float2bfloat16_rn(d[t]);
+      for (int i = 0; i < 8; ++i)
+        if (lane == i) dexp[c * s + g * 8 + i] = e[i];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        float d[6];
+        gtc_digits(x[q][i], gtc_pow2(7 - e[i]), d);
+#pragma unroll
+        for (int t = 0; t < 6; ++t)
+          *reinterpret_cast<__nv_bfloat16*>(my + t * 512 + rofs + i * 16) = __float2bfloat16_rn(d[t]);
+      }
+      __syncwarp();
+      uint4* dst = reinterpret_cast<uint4*>(dig + (size_t)(c * groups + g) * DIG_GROUP);
+      const uint4* src = reinterpret_cast<const uint4*>(my);
+#pragma unroll
+      for (int i = 0; i < DIG_GROUP / 16 / 32; ++i) dst[lane + 32 * i] = src[lane + 32 * i];
+      __syncwarp();
     }
-    __syncwarp();
-    uint4* dst = reinterpret_cast<uint4*>(dig + (size_t)task * DIG_GROUP);
-    const uint4* src = reinterpret_cast<const uint4*>(my);
-#pragma unroll
-    for (int i = 0; i < DIG_GROUP / 16 / 32; ++i) dst[lane + 32 * i] = src[lane + 32 * i];
-    __syncwarp();
   }
 }
 
 void launch_split_digits(cudaStream_t st, const float2* V, int64_t n, int s, unsigned char* dig,
                          int* dexp, const Ctl* ctl, int step, int num_sms) {
-  const int64_t tasks = ((n + 31) / 32) * (s / 8);
+  const int64_t tasks = ((n + 127) / 128) * (s / 8);
   int64_t grid = (tasks + 7) / 8;
   if (grid > 8LL * num_sms) grid = 8LL * num_sms;
   if (grid < 1) grid = 1;

@@ -1,0 +1,480 @@
+// Double-float basis update on the tensor cores (tcgen05), s = 8.
+//
+// Iteration k >= 2 of a lagged skeleton (Alg. 6 and 7) writes two n x 8
+// blocks in one pass over its inputs [V_1..V_{k-1}, U, W]:
+//   out1 = V_k = (sum_b in_b C1_b) T1^{-1},
+//   out2       = (sum_b in_b C2_b + out1 Chain) T2^{-1}   (T2 for BCGSI+LS only).
+// The contraction sum_b in_b [C1_b | C2_b] is a product of an n x K matrix
+// (K = 8 nin) with a K x 16 one, done here exactly on digits as in the
+// tensor-core Gram (kernels_tc.cu):
+//   * rows are taken in tiles of 128 (the MMA's M); for column kk of the
+//     inputs, e_kk is the exponent of its maximum over the tile (stored with
+//     the basis digits; computed here for U and W), and each value is six
+//     digits in units of 2^(e_kk - 7 - 8t);
+//   * the coefficient rows are scaled by 2^(e_kk - e_max) (exact) and split
+//     into six digits with one exponent f_n per output column n, so that
+//     sum_kk A[r][kk] B[kk][n] = sum_{t,u} (sum_kk dA dB) 2^(e_max + f_n - 14 - 8(t+u));
+//   * the level sums l = t + u <= 5 are exact in the FP32 tensor-memory
+//     accumulators over 64 columns (every term an integer <= 2^15, a level
+//     sum < 6 * 64 * 2^15 < 2^24), then added into a double-float accumulator
+//     per row and output column; the triangular solves and the chain term
+//     follow in double-float as in the FP32-pipe kernel.
+// The A operand comes straight from the stored digit planes (MN-major: 8 rows
+// of one column per 16 bytes, LBO = 12288 between 8-column blocks, SBO = 128
+// between 8-row groups); U and W are split here.
+#include <cfloat>
+#include <cuda_bf16.h>
+
+#include "df.cuh"
+#include "lsba_internal.cuh"
+#include "tc.cuh"
+
+namespace lsba {
+
+#define UT_THREADS 256
+#define UT_SUB 4                 // blocks per sub-chunk: 32 columns, two K-steps of 16
+#define UT_BLK 12288             // one block's digits for a 128-row tile: 6 digits x 16 row groups x 128 B
+#define UT_MAXK 256              // K = 8 nin <= 256
+#define UT_DIG_GROUP 3072        // stored layout: one 32-row chunk of an 8-column group
+
+struct UpdTcsArgs {
+  const unsigned char* dig;      // stored digits: block i at dig + i * dig_stride
+  const int* dexp;               // stored exponents: block i at dexp + i * dexp_stride
+  size_t dig_stride, dexp_stride;
+  int a;                         // stored input blocks V_1..V_a; inputs [V_1..V_a, U, W]
+  int nin, kpad;                 // nin = a + 2; kpad = 8 nin rounded up to 32
+  const float2* U;
+  const float2* W;
+  int64_t n;
+  float2* out1;
+  float2* out2;
+  const float2* cdf;             // k_coef_df layout for nin inputs and two outputs
+  int has_tri1, has_chain, has_tri2;
+  const Ctl* ctl;
+  int step;
+  int* err;
+};
+
+__device__ __forceinline__ float ut_round(float y) {
+  return __fsub_rn(__fadd_rn(y, 12582912.f), 12582912.f);
+}
+// Six digits of (hi, lo) in units of 2^(e - 7 - 8t); sc = 2^(7 - e).
+__device__ __forceinline__ void ut_digits(float2 x, float sc, float (&d)[6]) {
+  float y = __fmul_rn(x.x, sc);
+#pragma unroll
+  for (int t = 0; t < 6; ++t) {
+    const float q = ut_round(y);
+    d[t] = q;
+    if (t < 5) y = __fmul_rn(__fsub_rn(y, q), 256.f);
+  }
+  float z = __fmul_rn(__fmul_rn(x.y, sc), 16777216.f);
+#pragma unroll
+  for (int t = 3; t < 6; ++t) {
+    const float q = ut_round(z);
+    d[t] = __fadd_rn(d[t], q);
+    if (t < 5) z = __fmul_rn(__fsub_rn(z, q), 256.f);
+  }
+}
+__device__ __forceinline__ float ut_pow2(int k) {  // 2^k, k clamped to the normal range
+  k = max(-126, min(127, k));
+  return __int_as_float((127 + k) << 23);
+}
+__device__ __forceinline__ int ut_exp_of(float amax) {  // e with amax < 2^e
+  int e = amax > 0.f ? ((__float_as_int(amax) >> 23) & 255) - 126 : 0;
+  return max(e, -119);
+}
+__device__ __forceinline__ uint32_t ut_pack(float a, float b) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+  return *reinterpret_cast<const uint32_t*>(&h);
+}
+__device__ __forceinline__ void ut_cp16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void ut_cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void ut_cp_wait() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// Warp-wide: 8 consecutive 32-bit tensor-memory columns of the warp's lanes.
+__device__ __forceinline__ void ut_ld8(uint32_t taddr, float (&v)[8]) {
+  uint32_t r[8];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                 "=r"(r[7])
+               : "r"(taddr)
+               : "memory");
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__global__ void __launch_bounds__(UT_THREADS, 1) k_update_df_tcs(const __grid_constant__ UpdTcsArgs u) {
+  if (u.step >= 0 && *(volatile const int*)&u.ctl->update_step != u.step) return;
+  extern __shared__ __align__(1024) unsigned char sm[];
+  // Shared layout: A buffers [2][4 blocks][12 KB] | B digit stack | exponents | out1 rows | misc.
+  unsigned char* Abuf = sm;
+  unsigned char* Bst = sm + 2 * UT_SUB * UT_BLK;
+  const uint32_t SB = (uint32_t)(u.kpad / 8) * 128;     // B: bytes per 8 stack rows
+  int* ex = reinterpret_cast<int*>(Bst + 12 * SB);       // [UT_MAXK]
+  float2* o1x = reinterpret_cast<float2*>(ex + UT_MAXK); // [128][8] out1 rows for the chain
+  float* red = reinterpret_cast<float*>(o1x + 128 * 8);  // [16][16]
+  int* fexp = reinterpret_cast<int*>(red + 256);         // [16] f_n, then e_max at [16]
+  float2* tri = reinterpret_cast<float2*>(fexp + 32);    // chain, t1, t2 (3 x 64), r1, r2 (2 x 8)
+  float2* cf = tri + 3 * 64 + 16;                        // [K][16]: C1 | C2 rows, once per CTA
+  uint64_t* mmad = reinterpret_cast<uint64_t*>(cf + UT_MAXK * 16);  // [2]
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(mmad + 2);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int nin = u.nin, K = 8 * nin, a = u.a;
+  const int64_t nch = (u.n + 31) / 32, ntile = (u.n + 127) / 128;
+
+  // Zero the B stack once (padding columns stay zero), copy the triangular data.
+  for (uint32_t i = (uint32_t)tid * 16; i < 12 * SB; i += UT_THREADS * 16)
+    *reinterpret_cast<uint4*>(Bst + i) = make_uint4(0u, 0u, 0u, 0u);
+  {
+    const float2* c2 = u.cdf + (size_t)nin * 64;
+    const float2* chain = c2 + (size_t)nin * 64;
+    for (int e = tid; e < 3 * 64 + 16; e += UT_THREADS) tri[e] = chain[e];
+    // coefficient row kk = 8 b + q: [C1_b[q][0..7] | C2_b[q][0..7]]
+    for (int e = tid; e < 8 * nin * 16; e += UT_THREADS) {
+      const int kk = e >> 4, nn = e & 15, b = kk >> 3, q = kk & 7;
+      cf[e] = nn < 8 ? u.cdf[b * 64 + q * 8 + nn] : c2[b * 64 + q * 8 + (nn - 8)];
+    }
+  }
+  if (tid == 0) {
+    mbar_init(&mmad[0], 1);
+    mbar_init(&mmad[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) tc_alloc(tslot, 128);
+  tc_fence_smem();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tslot;
+  const float2* chain = tri;
+  const float2* t1 = tri + 64;
+  const float2* t2 = tri + 128;
+  const float2* r1 = tri + 192;
+  const float2* r2 = tri + 200;
+
+  // Split task of a thread for U and W: column uc (0..7 U, 8..15 W), rows 8 ur .. 8 ur + 7.
+  const int uc = tid & 15, ur = tid >> 4;
+  const float2* usrc = uc < 8 ? u.U + uc : u.W + (uc - 8);
+  // Epilogue role: rows 32 (warp % 4) + lane, outputs 8 (warp / 4) .. + 7.
+  const int erow = 32 * (warp & 3) + lane, ehalf = warp >> 2;
+  bool failed = false;
+  int gj = 0;  // sub-chunks issued so far (mbarrier phases)
+  const int nsub = (nin + UT_SUB - 1) / UT_SUB;
+
+  for (int64_t tile = blockIdx.x; tile < ntile && !failed; tile += gridDim.x) {
+    const int64_t r0 = tile * 128;
+    // Stored digit blocks go straight into the A buffer (MN-major per digit).
+    auto load_stored = [&](unsigned char* dst, int bi) {
+      for (int p = tid; p < 768; p += UT_THREADS) {
+        const int q = p / 192, rem = p % 192, t = rem >> 5, w = rem & 31;
+        const int64_t c = tile * 4 + q;
+        unsigned char* d = dst + t * 2048 + q * 512 + w * 16;
+        if (c < nch)
+          ut_cp16(d, u.dig + bi * u.dig_stride + (size_t)c * UT_DIG_GROUP + t * 512 + w * 16);
+        else
+          *reinterpret_cast<uint4*>(d) = make_uint4(0u, 0u, 0u, 0u);
+      }
+    };
+    // sub-chunk 0's stored blocks: their copies overlap the splitting below
+    for (int sl = 0; sl < UT_SUB && sl < a; ++sl) load_stored(Abuf + sl * UT_BLK, sl);
+    // ---- exponents of the stored columns (the tile maximum, kept per chunk)
+    for (int kk = tid; kk < 8 * a; kk += UT_THREADS) {
+      const int b = kk >> 3;
+      ex[kk] = (tile * 4 < nch) ? u.dexp[b * u.dexp_stride + (tile * 4) * 8 + (kk & 7)] : 0;
+    }
+    // ---- U and W: load, exponent over the tile, digits kept in registers
+    float2 x[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int64_t row = r0 + ur * 8 + k;
+      x[k] = row < u.n ? usrc[row * 8] : make_float2(0.f, 0.f);
+    }
+    float am = 0.f;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) am = fmaxf(am, fabsf(x[k].x));
+    red[ur * 16 + uc] = am;
+    __syncthreads();
+    float cm = 0.f;
+#pragma unroll
+    for (int i = 0; i < 16; ++i) cm = fmaxf(cm, red[i * 16 + uc]);
+    const int ue = ut_exp_of(cm);
+    if (ur == 0) ex[8 * a + uc] = ue;
+    uint4 udig[6];
+    {
+      float d[8][6];
+      const float sc = ut_pow2(7 - ue);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) ut_digits(x[k], sc, d[k]);
+#pragma unroll
+      for (int t = 0; t < 6; ++t) {
+        udig[t].x = ut_pack(d[0][t], d[1][t]);
+        udig[t].y = ut_pack(d[2][t], d[3][t]);
+        udig[t].z = ut_pack(d[4][t], d[5][t]);
+        udig[t].w = ut_pack(d[6][t], d[7][t]);
+      }
+    }
+    __syncthreads();  // ex complete; red free
+    // ---- e_max over the columns, then the coefficient digits
+    {
+      int em = -1000;
+      for (int kk = tid; kk < K; kk += UT_THREADS) em = max(em, ex[kk]);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) em = max(em, __shfl_xor_sync(0xffffffffu, em, o));
+      if (lane == 0) red[warp] = __int_as_float(em);
+    }
+    __syncthreads();
+    int emax = -1000;
+#pragma unroll
+    for (int i = 0; i < UT_THREADS / 32; ++i) emax = max(emax, __float_as_int(red[i]));
+    const int bn = tid & 15, bk0 = tid >> 4;   // coefficient task: output bn, rows bk0 + 16 i
+    float bmx = 0.f;
+    for (int kk = bk0; kk < K; kk += 16) {
+      const float2 v = cf[kk * 16 + bn];
+      const int dx = ex[kk] - emax;   // <= 0; below 2^-126 the column contributes nothing
+      bmx = fmaxf(bmx, fabsf(__fmul_rn(v.x, dx < -126 ? 0.f : ut_pow2(dx))));
+    }
+    __syncthreads();  // everyone has read red (emax)
+    red[bk0 * 16 + bn] = bmx;
+    __syncthreads();
+    float fm = 0.f;
+#pragma unroll
+    for (int i = 0; i < 16; ++i) fm = fmaxf(fm, red[i * 16 + bn]);
+    const int fe = ut_exp_of(fm);
+    if (bk0 == 0) fexp[bn] = fe;
+    {
+      const float sc = ut_pow2(7 - fe);
+      for (int kk = bk0; kk < K; kk += 16) {
+        float2 v = cf[kk * 16 + bn];
+        const int dx = ex[kk] - emax;
+        const float ps = dx < -126 ? 0.f : ut_pow2(dx);
+        v = make_float2(__fmul_rn(v.x, ps), __fmul_rn(v.y, ps));
+        float d[6];
+        ut_digits(v, sc, d);
+#pragma unroll
+        for (int t = 0; t < 6; ++t) {
+          const int r = 16 * t + bn;   // stack row: digit t of output bn
+          *reinterpret_cast<__nv_bfloat16*>(Bst + (uint32_t)(r >> 3) * SB + (uint32_t)(kk >> 3) * 128 +
+                                            (uint32_t)(r & 7) * 16 + (uint32_t)(kk & 7) * 2) =
+              __float2bfloat16_rn(d[t]);
+        }
+      }
+    }
+    ut_cp_commit();
+    // ---- sub-chunks: digits of 4 input blocks per buffer, MMAs, flushes
+    auto load_sub = [&](int j) {
+      unsigned char* A = Abuf + (size_t)(j & 1) * UT_SUB * UT_BLK;
+      for (int sl = 0; sl < UT_SUB; ++sl) {
+        const int bi = j * UT_SUB + sl;
+        unsigned char* dst = A + sl * UT_BLK;
+        if (bi < a) {
+          if (j > 0) load_stored(dst, bi);
+        } else if (bi < nin) {
+          // U (bi == a) or W (bi == a + 1): this thread's column, if it is that block's
+          if ((uc < 8) == (bi == a)) {
+#pragma unroll
+            for (int t = 0; t < 6; ++t)
+              *reinterpret_cast<uint4*>(dst + t * 2048 + ur * 128 + (uc & 7) * 16) = udig[t];
+          }
+        } else {
+          for (int p = tid; p < UT_BLK / 16; p += UT_THREADS)
+            *reinterpret_cast<uint4*>(dst + p * 16) = make_uint4(0u, 0u, 0u, 0u);
+        }
+      }
+      ut_cp_commit();
+    };
+    dfacc acc[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) acc[i] = dfacc{0.f, 0.f};
+    load_sub(0);
+    for (int j = 0; j < nsub; ++j) {
+      ut_cp_wait();
+      tc_fence_smem();
+      tc_fence_before();
+      __syncthreads();
+      tc_fence_after();
+      const int gcur = gj + j;
+      if (tid == 0) {
+        const uint32_t pa = smem_addr(Abuf + (size_t)(j & 1) * UT_SUB * UT_BLK);
+        const uint32_t pb = smem_addr(Bst);
+#pragma unroll
+        for (int t = 0; t < 6; ++t) {
+          const uint32_t idesc = tc_idesc_bf16_f32(128, 16 * (6 - t)) | (1u << 15);  // A MN-major
+#pragma unroll
+          for (int ks = 0; ks < 2; ++ks) {
+            const uint64_t ad = tc_smem_desc(pa + ks * 2 * UT_BLK + t * 2048, UT_BLK, 128);
+            const uint64_t bd = tc_smem_desc(pb + (uint32_t)(j * 4 + 2 * ks) * 128, 128, SB);
+            const uint32_t accum = ((j & 1) || t || ks) ? 1u : 0u;
+            tc_mma_bf16(tmem + (uint32_t)(16 * t), ad, bd, idesc, accum);
+          }
+        }
+        tc_commit(&mmad[gcur & 1]);
+      }
+      if (j + 1 < nsub) {
+        // buffer (j + 1) & 1 held sub-chunk j - 1: wait for its MMAs
+        if (j >= 1) {
+          const int gp = gcur - 1;
+          if (!mbar_wait_bounded(&mmad[gp & 1], (unsigned)((gp >> 1) & 1))) failed = true;
+        }
+        if (!failed) load_sub(j + 1);
+      }
+      if ((j & 1) || j + 1 == nsub) {
+        // flush: the level sums of this window into the accumulators
+        if (!failed && !mbar_wait_bounded(&mmad[gcur & 1], (unsigned)((gcur >> 1) & 1))) failed = true;
+        tc_fence_after();
+        if (!__syncthreads_or(failed)) {
+          const float s1 = ut_pow2(emax - 7);
+          float w[8];
+#pragma unroll
+          for (int i = 0; i < 8; ++i) w[i] = __fmul_rn(s1, ut_pow2(fexp[ehalf * 8 + i] - 7));
+          const uint32_t lb = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(8 * ehalf);
+#pragma unroll
+          for (int l = 0; l < 6; ++l) {
+            float v[8];
+            ut_ld8(lb + (uint32_t)(16 * l), v);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+              const float p = __fmul_rn(v[i], w[i]);
+              w[i] = __fmul_rn(w[i], 0.00390625f);
+              if (l < 3) {
+                const float2 t2s = df_two_sum(acc[i].s, p);
+                acc[i].s = t2s.x;
+                acc[i].c = __fadd_rn(acc[i].c, t2s.y);
+              } else {
+                acc[i].c = __fadd_rn(acc[i].c, p);
+              }
+            }
+          }
+#pragma unroll
+          for (int i = 0; i < 8; ++i) df_renorm(acc[i]);
+        } else {
+          failed = true;
+        }
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+      }
+      if (failed) break;
+    }
+    gj += nsub;
+    failed = __syncthreads_or(failed);
+    if (failed) break;
+    // ---- out1 = acc T1^{-1} (warps 0-3), then out2 (warps 4-7) with the chain
+    const int64_t row = r0 + erow;
+    if (ehalf == 0) {
+      float2 o1[8];
+      if (u.has_tri1) {
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+#pragma unroll
+          for (int q = 0; q < c; ++q) df_fms(acc[c], o1[q], t1[q * 8 + c]);
+          o1[c] = df_mul(df_value(acc[c]), r1[c]);
+        }
+      } else {
+#pragma unroll
+        for (int c = 0; c < 8; ++c) o1[c] = df_value(acc[c]);
+      }
+#pragma unroll
+      for (int c = 0; c < 8; ++c) o1x[erow * 8 + c] = o1[c];
+      if (row < u.n) {
+        float4* d1 = reinterpret_cast<float4*>(u.out1 + row * 8);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) d1[i] = make_float4(o1[2 * i].x, o1[2 * i].y, o1[2 * i + 1].x, o1[2 * i + 1].y);
+      }
+    }
+    __syncthreads();
+    if (ehalf == 1) {
+      if (u.has_chain) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const float2 oq = o1x[erow * 8 + q];
+#pragma unroll
+          for (int c = 0; c < 8; ++c) df_fma(acc[c], oq, chain[q * 8 + c]);
+        }
+      }
+      float2 o2[8];
+      if (u.has_tri2) {
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+#pragma unroll
+          for (int q = 0; q < c; ++q) df_fms(acc[c], o2[q], t2[q * 8 + c]);
+          o2[c] = df_mul(df_value(acc[c]), r2[c]);
+        }
+      } else {
+#pragma unroll
+        for (int c = 0; c < 8; ++c) o2[c] = df_value(acc[c]);
+      }
+      if (row < u.n) {
+        float4* d2 = reinterpret_cast<float4*>(u.out2 + row * 8);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) d2[i] = make_float4(o2[2 * i].x, o2[2 * i].y, o2[2 * i + 1].x, o2[2 * i + 1].y);
+      }
+    }
+    __syncthreads();
+  }
+  if (failed) {
+    if (tid == 0) {
+      if (u.err) atomicExch(u.err, 1);
+      for (int b2 = 0; b2 < 2; ++b2) {
+        mbar_wait_bounded(&mmad[b2], 0);
+        mbar_wait_bounded(&mmad[b2], 1);
+      }
+    }
+  }
+  ut_cp_wait();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0) tc_dealloc(tmem, 128);
+}
+
+bool update_tcs_eligible(int s, int nin, bool two) { return s == 8 && two && nin >= 3 && 8 * nin <= UT_MAXK; }
+
+size_t update_tcs_smem(int nin) {
+  const int kpad = ((8 * nin + 31) / 32) * 32;
+  const size_t SB = (size_t)(kpad / 8) * 128;
+  return 2 * UT_SUB * UT_BLK + 12 * SB + UT_MAXK * 4 + 128 * 8 * 8 + 256 * 4 + 32 * 4 +
+         (3 * 64 + 16) * 8 + UT_MAXK * 16 * 8 + 2 * 8 + 16;
+}
+
+void launch_update_tcs(cudaStream_t st, const unsigned char* dig, const int* dexp, int a,
+                       const float2* U, const float2* W, int64_t n, float2* out1, float2* out2,
+                       const double* coef1, const double* tri1, const double* coef2,
+                       const double* chain, const double* tri2, float2* cdf, const Ctl* ctl,
+                       int step, int* err, int num_sms) {
+  const int nin = a + 2;
+  launch_coef_df(st, nin, 8, true, coef1, coef2, chain, tri1, tri2, cdf, ctl, step);
+  static std::atomic<unsigned long long> attr_done{0};
+  once_per_device(attr_done, [] {
+    cudaFuncSetAttribute(k_update_df_tcs, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  });
+  UpdTcsArgs u;
+  u.dig = dig;
+  u.dexp = dexp;
+  u.dig_stride = digit_block_bytes(n, 8);
+  u.dexp_stride = digit_exp_count(n, 8);
+  u.a = a;
+  u.nin = nin;
+  u.kpad = ((8 * nin + 31) / 32) * 32;
+  u.U = U;
+  u.W = W;
+  u.n = n;
+  u.out1 = out1;
+  u.out2 = out2;
+  u.cdf = cdf;
+  u.has_tri1 = tri1 != nullptr;
+  u.has_chain = chain != nullptr;
+  u.has_tri2 = tri2 != nullptr;
+  u.ctl = ctl;
+  u.step = step;
+  u.err = err;
+  const int64_t tiles = (n + 127) / 128;
+  int64_t grid = num_sms;
+  if (grid > tiles) grid = tiles;
+  if (grid < 1) grid = 1;
+  k_update_df_tcs<<<(unsigned)grid, UT_THREADS, update_tcs_smem(nin), st>>>(u);
+}
+
+}  // namespace lsba

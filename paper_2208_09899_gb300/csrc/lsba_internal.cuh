@@ -167,6 +167,18 @@ size_t digit_exp_count(int64_t n, int s);
 void launch_split_digits(cudaStream_t st, const float2* V, int64_t n, int s, unsigned char* dig,
                          int* dexp, const Ctl* ctl, int step, int num_sms);
 bool gram_tcs_eligible(int s, int a, int b);
+// Coefficients of an update converted to double-float (k_coef_df layout).
+void launch_coef_df(cudaStream_t st, int nin, int s, bool two, const double* coef1,
+                    const double* coef2, const double* chain, const double* tri1,
+                    const double* tri2, float2* cdf, const Ctl* ctl, int step);
+// Tensor-core update of a lagged skeleton's iteration (kernels_tcu.cu): inputs
+// [V_1..V_a (stored digits), U, W], two outputs, s = 8, 8 (a + 2) <= 256.
+bool update_tcs_eligible(int s, int nin, bool two);
+void launch_update_tcs(cudaStream_t st, const unsigned char* dig, const int* dexp, int a,
+                       const float2* U, const float2* W, int64_t n, float2* out1, float2* out2,
+                       const double* coef1, const double* tri1, const double* coef2,
+                       const double* chain, const double* tri2, float2* cdf, const Ctl* ctl,
+                       int step, int* err, int num_sms);
 GramPlan plan_gram_tcs(int64_t n, int s, int a, int b, int num_sms);
 void launch_gram_tcs(cudaStream_t st, const GramPlan& p, const unsigned char* dig,
                      const int* dexp, int64_t n, int s, int a, const float2* U, const float2* W,
