@@ -164,34 +164,39 @@ __global__ void __launch_bounds__(UT_THREADS, 1) k_update_df_tcs(const __grid_co
   int gj = 0;  // sub-chunks issued so far (mbarrier phases)
   const int nsub = (nin + UT_SUB - 1) / UT_SUB;
 
-  for (int64_t tile = blockIdx.x; tile < ntile && !failed; tile += gridDim.x) {
-    const int64_t r0 = tile * 128;
-    // Stored digit blocks go straight into the A buffer (MN-major per digit).
-    auto load_stored = [&](unsigned char* dst, int bi) {
-      for (int p = tid; p < 768; p += UT_THREADS) {
-        const int q = p / 192, rem = p % 192, t = rem >> 5, w = rem & 31;
-        const int64_t c = tile * 4 + q;
-        unsigned char* d = dst + t * 2048 + q * 512 + w * 16;
-        if (c < nch)
-          ut_cp16(d, u.dig + bi * u.dig_stride + (size_t)c * UT_DIG_GROUP + t * 512 + w * 16);
-        else
-          *reinterpret_cast<uint4*>(d) = make_uint4(0u, 0u, 0u, 0u);
-      }
-    };
-    // sub-chunk 0's stored blocks: their copies overlap the splitting below
-    for (int sl = 0; sl < UT_SUB && sl < a; ++sl) load_stored(Abuf + sl * UT_BLK, sl);
-    // ---- exponents of the stored columns (the tile maximum, kept per chunk)
-    for (int kk = tid; kk < 8 * a; kk += UT_THREADS) {
-      const int b = kk >> 3;
-      ex[kk] = (tile * 4 < nch) ? u.dexp[b * u.dexp_stride + (tile * 4) * 8 + (kk & 7)] : 0;
+  // Stored digit blocks go straight into an A buffer (MN-major per digit).
+  auto load_stored = [&](int64_t tl, unsigned char* dst, int bi) {
+    for (int p = tid; p < 768; p += UT_THREADS) {
+      const int q = p / 192, rem = p % 192, t = rem >> 5, w = rem & 31;
+      const int64_t c = tl * 4 + q;
+      unsigned char* d = dst + t * 2048 + q * 512 + w * 16;
+      if (c < nch)
+        ut_cp16(d, u.dig + bi * u.dig_stride + (size_t)c * UT_DIG_GROUP + t * 512 + w * 16);
+      else
+        *reinterpret_cast<uint4*>(d) = make_uint4(0u, 0u, 0u, 0u);
     }
-    // ---- U and W: load, exponent over the tile, digits kept in registers
-    float2 x[8];
+  };
+  // A tile's first sub-chunk of stored blocks, its U and W rows and its stored
+  // exponents are fetched while the previous tile is finished (overlap).
+  float2 x[8];
+  int exv = 0;
+  auto prefetch = [&](int64_t tl) {
+    for (int sl = 0; sl < UT_SUB && sl < a; ++sl) load_stored(tl, Abuf + sl * UT_BLK, sl);
+    ut_cp_commit();
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
-      const int64_t row = r0 + ur * 8 + k;
+      const int64_t row = tl * 128 + ur * 8 + k;
       x[k] = row < u.n ? usrc[row * 8] : make_float2(0.f, 0.f);
     }
+    exv = tid < 8 * a ? u.dexp[(tid >> 3) * u.dexp_stride + (tl * 4) * 8 + (tid & 7)] : 0;
+  };
+  if (blockIdx.x < ntile) prefetch(blockIdx.x);
+
+  for (int64_t tile = blockIdx.x; tile < ntile && !failed; tile += gridDim.x) {
+    const int64_t r0 = tile * 128;
+    // ---- exponents of the stored columns (the tile maximum, kept per chunk)
+    if (tid < 8 * a) ex[tid] = exv;
+    // ---- U and W: exponent over the tile, digits kept in registers
     float am = 0.f;
 #pragma unroll
     for (int k = 0; k < 8; ++k) am = fmaxf(am, fabsf(x[k].x));
@@ -262,7 +267,6 @@ __global__ void __launch_bounds__(UT_THREADS, 1) k_update_df_tcs(const __grid_co
         }
       }
     }
-    ut_cp_commit();
     // ---- sub-chunks: digits of 4 input blocks per buffer, MMAs, flushes
     auto load_sub = [&](int j) {
       unsigned char* A = Abuf + (size_t)(j & 1) * UT_SUB * UT_BLK;
@@ -270,7 +274,7 @@ __global__ void __launch_bounds__(UT_THREADS, 1) k_update_df_tcs(const __grid_co
         const int bi = j * UT_SUB + sl;
         unsigned char* dst = A + sl * UT_BLK;
         if (bi < a) {
-          if (j > 0) load_stored(dst, bi);
+          if (j > 0) load_stored(tile, dst, bi);
         } else if (bi < nin) {
           // U (bi == a) or W (bi == a + 1): this thread's column, if it is that block's
           if ((uc < 8) == (bi == a)) {
@@ -361,6 +365,9 @@ __global__ void __launch_bounds__(UT_THREADS, 1) k_update_df_tcs(const __grid_co
     gj += nsub;
     failed = __syncthreads_or(failed);
     if (failed) break;
+    // Every MMA of this tile is done and both A buffers are free: start the
+    // next tile's copies and loads before finishing this one.
+    if (tile + gridDim.x < ntile) prefetch(tile + gridDim.x);
     // ---- out1 = acc T1^{-1} (warps 0-3), then out2 (warps 4-7) with the chain
     const int64_t row = r0 + erow;
     if (ehalf == 0) {
