@@ -460,7 +460,8 @@ def main():
     roofline = {
         "kernel": {"gram": ("k_gram_df_tma (k_gram_df_tc where a s >= 160) + k_gram_reduce_df" if is_df
                             else "k_gram + k_gram_reduce"),
-                   "update": ("k_coef_df+k_update_df" if is_df else "k_update"),
+                   "update": ("k_coef_df + k_update_df_tcs (tensor cores, iterations k >= 2) + "
+                              "k_split_digits + k_update_df_row" if is_df else "k_update"),
                    "spmm": f"k_spmm{suffix}"}[dom],
         "bound": "alu", "achieved": achieved_tflops, "peak": peak, "unit": "TFLOP/s",
         "frac": achieved_tflops / peak,
