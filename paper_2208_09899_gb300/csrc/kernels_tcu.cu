@@ -31,8 +31,9 @@
 
 namespace lsba {
 
-#define UT_THREADS 256
-#define UT_SUB 4                 // blocks per sub-chunk: 32 columns, two K-steps of 16
+#define UT_THREADS 128           // one thread per row of the 128-row tile; two CTAs per SM
+#define UT_SUB 2                 // blocks per sub-chunk: 16 columns, one K-step
+#define UT_FLUSH 4               // sub-chunks per exact accumulation window (64 columns)
 #define UT_BLK 12288             // one block's digits for a 128-row tile: 6 digits x 16 row groups x 128 B
 #define UT_MAXK 256              // K = 8 nin <= 256
 #define UT_DIG_GROUP 3072        // stored layout: one 32-row chunk of an 8-column group
@@ -106,38 +107,29 @@ __device__ __forceinline__ void ut_ld8(uint32_t taddr, float (&v)[8]) {
   for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-__global__ void __launch_bounds__(UT_THREADS, 1) k_update_df_tcs(const __grid_constant__ UpdTcsArgs u) {
+__global__ void __launch_bounds__(UT_THREADS, 2) k_update_df_tcs(const __grid_constant__ UpdTcsArgs u) {
   if (u.step >= 0 && *(volatile const int*)&u.ctl->update_step != u.step) return;
   extern __shared__ __align__(1024) unsigned char sm[];
-  // Shared layout: A buffers [2][4 blocks][12 KB] | B digit stack | exponents | out1 rows | misc.
+  // Shared layout: A buffers [2][UT_SUB blocks][12 KB] | B digit stack | exponents | misc.
   unsigned char* Abuf = sm;
   unsigned char* Bst = sm + 2 * UT_SUB * UT_BLK;
   const uint32_t SB = (uint32_t)(u.kpad / 8) * 128;     // B: bytes per 8 stack rows
   int* ex = reinterpret_cast<int*>(Bst + 12 * SB);       // [UT_MAXK]
-  float2* o1x = reinterpret_cast<float2*>(ex + UT_MAXK); // [128][8] out1 rows for the chain
-  float* red = reinterpret_cast<float*>(o1x + 128 * 8);  // [16][16]
-  int* fexp = reinterpret_cast<int*>(red + 256);         // [16] f_n, then e_max at [16]
+  float* red = reinterpret_cast<float*>(ex + UT_MAXK);   // [16][16]
+  int* fexp = reinterpret_cast<int*>(red + 256);         // [16]
   float2* tri = reinterpret_cast<float2*>(fexp + 32);    // chain, t1, t2 (3 x 64), r1, r2 (2 x 8)
-  float2* cf = tri + 3 * 64 + 16;                        // [K][16]: C1 | C2 rows, once per CTA
-  uint64_t* mmad = reinterpret_cast<uint64_t*>(cf + UT_MAXK * 16);  // [2]
+  uint64_t* mmad = reinterpret_cast<uint64_t*>(tri + 3 * 64 + 16);  // [2]
   uint32_t* tslot = reinterpret_cast<uint32_t*>(mmad + 2);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int nin = u.nin, K = 8 * nin, a = u.a;
   const int64_t nch = (u.n + 31) / 32, ntile = (u.n + 127) / 128;
+  const float2* c1g = u.cdf;
+  const float2* c2g = u.cdf + (size_t)nin * 64;
 
   // Zero the B stack once (padding columns stay zero), copy the triangular data.
   for (uint32_t i = (uint32_t)tid * 16; i < 12 * SB; i += UT_THREADS * 16)
     *reinterpret_cast<uint4*>(Bst + i) = make_uint4(0u, 0u, 0u, 0u);
-  {
-    const float2* c2 = u.cdf + (size_t)nin * 64;
-    const float2* chain = c2 + (size_t)nin * 64;
-    for (int e = tid; e < 3 * 64 + 16; e += UT_THREADS) tri[e] = chain[e];
-    // coefficient row kk = 8 b + q: [C1_b[q][0..7] | C2_b[q][0..7]]
-    for (int e = tid; e < 8 * nin * 16; e += UT_THREADS) {
-      const int kk = e >> 4, nn = e & 15, b = kk >> 3, q = kk & 7;
-      cf[e] = nn < 8 ? u.cdf[b * 64 + q * 8 + nn] : c2[b * 64 + q * 8 + (nn - 8)];
-    }
-  }
+  for (int e = tid; e < 3 * 64 + 16; e += UT_THREADS) tri[e] = c2g[(size_t)nin * 64 + e];
   if (tid == 0) {
     mbar_init(&mmad[0], 1);
     mbar_init(&mmad[1], 1);
@@ -155,11 +147,9 @@ __global__ void __launch_bounds__(UT_THREADS, 1) k_update_df_tcs(const __grid_co
   const float2* r1 = tri + 192;
   const float2* r2 = tri + 200;
 
-  // Split task of a thread for U and W: column uc (0..7 U, 8..15 W), rows 8 ur .. 8 ur + 7.
-  const int uc = tid & 15, ur = tid >> 4;
+  // U and W split tasks: column uc (0..7 U, 8..15 W), row groups ur0 and ur0 + 8.
+  const int uc = tid & 15, ur0 = tid >> 4;
   const float2* usrc = uc < 8 ? u.U + uc : u.W + (uc - 8);
-  // Epilogue role: rows 32 (warp % 4) + lane, outputs 8 (warp / 4) .. + 7.
-  const int erow = 32 * (warp & 3) + lane, ehalf = warp >> 2;
   bool failed = false;
   int gj = 0;  // sub-chunks issued so far (mbarrier phases)
   const int nsub = (nin + UT_SUB - 1) / UT_SUB;
@@ -178,47 +168,61 @@ __global__ void __launch_bounds__(UT_THREADS, 1) k_update_df_tcs(const __grid_co
   };
   // A tile's first sub-chunk of stored blocks, its U and W rows and its stored
   // exponents are fetched while the previous tile is finished (overlap).
-  float2 x[8];
-  int exv = 0;
+  float2 x[2][8];
+  int exv[2] = {0, 0};
   auto prefetch = [&](int64_t tl) {
     for (int sl = 0; sl < UT_SUB && sl < a; ++sl) load_stored(tl, Abuf + sl * UT_BLK, sl);
     ut_cp_commit();
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      const int64_t row = tl * 128 + ur * 8 + k;
-      x[k] = row < u.n ? usrc[row * 8] : make_float2(0.f, 0.f);
+    for (int h = 0; h < 2; ++h)
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const int64_t row = tl * 128 + (ur0 + 8 * h) * 8 + k;
+        x[h][k] = row < u.n ? usrc[row * 8] : make_float2(0.f, 0.f);
+      }
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int kk = tid + UT_THREADS * h;
+      exv[h] = kk < 8 * a ? u.dexp[(kk >> 3) * u.dexp_stride + (tl * 4) * 8 + (kk & 7)] : 0;
     }
-    exv = tid < 8 * a ? u.dexp[(tid >> 3) * u.dexp_stride + (tl * 4) * 8 + (tid & 7)] : 0;
   };
   if (blockIdx.x < ntile) prefetch(blockIdx.x);
 
   for (int64_t tile = blockIdx.x; tile < ntile && !failed; tile += gridDim.x) {
     const int64_t r0 = tile * 128;
     // ---- exponents of the stored columns (the tile maximum, kept per chunk)
-    if (tid < 8 * a) ex[tid] = exv;
-    // ---- U and W: exponent over the tile, digits kept in registers
-    float am = 0.f;
 #pragma unroll
-    for (int k = 0; k < 8; ++k) am = fmaxf(am, fabsf(x[k].x));
-    red[ur * 16 + uc] = am;
+    for (int h = 0; h < 2; ++h)
+      if (tid + UT_THREADS * h < 8 * a) ex[tid + UT_THREADS * h] = exv[h];
+    // ---- U and W: exponent over the tile, digits kept in registers
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      float am = 0.f;
+#pragma unroll
+      for (int k = 0; k < 8; ++k) am = fmaxf(am, fabsf(x[h][k].x));
+      red[(ur0 + 8 * h) * 16 + uc] = am;
+    }
     __syncthreads();
     float cm = 0.f;
 #pragma unroll
     for (int i = 0; i < 16; ++i) cm = fmaxf(cm, red[i * 16 + uc]);
     const int ue = ut_exp_of(cm);
-    if (ur == 0) ex[8 * a + uc] = ue;
-    uint4 udig[6];
+    if (ur0 == 0) ex[8 * a + uc] = ue;
+    uint4 udig[2][6];
     {
-      float d[8][6];
       const float sc = ut_pow2(7 - ue);
 #pragma unroll
-      for (int k = 0; k < 8; ++k) ut_digits(x[k], sc, d[k]);
+      for (int h = 0; h < 2; ++h) {
+        float d[8][6];
 #pragma unroll
-      for (int t = 0; t < 6; ++t) {
-        udig[t].x = ut_pack(d[0][t], d[1][t]);
-        udig[t].y = ut_pack(d[2][t], d[3][t]);
-        udig[t].z = ut_pack(d[4][t], d[5][t]);
-        udig[t].w = ut_pack(d[6][t], d[7][t]);
+        for (int k = 0; k < 8; ++k) ut_digits(x[h][k], sc, d[k]);
+#pragma unroll
+        for (int t = 0; t < 6; ++t) {
+          udig[h][t].x = ut_pack(d[0][t], d[1][t]);
+          udig[h][t].y = ut_pack(d[2][t], d[3][t]);
+          udig[h][t].z = ut_pack(d[4][t], d[5][t]);
+          udig[h][t].w = ut_pack(d[6][t], d[7][t]);
+        }
       }
     }
     __syncthreads();  // ex complete; red free
@@ -234,10 +238,11 @@ __global__ void __launch_bounds__(UT_THREADS, 1) k_update_df_tcs(const __grid_co
     int emax = -1000;
 #pragma unroll
     for (int i = 0; i < UT_THREADS / 32; ++i) emax = max(emax, __float_as_int(red[i]));
-    const int bn = tid & 15, bk0 = tid >> 4;   // coefficient task: output bn, rows bk0 + 16 i
+    const int bn = tid & 15, bk0 = tid >> 4;   // coefficient task: output bn, rows bk0 + 8 i
     float bmx = 0.f;
-    for (int kk = bk0; kk < K; kk += 16) {
-      const float2 v = cf[kk * 16 + bn];
+    for (int kk = bk0; kk < K; kk += UT_THREADS / 16) {
+      const int b = kk >> 3, q = kk & 7;
+      const float2 v = bn < 8 ? c1g[b * 64 + q * 8 + bn] : c2g[b * 64 + q * 8 + (bn - 8)];
       const int dx = ex[kk] - emax;   // <= 0; below 2^-126 the column contributes nothing
       bmx = fmaxf(bmx, fabsf(__fmul_rn(v.x, dx < -126 ? 0.f : ut_pow2(dx))));
     }
@@ -246,13 +251,14 @@ __global__ void __launch_bounds__(UT_THREADS, 1) k_update_df_tcs(const __grid_co
     __syncthreads();
     float fm = 0.f;
 #pragma unroll
-    for (int i = 0; i < 16; ++i) fm = fmaxf(fm, red[i * 16 + bn]);
+    for (int i = 0; i < UT_THREADS / 16; ++i) fm = fmaxf(fm, red[i * 16 + bn]);
     const int fe = ut_exp_of(fm);
     if (bk0 == 0) fexp[bn] = fe;
     {
       const float sc = ut_pow2(7 - fe);
-      for (int kk = bk0; kk < K; kk += 16) {
-        float2 v = cf[kk * 16 + bn];
+      for (int kk = bk0; kk < K; kk += UT_THREADS / 16) {
+        const int b = kk >> 3, q = kk & 7;
+        float2 v = bn < 8 ? c1g[b * 64 + q * 8 + bn] : c2g[b * 64 + q * 8 + (bn - 8)];
         const int dx = ex[kk] - emax;
         const float ps = dx < -126 ? 0.f : ut_pow2(dx);
         v = make_float2(__fmul_rn(v.x, ps), __fmul_rn(v.y, ps));
@@ -267,7 +273,7 @@ __global__ void __launch_bounds__(UT_THREADS, 1) k_update_df_tcs(const __grid_co
         }
       }
     }
-    // ---- sub-chunks: digits of 4 input blocks per buffer, MMAs, flushes
+    // ---- sub-chunks: digits of UT_SUB input blocks per buffer, MMAs, flushes
     auto load_sub = [&](int j) {
       unsigned char* A = Abuf + (size_t)(j & 1) * UT_SUB * UT_BLK;
       for (int sl = 0; sl < UT_SUB; ++sl) {
@@ -279,8 +285,10 @@ __global__ void __launch_bounds__(UT_THREADS, 1) k_update_df_tcs(const __grid_co
           // U (bi == a) or W (bi == a + 1): this thread's column, if it is that block's
           if ((uc < 8) == (bi == a)) {
 #pragma unroll
-            for (int t = 0; t < 6; ++t)
-              *reinterpret_cast<uint4*>(dst + t * 2048 + ur * 128 + (uc & 7) * 16) = udig[t];
+            for (int h = 0; h < 2; ++h)
+#pragma unroll
+              for (int t = 0; t < 6; ++t)
+                *reinterpret_cast<uint4*>(dst + t * 2048 + (ur0 + 8 * h) * 128 + (uc & 7) * 16) = udig[h][t];
           }
         } else {
           for (int p = tid; p < UT_BLK / 16; p += UT_THREADS)
@@ -289,9 +297,9 @@ __global__ void __launch_bounds__(UT_THREADS, 1) k_update_df_tcs(const __grid_co
       }
       ut_cp_commit();
     };
-    dfacc acc[8];
+    dfacc acc[16];
 #pragma unroll
-    for (int i = 0; i < 8; ++i) acc[i] = dfacc{0.f, 0.f};
+    for (int i = 0; i < 16; ++i) acc[i] = dfacc{0.f, 0.f};
     load_sub(0);
     for (int j = 0; j < nsub; ++j) {
       ut_cp_wait();
@@ -307,10 +315,10 @@ __global__ void __launch_bounds__(UT_THREADS, 1) k_update_df_tcs(const __grid_co
         for (int t = 0; t < 6; ++t) {
           const uint32_t idesc = tc_idesc_bf16_f32(128, 16 * (6 - t)) | (1u << 15);  // A MN-major
 #pragma unroll
-          for (int ks = 0; ks < 2; ++ks) {
+          for (int ks = 0; ks < UT_SUB / 2; ++ks) {
             const uint64_t ad = tc_smem_desc(pa + ks * 2 * UT_BLK + t * 2048, UT_BLK, 128);
-            const uint64_t bd = tc_smem_desc(pb + (uint32_t)(j * 4 + 2 * ks) * 128, 128, SB);
-            const uint32_t accum = ((j & 1) || t || ks) ? 1u : 0u;
+            const uint64_t bd = tc_smem_desc(pb + (uint32_t)(j * UT_SUB + 2 * ks) * 128, 128, SB);
+            const uint32_t accum = ((j % UT_FLUSH) || t || ks) ? 1u : 0u;
             tc_mma_bf16(tmem + (uint32_t)(16 * t), ad, bd, idesc, accum);
           }
         }
@@ -324,22 +332,22 @@ __global__ void __launch_bounds__(UT_THREADS, 1) k_update_df_tcs(const __grid_co
         }
         if (!failed) load_sub(j + 1);
       }
-      if ((j & 1) || j + 1 == nsub) {
+      if ((j % UT_FLUSH) == UT_FLUSH - 1 || j + 1 == nsub) {
         // flush: the level sums of this window into the accumulators
         if (!failed && !mbar_wait_bounded(&mmad[gcur & 1], (unsigned)((gcur >> 1) & 1))) failed = true;
         tc_fence_after();
         if (!__syncthreads_or(failed)) {
           const float s1 = ut_pow2(emax - 7);
-          float w[8];
+          float w[16];
 #pragma unroll
-          for (int i = 0; i < 8; ++i) w[i] = __fmul_rn(s1, ut_pow2(fexp[ehalf * 8 + i] - 7));
-          const uint32_t lb = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(8 * ehalf);
+          for (int i = 0; i < 16; ++i) w[i] = __fmul_rn(s1, ut_pow2(fexp[i] - 7));
+          const uint32_t lb = tmem + ((uint32_t)(32 * warp) << 16);
 #pragma unroll
           for (int l = 0; l < 6; ++l) {
-            float v[8];
-            ut_ld8(lb + (uint32_t)(16 * l), v);
+            float v[16];
+            tc_ld16(lb + (uint32_t)(16 * l), v);
 #pragma unroll
-            for (int i = 0; i < 8; ++i) {
+            for (int i = 0; i < 16; ++i) {
               const float p = __fmul_rn(v[i], w[i]);
               w[i] = __fmul_rn(w[i], 0.00390625f);
               if (l < 3) {
@@ -352,7 +360,7 @@ __global__ void __launch_bounds__(UT_THREADS, 1) k_update_df_tcs(const __grid_co
             }
           }
 #pragma unroll
-          for (int i = 0; i < 8; ++i) df_renorm(acc[i]);
+          for (int i = 0; i < 16; ++i) df_renorm(acc[i]);
         } else {
           failed = true;
         }
@@ -368,56 +376,47 @@ __global__ void __launch_bounds__(UT_THREADS, 1) k_update_df_tcs(const __grid_co
     // Every MMA of this tile is done and both A buffers are free: start the
     // next tile's copies and loads before finishing this one.
     if (tile + gridDim.x < ntile) prefetch(tile + gridDim.x);
-    // ---- out1 = acc T1^{-1} (warps 0-3), then out2 (warps 4-7) with the chain
-    const int64_t row = r0 + erow;
-    if (ehalf == 0) {
-      float2 o1[8];
-      if (u.has_tri1) {
+    // ---- row tid: out1 = acc[0..7] T1^{-1}; out2 = (acc[8..15] + out1 Chain) T2^{-1}
+    const int64_t row = r0 + tid;
+    float2 o1[8];
+    if (u.has_tri1) {
 #pragma unroll
-        for (int c = 0; c < 8; ++c) {
+      for (int c = 0; c < 8; ++c) {
 #pragma unroll
-          for (int q = 0; q < c; ++q) df_fms(acc[c], o1[q], t1[q * 8 + c]);
-          o1[c] = df_mul(df_value(acc[c]), r1[c]);
-        }
-      } else {
-#pragma unroll
-        for (int c = 0; c < 8; ++c) o1[c] = df_value(acc[c]);
+        for (int q = 0; q < c; ++q) df_fms(acc[c], o1[q], t1[q * 8 + c]);
+        o1[c] = df_mul(df_value(acc[c]), r1[c]);
       }
+    } else {
 #pragma unroll
-      for (int c = 0; c < 8; ++c) o1x[erow * 8 + c] = o1[c];
-      if (row < u.n) {
-        float4* d1 = reinterpret_cast<float4*>(u.out1 + row * 8);
-#pragma unroll
-        for (int i = 0; i < 4; ++i) d1[i] = make_float4(o1[2 * i].x, o1[2 * i].y, o1[2 * i + 1].x, o1[2 * i + 1].y);
-      }
+      for (int c = 0; c < 8; ++c) o1[c] = df_value(acc[c]);
     }
-    __syncthreads();
-    if (ehalf == 1) {
-      if (u.has_chain) {
+    if (row < u.n) {
+      float4* d1 = reinterpret_cast<float4*>(u.out1 + row * 8);
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          const float2 oq = o1x[erow * 8 + q];
+      for (int i = 0; i < 4; ++i) d1[i] = make_float4(o1[2 * i].x, o1[2 * i].y, o1[2 * i + 1].x, o1[2 * i + 1].y);
+    }
+    if (u.has_chain) {
 #pragma unroll
-          for (int c = 0; c < 8; ++c) df_fma(acc[c], oq, chain[q * 8 + c]);
-        }
+      for (int q = 0; q < 8; ++q)
+#pragma unroll
+        for (int c = 0; c < 8; ++c) df_fma(acc[8 + c], o1[q], chain[q * 8 + c]);
+    }
+    float2 o2[8];
+    if (u.has_tri2) {
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+#pragma unroll
+        for (int q = 0; q < c; ++q) df_fms(acc[8 + c], o2[q], t2[q * 8 + c]);
+        o2[c] = df_mul(df_value(acc[8 + c]), r2[c]);
       }
-      float2 o2[8];
-      if (u.has_tri2) {
+    } else {
 #pragma unroll
-        for (int c = 0; c < 8; ++c) {
+      for (int c = 0; c < 8; ++c) o2[c] = df_value(acc[8 + c]);
+    }
+    if (row < u.n) {
+      float4* d2 = reinterpret_cast<float4*>(u.out2 + row * 8);
 #pragma unroll
-          for (int q = 0; q < c; ++q) df_fms(acc[c], o2[q], t2[q * 8 + c]);
-          o2[c] = df_mul(df_value(acc[c]), r2[c]);
-        }
-      } else {
-#pragma unroll
-        for (int c = 0; c < 8; ++c) o2[c] = df_value(acc[c]);
-      }
-      if (row < u.n) {
-        float4* d2 = reinterpret_cast<float4*>(u.out2 + row * 8);
-#pragma unroll
-        for (int i = 0; i < 4; ++i) d2[i] = make_float4(o2[2 * i].x, o2[2 * i].y, o2[2 * i + 1].x, o2[2 * i + 1].y);
-      }
+      for (int i = 0; i < 4; ++i) d2[i] = make_float4(o2[2 * i].x, o2[2 * i].y, o2[2 * i + 1].x, o2[2 * i + 1].y);
     }
     __syncthreads();
   }
@@ -442,8 +441,8 @@ bool update_tcs_eligible(int s, int nin, bool two) { return s == 8 && two && nin
 size_t update_tcs_smem(int nin) {
   const int kpad = ((8 * nin + 31) / 32) * 32;
   const size_t SB = (size_t)(kpad / 8) * 128;
-  return 2 * UT_SUB * UT_BLK + 12 * SB + UT_MAXK * 4 + 128 * 8 * 8 + 256 * 4 + 32 * 4 +
-         (3 * 64 + 16) * 8 + UT_MAXK * 16 * 8 + 2 * 8 + 16;
+  return 2 * UT_SUB * UT_BLK + 12 * SB + UT_MAXK * 4 + 256 * 4 + 32 * 4 + (3 * 64 + 16) * 8 +
+         2 * 8 + 16;
 }
 
 void launch_update_tcs(cudaStream_t st, const unsigned char* dig, const int* dexp, int a,
@@ -478,7 +477,7 @@ void launch_update_tcs(cudaStream_t st, const unsigned char* dig, const int* dex
   u.step = step;
   u.err = err;
   const int64_t tiles = (n + 127) / 128;
-  int64_t grid = num_sms;
+  int64_t grid = 2LL * num_sms;
   if (grid > tiles) grid = tiles;
   if (grid < 1) grid = 1;
   k_update_df_tcs<<<(unsigned)grid, UT_THREADS, update_tcs_smem(nin), st>>>(u);
