@@ -601,10 +601,10 @@ static void enqueue_cycle(lsba_ctx* h, const lsba_csr* A, const double* Rstart, 
         in.p[k - 1] = h->Ub;
         in.p[k] = h->Wb;
         double* Vk = h->basis + (size_t)(k - 1) * blk;
-        if (h->use_tcs && update_tcs_eligible(s, k + 1, true)) {
+        if (h->use_tcs && k >= 2 && update_tcs_eligible(s, k + 1, true)) {
           prof_begin(h, LSBA_K_UPDATE);
           launch_update_tcs(st, h->dig, h->dexp, k - 1, (const float2*)h->Ub,
-                            (const float2*)h->Wb, n, (float2*)Vk, (float2*)h->Ub, w.coef1, w.tri1,
+                            (const float2*)h->Wb, nullptr, n, (float2*)Vk, (float2*)h->Ub, w.coef1, w.tri1,
                             w.coef2, w.chain, skel == SK_LS ? w.tri2 : nullptr, h->cdf, ctl, k,
                             &h->d_ctl->error, h->num_sms);
           prof_end(h);
@@ -902,7 +902,14 @@ static int run_cycles(lsba_handle h, const lsba_csr* A, const double* Bw, double
     }
     // Cycle end: X += V_j Xi C, U = V_{j+1} [M; -H], C <- c C.
     PROF(LSBA_K_SMALL, launch_small_end(st, w));
-    {
+    if (h->use_tcs && update_tcs_eligible(s, j + 1, true)) {
+      // on the stored digit planes of V_1..V_{j+1}; X's own term in double-float
+      prof_begin(h, LSBA_K_UPDATE);
+      launch_update_tcs(st, h->dig, h->dexp, j + 1, nullptr, nullptr, (const float2*)Xw, n,
+                        (float2*)Xw, (float2*)h->Ub, w.coef1, nullptr, w.coef2, nullptr, nullptr,
+                        h->cdf, h->d_ctl, LSBA_END_STEP, &h->d_ctl->error, h->num_sms);
+      prof_end(h);
+    } else {
       BlockPtrs in = basis_list(h, n, s, j + 1);
       in.p[j + 1] = Xw;
       do_update(h, in, j + 2, n, s, Xw, w.coef1, nullptr, h->Ub, w.coef2, nullptr, nullptr,

@@ -4,6 +4,11 @@
 // blocks in one pass over its inputs [V_1..V_{k-1}, U, W]:
 //   out1 = V_k = (sum_b in_b C1_b) T1^{-1},
 //   out2       = (sum_b in_b C2_b + out1 Chain) T2^{-1}   (T2 for BCGSI+LS only).
+// The cycle end (Eq. (7) and Thm. 1) writes X and the next residual block from
+// [V_1..V_{j+1}] and X in the same way, without the triangular factors; there
+// X's own term X C1_X is added in double-float in the epilogue and only the
+// basis terms go through the digits, so that the digit error is relative to
+// the correction, not to X (a restarted solve adds one correction per cycle).
 // The contraction sum_b in_b [C1_b | C2_b] is a product of an n x K matrix
 // (K = 8 nin) with a K x 16 one, done here exactly on digits as in the
 // tensor-core Gram (kernels_tc.cu):
@@ -43,9 +48,12 @@ struct UpdTcsArgs {
   const int* dexp;               // stored exponents: block i at dexp + i * dexp_stride
   size_t dig_stride, dexp_stride;
   int a;                         // stored input blocks V_1..V_a; inputs [V_1..V_a, U, W]
-  int nin, kpad;                 // nin = a + 2; kpad = 8 nin rounded up to 32
+  int nsplit;                    // blocks split here: 2 (U, W) or 0
+  int nin, kpad;                 // nin = a + nsplit; kpad = 8 nin rounded up to 32
+  int ncoef;                     // coefficient blocks: nin, or nin + 1 with X
   const float2* U;
   const float2* W;
+  const float2* X;               // optional addend block (coefficients after the nin blocks)
   int64_t n;
   float2* out1;
   float2* out2;
@@ -124,12 +132,12 @@ __global__ void __launch_bounds__(UT_THREADS, 2) k_update_df_tcs(const __grid_co
   const int nin = u.nin, K = 8 * nin, a = u.a;
   const int64_t nch = (u.n + 31) / 32, ntile = (u.n + 127) / 128;
   const float2* c1g = u.cdf;
-  const float2* c2g = u.cdf + (size_t)nin * 64;
+  const float2* c2g = u.cdf + (size_t)u.ncoef * 64;
 
   // Zero the B stack once (padding columns stay zero), copy the triangular data.
   for (uint32_t i = (uint32_t)tid * 16; i < 12 * SB; i += UT_THREADS * 16)
     *reinterpret_cast<uint4*>(Bst + i) = make_uint4(0u, 0u, 0u, 0u);
-  for (int e = tid; e < 3 * 64 + 16; e += UT_THREADS) tri[e] = c2g[(size_t)nin * 64 + e];
+  for (int e = tid; e < 3 * 64 + 16; e += UT_THREADS) tri[e] = c2g[(size_t)u.ncoef * 64 + e];
   if (tid == 0) {
     mbar_init(&mmad[0], 1);
     mbar_init(&mmad[1], 1);
@@ -149,7 +157,8 @@ __global__ void __launch_bounds__(UT_THREADS, 2) k_update_df_tcs(const __grid_co
 
   // U and W split tasks: column uc (0..7 U, 8..15 W), row groups ur0 and ur0 + 8.
   const int uc = tid & 15, ur0 = tid >> 4;
-  const float2* usrc = uc < 8 ? u.U + uc : u.W + (uc - 8);
+  const bool has_col = u.nsplit == 2;
+  const float2* usrc = has_col ? (uc < 8 ? u.U + uc : u.W + (uc - 8)) : nullptr;
   bool failed = false;
   int gj = 0;  // sub-chunks issued so far (mbarrier phases)
   const int nsub = (nin + UT_SUB - 1) / UT_SUB;
@@ -178,7 +187,7 @@ __global__ void __launch_bounds__(UT_THREADS, 2) k_update_df_tcs(const __grid_co
 #pragma unroll
       for (int k = 0; k < 8; ++k) {
         const int64_t row = tl * 128 + (ur0 + 8 * h) * 8 + k;
-        x[h][k] = row < u.n ? usrc[row * 8] : make_float2(0.f, 0.f);
+        x[h][k] = (has_col && row < u.n) ? usrc[row * 8] : make_float2(0.f, 0.f);
       }
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
@@ -195,21 +204,21 @@ __global__ void __launch_bounds__(UT_THREADS, 2) k_update_df_tcs(const __grid_co
     for (int h = 0; h < 2; ++h)
       if (tid + UT_THREADS * h < 8 * a) ex[tid + UT_THREADS * h] = exv[h];
     // ---- U and W: exponent over the tile, digits kept in registers
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      float am = 0.f;
-#pragma unroll
-      for (int k = 0; k < 8; ++k) am = fmaxf(am, fabsf(x[h][k].x));
-      red[(ur0 + 8 * h) * 16 + uc] = am;
-    }
-    __syncthreads();
-    float cm = 0.f;
-#pragma unroll
-    for (int i = 0; i < 16; ++i) cm = fmaxf(cm, red[i * 16 + uc]);
-    const int ue = ut_exp_of(cm);
-    if (ur0 == 0) ex[8 * a + uc] = ue;
     uint4 udig[2][6];
-    {
+    if (has_col) {
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        float am = 0.f;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) am = fmaxf(am, fabsf(x[h][k].x));
+        red[(ur0 + 8 * h) * 16 + uc] = am;
+      }
+      __syncthreads();
+      float cm = 0.f;
+#pragma unroll
+      for (int i = 0; i < 16; ++i) cm = fmaxf(cm, red[i * 16 + uc]);
+      const int ue = ut_exp_of(cm);
+      if (ur0 == 0) ex[8 * a + uc] = ue;
       const float sc = ut_pow2(7 - ue);
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
@@ -378,6 +387,26 @@ __global__ void __launch_bounds__(UT_THREADS, 2) k_update_df_tcs(const __grid_co
     if (tile + gridDim.x < ntile) prefetch(tile + gridDim.x);
     // ---- row tid: out1 = acc[0..7] T1^{-1}; out2 = (acc[8..15] + out1 Chain) T2^{-1}
     const int64_t row = r0 + tid;
+    if (u.X && row < u.n) {
+      // X's own term, in double-float (X may be out1: this thread reads the row first)
+      const float4* xr = reinterpret_cast<const float4*>(u.X + row * 8);
+      float2 xv[8];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const float4 v = xr[i];
+        xv[2 * i] = make_float2(v.x, v.y);
+        xv[2 * i + 1] = make_float2(v.z, v.w);
+      }
+      const float2* cx1 = c1g + (size_t)nin * 64;
+      const float2* cx2 = c2g + (size_t)nin * 64;
+#pragma unroll
+      for (int q = 0; q < 8; ++q)
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          df_fma(acc[c], xv[q], cx1[q * 8 + c]);
+          df_fma(acc[8 + c], xv[q], cx2[q * 8 + c]);
+        }
+    }
     float2 o1[8];
     if (u.has_tri1) {
 #pragma unroll
@@ -436,7 +465,7 @@ __global__ void __launch_bounds__(UT_THREADS, 2) k_update_df_tcs(const __grid_co
   if (warp == 0) tc_dealloc(tmem, 128);
 }
 
-bool update_tcs_eligible(int s, int nin, bool two) { return s == 8 && two && nin >= 3 && 8 * nin <= UT_MAXK; }
+bool update_tcs_eligible(int s, int nin, bool two) { return s == 8 && two && nin >= 1 && 8 * nin <= UT_MAXK; }
 
 size_t update_tcs_smem(int nin) {
   const int kpad = ((8 * nin + 31) / 32) * 32;
@@ -446,12 +475,14 @@ size_t update_tcs_smem(int nin) {
 }
 
 void launch_update_tcs(cudaStream_t st, const unsigned char* dig, const int* dexp, int a,
-                       const float2* U, const float2* W, int64_t n, float2* out1, float2* out2,
-                       const double* coef1, const double* tri1, const double* coef2,
+                       const float2* U, const float2* W, const float2* X, int64_t n, float2* out1,
+                       float2* out2, const double* coef1, const double* tri1, const double* coef2,
                        const double* chain, const double* tri2, float2* cdf, const Ctl* ctl,
                        int step, int* err, int num_sms) {
-  const int nin = a + 2;
-  launch_coef_df(st, nin, 8, true, coef1, coef2, chain, tri1, tri2, cdf, ctl, step);
+  const int nsplit = U ? 2 : 0;
+  const int nin = a + nsplit;
+  const int ncoef = nin + (X ? 1 : 0);
+  launch_coef_df(st, ncoef, 8, true, coef1, coef2, chain, tri1, tri2, cdf, ctl, step);
   static std::atomic<unsigned long long> attr_done{0};
   once_per_device(attr_done, [] {
     cudaFuncSetAttribute(k_update_df_tcs, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
@@ -462,10 +493,13 @@ void launch_update_tcs(cudaStream_t st, const unsigned char* dig, const int* dex
   u.dig_stride = digit_block_bytes(n, 8);
   u.dexp_stride = digit_exp_count(n, 8);
   u.a = a;
+  u.nsplit = nsplit;
   u.nin = nin;
+  u.ncoef = ncoef;
   u.kpad = ((8 * nin + 31) / 32) * 32;
   u.U = U;
   u.W = W;
+  u.X = X;
   u.n = n;
   u.out1 = out1;
   u.out2 = out2;
