@@ -9,7 +9,13 @@
 // X's own term X C1_X is added in double-float in the epilogue and only the
 // basis terms go through the digits, so that the digit error is relative to
 // the correction, not to X (a restarted solve adds one correction per cycle).
-// The contraction sum_b in_b [C1_b | C2_b] is a product of an n x K matrix
+// The triangular factors and the chain term act on the columns only, so they
+// are folded into the coefficients once per launch (k_coef_fold, FP64):
+//   C1' = C1 T1^{-1},   C2' = (C2 + C1' Chain) T2^{-1},
+// and out1 = sum_b in_b C1'_b, out2 = sum_b in_b C2'_b.  This is the same
+// product taken in another order; the rounding of a term is still relative to
+// its own size (the folded coefficients are rounded once to double-float).
+// The contraction sum_b in_b [C1'_b | C2'_b] is a product of an n x K matrix
 // (K = 8 nin) with a K x 16 one, done here exactly on digits as in the
 // tensor-core Gram (kernels_tc.cu):
 //   * rows are taken in tiles of 128 (the MMA's M); for column kk of the
@@ -22,8 +28,7 @@
 //   * the level sums l = t + u <= 5 are exact in the FP32 tensor-memory
 //     accumulators over 64 columns (every term an integer <= 2^15, a level
 //     sum < 6 * 64 * 2^15 < 2^24), then added into a double-float accumulator
-//     per row and output column; the triangular solves and the chain term
-//     follow in double-float as in the FP32-pipe kernel.
+//     per row and output column.
 // The A operand comes straight from the stored digit planes (MN-major: 8 rows
 // of one column per 16 bytes, LBO = 12288 between 8-column blocks, SBO = 128
 // between 8-row groups); U and W are split here.
@@ -57,8 +62,7 @@ struct UpdTcsArgs {
   int64_t n;
   float2* out1;
   float2* out2;
-  const float2* cdf;             // k_coef_df layout for nin inputs and two outputs
-  int has_tri1, has_chain, has_tri2;
+  const float2* cdf;             // folded coefficients: C1' (ncoef x 64), then C2'
   const Ctl* ctl;
   int step;
   int* err;
@@ -125,8 +129,7 @@ __global__ void __launch_bounds__(UT_THREADS, 2) k_update_df_tcs(const __grid_co
   int* ex = reinterpret_cast<int*>(Bst + 12 * SB);       // [UT_MAXK]
   float* red = reinterpret_cast<float*>(ex + UT_MAXK);   // [16][16]
   int* fexp = reinterpret_cast<int*>(red + 256);         // [16]
-  float2* tri = reinterpret_cast<float2*>(fexp + 32);    // chain, t1, t2 (3 x 64), r1, r2 (2 x 8)
-  uint64_t* mmad = reinterpret_cast<uint64_t*>(tri + 3 * 64 + 16);  // [2]
+  uint64_t* mmad = reinterpret_cast<uint64_t*>(fexp + 32);  // [2]
   uint32_t* tslot = reinterpret_cast<uint32_t*>(mmad + 2);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int nin = u.nin, K = 8 * nin, a = u.a;
@@ -134,10 +137,9 @@ __global__ void __launch_bounds__(UT_THREADS, 2) k_update_df_tcs(const __grid_co
   const float2* c1g = u.cdf;
   const float2* c2g = u.cdf + (size_t)u.ncoef * 64;
 
-  // Zero the B stack once (padding columns stay zero), copy the triangular data.
+  // Zero the B stack once (padding columns stay zero).
   for (uint32_t i = (uint32_t)tid * 16; i < 12 * SB; i += UT_THREADS * 16)
     *reinterpret_cast<uint4*>(Bst + i) = make_uint4(0u, 0u, 0u, 0u);
-  for (int e = tid; e < 3 * 64 + 16; e += UT_THREADS) tri[e] = c2g[(size_t)u.ncoef * 64 + e];
   if (tid == 0) {
     mbar_init(&mmad[0], 1);
     mbar_init(&mmad[1], 1);
@@ -149,11 +151,6 @@ __global__ void __launch_bounds__(UT_THREADS, 2) k_update_df_tcs(const __grid_co
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tslot;
-  const float2* chain = tri;
-  const float2* t1 = tri + 64;
-  const float2* t2 = tri + 128;
-  const float2* r1 = tri + 192;
-  const float2* r2 = tri + 200;
 
   // U and W split tasks: column uc (0..7 U, 8..15 W), row groups ur0 and ur0 + 8.
   const int uc = tid & 15, ur0 = tid >> 4;
@@ -385,7 +382,7 @@ __global__ void __launch_bounds__(UT_THREADS, 2) k_update_df_tcs(const __grid_co
     // Every MMA of this tile is done and both A buffers are free: start the
     // next tile's copies and loads before finishing this one.
     if (tile + gridDim.x < ntile) prefetch(tile + gridDim.x);
-    // ---- row tid: out1 = acc[0..7] T1^{-1}; out2 = (acc[8..15] + out1 Chain) T2^{-1}
+    // ---- row tid: out1 = acc[0..7], out2 = acc[8..15] (plus X's term)
     const int64_t row = r0 + tid;
     if (u.X && row < u.n) {
       // X's own term, in double-float (X may be out1: this thread reads the row first)
@@ -407,45 +404,20 @@ __global__ void __launch_bounds__(UT_THREADS, 2) k_update_df_tcs(const __grid_co
           df_fma(acc[8 + c], xv[q], cx2[q * 8 + c]);
         }
     }
-    float2 o1[8];
-    if (u.has_tri1) {
+    float2 o1[8], o2[8];
 #pragma unroll
-      for (int c = 0; c < 8; ++c) {
-#pragma unroll
-        for (int q = 0; q < c; ++q) df_fms(acc[c], o1[q], t1[q * 8 + c]);
-        o1[c] = df_mul(df_value(acc[c]), r1[c]);
-      }
-    } else {
-#pragma unroll
-      for (int c = 0; c < 8; ++c) o1[c] = df_value(acc[c]);
+    for (int c = 0; c < 8; ++c) {
+      o1[c] = df_value(acc[c]);
+      o2[c] = df_value(acc[8 + c]);
     }
     if (row < u.n) {
       float4* d1 = reinterpret_cast<float4*>(u.out1 + row * 8);
-#pragma unroll
-      for (int i = 0; i < 4; ++i) d1[i] = make_float4(o1[2 * i].x, o1[2 * i].y, o1[2 * i + 1].x, o1[2 * i + 1].y);
-    }
-    if (u.has_chain) {
-#pragma unroll
-      for (int q = 0; q < 8; ++q)
-#pragma unroll
-        for (int c = 0; c < 8; ++c) df_fma(acc[8 + c], o1[q], chain[q * 8 + c]);
-    }
-    float2 o2[8];
-    if (u.has_tri2) {
-#pragma unroll
-      for (int c = 0; c < 8; ++c) {
-#pragma unroll
-        for (int q = 0; q < c; ++q) df_fms(acc[8 + c], o2[q], t2[q * 8 + c]);
-        o2[c] = df_mul(df_value(acc[8 + c]), r2[c]);
-      }
-    } else {
-#pragma unroll
-      for (int c = 0; c < 8; ++c) o2[c] = df_value(acc[8 + c]);
-    }
-    if (row < u.n) {
       float4* d2 = reinterpret_cast<float4*>(u.out2 + row * 8);
 #pragma unroll
-      for (int i = 0; i < 4; ++i) d2[i] = make_float4(o2[2 * i].x, o2[2 * i].y, o2[2 * i + 1].x, o2[2 * i + 1].y);
+      for (int i = 0; i < 4; ++i) {
+        d1[i] = make_float4(o1[2 * i].x, o1[2 * i].y, o1[2 * i + 1].x, o1[2 * i + 1].y);
+        d2[i] = make_float4(o2[2 * i].x, o2[2 * i].y, o2[2 * i + 1].x, o2[2 * i + 1].y);
+      }
     }
     __syncthreads();
   }
@@ -470,8 +442,85 @@ bool update_tcs_eligible(int s, int nin, bool two) { return s == 8 && two && nin
 size_t update_tcs_smem(int nin) {
   const int kpad = ((8 * nin + 31) / 32) * 32;
   const size_t SB = (size_t)(kpad / 8) * 128;
-  return 2 * UT_SUB * UT_BLK + 12 * SB + UT_MAXK * 4 + 256 * 4 + 32 * 4 + (3 * 64 + 16) * 8 +
-         2 * 8 + 16;
+  return 2 * UT_SUB * UT_BLK + 12 * SB + UT_MAXK * 4 + 256 * 4 + 32 * 4 + 2 * 8 + 16;
+}
+
+struct CoefFoldArgs {
+  const double* coef1;           // K x 8 row-major (row q of block b at b * 8 + q)
+  const double* coef2;
+  const double* chain;           // 8 x 8, or nullptr
+  const double* tri1;            // 8 x 8 upper triangular, or nullptr
+  const double* tri2;
+  int rows;                      // K = 8 ncoef
+  float2* out;                   // C1' then C2', double-float
+  const Ctl* ctl;
+  int step;
+};
+
+#define FOLD_ROWS 16             // coefficient rows per 128-thread CTA, 8 lanes per row
+
+// Right-multiply the row held by an 8-lane group by T^{-1} (T upper
+// triangular, rinv its reciprocal diagonal): forward substitution in
+// double-float, one column per lane.
+__device__ __forceinline__ float2 fold_trsm(float2 v, const float2* T, const float2* rinv, int c) {
+  dfacc t{v.x, v.y};
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const float2 own = df_mul(df_value(t), rinv[q]);
+    const float2 oq = make_float2(__shfl_sync(0xffffffffu, own.x, q, 8), __shfl_sync(0xffffffffu, own.y, q, 8));
+    if (c == q) t = dfacc{oq.x, oq.y};
+    else if (c > q) df_fms(t, oq, T[q * 8 + c]);
+  }
+  return df_value(t);
+}
+
+// C1' = C1 T1^{-1} and C2' = (C2 + C1' Chain) T2^{-1}, row by row.  FP64 is
+// used only to convert the inputs (spread over all threads: the FP64 pipe is
+// narrow); the substitutions run in double-float with one lane per column.
+__global__ void __launch_bounds__(128) k_coef_fold(const __grid_constant__ CoefFoldArgs f) {
+  if (f.step >= 0 && *(volatile const int*)&f.ctl->update_step != f.step) return;
+  __shared__ float2 tm[3 * 64 + 16];               // T1, T2, Chain, 1 / diag(T1), 1 / diag(T2)
+  __shared__ float2 cr[2][FOLD_ROWS * 8];          // this CTA's rows of C1 and C2
+  const int tid = threadIdx.x;
+  const int r0 = blockIdx.x * FOLD_ROWS;
+  for (int e = tid; e < 3 * 64 + 16 + 2 * FOLD_ROWS * 8; e += 128) {
+    float2 v = make_float2(0.f, 0.f);
+    if (e < 64) {
+      if (f.tri1) v = df_from_double(f.tri1[e]);
+    } else if (e < 128) {
+      if (f.tri2) v = df_from_double(f.tri2[e - 64]);
+    } else if (e < 192) {
+      if (f.chain) v = df_from_double(f.chain[e - 128]);
+    } else if (e < 200) {
+      if (f.tri1) v = df_from_double(1.0 / f.tri1[(e - 192) * 9]);
+    } else if (e < 208) {
+      if (f.tri2) v = df_from_double(1.0 / f.tri2[(e - 200) * 9]);
+    } else {
+      const int k = e - 208, m = k / (FOLD_ROWS * 8), o = k % (FOLD_ROWS * 8);
+      const int r = r0 + o / 8;
+      if (r < f.rows) v = df_from_double((m ? f.coef2 : f.coef1)[(size_t)r * 8 + (o & 7)]);
+    }
+    if (e < 208) tm[e] = v;
+    else cr[(e - 208) / (FOLD_ROWS * 8)][(e - 208) % (FOLD_ROWS * 8)] = v;
+  }
+  __syncthreads();
+  const int rl = tid >> 3, c = tid & 7, r = r0 + rl;
+  float2 o1 = cr[0][rl * 8 + c];
+  if (f.tri1) o1 = fold_trsm(o1, tm, tm + 192, c);
+  dfacc a2{cr[1][rl * 8 + c].x, cr[1][rl * 8 + c].y};
+  if (f.chain) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const float2 oq = make_float2(__shfl_sync(0xffffffffu, o1.x, q, 8), __shfl_sync(0xffffffffu, o1.y, q, 8));
+      df_fma(a2, oq, tm[128 + q * 8 + c]);
+    }
+  }
+  float2 o2 = df_value(a2);
+  if (f.tri2) o2 = fold_trsm(o2, tm + 64, tm + 200, c);
+  if (r < f.rows) {
+    f.out[(size_t)r * 8 + c] = o1;
+    f.out[(size_t)f.rows * 8 + (size_t)r * 8 + c] = o2;
+  }
 }
 
 void launch_update_tcs(cudaStream_t st, const unsigned char* dig, const int* dexp, int a,
@@ -482,7 +531,17 @@ void launch_update_tcs(cudaStream_t st, const unsigned char* dig, const int* dex
   const int nsplit = U ? 2 : 0;
   const int nin = a + nsplit;
   const int ncoef = nin + (X ? 1 : 0);
-  launch_coef_df(st, ncoef, 8, true, coef1, coef2, chain, tri1, tri2, cdf, ctl, step);
+  CoefFoldArgs f;
+  f.coef1 = coef1;
+  f.coef2 = coef2;
+  f.chain = chain;
+  f.tri1 = tri1;
+  f.tri2 = tri2;
+  f.rows = 8 * ncoef;
+  f.out = cdf;
+  f.ctl = ctl;
+  f.step = step;
+  k_coef_fold<<<(f.rows + FOLD_ROWS - 1) / FOLD_ROWS, 128, 0, st>>>(f);
   static std::atomic<unsigned long long> attr_done{0};
   once_per_device(attr_done, [] {
     cudaFuncSetAttribute(k_update_df_tcs, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
@@ -504,9 +563,6 @@ void launch_update_tcs(cudaStream_t st, const unsigned char* dig, const int* dex
   u.out1 = out1;
   u.out2 = out2;
   u.cdf = cdf;
-  u.has_tri1 = tri1 != nullptr;
-  u.has_chain = chain != nullptr;
-  u.has_tri2 = tri2 != nullptr;
   u.ctl = ctl;
   u.step = step;
   u.err = err;
