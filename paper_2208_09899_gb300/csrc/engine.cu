@@ -603,16 +603,19 @@ static void enqueue_cycle(lsba_ctx* h, const lsba_csr* A, const double* Rstart, 
         double* Vk = h->basis + (size_t)(k - 1) * blk;
         if (h->use_tcs && k >= 2 && update_tcs_eligible(s, k + 1, true)) {
           prof_begin(h, LSBA_K_UPDATE);
+          // V_k's digit planes come out of the same pass
           launch_update_tcs(st, h->dig, h->dexp, k - 1, (const float2*)h->Ub,
-                            (const float2*)h->Wb, nullptr, n, (float2*)Vk, (float2*)h->Ub, w.coef1, w.tri1,
-                            w.coef2, w.chain, skel == SK_LS ? w.tri2 : nullptr, h->cdf, ctl, k,
+                            (const float2*)h->Wb, nullptr, n, (float2*)Vk, (float2*)h->Ub, w.coef1,
+                            w.tri1, w.coef2, w.chain, skel == SK_LS ? w.tri2 : nullptr, h->cdf,
+                            h->dig + (size_t)(k - 1) * digit_block_bytes(n, s),
+                            h->dexp + (size_t)(k - 1) * digit_exp_count(n, s), ctl, k,
                             &h->d_ctl->error, h->num_sms);
           prof_end(h);
         } else {
           do_update(h, in, k + 1, n, s, Vk, w.coef1, w.tri1, h->Ub, w.coef2, w.chain,
                     skel == SK_LS ? w.tri2 : nullptr, ctl, k);
+          if (h->use_tcs) split_basis(h, k - 1, n, s, ctl, k);
         }
-        if (h->use_tcs) split_basis(h, k - 1, n, s, ctl, k);
       }
     }
   }
@@ -907,7 +910,8 @@ static int run_cycles(lsba_handle h, const lsba_csr* A, const double* Bw, double
       prof_begin(h, LSBA_K_UPDATE);
       launch_update_tcs(st, h->dig, h->dexp, j + 1, nullptr, nullptr, (const float2*)Xw, n,
                         (float2*)Xw, (float2*)h->Ub, w.coef1, nullptr, w.coef2, nullptr, nullptr,
-                        h->cdf, h->d_ctl, LSBA_END_STEP, &h->d_ctl->error, h->num_sms);
+                        h->cdf, nullptr, nullptr, h->d_ctl, LSBA_END_STEP, &h->d_ctl->error,
+                        h->num_sms);
       prof_end(h);
     } else {
       BlockPtrs in = basis_list(h, n, s, j + 1);

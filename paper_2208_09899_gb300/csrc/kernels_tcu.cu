@@ -63,6 +63,8 @@ struct UpdTcsArgs {
   float2* out1;
   float2* out2;
   const float2* cdf;             // folded coefficients: C1' (ncoef x 64), then C2'
+  unsigned char* dig_out;        // optional: digit planes and exponents of out1, in the
+  int* dexp_out;                 //   stored layout (kernels_tc.cu), written from registers
   const Ctl* ctl;
   int step;
   int* err;
@@ -419,6 +421,43 @@ __global__ void __launch_bounds__(UT_THREADS, 2) k_update_df_tcs(const __grid_co
         d2[i] = make_float4(o2[2 * i].x, o2[2 * i].y, o2[2 * i + 1].x, o2[2 * i + 1].y);
       }
     }
+    if (u.dig_out) {
+      // out1's digits for the later Grams and updates, exactly as the split
+      // kernel would make them from the stored values (rows past n are zero):
+      // per column the exponent of the tile maximum, then six digits per value
+      // into the free A buffer, then 16-byte stores of the tile's four chunks.
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        float am = fabsf(o1[i].x);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) am = fmaxf(am, __shfl_xor_sync(0xffffffffu, am, o));
+        if (lane == 0) red[warp * 8 + i] = am;
+      }
+      __syncthreads();
+      unsigned char* stg = Abuf + UT_SUB * UT_BLK;
+      const uint32_t rofs = (uint32_t)warp * UT_DIG_GROUP + (uint32_t)(lane >> 4) * 256 +
+                            (uint32_t)((lane >> 3) & 1) * 128 + (uint32_t)(lane & 7) * 2;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const float cm = fmaxf(fmaxf(red[i], red[8 + i]), fmaxf(red[16 + i], red[24 + i]));
+        const int e = ut_exp_of(cm);
+        float d[6];
+        ut_digits(o1[i], ut_pow2(7 - e), d);
+#pragma unroll
+        for (int t = 0; t < 6; ++t)
+          *reinterpret_cast<__nv_bfloat16*>(stg + rofs + t * 512 + i * 16) = __float2bfloat16_rn(d[t]);
+      }
+      const int nq = nch - tile * 4 < 4 ? (int)(nch - tile * 4) : 4;   // chunks inside n
+      if (tid < 8 * nq) {
+        const int i = tid & 7;
+        const float cm = fmaxf(fmaxf(red[i], red[8 + i]), fmaxf(red[16 + i], red[24 + i]));
+        u.dexp_out[(tile * 4 + (tid >> 3)) * 8 + i] = ut_exp_of(cm);
+      }
+      __syncthreads();
+      uint4* dst = reinterpret_cast<uint4*>(u.dig_out + (size_t)tile * 4 * UT_DIG_GROUP);
+      const uint4* src = reinterpret_cast<const uint4*>(stg);
+      for (int p = tid; p < nq * (UT_DIG_GROUP / 16); p += UT_THREADS) dst[p] = src[p];
+    }
     __syncthreads();
   }
   if (failed) {
@@ -526,8 +565,8 @@ __global__ void __launch_bounds__(128) k_coef_fold(const __grid_constant__ CoefF
 void launch_update_tcs(cudaStream_t st, const unsigned char* dig, const int* dexp, int a,
                        const float2* U, const float2* W, const float2* X, int64_t n, float2* out1,
                        float2* out2, const double* coef1, const double* tri1, const double* coef2,
-                       const double* chain, const double* tri2, float2* cdf, const Ctl* ctl,
-                       int step, int* err, int num_sms) {
+                       const double* chain, const double* tri2, float2* cdf, unsigned char* dig_out,
+                       int* dexp_out, const Ctl* ctl, int step, int* err, int num_sms) {
   const int nsplit = U ? 2 : 0;
   const int nin = a + nsplit;
   const int ncoef = nin + (X ? 1 : 0);
@@ -563,11 +602,17 @@ void launch_update_tcs(cudaStream_t st, const unsigned char* dig, const int* dex
   u.out1 = out1;
   u.out2 = out2;
   u.cdf = cdf;
+  u.dig_out = dig_out;
+  u.dexp_out = dexp_out;
   u.ctl = ctl;
   u.step = step;
   u.err = err;
+  // Two CTAs per SM, two short of filling the GPU: the SMs left with one CTA
+  // have room for the small side kernel of the same iteration (512 threads x
+  // 64 registers), which then runs beside this pass instead of after it,
+  // where it would hold an SM that the next Gram's persistent grid needs.
   const int64_t tiles = (n + 127) / 128;
-  int64_t grid = 2LL * num_sms;
+  int64_t grid = 2LL * num_sms - 2;
   if (grid > tiles) grid = tiles;
   if (grid < 1) grid = 1;
   k_update_df_tcs<<<(unsigned)grid, UT_THREADS, update_tcs_smem(nin), st>>>(u);

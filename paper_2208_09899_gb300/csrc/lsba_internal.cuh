@@ -174,13 +174,14 @@ void launch_coef_df(cudaStream_t st, int nin, int s, bool two, const double* coe
 // Tensor-core update (kernels_tcu.cu): inputs [V_1..V_a (stored digits), U, W]
 // (U = W = nullptr: [V_1..V_a] only) plus an optional block X added in
 // double-float (coefficients after the other inputs'), two outputs, s = 8,
-// 8 nin <= 256 with nin the digit inputs.
+// 8 nin <= 256 with nin the digit inputs.  dig_out / dexp_out (optional)
+// receive out1's digit planes, as launch_split_digits would write them.
 bool update_tcs_eligible(int s, int nin, bool two);
 void launch_update_tcs(cudaStream_t st, const unsigned char* dig, const int* dexp, int a,
                        const float2* U, const float2* W, const float2* X, int64_t n, float2* out1,
                        float2* out2, const double* coef1, const double* tri1, const double* coef2,
-                       const double* chain, const double* tri2, float2* cdf, const Ctl* ctl,
-                       int step, int* err, int num_sms);
+                       const double* chain, const double* tri2, float2* cdf, unsigned char* dig_out,
+                       int* dexp_out, const Ctl* ctl, int step, int* err, int num_sms);
 GramPlan plan_gram_tcs(int64_t n, int s, int a, int b, int num_sms);
 void launch_gram_tcs(cudaStream_t st, const GramPlan& p, const unsigned char* dig,
                      const int* dexp, int64_t n, int s, int a, const float2* U, const float2* W,

@@ -159,6 +159,29 @@ class DeviceCSR:
         return d
 
 
+def _host_ptr(a) -> int:
+    """Address of a contiguous host array (numpy array or CPU torch tensor)."""
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("host arrays must be contiguous")
+        return a.ctypes.data
+    if a.device.type != "cpu" or not a.is_contiguous():
+        raise ValueError("host tensors must be contiguous CPU tensors")
+    return a.data_ptr()
+
+
+class PinnedCSR:
+    """A host CSR matrix copied into page-locked memory (the H2D copies of
+    lsba_solve_host then run as DMA at the link's bandwidth)."""
+
+    def __init__(self, A):
+        import torch
+        self.n, self.nnz = int(A.n), int(A.nnz)
+        self.rowptr = torch.from_numpy(np.ascontiguousarray(A.rowptr, dtype=np.int32)).pin_memory()
+        self.colidx = torch.from_numpy(np.ascontiguousarray(A.colidx, dtype=np.int32)).pin_memory()
+        self.vals = torch.from_numpy(np.ascontiguousarray(A.vals, dtype=np.float64)).pin_memory()
+
+
 class Solver:
     """A solver handle bound to one device and the current torch stream."""
 
@@ -209,16 +232,33 @@ class Solver:
                                           s, m, tol, SKELETONS[skeleton]),
                       (LSBA_OK, LSBA_NOT_CONVERGED, LSBA_BREAKDOWN))
 
-    def solve_host(self, A, B: np.ndarray, m: int, tol: float, skeleton: str = "bcgsi_ls"):
-        """Host buffers in, host X out (copies inside the call)."""
-        B = np.ascontiguousarray(B, dtype=np.float64)
+    def solve_host(self, A, B, m: int, tol: float, skeleton: str = "bcgsi_ls", X=None):
+        """Host buffers in, host X out (copies inside the call).
+
+        A is a host CSR (numpy arrays, or a `PinnedCSR`); B (n x s) and the
+        optional output X are numpy arrays or CPU torch tensors (pinned memory
+        makes the copies asynchronous DMA).  Returns (X, status)."""
+        if isinstance(A, PinnedCSR):
+            rp, ci, va = A.rowptr, A.colidx, A.vals
+        else:
+            rp = np.ascontiguousarray(A.rowptr, dtype=np.int32)
+            ci = np.ascontiguousarray(A.colidx, dtype=np.int32)
+            va = np.ascontiguousarray(A.vals, dtype=np.float64)
+        if isinstance(B, np.ndarray):
+            B = np.ascontiguousarray(B, dtype=np.float64)
+            if X is None:
+                X = np.empty_like(B)
+        else:
+            import torch
+            if B.dtype != torch.float64 or B.device.type != "cpu" or not B.is_contiguous():
+                raise ValueError("B must be a contiguous float64 CPU tensor")
+            if X is None:
+                X = torch.empty_like(B)
+        if tuple(X.shape) != tuple(B.shape):
+            raise ValueError("X must have the shape of B")
         self._last_s = B.shape[1]
-        X = np.empty_like(B)
-        rp = np.ascontiguousarray(A.rowptr, dtype=np.int32)
-        ci = np.ascontiguousarray(A.colidx, dtype=np.int32)
-        va = np.ascontiguousarray(A.vals, dtype=np.float64)
-        st = self.lib.lsba_solve_host(self.h, A.n, A.nnz, rp.ctypes.data, ci.ctypes.data,
-                                      va.ctypes.data, B.ctypes.data, X.ctypes.data, B.shape[1], m,
+        st = self.lib.lsba_solve_host(self.h, A.n, A.nnz, _host_ptr(rp), _host_ptr(ci),
+                                      _host_ptr(va), _host_ptr(B), _host_ptr(X), B.shape[1], m,
                                       tol, SKELETONS[skeleton])
         _check(st, (LSBA_OK, LSBA_NOT_CONVERGED, LSBA_BREAKDOWN))
         return X, st

@@ -304,6 +304,11 @@ def test_bitwise_reproducible_and_host_api(env):
     sv = lsba.Solver(0)
     X3, code = sv.solve_host(A, B, 10, 1e-10, "bcgsi_ls")
     assert code == 0 and np.array_equal(X1, X3)
+    # pinned host tensors (the bench's end-to-end path)
+    hB = torch.from_numpy(np.ascontiguousarray(B)).pin_memory()
+    hX = torch.empty_like(hB).pin_memory()
+    X4, code = sv.solve_host(lsba.PinnedCSR(A), hB, 10, 1e-10, "bcgsi_ls", X=hX)
+    assert code == 0 and X4 is hX and np.array_equal(X1, hX.numpy())
 
 
 _LAPL512 = {}
