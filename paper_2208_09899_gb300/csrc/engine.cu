@@ -437,7 +437,7 @@ static int pull_ctl(lsba_ctx* h) {
     prof_end(h);            \
   } while (0)
 
-enum { SK_BCGS = 0, SK_PIP = 1, SK_LS = 2, SK_ICWY = 3, SK_CWY = 4 };
+enum { SK_BCGS = 0, SK_PIP = 1, SK_LS = 2, SK_ICWY = 3, SK_CWY = 4, SK_BMGS = 5 };
 static bool lagged(int skel) { return skel == SK_LS || skel == SK_ICWY || skel == SK_CWY; }
 
 // Precision dispatch of the three bandwidth-shaped passes (profiled).  In the
@@ -542,7 +542,31 @@ static void enqueue_cycle(lsba_ctx* h, const lsba_csr* A, const double* Rstart, 
   const int kmax = lagged(skel) ? m_cur + 1 : m_cur;
   const size_t blk = (size_t)n * s;
   for (int k = 1; k <= kmax; ++k) {
-    if (skel == SK_PIP || skel == SK_BCGS) {
+    if (skel == SK_BMGS) {
+      // Alg. 2: one Gram and one in-place update per earlier basis block, then CholQR.
+      const double* Vk = h->basis + (size_t)(k - 1) * blk;
+      do_spmm(h, A, Vk, h->Wb, s, ctl, 1);
+      BlockPtrs R;
+      memset(&R, 0, sizeof(R));
+      R.p[0] = h->Wb;
+      for (int jb = 1; jb <= k; ++jb) {
+        BlockPtrs L;
+        memset(&L, 0, sizeof(L));
+        L.p[0] = h->basis + (size_t)(jb - 1) * blk;
+        do_gram(h, L, 1, R, 1, n, s, ctl, 1);
+        if (jb == 1) wait_side(h, k - 1);
+        PROF(LSBA_K_SMALL, launch_small_step(st, w, k, jb - 1));
+        BlockPtrs in = L;
+        in.p[1] = h->Wb;
+        do_update(h, in, 2, n, s, h->Wb, w.coef1, nullptr, nullptr, nullptr, nullptr, nullptr,
+                  ctl, k);
+      }
+      do_gram(h, R, 1, R, 1, n, s, ctl, 1);
+      PROF(LSBA_K_SMALL, launch_small_step(st, w, k, k));
+      enqueue_side(h, k);
+      do_update(h, R, 1, n, s, h->basis + (size_t)k * blk, w.coef1, w.tri1, nullptr, nullptr,
+                nullptr, nullptr, ctl, k);
+    } else if (skel == SK_PIP || skel == SK_BCGS) {
       const double* Vk = h->basis + (size_t)(k - 1) * blk;
       do_spmm(h, A, Vk, h->Wb, s, ctl, 1);
       BlockPtrs L = basis_list(h, n, s, k);
@@ -750,6 +774,7 @@ static int skel_code(lsba_skeleton s) {
     case LSBA_BCGSI_LS: return SK_LS;
     case LSBA_BMGS_ICWY: return SK_ICWY;
     case LSBA_BMGS_CWY: return SK_CWY;
+    case LSBA_BMGS: return SK_BMGS;
     default: return -1;
   }
 }
@@ -880,7 +905,9 @@ static int run_cycles(lsba_handle h, const lsba_csr* A, const double* Bw, double
     S.steps += j;
     const int a_calls = lagged(skel) ? j + 1 + f : j + f;
     S.a_calls += a_calls;
-    S.syncs += (skel == SK_BCGS) ? 2 * a_calls : a_calls;
+    S.syncs += (skel == SK_BCGS)   ? 2 * a_calls
+               : (skel == SK_BMGS) ? a_calls * (a_calls + 3) / 2   // k + 1 in step k
+                                   : a_calls;
     S.v_apps += vper * j + (j > 0 ? vcyc : 0);
     if (!std::isnan(c->est)) S.relres_est = c->est;
     if (cycle == 1 && record_first && h->opt.record_history) {

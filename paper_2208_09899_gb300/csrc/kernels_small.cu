@@ -30,7 +30,7 @@ namespace lsba {
 #define NT LSBA_SMALL_THREADS
 #define NWARPS (NT / 32)
 
-enum { SK_BCGS = 0, SK_PIP = 1, SK_LS = 2, SK_ICWY = 3, SK_CWY = 4 };
+enum { SK_BCGS = 0, SK_PIP = 1, SK_LS = 2, SK_ICWY = 3, SK_CWY = 4, SK_BMGS = 5 };
 
 __device__ __forceinline__ double warp_sum(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -687,6 +687,28 @@ __device__ void step_bcgs(const SmallWs& w, int k, int phase, Shared& sh) {
   }
 }
 
+// BMGS-Arnoldi (Alg. 2), iteration k.  Phase p < k: the Gram is V_{p+1}^T W;
+// H_{p+1,k} = G and W <- W - V_{p+1} H_{p+1,k} in place (inputs [V_{p+1}, W]).
+// Phase k: [V_{k+1}, H_{k+1,k}] = CholQR(W), as in BCGS.
+__device__ void step_bmgs(const SmallWs& w, int k, int phase, Shared& sh) {
+  if (phase >= k) {
+    step_bcgs(w, k, 1, sh);
+    return;
+  }
+  const int s = w.s, ldH = w.ldH;
+  const double* G = w.G;
+  double* Hk = w.H + (size_t)(k - 1) * s * ldH + (size_t)phase * s;
+  if (phase == 0) record_gram(w, G, s, s);
+  for (int e = threadIdx.x; e < s * s; e += NT) {
+    const int i = e % s, c = e / s;
+    Hk[i + c * ldH] = G[i * s + c];
+  }
+  for (int e = threadIdx.x; e < s * s; e += NT) w.coef1[e] = -G[e];
+  put_coef(w.coef1, 1, s, nullptr, 0, 1.0);
+  __syncthreads();
+  if (threadIdx.x == 0) w.ctl->update_step = k;
+}
+
 // Lagged skeletons, iteration k = 1: H_{1,1} = <U, W> (= J), U <- W - V_1 H_{1,1}.
 // Inputs [V_1, W]; out1 = U.
 __device__ void step_lagged_first(const SmallWs& w, Shared& sh) {
@@ -879,6 +901,7 @@ __global__ void __launch_bounds__(NT) k_small_step(SmallWs w, int k, int phase) 
   switch (w.skel) {
     case SK_PIP: step_pip(w, k, sh); break;
     case SK_BCGS: step_bcgs(w, k, phase, sh); break;
+    case SK_BMGS: step_bmgs(w, k, phase, sh); break;
     case SK_ICWY:
     case SK_CWY:
       if (k == 1) step_lagged_first(w, sh);

@@ -57,3 +57,15 @@ def test_invalid_arguments_without_gpu(lib):
     assert lib.lsba_get_stats(None, None) == 3
     assert lib.lsba_destroy(None) == 3
     assert lib.lsba_create(None, 0, None, None) == 3
+
+
+def test_binding_enums_match_header():
+    """The binding's skeleton, modification and precision codes are the
+    header's enumerators (the skeleton names are the paper's, lower case)."""
+    from paper_2208_09899_gb300 import lsba
+    src = open(os.path.join(ROOT, "include", "lsba.h")).read()
+    body = re.search(r"typedef enum \{([^}]*)\} lsba_skeleton;", src).group(1)
+    header = {m.group(1).lower(): int(m.group(2))
+              for m in re.finditer(r"LSBA_(\w+)\s*=\s*(\d+)", body)}
+    assert header == lsba.SKELETONS
+    assert "bmgs" in header and "bcgsi_ls" in header

@@ -176,15 +176,23 @@ def _compare_solve(lsba, A, B, m, tol, sk, mod, max_restarts=50, first_cycle_tol
         (ref.cycles, ref.steps, ref.a_calls, ref.syncs, ref.v_apps)
     # First cycle: Gram outputs and Hessenberg.
     fc = ref.first_cycle
-    assert len(hist["grams"]) == len(fc["grams"])
-    for g_gpu, g_ref in zip(hist["grams"], fc["grams"]):
-        assert g_gpu.shape == g_ref.shape
-        assert _rel(g_gpu, g_ref) <= first_cycle_tol
-    assert _rel(hist["first_beta"], fc["Beta"]) <= first_cycle_tol
     j = fc["j"]
     s = B.shape[1]
     Hr = fc["H"]
     Hg = hist["first_H"]
+    assert len(hist["grams"]) == len(fc["grams"])
+    for i, (g_gpu, g_ref) in enumerate(zip(hist["grams"], fc["grams"])):
+        assert g_gpu.shape == g_ref.shape
+        scale = np.linalg.norm(g_ref)
+        if sk == "bmgs" and j > 0:
+            # BMGS records its first Gram of step k, H_{1,k} = V_1^T A V_k, which
+            # vanishes for k >= 3 when A is symmetric (H is then block
+            # tridiagonal): measure it against the step's whole H column (the
+            # last completed one for a step that flagged).
+            c = min(i, j - 1)
+            scale = max(scale, np.linalg.norm(Hr[:(c + 2) * s, c * s:(c + 1) * s]))
+        assert np.linalg.norm(g_gpu - g_ref) <= first_cycle_tol * (scale if scale > 0 else 1.0)
+    assert _rel(hist["first_beta"], fc["Beta"]) <= first_cycle_tol
     assert Hg.shape == Hr.shape
     for c in range(j):
         col_r = Hr[:(c + 2) * s, c * s:(c + 1) * s]
@@ -217,7 +225,7 @@ def test_config1_tridiag_bgmres_bcgsi_ls(env, precision):
 
 @pytest.mark.parametrize("precision", ["df", "fp64"])
 @pytest.mark.parametrize("mod", ["gmres", "fom"])
-@pytest.mark.parametrize("sk", ["bcgs", "bcgs_pip", "bcgsi_ls", "bmgs_icwy", "bmgs_cwy"])
+@pytest.mark.parametrize("sk", ["bcgs", "bcgs_pip", "bcgsi_ls", "bmgs_icwy", "bmgs_cwy", "bmgs"])
 def test_all_skeletons_laplacian(env, sk, mod, precision):
     torch, lsba = env
     A = W.laplacian_2d(40, 37)
@@ -251,7 +259,7 @@ def test_wide_blocks(env, s, sk, precision, expect):
     assert st["precision"] == lsba.PRECISIONS[expect]
 
 
-@pytest.mark.parametrize("sk", ["bcgs_pip", "bcgsi_ls", "bmgs_icwy", "bcgs"])
+@pytest.mark.parametrize("sk", ["bcgs_pip", "bcgsi_ls", "bmgs_icwy", "bcgs", "bmgs"])
 def test_adaptive_restart_injected_flag(env, sk):
     torch, lsba = env
     A = W.laplacian_2d(30)
