@@ -9,7 +9,8 @@ with low-synchronization skeletons", arXiv 2208.09899):
 
 * Problem A X = B, A n x n sparse, B n x s (Sec. 2, Eq. (1)); real FP64 only.
 * Classical block inner product <X, Y> = X^T Y and scaling quotient
-  N(X) = R of X = Q R (Sec. 2.2, Table 1).
+  N(X) = R of X = Q R (Sec. 2.2, Table 1); global block inner product
+  <X, Y> = tr(X^T Y)/s I_s with N(X) = ||X||_F/sqrt(s) I_s (Table 1).
 * Muscle CholQR: R = chol(X^T X), Q = X R^{-1} (Sec. 2.3; the muscle list of Sec. 5).
 * Skeletons, each written from its algorithm in the paper's order:
   BMGS-Arnoldi (Alg. 2), BCGS (the condensed loop of Sec. 3.1),
@@ -83,6 +84,30 @@ def inner(X: np.ndarray, Y: np.ndarray) -> np.ndarray:
     return X.T @ Y
 
 
+def global_inner(s: int):
+    """The global block inner product of Table 1 for blocks of s columns:
+    block (i, j) of <X, Y> is tr(X_i^T Y_j)/s I_s, X_i and Y_j the i-th and
+    j-th s-column blocks of X and Y (a block vector list is concatenated)."""
+    def ip(X: np.ndarray, Y: np.ndarray) -> np.ndarray:
+        a, b = X.shape[1] // s, Y.shape[1] // s
+        G = np.zeros((a * s, b * s))
+        for i in range(a):
+            for j in range(b):
+                t = np.sum(X[:, i * s:(i + 1) * s] * Y[:, j * s:(j + 1) * s]) / s
+                G[i * s:(i + 1) * s, j * s:(j + 1) * s] = t * np.eye(s)
+        return G
+    return ip
+
+
+def block_inner_product(name: str, s: int):
+    """The block inner product named "classical" or "global" (Table 1)."""
+    if name == "classical":
+        return inner
+    if name == "global":
+        return global_inner(s)
+    raise ValueError(name)
+
+
 def chol_flag(G: np.ndarray):
     """Upper Cholesky factor R (G = R^T R) read from the upper triangle of G,
     with the NaN-flag of Sec. 4 (reading R1).  Returns (R, flag)."""
@@ -119,9 +144,11 @@ def left_solve_upper_T(R: np.ndarray, Y: np.ndarray) -> np.ndarray:
     return Z
 
 
-def cholqr(X: np.ndarray):
-    """CholQR muscle: R = chol(X^T X), Q = X R^{-1}.  Returns (Q, R, flag)."""
-    R, flag = chol_flag(inner(X, X))
+def cholqr(X: np.ndarray, ip=inner):
+    """CholQR muscle: R = chol(<X, X>), Q = X R^{-1}.  Returns (Q, R, flag).
+    Under the global inner product <X, X> = ||X||_F^2/s I_s, so R is the
+    global scaling quotient ||X||_F/sqrt(s) I_s (Table 1)."""
+    R, flag = chol_flag(ip(X, X))
     if flag:
         return None, R, True
     return right_solve_upper(X, R), R, False
@@ -143,8 +170,10 @@ class _Arnoldi:
     relation j is complete, ("flag", j) when chol flagged while completing
     relation j, or ("none", 0)."""
 
-    def __init__(self, A, V1: np.ndarray, m: int, counts: dict, grams: list | None):
+    def __init__(self, A, V1: np.ndarray, m: int, counts: dict, grams: list | None,
+                 ip=inner):
         self.A, self.m = A, m
+        self.ip = ip
         n, s = V1.shape
         self.n, self.s = n, s
         self.V = [V1]
@@ -197,14 +226,14 @@ class BMGS(_Arnoldi):
         k = self.k
         W = self._matvec(self.V[k - 1])
         for j in range(1, k + 1):
-            Hjk = inner(self.V[j - 1], W)
+            Hjk = self.ip(self.V[j - 1], W)
             self._sync()
             if j == 1:
                 self._record(Hjk)
             self.set_Hb(j, k, Hjk)
             W = W - self.V[j - 1] @ Hjk
         self._sync()
-        Q, R, flag = cholqr(W)
+        Q, R, flag = cholqr(W, self.ip)
         if flag or force_flag:
             return ("flag", k)
         self.V.append(Q)
@@ -220,13 +249,13 @@ class BCGS(_Arnoldi):
         k = self.k
         W = self._matvec(self.V[k - 1])
         Vk = self.basis(k)
-        Hc = inner(Vk, W)
+        Hc = self.ip(Vk, W)
         self._sync()
         self._record(Hc)
         self.set_Hcol(1, k, k, Hc)
         W = W - Vk @ Hc
         self._sync()
-        Q, R, flag = cholqr(W)
+        Q, R, flag = cholqr(W, self.ip)
         if flag or force_flag:
             return ("flag", k)
         self.V.append(Q)
@@ -242,7 +271,7 @@ class BCGS_PIP(_Arnoldi):
         k, s = self.k, self.s
         W = self._matvec(self.V[k - 1])
         Vk = self.basis(k)
-        G = inner(np.hstack([Vk, W]), W)          # [H_{1:k,k}; Omega]
+        G = self.ip(np.hstack([Vk, W]), W)          # [H_{1:k,k}; Omega]
         self._sync()
         self._record(G)
         Hc, Om = G[:k * s], G[k * s:]
@@ -269,14 +298,14 @@ class BMGS_CWY(_Arnoldi):
         k, s = self.k, self.s
         W = self._matvec(self.U)
         if k == 1:
-            H11 = inner(self.U, W)
+            H11 = self.ip(self.U, W)
             self._sync()
             self._record(H11)
             self.set_Hb(1, 1, H11)
             self.U = W - self.V[0] @ H11
             return ("none", 0)
         Vkm1 = self.basis(k - 1)
-        G = inner(np.hstack([Vkm1, self.U]), np.hstack([self.U, W]))
+        G = self.ip(np.hstack([Vkm1, self.U]), np.hstack([self.U, W]))
         self._sync()
         self._record(G)
         Y, Z = G[:(k - 1) * s, :s], G[:(k - 1) * s, s:]
@@ -318,7 +347,7 @@ class BCGSI_LS(_Arnoldi):
         k, s = self.k, self.s
         W = self._matvec(self.U)
         if k == 1:
-            J = inner(self.U, W)
+            J = self.ip(self.U, W)
             self._sync()
             self._record(J)
             self.J = J
@@ -326,7 +355,7 @@ class BCGSI_LS(_Arnoldi):
             self.U = W - self.V[0] @ J
             return ("none", 0)
         Vkm1 = self.basis(k - 1)
-        G = inner(np.hstack([Vkm1, self.U]), np.hstack([self.U, W]))
+        G = self.ip(np.hstack([Vkm1, self.U]), np.hstack([self.U, W]))
         self._sync()
         self._record(G)
         Y, Z = G[:(k - 1) * s, :s], G[:(k - 1) * s, s:]
@@ -353,14 +382,15 @@ _VAPPS = {"bmgs": (2, 0), "bcgs": (2, 0), "bcgs_pip": (3, 0),
           "bmgs_cwy": (3, 1), "bmgs_icwy": (3, 1), "bcgsi_ls": (4, 1)}
 
 
-def arnoldi(A, B: np.ndarray, m: int, skeleton: str):
+def arnoldi(A, B: np.ndarray, m: int, skeleton: str, inner_product: str = "classical"):
     """m steps of a block Arnoldi skeleton from B (no restarts, no flags expected).
     Returns (V_{m+1} as n x (m+1)s, H_{m+1,m}, Beta)."""
     counts = {"a_calls": 0, "syncs": 0}
-    V1, Beta, flag = cholqr(B)
+    ip = block_inner_product(inner_product, B.shape[1])
+    V1, Beta, flag = cholqr(B, ip)
     if flag:
         raise FloatingPointError("CholQR of B flagged")
-    ar = _CLASSES[skeleton](A, V1, m, counts, None)
+    ar = _CLASSES[skeleton](A, V1, m, counts, None, ip=ip)
     j = 0
     while j < m:
         kind, jj = ar.advance()
@@ -433,7 +463,8 @@ class Result:
 def solve(A, B: np.ndarray, m: int, tol: float, skeleton: str = "bcgsi_ls",
           modification: str = "gmres", max_restarts: int = 50, adaptive: bool = True,
           verify_true_residual: bool = True, inject_flags=(), record_first_cycle: bool = False,
-          true_residual_each_cycle: bool = False, X_star: np.ndarray | None = None) -> Result:
+          true_residual_each_cycle: bool = False, X_star: np.ndarray | None = None,
+          inner_product: str = "classical") -> Result:
     """Restarted, adaptively restarted modified BFOM (BFOM or BGMRES) for A X = B
     with the given block Arnoldi skeleton; X_0 = 0.
 
@@ -444,6 +475,7 @@ def solve(A, B: np.ndarray, m: int, tol: float, skeleton: str = "bcgsi_ls",
         raise ValueError(skeleton)
     B = np.asarray(B, dtype=np.float64)
     n, s = B.shape
+    ip = block_inner_product(inner_product, s)
     normB = np.linalg.norm(B)
     X = np.zeros((n, s))
     C = np.eye(s)
@@ -460,13 +492,13 @@ def solve(A, B: np.ndarray, m: int, tol: float, skeleton: str = "bcgsi_ls",
             res.status = NOT_CONVERGED
             break
         counts["syncs"] += 1
-        V1, Beta, flag = cholqr(R_start)
+        V1, Beta, flag = cholqr(R_start, ip)
         if flag:
             res.status = BREAKDOWN if cycle == 1 else NOT_CONVERGED
             res.cycles = cycle
             break
         grams = [] if (record_first_cycle and cycle == 1) else None
-        ar = _CLASSES[skeleton](A, V1, m_cur, counts, grams)
+        ar = _CLASSES[skeleton](A, V1, m_cur, counts, grams, ip=ip)
         res.m_cur.append(m_cur)
         j, converged, flagged = 0, False, 0
         coeffs = None

@@ -372,3 +372,62 @@ def test_low_sync_corrections_on_the_paper_tridiag():
     assert O.arnoldi_residual(A, V, H, 30, 2) <= 3.5e-16 * np.linalg.norm(H)
     V, H, _ = O.arnoldi(A, B, 20, "bmgs_icwy")
     assert O.loss_of_orthogonality(V) < 1e-4
+
+
+# ------------------------------------------------------------------ global inner product
+
+def _kron_identity(A, s):
+    """I_s (x) A in CSR: the operator of the vectorized block system."""
+    rows, cols, vals = [], [], []
+    D = A.to_dense()
+    r, c = np.nonzero(D)
+    for b in range(s):
+        rows.append(r + b * A.n)
+        cols.append(c + b * A.n)
+        vals.append(D[r, c])
+    return W._from_coo(A.n * s, np.concatenate(rows), np.concatenate(cols), np.concatenate(vals))
+
+
+def test_global_inner_product_definition():
+    """Table 1: block (i, j) of <X, Y> is tr(X_i^T Y_j)/s I_s; for s = 1 it is
+    the classical product; the global scaling quotient is ||X||_F/sqrt(s) I_s."""
+    rng = np.random.default_rng(7)
+    s = 3
+    X, Y = rng.standard_normal((40, 2 * s)), rng.standard_normal((40, 3 * s))
+    G = O.global_inner(s)(X, Y)
+    for i in range(2):
+        for j in range(3):
+            t = np.trace(X[:, i * s:(i + 1) * s].T @ Y[:, j * s:(j + 1) * s]) / s
+            assert np.allclose(G[i * s:(i + 1) * s, j * s:(j + 1) * s], t * np.eye(s), atol=1e-13)
+    x, y = rng.standard_normal((40, 4)), rng.standard_normal((40, 4))
+    assert np.allclose(O.global_inner(1)(x, y), x.T @ y, atol=1e-13)
+    Q, R, flag = O.cholqr(X[:, :s], O.global_inner(s))
+    assert not flag
+    assert np.allclose(R, np.linalg.norm(X[:, :s]) / np.sqrt(s) * np.eye(s), rtol=1e-14)
+    assert np.isclose(np.linalg.norm(Q), np.sqrt(s), rtol=1e-14)
+
+
+@pytest.mark.parametrize("sk", O.SKELETONS)
+def test_global_method_is_the_vectorized_single_vector_method(sk):
+    """Under the global inner product a block method on (A, B) is the s = 1
+    method on (I_s (x) A, vec B) (the global product is the Euclidean product of
+    the vectorized blocks, divided by s): same restart log and steps, the same X,
+    and H = h (x) I_s with h the single-vector Hessenberg matrix."""
+    A = W.laplacian_2d(12, 11)
+    s = 3
+    B = W.gaussian_block(A.n, s, 5)
+    K = _kron_identity(A, s)
+    b = B.T.reshape(-1, 1).copy()
+    g = O.solve(A, B, 6, 1e-10, sk, inner_product="global", max_restarts=400)
+    c = O.solve(K, b, 6, 1e-10, sk, max_restarts=400)
+    assert g.status == c.status == O.OK
+    assert g.cycle_m == c.cycle_m and g.steps == c.steps
+    Xc = c.X.reshape(s, A.n).T
+    assert np.linalg.norm(g.X - Xc) <= 1e-12 * np.linalg.norm(Xc)
+    V, H, Beta = O.arnoldi(A, B, 5, sk, inner_product="global")
+    v, h, beta = O.arnoldi(K, b, 5, sk)
+    assert np.allclose(H, np.kron(h, np.eye(s)), rtol=0, atol=1e-12 * np.abs(h).max())
+    assert np.allclose(Beta, beta[0, 0] / np.sqrt(s) * np.eye(s), rtol=1e-14)
+    # global block orthonormality: tr(V_i^T V_j)/s = delta_ij
+    Gv = O.global_inner(s)(V, V)
+    assert np.allclose(Gv, np.eye(6 * s), atol=1e-12)

@@ -38,6 +38,12 @@ MUTATIONS = {
                    "R[j, c] = (G[c, j] * 1.0000001 - np.dot(R[:j, j], R[:j, c])) / R[j, j]"),
     # adaptive restart keeps the flagged relation (Sec. 4)
     "restart_off_by_one": ("m_cur = flagged - 1", "m_cur = flagged"),
+    # global inner product without the 1/s of Table 1
+    "global_no_scale": ("t = np.sum(X[:, i * s:(i + 1) * s] * Y[:, j * s:(j + 1) * s]) / s",
+                        "t = np.sum(X[:, i * s:(i + 1) * s] * Y[:, j * s:(j + 1) * s])"),
+    # global inner product summing every entry product of the two blocks (not the trace)
+    "global_all_pairs": ("t = np.sum(X[:, i * s:(i + 1) * s] * Y[:, j * s:(j + 1) * s]) / s",
+                         "t = np.sum(X[:, i * s:(i + 1) * s].T @ Y[:, j * s:(j + 1) * s]) / s"),
 }
 
 
@@ -100,6 +106,18 @@ def _pins_pass(O):
             return False
         r = O.solve(A, B, 8, 1e-9, "bcgs_pip", inject_flags=[(1, 5)])
         if r.cycle_m[0] != 4 or any(mc != 4 for mc in r.m_cur[1:]):
+            return False
+        # Global inner product: the block method is the single-vector method on
+        # (I_s (x) A, vec B) (Table 1).
+        Ag = W.laplacian_2d(9, 8)
+        Bg = W.gaussian_block(Ag.n, 2, 5)
+        D = Ag.to_dense()
+        r_, c_ = np.nonzero(D)
+        K = W._from_coo(2 * Ag.n, np.concatenate([r_, r_ + Ag.n]), np.concatenate([c_, c_ + Ag.n]),
+                        np.concatenate([D[r_, c_], D[r_, c_]]))
+        g = O.solve(Ag, Bg, 5, 1e-10, "bcgsi_ls", inner_product="global", max_restarts=300)
+        c = O.solve(K, Bg.T.reshape(-1, 1).copy(), 5, 1e-10, "bcgsi_ls", max_restarts=300)
+        if g.steps != c.steps or np.linalg.norm(g.X - c.X.reshape(2, Ag.n).T) > 1e-12 * np.linalg.norm(g.X):
             return False
         return True
     except Exception:
