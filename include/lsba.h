@@ -115,10 +115,18 @@ typedef struct {
                                     it (exact digit products, 48-bit accuracy); 2:
                                     every pass whose shape it allows; 0: FP32-pipe
                                     kernels only.                                      */
-  int32_t reserved[2];
+  int32_t inner_product;         /* block inner product (Sec. 2.2, Table 1):
+                                    LSBA_IP_CLASSICAL (default): <X, Y> = X^T Y, muscle
+                                    CholQR; LSBA_IP_GLOBAL: <X, Y> = tr(X^T Y)/s I_s,
+                                    muscle the global scaling quotient ||X||_F/sqrt(s)
+                                    I_s.  Every skeleton takes either; the Gram passes
+                                    are the same, and each s x s block of their result
+                                    is replaced by its trace / s times I_s.            */
+  int32_t reserved[1];
 } lsba_options;
 
 enum { LSBA_PREC_FP64 = 0, LSBA_PREC_DF = 1, LSBA_PREC_AUTO = 2, LSBA_PREC_FP32_IR = 3 };
+enum { LSBA_IP_CLASSICAL = 0, LSBA_IP_GLOBAL = 1 };
 
 /* Counters and outcome of the last lsba_solve. */
 typedef struct {

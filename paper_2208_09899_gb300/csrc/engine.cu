@@ -99,7 +99,7 @@ struct CycleKey {
   const void* a_lowprec;
   const double* rstart;
   int64_t n;
-  int s, m_cur, start_flags, skel, modification, mode, tensor_cores;
+  int s, m_cur, start_flags, skel, modification, mode, tensor_cores, global_ip;
   uint64_t ws_gen;
   bool operator==(const CycleKey& o) const { return memcmp(this, &o, sizeof(*this)) == 0; }
 };
@@ -805,6 +805,7 @@ static int run_cycle_body(lsba_handle h, const lsba_csr* A, const double* Rstart
     key.modification = h->ws.modification;
     key.mode = h->mode;
     key.tensor_cores = h->opt.tensor_cores;
+    key.global_ip = h->ws.global_ip;
     key.ws_gen = h->ws_gen;
     for (auto& e : h->graphs)
       if (e.key == key) g = &e;
@@ -1019,7 +1020,8 @@ static int solve_impl(lsba_handle h, const lsba_csr* A, const double* d_B, doubl
   if (!A || !d_B || !d_X || skel < 0 || s < 1 || s > LSBA_MAX_S || m < 1 ||
       (int64_t)(m + 1) * s > LSBA_MAX_MS || m + 3 > LSBA_MAXB || A->n < 1 || A->nnz < 0 ||
       A->nnz >= (int64_t)1 << 31 || !A->d_rowptr || (A->nnz > 0 && (!A->d_colidx || !A->d_vals)) ||
-      !(tol >= 0.0) || h->opt.max_restarts < 0)
+      !(tol >= 0.0) || h->opt.max_restarts < 0 ||
+      (h->opt.inner_product != LSBA_IP_CLASSICAL && h->opt.inner_product != LSBA_IP_GLOBAL))
     return h->stats.status = LSBA_INVALID_ARG;
   const int64_t n = A->n;
   CK(cudaSetDevice(h->device));
@@ -1028,6 +1030,7 @@ static int solve_impl(lsba_handle h, const lsba_csr* A, const double* d_B, doubl
   SmallWs& w = h->ws;
   w.skel = skel;
   w.modification = h->opt.modification == LSBA_FOM ? 0 : 1;
+  w.global_ip = h->opt.inner_product == LSBA_IP_GLOBAL ? 1 : 0;
   cudaStream_t st = h->stream;
   const size_t blk = (size_t)n * s;
   // Working precision of the SpMM / Gram / update passes.

@@ -570,6 +570,25 @@ __device__ __forceinline__ bool injected(const SmallWs& w, int relation) {
 
 // ---------------------------------------------------------------- cycle start
 // flags: bit 0 = first cycle (compute ||B||_F from the Gram), bit 1 = reset C = I.
+// Global block inner product (Table 1): the Gram passes compute the classical
+// products of the blocks; each s x s block of the reduced result (a x b blocks,
+// row-major) becomes tr(block)/s I_s before anything reads it.  Every later
+// small-matrix operation then stays in the span of I_s (chol(t I) = sqrt(t) I,
+// products and solves of such blocks), which is the global method.
+__device__ void project_global(const SmallWs& w, int a, int b) {
+  double* G = const_cast<double*>(w.G);
+  const int s = w.s, cols = b * s;
+  for (int blk = threadIdx.x; blk < a * b; blk += NT) {
+    double* g = G + (size_t)(blk / b) * s * cols + (size_t)(blk % b) * s;
+    double t = 0.0;
+    for (int i = 0; i < s; ++i) t += g[(size_t)i * cols + i];
+    t /= s;
+    for (int i = 0; i < s; ++i)
+      for (int c = 0; c < s; ++c) g[(size_t)i * cols + c] = i == c ? t : 0.0;
+  }
+  __syncthreads();
+}
+
 __global__ void __launch_bounds__(NT) k_small_start(SmallWs w, int flags) {
   const int first_cycle = flags & 1;
   __shared__ Shared sh;
@@ -577,6 +596,7 @@ __global__ void __launch_bounds__(NT) k_small_start(SmallWs w, int flags) {
   Ctl* ctl = w.ctl;
   // G = R_start^T R_start (s x s row-major == col-major since symmetric in exact
   // arithmetic; the upper triangle read as G[a*s + c], a <= c).
+  if (w.global_ip) project_global(w, 1, 1);
   int flag = cta_chol(w.G, s, s, sh.R, &sh.flag);
   if (first_cycle) {
     if (threadIdx.x == 0) {
@@ -898,6 +918,14 @@ __global__ void __launch_bounds__(NT) k_small_step(SmallWs w, int k, int phase) 
     w.ctl->k = k;
   }
   __syncthreads();
+  if (w.global_ip) {
+    // block shape of this step's Gram
+    int a = 1, b = 1;
+    if (w.skel == SK_PIP) a = k + 1;
+    else if (w.skel == SK_BCGS && phase == 0) a = k;
+    else if ((w.skel == SK_LS || w.skel == SK_ICWY || w.skel == SK_CWY) && k >= 2) a = k, b = 2;
+    project_global(w, a, b);
+  }
   switch (w.skel) {
     case SK_PIP: step_pip(w, k, sh); break;
     case SK_BCGS: step_bcgs(w, k, phase, sh); break;

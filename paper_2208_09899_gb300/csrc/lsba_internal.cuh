@@ -69,6 +69,7 @@ struct BlockPtrs {
 // Device workspace of the small kernels (all device pointers).
 struct SmallWs {
   int s, m, skel, modification;
+  int global_ip;       // 1: global block inner product (each s x s Gram block -> tr/s I)
   int ldH;             // (m+2)*s
   int ldT;             // (m+2)*s
   int ldR;             // (m+1)*s

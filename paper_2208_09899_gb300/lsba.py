@@ -21,6 +21,7 @@ LSBA_OUT_OF_MEMORY, LSBA_CUDA_ERROR, LSBA_DEVICE_TIMEOUT = 4, 5, 6
 SKELETONS = {"bcgs": 0, "bcgs_pip": 1, "bcgsi_ls": 2, "bmgs_icwy": 3, "bmgs_cwy": 4, "bmgs": 5}
 MODIFICATIONS = {"fom": 0, "gmres": 1}
 PRECISIONS = {"fp64": 0, "df": 1, "auto": 2, "fp32_ir": 3}
+INNER_PRODUCTS = {"classical": 0, "global": 1}
 
 EXPORTED = ("lsba_default_options", "lsba_create", "lsba_set_options", "lsba_solve",
             "lsba_solve_host", "lsba_get_stats", "lsba_get_history", "lsba_status_string",
@@ -37,7 +38,8 @@ class Options(C.Structure):
                 ("inject_flag_relation", C.c_int32), ("profile", C.c_int32),
                 ("precision", C.c_int32), ("ir_max_outer", C.c_int32),
                 ("ir_inner_tol", C.c_double), ("cuda_graphs", C.c_int32),
-                ("tensor_cores", C.c_int32), ("reserved", C.c_int32 * 2)]
+                ("tensor_cores", C.c_int32), ("inner_product", C.c_int32),
+                ("reserved", C.c_int32 * 1)]
 
 
 class Stats(C.Structure):
@@ -205,6 +207,8 @@ class Solver:
                 v = MODIFICATIONS[v]
             if k == "precision" and isinstance(v, str):
                 v = PRECISIONS[v]
+            if k == "inner_product" and isinstance(v, str):
+                v = INNER_PRODUCTS[v]
             if isinstance(v, bool):
                 v = int(v)
             setattr(self.opt, k, v)

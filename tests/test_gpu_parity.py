@@ -166,7 +166,8 @@ def _compare_solve(lsba, A, B, m, tol, sk, mod, max_restarts=50, first_cycle_tol
     ref = O.solve(A, B, m, tol, sk, modification=mod, max_restarts=max_restarts,
                   record_first_cycle=True, inject_flags=inject,
                   adaptive=bool(kw.get("adaptive_restart", 1)),
-                  verify_true_residual=bool(kw.get("verify_true_residual", 1)))
+                  verify_true_residual=bool(kw.get("verify_true_residual", 1)),
+                  inner_product=kw.get("inner_product", "classical"))
     # Same restart decisions.
     assert hist["cycle_m"] == ref.cycle_m, (hist["cycle_m"], ref.cycle_m)
     assert hist["cycle_flag"] == ref.cycle_flag
@@ -231,6 +232,24 @@ def test_all_skeletons_laplacian(env, sk, mod, precision):
     A = W.laplacian_2d(40, 37)
     B = W.gaussian_block(A.n, 4, 3)
     _compare_solve(lsba, A, B, 8, 1e-10, sk, mod, max_restarts=200, precision=precision)
+
+
+@pytest.mark.parametrize("precision", ["df", "fp64"])
+@pytest.mark.parametrize("sk", ["bcgs", "bcgs_pip", "bcgsi_ls", "bmgs_icwy", "bmgs_cwy", "bmgs"])
+def test_global_inner_product(env, sk, precision):
+    """Global block inner product (Table 1) on every skeleton: the same restart
+    log, counters, first-cycle Grams and Hessenberg (whose s x s blocks are
+    multiples of I_s) and X as the oracle's global method."""
+    torch, lsba = env
+    A = W.laplacian_2d(40, 37)
+    B = W.gaussian_block(A.n, 4, 3)
+    X, st, hist, ref = _compare_solve(lsba, A, B, 8, 1e-10, sk, "gmres", max_restarts=300,
+                                      precision=precision, inner_product="global")
+    H = hist["first_H"]
+    s = 4
+    for c in range(ref.first_cycle["j"]):
+        blk = H[c * s:(c + 1) * s, c * s:(c + 1) * s]
+        assert np.allclose(blk, blk[0, 0] * np.eye(s), rtol=0, atol=1e-14 * abs(blk[0, 0]))
 
 
 @pytest.mark.parametrize("s", [1, 3, 5, 16])
