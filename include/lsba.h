@@ -55,7 +55,8 @@ typedef enum {
   LSBA_BCGSI_LS = 2,        /* Alg. 7, 1 sync per step, lagged normalization  */
   LSBA_BMGS_ICWY = 3,       /* Alg. 6 (inverse compact WY branch)             */
   LSBA_BMGS_CWY = 4,        /* Alg. 6 (compact WY branch)                     */
-  LSBA_BMGS = 5             /* Alg. 2, k + 1 syncs in step k (the comparator)  */
+  LSBA_BMGS = 5,            /* Alg. 2, k + 1 syncs in step k (the comparator)  */
+  LSBA_BCGS_PIO = 6         /* Alg. 4, 2 syncs per step (muscle CholQR)        */
 } lsba_skeleton;
 
 /* Low-rank modification of BFOM (Sec. 2.4.1, Eq. (7)). */

@@ -14,7 +14,8 @@ with low-synchronization skeletons", arXiv 2208.09899):
 * Muscle CholQR: R = chol(X^T X), Q = X R^{-1} (Sec. 2.3; the muscle list of Sec. 5).
 * Skeletons, each written from its algorithm in the paper's order:
   BMGS-Arnoldi (Alg. 2), BCGS (the condensed loop of Sec. 3.1),
-  BCGS-PIP-Arnoldi (Alg. 3), BMGS-CWY / BMGS-ICWY-Arnoldi (Alg. 6, both branches),
+  BCGS-PIP-Arnoldi (Alg. 3), BCGS-PIO-Arnoldi (Alg. 4, reading R12),
+  BMGS-CWY / BMGS-ICWY-Arnoldi (Alg. 6, both branches),
   BCGSI+LS-Arnoldi (Alg. 7).
 * Modified BFOM  X_m = V_m (H_m + M)^{-1} E_1 B  (Eq. (7)); M = 0 gives BFOM,
   M = H_m^{-T} E_m H_{m+1,m}^T H_{m+1,m} E_m^T gives BGMRES (Sec. 2.4.1).
@@ -57,6 +58,13 @@ design notes of the repository):
       "reach a specified error tolerance"); ``X_star`` selects that stopping
       test instead of the residual estimate (used only to compare with the
       paper's tables).
+  R12 Alg. 4 (BCGS-PIO) with the CholQR muscle: the muscle's R factor of
+      [W 0; 0 H_{1:k,k}] is block diagonal, diag(chol(<W, W>), chol(H^T H))
+      (the Cholesky factor of a block-diagonal Gram), so H_{k+1,k} =
+      chol(R_W^T R_W - R_H^T R_H); a flag of either muscle factor is a flag
+      of the step.  Two syncs per step (the inner product and the muscle's
+      <W, W>); V-applications as for PIP (3 per step).  Under the global inner
+      product the muscle acts on W with the global scaling quotient.
 """
 from __future__ import annotations
 
@@ -65,7 +73,7 @@ from dataclasses import dataclass, field
 import numpy as np
 import scipy.sparse
 
-SKELETONS = ("bmgs", "bcgs", "bcgs_pip", "bmgs_cwy", "bmgs_icwy", "bcgsi_ls")
+SKELETONS = ("bmgs", "bcgs", "bcgs_pip", "bcgs_pio", "bmgs_cwy", "bmgs_icwy", "bcgsi_ls")
 LAGGED = ("bmgs_cwy", "bmgs_icwy", "bcgsi_ls")
 
 OK, NOT_CONVERGED, BREAKDOWN = 0, 1, 2
@@ -284,6 +292,33 @@ class BCGS_PIP(_Arnoldi):
         return ("rel", k)
 
 
+class BCGS_PIO(_Arnoldi):
+    """BCGS-PIO-Arnoldi, Alg. 4, with the CholQR muscle (reading R12)."""
+
+    def advance(self, force_flag=False):
+        self.k += 1
+        k = self.k
+        W = self._matvec(self.V[k - 1])
+        Vk = self.basis(k)
+        Hc = self.ip(Vk, W)
+        self._sync()
+        self._record(Hc)
+        # The muscle on [W 0; 0 H_{1:k,k}]: its Gram is block diagonal, and so
+        # is its Cholesky factor.
+        RW, flag_w = chol_flag(self.ip(W, W))
+        self._sync()
+        RH, flag_h = chol_flag(Hc.T @ Hc)
+        if flag_w or flag_h or force_flag:
+            return ("flag", k)
+        R, flag = chol_flag(RW.T @ RW - RH.T @ RH)
+        if flag:
+            return ("flag", k)
+        self.set_Hcol(1, k, k, Hc)
+        self.set_Hb(k + 1, k, R)
+        self.V.append(right_solve_upper(W - Vk @ Hc, R))
+        return ("rel", k)
+
+
 class BMGS_CWY(_Arnoldi):
     """BMGS-CWY (red) / BMGS-ICWY (blue) Arnoldi, Alg. 6 (readings R3, R5)."""
     inverse = False
@@ -375,10 +410,10 @@ class BCGSI_LS(_Arnoldi):
         return ("rel", k - 1)
 
 
-_CLASSES = {"bmgs": BMGS, "bcgs": BCGS, "bcgs_pip": BCGS_PIP,
+_CLASSES = {"bmgs": BMGS, "bcgs": BCGS, "bcgs_pip": BCGS_PIP, "bcgs_pio": BCGS_PIO,
             "bmgs_cwy": BMGS_CWY, "bmgs_icwy": BMGS_ICWY, "bcgsi_ls": BCGSI_LS}
 
-_VAPPS = {"bmgs": (2, 0), "bcgs": (2, 0), "bcgs_pip": (3, 0),
+_VAPPS = {"bmgs": (2, 0), "bcgs": (2, 0), "bcgs_pip": (3, 0), "bcgs_pio": (3, 0),
           "bmgs_cwy": (3, 1), "bmgs_icwy": (3, 1), "bcgsi_ls": (4, 1)}
 
 

@@ -437,7 +437,7 @@ static int pull_ctl(lsba_ctx* h) {
     prof_end(h);            \
   } while (0)
 
-enum { SK_BCGS = 0, SK_PIP = 1, SK_LS = 2, SK_ICWY = 3, SK_CWY = 4, SK_BMGS = 5 };
+enum { SK_BCGS = 0, SK_PIP = 1, SK_LS = 2, SK_ICWY = 3, SK_CWY = 4, SK_BMGS = 5, SK_PIO = 6 };
 static bool lagged(int skel) { return skel == SK_LS || skel == SK_ICWY || skel == SK_CWY; }
 
 // Precision dispatch of the three bandwidth-shaped passes (profiled).  In the
@@ -566,7 +566,7 @@ static void enqueue_cycle(lsba_ctx* h, const lsba_csr* A, const double* Rstart, 
       enqueue_side(h, k);
       do_update(h, R, 1, n, s, h->basis + (size_t)k * blk, w.coef1, w.tri1, nullptr, nullptr,
                 nullptr, nullptr, ctl, k);
-    } else if (skel == SK_PIP || skel == SK_BCGS) {
+    } else if (skel == SK_PIP || skel == SK_PIO || skel == SK_BCGS) {
       const double* Vk = h->basis + (size_t)(k - 1) * blk;
       do_spmm(h, A, Vk, h->Wb, s, ctl, 1);
       BlockPtrs L = basis_list(h, n, s, k);
@@ -576,7 +576,8 @@ static void enqueue_cycle(lsba_ctx* h, const lsba_csr* A, const double* Rstart, 
       BlockPtrs in = basis_list(h, n, s, k);
       in.p[k] = h->Wb;
       double* Vnext = h->basis + (size_t)k * blk;
-      if (skel == SK_PIP) {
+      if (skel == SK_PIP || skel == SK_PIO) {
+        // one fused Gram [V_k W]^T W (for PIO it also gives the muscle's <W, W>)
         L.p[k] = h->Wb;
         do_gram(h, L, k + 1, R, 1, n, s, ctl, 1);
         wait_side(h, k - 1);
@@ -775,6 +776,7 @@ static int skel_code(lsba_skeleton s) {
     case LSBA_BMGS_ICWY: return SK_ICWY;
     case LSBA_BMGS_CWY: return SK_CWY;
     case LSBA_BMGS: return SK_BMGS;
+    case LSBA_BCGS_PIO: return SK_PIO;
     default: return -1;
   }
 }
@@ -866,7 +868,7 @@ static int run_cycles(lsba_handle h, const lsba_csr* A, const double* Bw, double
   cudaStream_t st = h->stream;
   Ctl* c = h->h_ctl;
   lsba_stats& S = h->stats;
-  const int vper = (skel == SK_LS) ? 4 : (skel == SK_PIP || lagged(skel)) ? 3 : 2;
+  const int vper = (skel == SK_LS) ? 4 : (skel == SK_PIP || skel == SK_PIO || lagged(skel)) ? 3 : 2;
   const int vcyc = lagged(skel) ? 1 : 0;
   int rc;
   CK(cudaMemsetAsync(Xw, 0, sizeof(double) * (size_t)n * s, st));
@@ -906,7 +908,7 @@ static int run_cycles(lsba_handle h, const lsba_csr* A, const double* Bw, double
     S.steps += j;
     const int a_calls = lagged(skel) ? j + 1 + f : j + f;
     S.a_calls += a_calls;
-    S.syncs += (skel == SK_BCGS)   ? 2 * a_calls
+    S.syncs += (skel == SK_BCGS || skel == SK_PIO) ? 2 * a_calls
                : (skel == SK_BMGS) ? a_calls * (a_calls + 3) / 2   // k + 1 in step k
                                    : a_calls;
     S.v_apps += vper * j + (j > 0 ? vcyc : 0);

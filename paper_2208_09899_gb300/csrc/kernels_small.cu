@@ -30,7 +30,7 @@ namespace lsba {
 #define NT LSBA_SMALL_THREADS
 #define NWARPS (NT / 32)
 
-enum { SK_BCGS = 0, SK_PIP = 1, SK_LS = 2, SK_ICWY = 3, SK_CWY = 4, SK_BMGS = 5 };
+enum { SK_BCGS = 0, SK_PIP = 1, SK_LS = 2, SK_ICWY = 3, SK_CWY = 4, SK_BMGS = 5, SK_PIO = 6 };
 
 __device__ __forceinline__ double warp_sum(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -631,8 +631,12 @@ __global__ void __launch_bounds__(NT) k_small_start(SmallWs w, int flags) {
 }
 
 // ---------------------------------------------------------------- one step
+// The end of a PIP / PIO step once R = H_{k+1,k} is in sh.R: store H_{1:k+1,k}
+// and the coefficients of V_{k+1} = (W - V_k Hc) R^{-1} (inputs [V_1..V_k, W]).
+__device__ void pip_finish(const SmallWs& w, int k, Shared& sh);
+
 __device__ void step_pip(const SmallWs& w, int k, Shared& sh) {
-  const int s = w.s, ks = k * s, ldH = w.ldH;
+  const int s = w.s, ks = k * s;
   const double* G = w.G;  // ((k+1)s x s) row-major: element (i, c) at G[i*s + c]
   record_gram(w, G, (k + 1) * s, s);
   // S = Omega - Hc^T Hc ; Hc(i,c) = G[i*s+c] is, as a col-major matrix, Hc^T with ld s.
@@ -647,6 +651,45 @@ __device__ void step_pip(const SmallWs& w, int k, Shared& sh) {
     flag_exit(w, k);
     return;
   }
+  pip_finish(w, k, sh);
+}
+
+// BCGS-PIO (Alg. 4) with the CholQR muscle: the muscle's factor of
+// [W 0; 0 Hc] is diag(R_W, R_H), R_W = chol(W^T W) (the Omega block of the
+// fused Gram), R_H = chol(Hc^T Hc); then H_{k+1,k} = chol(R_W^T R_W - R_H^T R_H).
+__device__ void step_pio(const SmallWs& w, int k, Shared& sh) {
+  const int s = w.s, ks = k * s;
+  const double* G = w.G;
+  record_gram(w, G, ks, s);   // the inner product <V_k, W>; <W, W> is the muscle's
+  cta_gemm_s(s, s, ks, 1.0, G, s, false, G, s, true, 0.0, sh.A, s);
+  __syncthreads();
+  const int flag_h = cta_chol(sh.A, s, s, sh.R, &sh.flag);
+  for (int e = threadIdx.x; e < s * s; e += NT) {
+    const int a = e % s, c = e / s;
+    sh.B[e] = sh.R[e];
+    sh.A[a + c * s] = G[(ks + a) * s + c];
+  }
+  __syncthreads();
+  const int flag_w = cta_chol(sh.A, s, s, sh.R, &sh.flag);
+  if (flag_w || flag_h || injected(w, k)) {
+    flag_exit(w, k);
+    return;
+  }
+  cta_gemm_s(s, s, s, 1.0, sh.R, s, true, sh.R, s, false, 0.0, sh.A, s);
+  __syncthreads();
+  cta_gemm_s(s, s, s, -1.0, sh.B, s, true, sh.B, s, false, 1.0, sh.A, s);
+  __syncthreads();
+  const int flag = cta_chol(sh.A, s, s, sh.R, &sh.flag);
+  if (flag) {
+    flag_exit(w, k);
+    return;
+  }
+  pip_finish(w, k, sh);
+}
+
+__device__ void pip_finish(const SmallWs& w, int k, Shared& sh) {
+  const int s = w.s, ks = k * s, ldH = w.ldH;
+  const double* G = w.G;
   double* Hk = w.H + (size_t)(k - 1) * s * ldH;
   for (int e = threadIdx.x; e < ks * s; e += NT) {
     const int i = e % ks, c = e / ks;
@@ -921,7 +964,7 @@ __global__ void __launch_bounds__(NT) k_small_step(SmallWs w, int k, int phase) 
   if (w.global_ip) {
     // block shape of this step's Gram
     int a = 1, b = 1;
-    if (w.skel == SK_PIP) a = k + 1;
+    if (w.skel == SK_PIP || w.skel == SK_PIO) a = k + 1;
     else if (w.skel == SK_BCGS && phase == 0) a = k;
     else if ((w.skel == SK_LS || w.skel == SK_ICWY || w.skel == SK_CWY) && k >= 2) a = k, b = 2;
     project_global(w, a, b);
@@ -930,6 +973,7 @@ __global__ void __launch_bounds__(NT) k_small_step(SmallWs w, int k, int phase) 
     case SK_PIP: step_pip(w, k, sh); break;
     case SK_BCGS: step_bcgs(w, k, phase, sh); break;
     case SK_BMGS: step_bmgs(w, k, phase, sh); break;
+    case SK_PIO: step_pio(w, k, sh); break;
     case SK_ICWY:
     case SK_CWY:
       if (k == 1) step_lagged_first(w, sh);

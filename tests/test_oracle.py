@@ -105,7 +105,7 @@ def test_arnoldi_relation_and_orthogonality(sk):
     eps = np.finfo(float).eps
     kappa = np.linalg.cond(np.hstack([B, A.to_dense() @ V[:, :m * s]]))
     loo = O.loss_of_orthogonality(V)
-    if sk in ("bcgs_pip", "bcgs"):
+    if sk in ("bcgs_pip", "bcgs_pio", "bcgs"):
         if eps * kappa ** 2 < 1:
             assert loo <= 100 * eps * kappa ** 2
     else:
@@ -120,7 +120,7 @@ def test_arnoldi_relation_and_orthogonality(sk):
     # Few steps, better-conditioned [B, A V]: orthogonal to O(eps) (O(eps) kappa^2
     # for the Pythagorean/classical skeletons).
     V4, _, _ = O.arnoldi(A, B, 3, sk)
-    assert O.loss_of_orthogonality(V4) < (1e-10 if sk in ("bcgs_pip", "bcgs") else 1e-13)
+    assert O.loss_of_orthogonality(V4) < (1e-10 if sk in ("bcgs_pip", "bcgs_pio", "bcgs") else 1e-13)
 
 
 @pytest.mark.parametrize("sk", [k for k in O.SKELETONS if k != "bmgs"])
@@ -283,7 +283,7 @@ def test_counter_identities(sk):
     js = r.cycle_m
     lag = sk in O.LAGGED
     syn = {"bmgs": lambda j: 1 + j * (j + 1) // 2 + j, "bcgs": lambda j: 1 + 2 * j,
-           "bcgs_pip": lambda j: 1 + j}.get(sk, lambda j: 1 + j + 1)
+           "bcgs_pip": lambda j: 1 + j, "bcgs_pio": lambda j: 1 + 2 * j}.get(sk, lambda j: 1 + j + 1)
     assert r.syncs == sum(syn(j) for j in js)
     assert r.a_calls == sum(j + (1 if lag else 0) for j in js)
     assert r.steps == sum(js)

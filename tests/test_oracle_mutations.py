@@ -38,6 +38,10 @@ MUTATIONS = {
                    "R[j, c] = (G[c, j] * 1.0000001 - np.dot(R[:j, j], R[:j, c])) / R[j, j]"),
     # adaptive restart keeps the flagged relation (Sec. 4)
     "restart_off_by_one": ("m_cur = flagged - 1", "m_cur = flagged"),
+    # sign of the Pythagorean correction in PIO (Alg. 4)
+    "pio_sign": ("R, flag = chol_flag(RW.T @ RW - RH.T @ RH)", "R, flag = chol_flag(RW.T @ RW + RH.T @ RH)"),
+    # PIO's muscle factor of H taken from H H^T's wrong side
+    "pio_HHt": ("RH, flag_h = chol_flag(Hc.T @ Hc)", "RH, flag_h = chol_flag(Hc[-Hc.shape[1]:] @ Hc[-Hc.shape[1]:].T)"),
     # global inner product without the 1/s of Table 1
     "global_no_scale": ("t = np.sum(X[:, i * s:(i + 1) * s] * Y[:, j * s:(j + 1) * s]) / s",
                         "t = np.sum(X[:, i * s:(i + 1) * s] * Y[:, j * s:(j + 1) * s])"),
@@ -88,7 +92,7 @@ def _pins_pass(O):
             V, H, Beta = O.arnoldi(A, B, 8, sk)
             if O.arnoldi_residual(A, V, H, 8, 3) > 1e-12 * np.linalg.norm(V):
                 return False
-            if O.loss_of_orthogonality(V) > (1e-6 if sk == "bcgs_pip" else 1e-10):
+            if O.loss_of_orthogonality(V) > (1e-6 if sk in ("bcgs_pip", "bcgs_pio") else 1e-10):
                 return False
             rhs = np.zeros((27, 3))
             rhs[:3] = Beta
