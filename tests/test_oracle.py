@@ -431,3 +431,19 @@ def test_global_method_is_the_vectorized_single_vector_method(sk):
     # global block orthonormality: tr(V_i^T V_j)/s = delta_ij
     Gv = O.global_inner(s)(V, V)
     assert np.allclose(Gv, np.eye(6 * s), atol=1e-12)
+
+
+@pytest.mark.parametrize("sk", ["bmgs", "bmgs_cwy", "bmgs_icwy", "bcgsi_ls", "bcgs_pip"])
+def test_paper_tridiag_table_global_rows(sk):
+    """Appendix table for tridiag, global rows (gl-skeleton o gl-fom): the
+    global inner product with the global muscle reproduces the printed cycle,
+    iteration, A-call, V-application and sync counts exactly."""
+    g = json.load(open(GOLDEN))
+    row = g["global_rows"][sk]
+    A, B = W.paper_tridiag(1000)
+    Xs = np.linalg.solve(A.to_dense(), B)
+    r = O.solve(A, B, 70, 1e-10, sk, modification="fom", max_restarts=100,
+                verify_true_residual=False, X_star=Xs, inner_product="global")
+    assert r.status == O.OK
+    assert (r.cycles, r.steps, r.a_calls, r.v_apps, r.syncs) == \
+        (row["cycles"], row["iters"], row["A"], row["V"], row["sync"])
