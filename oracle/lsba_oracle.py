@@ -15,6 +15,7 @@ with low-synchronization skeletons", arXiv 2208.09899):
 * Skeletons, each written from its algorithm in the paper's order:
   BMGS-Arnoldi (Alg. 2), BCGS (the condensed loop of Sec. 3.1),
   BCGS-PIP-Arnoldi (Alg. 3), BCGS-PIO-Arnoldi (Alg. 4, reading R12),
+  BMGS-SVL / BMGS-LTS-Arnoldi (Alg. 5, both branches, reading R13),
   BMGS-CWY / BMGS-ICWY-Arnoldi (Alg. 6, both branches),
   BCGSI+LS-Arnoldi (Alg. 7).
 * Modified BFOM  X_m = V_m (H_m + M)^{-1} E_1 B  (Eq. (7)); M = 0 gives BFOM,
@@ -65,6 +66,12 @@ design notes of the repository):
       of the step.  Two syncs per step (the inner product and the muscle's
       <W, W>); V-applications as for PIP (3 per step).  Under the global inner
       product the muscle acts on W with the global scaling quotient.
+  R13 Alg. 5 (BMGS-SVL / BMGS-LTS) with a muscle whose T factor is I_s: CholQR
+      (classical) or the global scaling quotient (global), whose blocks are
+      orthonormal in the block inner product, so T_{k+1,k+1} = I_s and T stays
+      unit block upper triangular.  The paper pairs the classical variants
+      with the column muscles MGS-SVL / MGS-LTS, which are not built here.
+      Syncs: Y, the muscle and Z, three per step; V-applications 3 per step.
 """
 from __future__ import annotations
 
@@ -73,7 +80,8 @@ from dataclasses import dataclass, field
 import numpy as np
 import scipy.sparse
 
-SKELETONS = ("bmgs", "bcgs", "bcgs_pip", "bcgs_pio", "bmgs_cwy", "bmgs_icwy", "bcgsi_ls")
+SKELETONS = ("bmgs", "bcgs", "bcgs_pip", "bcgs_pio", "bmgs_svl", "bmgs_lts", "bmgs_cwy",
+             "bmgs_icwy", "bcgsi_ls")
 LAGGED = ("bmgs_cwy", "bmgs_icwy", "bcgsi_ls")
 
 OK, NOT_CONVERGED, BREAKDOWN = 0, 1, 2
@@ -319,6 +327,43 @@ class BCGS_PIO(_Arnoldi):
         return ("rel", k)
 
 
+class BMGS_SVL(_Arnoldi):
+    """BMGS-SVL-Arnoldi, Alg. 5 (red branch), reading R13."""
+    lts = False
+
+    def __init__(self, *args, **kw):
+        super().__init__(*args, **kw)
+        self.T = np.eye((self.m + 2) * self.s)      # T = I; T_{1,1} = I_s from the muscle
+
+    def advance(self, force_flag=False):
+        self.k += 1
+        k, s = self.k, self.s
+        W = self._matvec(self.V[k - 1])
+        Vk = self.basis(k)
+        Y = self.ip(Vk, W)
+        self._sync()
+        self._record(Y)
+        Tk = self.T[:k * s, :k * s]
+        Hc = unit_upper_T_solve(Tk, Y) if self.lts else Tk.T @ Y
+        self._sync()
+        Q, R, flag = cholqr(W - Vk @ Hc, self.ip)
+        if flag or force_flag:
+            return ("flag", k)
+        self.V.append(Q)
+        self.set_Hcol(1, k, k, Hc)
+        self.set_Hb(k + 1, k, R)
+        Z = self.ip(Vk, Q)
+        self._sync()
+        # T_{k+1,k+1} = I_s (the muscle's T factor)
+        self.T[:k * s, k * s:(k + 1) * s] = Z if self.lts else -Tk @ Z
+        return ("rel", k)
+
+
+class BMGS_LTS(BMGS_SVL):
+    """BMGS-LTS-Arnoldi, Alg. 5 (blue branch), reading R13."""
+    lts = True
+
+
 class BMGS_CWY(_Arnoldi):
     """BMGS-CWY (red) / BMGS-ICWY (blue) Arnoldi, Alg. 6 (readings R3, R5)."""
     inverse = False
@@ -411,9 +456,11 @@ class BCGSI_LS(_Arnoldi):
 
 
 _CLASSES = {"bmgs": BMGS, "bcgs": BCGS, "bcgs_pip": BCGS_PIP, "bcgs_pio": BCGS_PIO,
+            "bmgs_svl": BMGS_SVL, "bmgs_lts": BMGS_LTS,
             "bmgs_cwy": BMGS_CWY, "bmgs_icwy": BMGS_ICWY, "bcgsi_ls": BCGSI_LS}
 
 _VAPPS = {"bmgs": (2, 0), "bcgs": (2, 0), "bcgs_pip": (3, 0), "bcgs_pio": (3, 0),
+          "bmgs_svl": (3, 0), "bmgs_lts": (3, 0),
           "bmgs_cwy": (3, 1), "bmgs_icwy": (3, 1), "bcgsi_ls": (4, 1)}
 
 

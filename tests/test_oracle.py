@@ -283,7 +283,8 @@ def test_counter_identities(sk):
     js = r.cycle_m
     lag = sk in O.LAGGED
     syn = {"bmgs": lambda j: 1 + j * (j + 1) // 2 + j, "bcgs": lambda j: 1 + 2 * j,
-           "bcgs_pip": lambda j: 1 + j, "bcgs_pio": lambda j: 1 + 2 * j}.get(sk, lambda j: 1 + j + 1)
+           "bcgs_pip": lambda j: 1 + j, "bcgs_pio": lambda j: 1 + 2 * j,
+           "bmgs_svl": lambda j: 1 + 3 * j, "bmgs_lts": lambda j: 1 + 3 * j}.get(sk, lambda j: 1 + j + 1)
     assert r.syncs == sum(syn(j) for j in js)
     assert r.a_calls == sum(j + (1 if lag else 0) for j in js)
     assert r.steps == sum(js)
@@ -433,7 +434,8 @@ def test_global_method_is_the_vectorized_single_vector_method(sk):
     assert np.allclose(Gv, np.eye(6 * s), atol=1e-12)
 
 
-@pytest.mark.parametrize("sk", ["bmgs", "bmgs_cwy", "bmgs_icwy", "bcgsi_ls", "bcgs_pip"])
+@pytest.mark.parametrize("sk", ["bmgs", "bmgs_svl", "bmgs_lts", "bmgs_cwy", "bmgs_icwy", "bcgsi_ls",
+                                "bcgs_pip"])
 def test_paper_tridiag_table_global_rows(sk):
     """Appendix table for tridiag, global rows (gl-skeleton o gl-fom): the
     global inner product with the global muscle reproduces the printed cycle,
@@ -447,3 +449,29 @@ def test_paper_tridiag_table_global_rows(sk):
     assert r.status == O.OK
     assert (r.cycles, r.steps, r.a_calls, r.v_apps, r.syncs) == \
         (row["cycles"], row["iters"], row["A"], row["V"], row["sync"])
+
+
+@pytest.mark.parametrize("sk", ["bmgs_svl", "bmgs_lts"])
+def test_svl_lts_classical_rows_and_stability(sk):
+    """Alg. 5 with the CholQR muscle (reading R13).  The appendix table's
+    classical rows use the column muscles MGS-SVL / MGS-LTS; the skeleton still
+    takes 2 cycles and 96 +- 2 iterations with the table's identities
+    (A-calls = iterations, V = 3 x iterations).  Table 1: loss of
+    orthogonality O(eps) kappa, like BMGS, on the paper's tridiag (n = 100),
+    where BCGS has already lost orthogonality completely."""
+    g = json.load(open(GOLDEN))
+    row = g["classical_rows"][sk]
+    A, B = W.paper_tridiag(1000)
+    Xs = np.linalg.solve(A.to_dense(), B)
+    r = O.solve(A, B, 70, 1e-10, sk, modification="fom", max_restarts=100,
+                verify_true_residual=False, X_star=Xs)
+    assert r.status == O.OK and r.cycles == row["cycles"]
+    assert abs(r.steps - row["iters"]) <= 2
+    assert row["A"] == row["iters"] and r.a_calls == r.steps
+    assert row["V"] == 3 * row["iters"] and r.v_apps == 3 * r.steps
+    Ap, Bp = W.paper_tridiag(100)
+    V, H, _ = O.arnoldi(Ap, Bp, 20, sk)
+    kappa = np.linalg.cond(np.hstack([Bp, Ap.to_dense() @ V[:, :40]]))
+    assert O.loss_of_orthogonality(V) <= 100 * np.finfo(float).eps * kappa
+    Vb, _, _ = O.arnoldi(Ap, Bp, 20, "bcgs")
+    assert O.loss_of_orthogonality(Vb) > 0.1

@@ -42,6 +42,11 @@ MUTATIONS = {
     "pio_sign": ("R, flag = chol_flag(RW.T @ RW - RH.T @ RH)", "R, flag = chol_flag(RW.T @ RW + RH.T @ RH)"),
     # PIO's muscle factor of H taken from H H^T's wrong side
     "pio_HHt": ("RH, flag_h = chol_flag(Hc.T @ Hc)", "RH, flag_h = chol_flag(Hc[-Hc.shape[1]:] @ Hc[-Hc.shape[1]:].T)"),
+    # SVL's T column without its sign (Alg. 5, red)
+    "svl_sign": ("self.T[:k * s, k * s:(k + 1) * s] = Z if self.lts else -Tk @ Z",
+                 "self.T[:k * s, k * s:(k + 1) * s] = Z if self.lts else Tk @ Z"),
+    # LTS multiplies by T^T instead of solving with it (Alg. 5, blue)
+    "lts_mult": ("Hc = unit_upper_T_solve(Tk, Y) if self.lts else Tk.T @ Y", "Hc = Tk.T @ Y"),
     # global inner product without the 1/s of Table 1
     "global_no_scale": ("t = np.sum(X[:, i * s:(i + 1) * s] * Y[:, j * s:(j + 1) * s]) / s",
                         "t = np.sum(X[:, i * s:(i + 1) * s] * Y[:, j * s:(j + 1) * s])"),
@@ -80,6 +85,11 @@ def _pins_pass(O):
         V, H, _ = O.arnoldi(Ap, Bp, 20, "bmgs_icwy")
         if O.loss_of_orthogonality(V) > 1e-4:
             return False
+        for sk in ("bmgs_svl", "bmgs_lts"):
+            V, H, _ = O.arnoldi(Ap, Bp, 20, sk)
+            kappa = np.linalg.cond(np.hstack([Bp, Ap.to_dense() @ V[:, :40]]))
+            if O.loss_of_orthogonality(V) > 100 * np.finfo(float).eps * kappa:
+                return False
         V, H, _ = O.arnoldi(Ap, Bp, 30, "bcgsi_ls")
         if O.loss_of_orthogonality(V) > 1e-12:
             return False
