@@ -56,7 +56,9 @@ typedef enum {
   LSBA_BMGS_ICWY = 3,       /* Alg. 6 (inverse compact WY branch)             */
   LSBA_BMGS_CWY = 4,        /* Alg. 6 (compact WY branch)                     */
   LSBA_BMGS = 5,            /* Alg. 2, k + 1 syncs in step k (the comparator)  */
-  LSBA_BCGS_PIO = 6         /* Alg. 4, 2 syncs per step (muscle CholQR)        */
+  LSBA_BCGS_PIO = 6,        /* Alg. 4, 2 syncs per step (muscle CholQR)        */
+  LSBA_BMGS_SVL = 7,        /* Alg. 5 (Schreiber-Van Loan), 3 syncs per step    */
+  LSBA_BMGS_LTS = 8         /* Alg. 5 (lower triangular solve), 3 syncs per step */
 } lsba_skeleton;
 
 /* Low-rank modification of BFOM (Sec. 2.4.1, Eq. (7)). */

@@ -437,7 +437,8 @@ static int pull_ctl(lsba_ctx* h) {
     prof_end(h);            \
   } while (0)
 
-enum { SK_BCGS = 0, SK_PIP = 1, SK_LS = 2, SK_ICWY = 3, SK_CWY = 4, SK_BMGS = 5, SK_PIO = 6 };
+enum { SK_BCGS = 0, SK_PIP = 1, SK_LS = 2, SK_ICWY = 3, SK_CWY = 4, SK_BMGS = 5, SK_PIO = 6,
+       SK_SVL = 7, SK_LTS = 8 };
 static bool lagged(int skel) { return skel == SK_LS || skel == SK_ICWY || skel == SK_CWY; }
 
 // Precision dispatch of the three bandwidth-shaped passes (profiled).  In the
@@ -542,7 +543,33 @@ static void enqueue_cycle(lsba_ctx* h, const lsba_csr* A, const double* Rstart, 
   const int kmax = lagged(skel) ? m_cur + 1 : m_cur;
   const size_t blk = (size_t)n * s;
   for (int k = 1; k <= kmax; ++k) {
-    if (skel == SK_BMGS) {
+    if (skel == SK_SVL || skel == SK_LTS) {
+      // Alg. 5: Y = <V_k, W>, H = T^T Y or T^{-T} Y, W <- W - V_k H in place;
+      // CholQR of W; Z = <V_k, V_{k+1}> updates T's new block column.
+      const double* Vk = h->basis + (size_t)(k - 1) * blk;
+      double* Vnext = h->basis + (size_t)k * blk;
+      do_spmm(h, A, Vk, h->Wb, s, ctl, 1);
+      BlockPtrs L = basis_list(h, n, s, k);
+      BlockPtrs R;
+      memset(&R, 0, sizeof(R));
+      R.p[0] = h->Wb;
+      do_gram(h, L, k, R, 1, n, s, ctl, 1);
+      wait_side(h, k - 1);
+      PROF(LSBA_K_SMALL, launch_small_step(st, w, k, 0));
+      BlockPtrs in = basis_list(h, n, s, k);
+      in.p[k] = h->Wb;
+      do_update(h, in, k + 1, n, s, h->Wb, w.coef1, nullptr, nullptr, nullptr, nullptr, nullptr,
+                ctl, k);
+      do_gram(h, R, 1, R, 1, n, s, ctl, 1);
+      PROF(LSBA_K_SMALL, launch_small_step(st, w, k, 1));
+      do_update(h, R, 1, n, s, Vnext, w.coef1, w.tri1, nullptr, nullptr, nullptr, nullptr, ctl, k);
+      BlockPtrs Rn;
+      memset(&Rn, 0, sizeof(Rn));
+      Rn.p[0] = Vnext;
+      do_gram(h, L, k, Rn, 1, n, s, ctl, 1);
+      PROF(LSBA_K_SMALL, launch_small_step(st, w, k, 2));
+      enqueue_side(h, k);
+    } else if (skel == SK_BMGS) {
       // Alg. 2: one Gram and one in-place update per earlier basis block, then CholQR.
       const double* Vk = h->basis + (size_t)(k - 1) * blk;
       do_spmm(h, A, Vk, h->Wb, s, ctl, 1);
@@ -777,6 +804,8 @@ static int skel_code(lsba_skeleton s) {
     case LSBA_BMGS_CWY: return SK_CWY;
     case LSBA_BMGS: return SK_BMGS;
     case LSBA_BCGS_PIO: return SK_PIO;
+    case LSBA_BMGS_SVL: return SK_SVL;
+    case LSBA_BMGS_LTS: return SK_LTS;
     default: return -1;
   }
 }
@@ -868,7 +897,11 @@ static int run_cycles(lsba_handle h, const lsba_csr* A, const double* Bw, double
   cudaStream_t st = h->stream;
   Ctl* c = h->h_ctl;
   lsba_stats& S = h->stats;
-  const int vper = (skel == SK_LS) ? 4 : (skel == SK_PIP || skel == SK_PIO || lagged(skel)) ? 3 : 2;
+  const int vper = (skel == SK_LS) ? 4
+                   : (skel == SK_PIP || skel == SK_PIO || skel == SK_SVL || skel == SK_LTS ||
+                      lagged(skel))
+                       ? 3
+                       : 2;
   const int vcyc = lagged(skel) ? 1 : 0;
   int rc;
   CK(cudaMemsetAsync(Xw, 0, sizeof(double) * (size_t)n * s, st));
@@ -908,7 +941,8 @@ static int run_cycles(lsba_handle h, const lsba_csr* A, const double* Bw, double
     S.steps += j;
     const int a_calls = lagged(skel) ? j + 1 + f : j + f;
     S.a_calls += a_calls;
-    S.syncs += (skel == SK_BCGS || skel == SK_PIO) ? 2 * a_calls
+    S.syncs += (skel == SK_SVL || skel == SK_LTS) ? 3 * a_calls - f   // a flagged step stops before Z
+               : (skel == SK_BCGS || skel == SK_PIO) ? 2 * a_calls
                : (skel == SK_BMGS) ? a_calls * (a_calls + 3) / 2   // k + 1 in step k
                                    : a_calls;
     S.v_apps += vper * j + (j > 0 ? vcyc : 0);

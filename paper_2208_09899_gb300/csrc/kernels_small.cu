@@ -30,7 +30,8 @@ namespace lsba {
 #define NT LSBA_SMALL_THREADS
 #define NWARPS (NT / 32)
 
-enum { SK_BCGS = 0, SK_PIP = 1, SK_LS = 2, SK_ICWY = 3, SK_CWY = 4, SK_BMGS = 5, SK_PIO = 6 };
+enum { SK_BCGS = 0, SK_PIP = 1, SK_LS = 2, SK_ICWY = 3, SK_CWY = 4, SK_BMGS = 5, SK_PIO = 6,
+       SK_SVL = 7, SK_LTS = 8 };
 
 __device__ __forceinline__ double warp_sum(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -772,6 +773,69 @@ __device__ void step_bmgs(const SmallWs& w, int k, int phase, Shared& sh) {
   if (threadIdx.x == 0) w.ctl->update_step = k;
 }
 
+// BMGS-SVL / BMGS-LTS-Arnoldi (Alg. 5), iteration k; T is unit block upper
+// triangular (the muscle's T_{k+1,k+1} is I_s), its strict upper part in w.T.
+// Phase 0: Y = <V_k, W> (ks x s); H_{1:k,k} = T^T Y (SVL) or T^{-T} Y (LTS);
+//   W <- W - V_k H_{1:k,k} in place.
+// Phase 1: [V_{k+1}, H_{k+1,k}] = CholQR(W), as in BCGS.
+// Phase 2: Z = <V_k, V_{k+1}>; T_{1:k,k+1} = -T Z (SVL) or Z (LTS); the
+//   relation is then complete for the side kernel.
+__device__ void step_svl(const SmallWs& w, int k, int phase, bool lts, Shared& sh) {
+  const int s = w.s, ks = k * s, ldH = w.ldH, ldT = w.ldT;
+  const double* G = w.G;
+  if (phase == 1) {
+    step_bcgs(w, k, 1, sh);   // its side fields are reset by phase 2's entry
+    return;
+  }
+  if (phase == 0) {
+    record_gram(w, G, ks, s);
+    double* ZP = w.work;             // ks x s, ld ks
+    for (int e = threadIdx.x; e < ks * s; e += NT) {
+      const int i = e % ks, c = e / ks;
+      ZP[i + c * ks] = G[i * s + c];
+    }
+    __syncthreads();
+    if (lts) cta_unit_upper_T_solve(w.T, ldT, k, s, ZP, ks, s);
+    else cta_unit_upper_T_mult(w.T, ldT, k, s, ZP, ks, s, w.work + ks * s);
+    double* Hk = w.H + (size_t)(k - 1) * s * ldH;
+    for (int e = threadIdx.x; e < ks * s; e += NT) {
+      const int i = e % ks, c = e / ks;
+      Hk[i + c * ldH] = ZP[i + c * ks];
+    }
+    for (int b = 0; b < k; ++b) put_coef(w.coef1, b, s, ZP + b * s, ks, -1.0);
+    put_coef(w.coef1, k, s, nullptr, 0, 1.0);
+    __syncthreads();
+    if (threadIdx.x == 0) w.ctl->update_step = k;
+    return;
+  }
+  double* Tk = w.T + (size_t)ks * ldT;   // block column k + 1, rows 1..k
+  if (lts) {
+    for (int e = threadIdx.x; e < ks * s; e += NT) {
+      const int i = e % ks, c = e / ks;
+      Tk[i + c * ldT] = G[i * s + c];
+    }
+  } else {
+    double* tmp = w.work;            // ks x s, ld ks
+    for (int e = threadIdx.x; e < ks * s; e += NT) {
+      const int r = e % ks, c = e / ks;
+      double acc = G[r * s + c];
+      for (int q = (r / s + 1) * s; q < ks; ++q) acc = fma(w.T[r + q * ldT], G[q * s + c], acc);
+      tmp[r + c * ks] = -acc;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < ks * s; e += NT) {
+      const int i = e % ks, c = e / ks;
+      Tk[i + c * ldT] = tmp[i + c * ks];
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    w.ctl->side_step = k;
+    w.ctl->side_rel = k;
+    w.ctl->side_J = 0;
+  }
+}
+
 // Lagged skeletons, iteration k = 1: H_{1,1} = <U, W> (= J), U <- W - V_1 H_{1,1}.
 // Inputs [V_1, W]; out1 = U.
 __device__ void step_lagged_first(const SmallWs& w, Shared& sh) {
@@ -966,6 +1030,7 @@ __global__ void __launch_bounds__(NT) k_small_step(SmallWs w, int k, int phase) 
     int a = 1, b = 1;
     if (w.skel == SK_PIP || w.skel == SK_PIO) a = k + 1;
     else if (w.skel == SK_BCGS && phase == 0) a = k;
+    else if ((w.skel == SK_SVL || w.skel == SK_LTS) && phase != 1) a = k;
     else if ((w.skel == SK_LS || w.skel == SK_ICWY || w.skel == SK_CWY) && k >= 2) a = k, b = 2;
     project_global(w, a, b);
   }
@@ -974,6 +1039,8 @@ __global__ void __launch_bounds__(NT) k_small_step(SmallWs w, int k, int phase) 
     case SK_BCGS: step_bcgs(w, k, phase, sh); break;
     case SK_BMGS: step_bmgs(w, k, phase, sh); break;
     case SK_PIO: step_pio(w, k, sh); break;
+    case SK_SVL: step_svl(w, k, phase, false, sh); break;
+    case SK_LTS: step_svl(w, k, phase, true, sh); break;
     case SK_ICWY:
     case SK_CWY:
       if (k == 1) step_lagged_first(w, sh);

@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(HERE, "_lib", "liblsba.so")
 LSBA_OK, LSBA_NOT_CONVERGED, LSBA_BREAKDOWN, LSBA_INVALID_ARG = 0, 1, 2, 3
 LSBA_OUT_OF_MEMORY, LSBA_CUDA_ERROR, LSBA_DEVICE_TIMEOUT = 4, 5, 6
 SKELETONS = {"bcgs": 0, "bcgs_pip": 1, "bcgsi_ls": 2, "bmgs_icwy": 3, "bmgs_cwy": 4, "bmgs": 5,
-             "bcgs_pio": 6}
+             "bcgs_pio": 6, "bmgs_svl": 7, "bmgs_lts": 8}
 MODIFICATIONS = {"fom": 0, "gmres": 1}
 PRECISIONS = {"fp64": 0, "df": 1, "auto": 2, "fp32_ir": 3}
 INNER_PRODUCTS = {"classical": 0, "global": 1}

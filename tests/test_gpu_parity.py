@@ -227,7 +227,7 @@ def test_config1_tridiag_bgmres_bcgsi_ls(env, precision):
 @pytest.mark.parametrize("precision", ["df", "fp64"])
 @pytest.mark.parametrize("mod", ["gmres", "fom"])
 @pytest.mark.parametrize("sk", ["bcgs", "bcgs_pip", "bcgsi_ls", "bmgs_icwy", "bmgs_cwy", "bmgs",
-                                "bcgs_pio"])
+                                "bcgs_pio", "bmgs_svl", "bmgs_lts"])
 def test_all_skeletons_laplacian(env, sk, mod, precision):
     torch, lsba = env
     A = W.laplacian_2d(40, 37)
@@ -237,7 +237,7 @@ def test_all_skeletons_laplacian(env, sk, mod, precision):
 
 @pytest.mark.parametrize("precision", ["df", "fp64"])
 @pytest.mark.parametrize("sk", ["bcgs", "bcgs_pip", "bcgsi_ls", "bmgs_icwy", "bmgs_cwy", "bmgs",
-                                "bcgs_pio"])
+                                "bcgs_pio", "bmgs_svl", "bmgs_lts"])
 def test_global_inner_product(env, sk, precision):
     """Global block inner product (Table 1) on every skeleton: the same restart
     log, counters, first-cycle Grams and Hessenberg (whose s x s blocks are
@@ -280,7 +280,8 @@ def test_wide_blocks(env, s, sk, precision, expect):
     assert st["precision"] == lsba.PRECISIONS[expect]
 
 
-@pytest.mark.parametrize("sk", ["bcgs_pip", "bcgsi_ls", "bmgs_icwy", "bcgs", "bmgs", "bcgs_pio"])
+@pytest.mark.parametrize("sk", ["bcgs_pip", "bcgsi_ls", "bmgs_icwy", "bcgs", "bmgs", "bcgs_pio",
+                                "bmgs_svl", "bmgs_lts"])
 def test_adaptive_restart_injected_flag(env, sk):
     torch, lsba = env
     A = W.laplacian_2d(30)
