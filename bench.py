@@ -458,10 +458,13 @@ def main():
     peak = DF_PEAK_TFLOPS if is_df else FP64_PEAK_TFLOPS
     suffix = "_df" if is_df else ""
     roofline = {
-        "kernel": {"gram": ("k_gram_df_tma (k_gram_df_tc where a s >= 160) + k_gram_reduce_df" if is_df
+        "kernel": {"gram": ("k_gram_df_tcs (stored digits, tensor cores, iterations k >= 2) + "
+                            "k_gram_df_tma (start block, k = 1) + k_gram_reduce_df" if is_df
                             else "k_gram + k_gram_reduce"),
-                   "update": ("k_coef_df + k_update_df_tcs (tensor cores, iterations k >= 2) + "
-                              "k_split_digits + k_update_df_row" if is_df else "k_update"),
+                   "update": ("k_coef_fold + k_update_df_tcs (tensor cores, iterations k >= 2 and "
+                              "the cycle end; also writes the new block's digit planes) + k_coef_df + "
+                              "k_update_df_row (start block, k = 1) + k_split_digits (start block)"
+                              if is_df else "k_update"),
                    "spmm": f"k_spmm{suffix}"}[dom],
         "bound": "alu", "achieved": achieved_tflops, "peak": peak, "unit": "TFLOP/s",
         "frac": achieved_tflops / peak,
