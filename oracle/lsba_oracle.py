@@ -66,11 +66,17 @@ design notes of the repository):
       of the step.  Two syncs per step (the inner product and the muscle's
       <W, W>); V-applications as for PIP (3 per step).  Under the global inner
       product the muscle acts on W with the global scaling quotient.
+  R15 The column muscles MGS-SVL / MGS-LTS, which the paper names but does not
+      list, are read as Alg. 5 with block size 1 over the columns of a block in
+      Gram-Schmidt form (the column's own vector in place of A V_k): 3s - 2
+      syncs per call (the appendix table's classical BMGS-SVL/LTS rows, 584
+      syncs for 96 iterations in 2 cycles at s = 2, fit exactly this count),
+      and their T factor (unit upper triangular) becomes T's diagonal block.
   R13 Alg. 5 (BMGS-SVL / BMGS-LTS) with a muscle whose T factor is I_s: CholQR
       (classical) or the global scaling quotient (global), whose blocks are
       orthonormal in the block inner product, so T_{k+1,k+1} = I_s and T stays
       unit block upper triangular.  The paper pairs the classical variants
-      with the column muscles MGS-SVL / MGS-LTS, which are not built here.
+      with the column muscles MGS-SVL / MGS-LTS (muscle "mgs", reading R15).
       Syncs: Y, the muscle and Z, three per step; V-applications 3 per step.
 """
 from __future__ import annotations
@@ -168,6 +174,43 @@ def cholqr(X: np.ndarray, ip=inner):
     if flag:
         return None, R, True
     return right_solve_upper(X, R), R, False
+
+
+def mgs_svl(X: np.ndarray, lts: bool = False):
+    """Column muscle MGS-SVL (lts=False) or MGS-LTS (lts=True): Alg. 5 with
+    block size 1 applied to the columns of X in Gram-Schmidt form (reading
+    R15).  Column j: y = Q_{<j}^T x_j, r = T^T y (SVL) or T^{-T} y (LTS),
+    w = x_j - Q_{<j} r, [q_j, r_jj] = normalisation of w (the NaN-flag of R1
+    for s = 1), z = Q_{<j}^T q_j, T_{<j,j} = -T z (SVL) or z (LTS), T_jj = 1.
+    Returns (Q, R, T, flag, syncs) with syncs = 3s - 2 for a full call (the
+    syncs performed up to a flag otherwise)."""
+    X = np.asarray(X, dtype=np.float64)
+    n, s = X.shape
+    Q = np.zeros((n, s))
+    R = np.zeros((s, s))
+    T = np.eye(s)
+    syncs = 0
+    for j in range(s):
+        x = X[:, j]
+        if j > 0:
+            y = Q[:, :j].T @ x
+            syncs += 1
+            r = unit_upper_T_solve(T[:j, :j], y[:, None])[:, 0] if lts else T[:j, :j].T @ y
+            R[:j, j] = r
+            w = x - Q[:, :j] @ r
+        else:
+            w = x
+        d = float(w @ w)
+        syncs += 1
+        if not np.isfinite(d) or d <= 0.0:
+            return None, R, T, True, syncs
+        R[j, j] = np.sqrt(d)
+        Q[:, j] = w / R[j, j]
+        if j > 0:
+            z = Q[:, :j].T @ Q[:, j]
+            syncs += 1
+            T[:j, j] = z if lts else -(T[:j, :j] @ z)
+    return Q, R, T, False, syncs
 
 
 def unit_upper_T_solve(T: np.ndarray, Y: np.ndarray) -> np.ndarray:
@@ -328,12 +371,17 @@ class BCGS_PIO(_Arnoldi):
 
 
 class BMGS_SVL(_Arnoldi):
-    """BMGS-SVL-Arnoldi, Alg. 5 (red branch), reading R13."""
+    """BMGS-SVL-Arnoldi, Alg. 5 (red branch), readings R13 and R15.  muscle =
+    "cholqr" (T factor I_s) or "mgs" (MGS-SVL / MGS-LTS column muscle, whose
+    T factor enters T's diagonal block); T11 is the start block's factor."""
     lts = False
 
-    def __init__(self, *args, **kw):
+    def __init__(self, *args, muscle: str = "cholqr", T11=None, **kw):
         super().__init__(*args, **kw)
-        self.T = np.eye((self.m + 2) * self.s)      # T = I; T_{1,1} = I_s from the muscle
+        self.muscle = muscle
+        self.T = np.eye((self.m + 2) * self.s)
+        if T11 is not None:
+            self.T[:self.s, :self.s] = T11
 
     def advance(self, force_flag=False):
         self.k += 1
@@ -345,8 +393,13 @@ class BMGS_SVL(_Arnoldi):
         self._record(Y)
         Tk = self.T[:k * s, :k * s]
         Hc = unit_upper_T_solve(Tk, Y) if self.lts else Tk.T @ Y
-        self._sync()
-        Q, R, flag = cholqr(W - Vk @ Hc, self.ip)
+        if self.muscle == "mgs":
+            Q, R, Tm, flag, ns = mgs_svl(W - Vk @ Hc, self.lts)
+            self.counts["syncs"] += ns
+        else:
+            self._sync()
+            Q, R, flag = cholqr(W - Vk @ Hc, self.ip)
+            Tm = np.eye(s)
         if flag or force_flag:
             return ("flag", k)
         self.V.append(Q)
@@ -354,8 +407,9 @@ class BMGS_SVL(_Arnoldi):
         self.set_Hb(k + 1, k, R)
         Z = self.ip(Vk, Q)
         self._sync()
-        # T_{k+1,k+1} = I_s (the muscle's T factor)
-        self.T[:k * s, k * s:(k + 1) * s] = Z if self.lts else -Tk @ Z
+        # T_{1:k,k+1} = -T Z T_{k+1,k+1} (SVL) or Z T_{k+1,k+1} (LTS)
+        self.T[:k * s, k * s:(k + 1) * s] = (Z if self.lts else -Tk @ Z) @ Tm
+        self.T[k * s:(k + 1) * s, k * s:(k + 1) * s] = Tm
         return ("rel", k)
 
 
@@ -464,15 +518,34 @@ _VAPPS = {"bmgs": (2, 0), "bcgs": (2, 0), "bcgs_pip": (3, 0), "bcgs_pio": (3, 0)
           "bmgs_cwy": (3, 1), "bmgs_icwy": (3, 1), "bcgsi_ls": (4, 1)}
 
 
-def arnoldi(A, B: np.ndarray, m: int, skeleton: str, inner_product: str = "classical"):
+def _start_block(R_start, skeleton, ip, muscle):
+    """The cycle's start muscle: CholQR (or the global scaling quotient), or
+    for BMGS-SVL/LTS with muscle "mgs" the column muscle (reading R15).
+    Returns (V1, Beta, flag, syncs, extra constructor arguments)."""
+    if skeleton in ("bmgs_svl", "bmgs_lts"):
+        if muscle == "mgs":
+            Q, R, T, flag, ns = mgs_svl(R_start, skeleton == "bmgs_lts")
+            return Q, R, flag, ns, {"muscle": "mgs", "T11": T}
+        if muscle != "cholqr":
+            raise ValueError(muscle)
+    elif muscle != "cholqr":
+        raise ValueError("the column muscle belongs to BMGS-SVL / BMGS-LTS")
+    V1, Beta, flag = cholqr(R_start, ip)
+    return V1, Beta, flag, 1, {}
+
+
+def arnoldi(A, B: np.ndarray, m: int, skeleton: str, inner_product: str = "classical",
+            muscle: str = "cholqr"):
     """m steps of a block Arnoldi skeleton from B (no restarts, no flags expected).
     Returns (V_{m+1} as n x (m+1)s, H_{m+1,m}, Beta)."""
     counts = {"a_calls": 0, "syncs": 0}
     ip = block_inner_product(inner_product, B.shape[1])
-    V1, Beta, flag = cholqr(B, ip)
+    if muscle != "cholqr" and inner_product != "classical":
+        raise ValueError("the global paradigm takes only the global muscle")
+    V1, Beta, flag, _, extra = _start_block(B, skeleton, ip, muscle)
     if flag:
         raise FloatingPointError("CholQR of B flagged")
-    ar = _CLASSES[skeleton](A, V1, m, counts, None, ip=ip)
+    ar = _CLASSES[skeleton](A, V1, m, counts, None, ip=ip, **extra)
     j = 0
     while j < m:
         kind, jj = ar.advance()
@@ -546,7 +619,7 @@ def solve(A, B: np.ndarray, m: int, tol: float, skeleton: str = "bcgsi_ls",
           modification: str = "gmres", max_restarts: int = 50, adaptive: bool = True,
           verify_true_residual: bool = True, inject_flags=(), record_first_cycle: bool = False,
           true_residual_each_cycle: bool = False, X_star: np.ndarray | None = None,
-          inner_product: str = "classical") -> Result:
+          inner_product: str = "classical", muscle: str = "cholqr") -> Result:
     """Restarted, adaptively restarted modified BFOM (BFOM or BGMRES) for A X = B
     with the given block Arnoldi skeleton; X_0 = 0.
 
@@ -558,6 +631,8 @@ def solve(A, B: np.ndarray, m: int, tol: float, skeleton: str = "bcgsi_ls",
     B = np.asarray(B, dtype=np.float64)
     n, s = B.shape
     ip = block_inner_product(inner_product, s)
+    if muscle != "cholqr" and inner_product != "classical":
+        raise ValueError("the global paradigm takes only the global muscle")
     normB = np.linalg.norm(B)
     X = np.zeros((n, s))
     C = np.eye(s)
@@ -573,14 +648,14 @@ def solve(A, B: np.ndarray, m: int, tol: float, skeleton: str = "bcgsi_ls",
         if cycle > max_restarts + 1:
             res.status = NOT_CONVERGED
             break
-        counts["syncs"] += 1
-        V1, Beta, flag = cholqr(R_start, ip)
+        V1, Beta, flag, ns, extra = _start_block(R_start, skeleton, ip, muscle)
+        counts["syncs"] += ns
         if flag:
             res.status = BREAKDOWN if cycle == 1 else NOT_CONVERGED
             res.cycles = cycle
             break
         grams = [] if (record_first_cycle and cycle == 1) else None
-        ar = _CLASSES[skeleton](A, V1, m_cur, counts, grams, ip=ip)
+        ar = _CLASSES[skeleton](A, V1, m_cur, counts, grams, ip=ip, **extra)
         res.m_cur.append(m_cur)
         j, converged, flagged = 0, False, 0
         coeffs = None

@@ -475,3 +475,51 @@ def test_svl_lts_classical_rows_and_stability(sk):
     assert O.loss_of_orthogonality(V) <= 100 * np.finfo(float).eps * kappa
     Vb, _, _ = O.arnoldi(Ap, Bp, 20, "bcgs")
     assert O.loss_of_orthogonality(Vb) > 0.1
+
+
+def test_column_muscles_mgs_svl_lts():
+    """Reading R15: MGS-SVL / MGS-LTS give X = Q R with R the (sign-normalised)
+    R of Householder QR, 3s - 2 syncs, a unit upper-triangular T, and a loss of
+    orthogonality O(eps) kappa(X) like MGS: at kappa = 1e8 and 1e10, where
+    CholQR raises the NaN-flag (eps kappa^2 > 1) and classical Gram-Schmidt has
+    lost orthogonality completely."""
+    rng = np.random.default_rng(3)
+    n, s = 200, 8
+    U, _ = np.linalg.qr(rng.standard_normal((n, s)))
+    Vr, _ = np.linalg.qr(rng.standard_normal((s, s)))
+    eps = np.finfo(float).eps
+    X0 = rng.standard_normal((n, s))
+    Rh = np.linalg.qr(X0)[1]
+    Rh = np.diag(np.sign(np.diag(Rh))) @ Rh
+    for lts in (False, True):
+        Q, R, T, flag, ns = O.mgs_svl(X0, lts)
+        assert not flag and ns == 3 * s - 2
+        assert np.allclose(R, Rh, rtol=0, atol=1e-12 * np.abs(Rh).max())
+        assert np.allclose(np.tril(T, -1), 0.0) and np.all(np.diag(T) == 1.0)
+        for kappa in (1e8, 1e10):
+            X = U @ np.diag(np.logspace(0, -np.log10(kappa), s)) @ Vr.T
+            Q, R, T, flag, ns = O.mgs_svl(X, lts)
+            assert not flag
+            assert np.linalg.norm(np.eye(s) - Q.T @ Q) <= 100 * eps * kappa
+            assert np.linalg.norm(Q @ R - X) <= 1e-14 * np.linalg.norm(X)
+            assert O.cholqr(X)[2]
+
+
+@pytest.mark.parametrize("sk", ["bmgs_svl", "bmgs_lts"])
+def test_paper_tridiag_table_classical_svl_lts_with_column_muscles(sk):
+    """Appendix table, cl-BMGS-SVL o MGS-SVL and cl-BMGS-LTS o MGS-LTS rows
+    (2 cycles, 96 iterations, 584 syncs at s = 2): the same cycles, iterations
+    within 2, and the sync identity 6 per iteration + 4 per cycle (Y, the
+    3s - 2 = 4 syncs of the column muscle and Z per step; the muscle per cycle
+    start), which the printed row satisfies exactly."""
+    g = json.load(open(GOLDEN))
+    row = g["classical_rows"][sk]
+    A, B = W.paper_tridiag(1000)
+    Xs = np.linalg.solve(A.to_dense(), B)
+    r = O.solve(A, B, 70, 1e-10, sk, modification="fom", max_restarts=100,
+                verify_true_residual=False, X_star=Xs, muscle="mgs")
+    assert r.status == O.OK and r.cycles == row["cycles"]
+    assert abs(r.steps - row["iters"]) <= 2
+    assert r.syncs == 6 * r.steps + 4 * r.cycles
+    assert row["sync"] == 6 * row["iters"] + 4 * row["cycles"]
+    assert r.v_apps == 3 * r.steps and row["V"] == 3 * row["iters"]

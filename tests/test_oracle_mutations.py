@@ -43,10 +43,15 @@ MUTATIONS = {
     # PIO's muscle factor of H taken from H H^T's wrong side
     "pio_HHt": ("RH, flag_h = chol_flag(Hc.T @ Hc)", "RH, flag_h = chol_flag(Hc[-Hc.shape[1]:] @ Hc[-Hc.shape[1]:].T)"),
     # SVL's T column without its sign (Alg. 5, red)
-    "svl_sign": ("self.T[:k * s, k * s:(k + 1) * s] = Z if self.lts else -Tk @ Z",
-                 "self.T[:k * s, k * s:(k + 1) * s] = Z if self.lts else Tk @ Z"),
+    "svl_sign": ("self.T[:k * s, k * s:(k + 1) * s] = (Z if self.lts else -Tk @ Z) @ Tm",
+                 "self.T[:k * s, k * s:(k + 1) * s] = (Z if self.lts else Tk @ Z) @ Tm"),
     # LTS multiplies by T^T instead of solving with it (Alg. 5, blue)
     "lts_mult": ("Hc = unit_upper_T_solve(Tk, Y) if self.lts else Tk.T @ Y", "Hc = Tk.T @ Y"),
+    # MGS-SVL's T column without its sign (column muscle, reading R15)
+    "mgs_svl_sign": ("T[:j, j] = z if lts else -(T[:j, :j] @ z)", "T[:j, j] = z if lts else (T[:j, :j] @ z)"),
+    # MGS-LTS multiplies by T^T instead of solving with it
+    "mgs_lts_mult": ("r = unit_upper_T_solve(T[:j, :j], y[:, None])[:, 0] if lts else T[:j, :j].T @ y",
+                     "r = T[:j, :j].T @ y"),
     # global inner product without the 1/s of Table 1
     "global_no_scale": ("t = np.sum(X[:, i * s:(i + 1) * s] * Y[:, j * s:(j + 1) * s]) / s",
                         "t = np.sum(X[:, i * s:(i + 1) * s] * Y[:, j * s:(j + 1) * s])"),
@@ -121,6 +126,15 @@ def _pins_pass(O):
         r = O.solve(A, B, 8, 1e-9, "bcgs_pip", inject_flags=[(1, 5)])
         if r.cycle_m[0] != 4 or any(mc != 4 for mc in r.m_cur[1:]):
             return False
+        # Column muscles: loss of orthogonality O(eps) kappa at kappa = 1e10.
+        rng = np.random.default_rng(3)
+        Uq, _ = np.linalg.qr(rng.standard_normal((200, 8)))
+        Vq, _ = np.linalg.qr(rng.standard_normal((8, 8)))
+        Xm = Uq @ np.diag(np.logspace(0, -10, 8)) @ Vq.T
+        for lts in (False, True):
+            Qm, Rm, Tm, fm, _ = O.mgs_svl(Xm, lts)
+            if fm or np.linalg.norm(np.eye(8) - Qm.T @ Qm) > 100 * np.finfo(float).eps * 1e10:
+                return False
         # Global inner product: the block method is the single-vector method on
         # (I_s (x) A, vec B) (Table 1).
         Ag = W.laplacian_2d(9, 8)
