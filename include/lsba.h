@@ -125,11 +125,18 @@ typedef struct {
                                     I_s.  Every skeleton takes either; the Gram passes
                                     are the same, and each s x s block of their result
                                     is replaced by its trace / s times I_s.            */
-  int32_t reserved[1];
+  int32_t muscle;                /* muscle of BMGS-SVL / BMGS-LTS under the classical
+                                    product: LSBA_MUSCLE_CHOLQR (default) or
+                                    LSBA_MUSCLE_COLUMN, the column muscles MGS-SVL /
+                                    MGS-LTS (3s - 2 syncs per call, Sec. 5 list of
+                                    muscles); any other skeleton or the global
+                                    product with LSBA_MUSCLE_COLUMN is
+                                    LSBA_INVALID_ARG.                                  */
 } lsba_options;
 
 enum { LSBA_PREC_FP64 = 0, LSBA_PREC_DF = 1, LSBA_PREC_AUTO = 2, LSBA_PREC_FP32_IR = 3 };
 enum { LSBA_IP_CLASSICAL = 0, LSBA_IP_GLOBAL = 1 };
+enum { LSBA_MUSCLE_CHOLQR = 0, LSBA_MUSCLE_COLUMN = 1 };
 
 /* Counters and outcome of the last lsba_solve. */
 typedef struct {

@@ -99,7 +99,7 @@ struct CycleKey {
   const void* a_lowprec;
   const double* rstart;
   int64_t n;
-  int s, m_cur, start_flags, skel, modification, mode, tensor_cores, global_ip;
+  int s, m_cur, start_flags, skel, modification, mode, tensor_cores, global_ip, col_muscle, pad;
   uint64_t ws_gen;
   bool operator==(const CycleKey& o) const { return memcmp(this, &o, sizeof(*this)) == 0; }
 };
@@ -231,7 +231,7 @@ static size_t max_partials(int64_t n, int s, int mmax, int sms, size_t* qmax_out
 #define LSBA_HIST_RESTARTS 4096
 struct SmallLayout {
   size_t oH, oT, oJ, oc1, oc2, och, ot1, ot2, oRb, orf, otau, otw, og, oTf, ogf, ocf, ouf, oC,
-      oBc, oXi, oMv, owk, osz, osy, osr, ohe, ogh;
+      oBc, oXi, oMv, owk, osz, osy, osr, ohe, ogh, omu;
   size_t hist_cap, gram_hist_cap, total;
 };
 
@@ -275,6 +275,7 @@ static SmallLayout small_layout(int s, int m, int max_restarts) {
   L.osr = take(ss);
   L.ohe = take(L.hist_cap);
   L.ogh = take(L.gram_hist_cap);
+  L.omu = take(muscle_area_doubles(s));
   L.total = off;
   return L;
 }
@@ -361,6 +362,7 @@ static int ensure_ws(lsba_ctx* h, int64_t n, int s, int m) {
   w.saveR = b + osr;
   w.hist_est = b + ohe;
   w.gram_hist = b + ogh;
+  w.mus = b + L.omu;
   w.hist_cycle = h->ismall;
   w.hist_j = h->ismall + hist_cap;
   w.gram_dims = h->ismall + 2 * hist_cap;
@@ -536,9 +538,19 @@ static void enqueue_cycle(lsba_ctx* h, const lsba_csr* A, const double* Rstart, 
   BlockPtrs one;
   memset(&one, 0, sizeof(one));
   one.p[0] = Rstart;
-  do_gram(h, one, 1, one, 1, n, s, ctl, 0);
-  PROF(LSBA_K_SMALL, launch_small_start(st, w, start_flags));
-  do_update(h, one, 1, n, s, h->basis, w.coef1, w.tri1, nullptr, nullptr, nullptr, nullptr, ctl, 0);
+  if (w.col_muscle) {
+    // V_1 from R_start by the column muscle, in place in the first basis block
+    const size_t esz = h->mode == MODE_F32 ? sizeof(float) : sizeof(double);
+    cudaMemcpyAsync(h->basis, Rstart, esz * (size_t)n * s, cudaMemcpyDeviceToDevice, st);
+    PROF(LSBA_K_GRAM, launch_col_muscle(st, h->basis, h->mode, n, s, skel == SK_LTS, w.mus, ctl,
+                                        -1, h->num_sms));
+    PROF(LSBA_K_SMALL, launch_small_start(st, w, start_flags));
+  } else {
+    do_gram(h, one, 1, one, 1, n, s, ctl, 0);
+    PROF(LSBA_K_SMALL, launch_small_start(st, w, start_flags));
+    do_update(h, one, 1, n, s, h->basis, w.coef1, w.tri1, nullptr, nullptr, nullptr, nullptr, ctl,
+              0);
+  }
   if (h->use_tcs) split_basis(h, 0, n, s, ctl, 0);
   const int kmax = lagged(skel) ? m_cur + 1 : m_cur;
   const size_t blk = (size_t)n * s;
@@ -560,9 +572,19 @@ static void enqueue_cycle(lsba_ctx* h, const lsba_csr* A, const double* Rstart, 
       in.p[k] = h->Wb;
       do_update(h, in, k + 1, n, s, h->Wb, w.coef1, nullptr, nullptr, nullptr, nullptr, nullptr,
                 ctl, k);
-      do_gram(h, R, 1, R, 1, n, s, ctl, 1);
-      PROF(LSBA_K_SMALL, launch_small_step(st, w, k, 1));
-      do_update(h, R, 1, n, s, Vnext, w.coef1, w.tri1, nullptr, nullptr, nullptr, nullptr, ctl, k);
+      if (w.col_muscle) {
+        // MGS-SVL / MGS-LTS on W in place, then V_{k+1} = W
+        PROF(LSBA_K_GRAM, launch_col_muscle(st, h->Wb, h->mode, n, s, skel == SK_LTS, w.mus, ctl,
+                                            k, h->num_sms));
+        PROF(LSBA_K_SMALL, launch_small_step(st, w, k, 1));
+        do_update(h, R, 1, n, s, Vnext, w.coef1, nullptr, nullptr, nullptr, nullptr, nullptr, ctl,
+                  k);
+      } else {
+        do_gram(h, R, 1, R, 1, n, s, ctl, 1);
+        PROF(LSBA_K_SMALL, launch_small_step(st, w, k, 1));
+        do_update(h, R, 1, n, s, Vnext, w.coef1, w.tri1, nullptr, nullptr, nullptr, nullptr, ctl,
+                  k);
+      }
       BlockPtrs Rn;
       memset(&Rn, 0, sizeof(Rn));
       Rn.p[0] = Vnext;
@@ -837,6 +859,7 @@ static int run_cycle_body(lsba_handle h, const lsba_csr* A, const double* Rstart
     key.mode = h->mode;
     key.tensor_cores = h->opt.tensor_cores;
     key.global_ip = h->ws.global_ip;
+    key.col_muscle = h->ws.col_muscle;
     key.ws_gen = h->ws_gen;
     for (auto& e : h->graphs)
       if (e.key == key) g = &e;
@@ -924,9 +947,12 @@ static int run_cycles(lsba_handle h, const lsba_csr* A, const double* Bw, double
     c->record = (record_first && h->opt.record_history) ? 1 : 0;
     c->m_cur = m_cur;
     c->inject_relation = (cycle == h->opt.inject_flag_cycle) ? h->opt.inject_flag_relation : -1;
+    c->muscle_syncs = 0;
     if ((rc = run_cycle_body(h, A, Rstart, n, s, m_cur, start_flags)) != LSBA_OK) return rc;
     if (c->error) return LSBA_DEVICE_TIMEOUT;
-    S.syncs += 1;
+    // the start block's muscle: CholQR one sync; the column muscle counts its
+    // own syncs on the device (the start's and every step's)
+    S.syncs += w.col_muscle ? c->muscle_syncs : 1;
     S.cycles += 1;
     if (c->start_flag) {
       status = (cycle == 1) ? LSBA_BREAKDOWN : LSBA_NOT_CONVERGED;
@@ -941,7 +967,8 @@ static int run_cycles(lsba_handle h, const lsba_csr* A, const double* Bw, double
     S.steps += j;
     const int a_calls = lagged(skel) ? j + 1 + f : j + f;
     S.a_calls += a_calls;
-    S.syncs += (skel == SK_SVL || skel == SK_LTS) ? 3 * a_calls - f   // a flagged step stops before Z
+    S.syncs += (skel == SK_SVL || skel == SK_LTS)
+                   ? (w.col_muscle ? 2 * a_calls - f : 3 * a_calls - f)   // Y, (muscle), Z; a flagged step has no Z
                : (skel == SK_BCGS || skel == SK_PIO) ? 2 * a_calls
                : (skel == SK_BMGS) ? a_calls * (a_calls + 3) / 2   // k + 1 in step k
                                    : a_calls;
@@ -1057,7 +1084,10 @@ static int solve_impl(lsba_handle h, const lsba_csr* A, const double* d_B, doubl
       (int64_t)(m + 1) * s > LSBA_MAX_MS || m + 3 > LSBA_MAXB || A->n < 1 || A->nnz < 0 ||
       A->nnz >= (int64_t)1 << 31 || !A->d_rowptr || (A->nnz > 0 && (!A->d_colidx || !A->d_vals)) ||
       !(tol >= 0.0) || h->opt.max_restarts < 0 ||
-      (h->opt.inner_product != LSBA_IP_CLASSICAL && h->opt.inner_product != LSBA_IP_GLOBAL))
+      (h->opt.inner_product != LSBA_IP_CLASSICAL && h->opt.inner_product != LSBA_IP_GLOBAL) ||
+      (h->opt.muscle != LSBA_MUSCLE_CHOLQR &&
+       (h->opt.muscle != LSBA_MUSCLE_COLUMN || (skel != SK_SVL && skel != SK_LTS) ||
+        h->opt.inner_product != LSBA_IP_CLASSICAL)))
     return h->stats.status = LSBA_INVALID_ARG;
   const int64_t n = A->n;
   CK(cudaSetDevice(h->device));
@@ -1067,6 +1097,7 @@ static int solve_impl(lsba_handle h, const lsba_csr* A, const double* d_B, doubl
   w.skel = skel;
   w.modification = h->opt.modification == LSBA_FOM ? 0 : 1;
   w.global_ip = h->opt.inner_product == LSBA_IP_GLOBAL ? 1 : 0;
+  w.col_muscle = h->opt.muscle == LSBA_MUSCLE_COLUMN ? 1 : 0;
   cudaStream_t st = h->stream;
   const size_t blk = (size_t)n * s;
   // Working precision of the SpMM / Gram / update passes.

@@ -206,9 +206,11 @@ __device__ void cta_tri_inverse(const double* R, int s, double* Ri) {
 
 // Y (kb*s x cols, ldy) <- T^{-T} Y for unit upper-triangular T (ldt) given by
 // its strictly upper blocks: block forward substitution Y_i -= sum_{l<i} T_{l,i}^T Y_l.
+// diag: T's diagonal blocks are unit upper triangular (the column muscle's T
+// factors) rather than I_s, and their strict upper parts take part too.
 __device__ void cta_unit_upper_T_solve(const double* T, int ldt, int kb, int s, double* Y, int ldy,
-                                       int cols) {
-  for (int i = 1; i < kb; ++i) {
+                                       int cols, bool diag = false) {
+  for (int i = diag ? 0 : 1; i < kb; ++i) {
     // Y_i -= T(0:i s, i s:(i+1) s)^T Y(0:i s, :)
     for (int e = threadIdx.x; e < s * cols; e += NT) {
       const int a = e % s, c = e / s;
@@ -223,19 +225,30 @@ __device__ void cta_unit_upper_T_solve(const double* T, int ldt, int kb, int s, 
       Y[i * s + a + c * ldy] -= (acc0 + acc1);
     }
     __syncthreads();
+    if (diag) {
+      // Y_i <- T_ii^{-T} Y_i, forward substitution over the block's rows
+      for (int a = 1; a < s; ++a) {
+        for (int c = threadIdx.x; c < cols; c += NT) {
+          double acc = 0.0;
+          for (int b = 0; b < a; ++b) acc = fma(T[i * s + b + (i * s + a) * ldt], Y[i * s + b + c * ldy], acc);
+          Y[i * s + a + c * ldy] -= acc;
+        }
+        __syncthreads();
+      }
+    }
   }
 }
 
 // Y <- T^T Y for unit upper-triangular T (the compact-WY branch of Alg. 6).
 __device__ void cta_unit_upper_T_mult(const double* T, int ldt, int kb, int s, double* Y, int ldy,
-                                      int cols, double* tmp) {
+                                      int cols, double* tmp, bool diag = false) {
   const int rows = kb * s;
   for (int e = threadIdx.x; e < rows * cols; e += NT) {
     const int r = e % rows, c = e / rows;
-    const int ib = r / s;
+    const int qend = diag ? r : (r / s) * s;
     double acc = Y[r + c * ldy];
     const double* tcol = T + r * ldt;
-    for (int q = 0; q < ib * s; ++q) acc = fma(tcol[q], Y[q + c * ldy], acc);
+    for (int q = 0; q < qend; ++q) acc = fma(tcol[q], Y[q + c * ldy], acc);
     tmp[r + c * rows] = acc;
   }
   __syncthreads();
@@ -597,13 +610,33 @@ __global__ void __launch_bounds__(NT) k_small_start(SmallWs w, int flags) {
   Ctl* ctl = w.ctl;
   // G = R_start^T R_start (s x s row-major == col-major since symmetric in exact
   // arithmetic; the upper triangle read as G[a*s + c], a <= c).
-  if (w.global_ip) project_global(w, 1, 1);
-  int flag = cta_chol(w.G, s, s, sh.R, &sh.flag);
-  if (first_cycle) {
-    if (threadIdx.x == 0) {
-      double tr = 0.0;
-      for (int a = 0; a < s; ++a) tr += w.G[a * s + a];
-      ctl->normB = sqrt(tr);
+  int flag;
+  if (w.col_muscle) {
+    // The column muscle has made V_1 from R_start in place: Beta = R, and its
+    // T factor is T's first diagonal block; ||R_start||_F = ||R||_F.
+    const double* mR = w.mus;
+    const double* mT = w.mus + s * s;
+    flag = w.mus[2 * s * s + s] != 0.0 ? 1 : 0;
+    for (int e = threadIdx.x; e < s * s; e += NT) {
+      const int a = e % s, c = e / s;
+      sh.R[e] = flag ? 0.0 : mR[e];
+      w.T[a + c * w.ldT] = a < c && !flag ? mT[e] : 0.0;
+    }
+    __syncthreads();
+    if (first_cycle && threadIdx.x == 0) {
+      double t = 0.0;
+      for (int e = 0; e < s * s; ++e) t += mR[e] * mR[e];
+      ctl->normB = sqrt(t);
+    }
+  } else {
+    if (w.global_ip) project_global(w, 1, 1);
+    flag = cta_chol(w.G, s, s, sh.R, &sh.flag);
+    if (first_cycle) {
+      if (threadIdx.x == 0) {
+        double tr = 0.0;
+        for (int a = 0; a < s; ++a) tr += w.G[a * s + a];
+        ctl->normB = sqrt(tr);
+      }
     }
   }
   __syncthreads();
@@ -783,8 +816,29 @@ __device__ void step_bmgs(const SmallWs& w, int k, int phase, Shared& sh) {
 __device__ void step_svl(const SmallWs& w, int k, int phase, bool lts, Shared& sh) {
   const int s = w.s, ks = k * s, ldH = w.ldH, ldT = w.ldT;
   const double* G = w.G;
-  if (phase == 1) {
+  if (phase == 1 && !w.col_muscle) {
     step_bcgs(w, k, 1, sh);   // its side fields are reset by phase 2's entry
+    return;
+  }
+  if (phase == 1) {
+    // The column muscle has made W = V_{k+1} H_{k+1,k} in place (R and its
+    // T factor in w.mus): H_{k+1,k} = R, T_{k+1,k+1} = T_m, then V_{k+1} = W.
+    const double* mR = w.mus;
+    const double* mT = w.mus + s * s;
+    if (w.mus[2 * s * s + s] != 0.0 || injected(w, k)) {
+      flag_exit(w, k);
+      return;
+    }
+    double* Hk = w.H + (size_t)(k - 1) * s * ldH;
+    double* Tkk = w.T + (size_t)ks * ldT + ks;
+    for (int e = threadIdx.x; e < s * s; e += NT) {
+      const int a = e % s, c = e / s;
+      Hk[ks + a + c * ldH] = mR[a + c * s];
+      Tkk[a + c * ldT] = a < c ? mT[a + c * s] : 0.0;   // strict upper part; the unit diagonal is implied
+    }
+    put_coef(w.coef1, 0, s, nullptr, 0, 1.0);
+    __syncthreads();
+    if (threadIdx.x == 0) w.ctl->update_step = k;
     return;
   }
   if (phase == 0) {
@@ -795,8 +849,8 @@ __device__ void step_svl(const SmallWs& w, int k, int phase, bool lts, Shared& s
       ZP[i + c * ks] = G[i * s + c];
     }
     __syncthreads();
-    if (lts) cta_unit_upper_T_solve(w.T, ldT, k, s, ZP, ks, s);
-    else cta_unit_upper_T_mult(w.T, ldT, k, s, ZP, ks, s, w.work + ks * s);
+    if (lts) cta_unit_upper_T_solve(w.T, ldT, k, s, ZP, ks, s, w.col_muscle != 0);
+    else cta_unit_upper_T_mult(w.T, ldT, k, s, ZP, ks, s, w.work + ks * s, w.col_muscle != 0);
     double* Hk = w.H + (size_t)(k - 1) * s * ldH;
     for (int e = threadIdx.x; e < ks * s; e += NT) {
       const int i = e % ks, c = e / ks;
@@ -808,25 +862,28 @@ __device__ void step_svl(const SmallWs& w, int k, int phase, bool lts, Shared& s
     if (threadIdx.x == 0) w.ctl->update_step = k;
     return;
   }
-  double* Tk = w.T + (size_t)ks * ldT;   // block column k + 1, rows 1..k
-  if (lts) {
-    for (int e = threadIdx.x; e < ks * s; e += NT) {
-      const int i = e % ks, c = e / ks;
-      Tk[i + c * ldT] = G[i * s + c];
+  // T_{1:k,k+1} = -T_{1:k,1:k} Z T_{k+1,k+1} (SVL) or Z T_{k+1,k+1} (LTS); the
+  // diagonal blocks of T are I_s except with the column muscle.
+  double* Tk = w.T + (size_t)ks * ldT;            // block column k + 1, rows 1..k
+  const double* Tm = Tk + ks;                      // T_{k+1,k+1}, strict upper part
+  double* tmp = w.work;                            // ks x s, ld ks
+  for (int e = threadIdx.x; e < ks * s; e += NT) {
+    const int r = e % ks, c = e / ks;
+    double acc = G[r * s + c];
+    if (!lts) {
+      for (int q = w.col_muscle ? r + 1 : (r / s + 1) * s; q < ks; ++q)
+        acc = fma(w.T[r + q * ldT], G[q * s + c], acc);
+      acc = -acc;
     }
-  } else {
-    double* tmp = w.work;            // ks x s, ld ks
-    for (int e = threadIdx.x; e < ks * s; e += NT) {
-      const int r = e % ks, c = e / ks;
-      double acc = G[r * s + c];
-      for (int q = (r / s + 1) * s; q < ks; ++q) acc = fma(w.T[r + q * ldT], G[q * s + c], acc);
-      tmp[r + c * ks] = -acc;
-    }
-    __syncthreads();
-    for (int e = threadIdx.x; e < ks * s; e += NT) {
-      const int i = e % ks, c = e / ks;
-      Tk[i + c * ldT] = tmp[i + c * ks];
-    }
+    tmp[r + c * ks] = acc;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < ks * s; e += NT) {
+    const int i = e % ks, c = e / ks;
+    double v = tmp[i + c * ks];
+    if (w.col_muscle)
+      for (int q = 0; q < c; ++q) v = fma(tmp[i + q * ks], Tm[q + c * ldT], v);
+    Tk[i + c * ldT] = v;
   }
   __syncthreads();
   if (threadIdx.x == 0) {

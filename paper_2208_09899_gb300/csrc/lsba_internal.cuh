@@ -49,7 +49,7 @@ struct Ctl {
   int n_gram_hist;     // Gram outputs recorded (first cycle)
   int gram_hist_used;  // doubles used in the Gram history buffer
   int gram_hist_cap;
-  int pad;
+  int muscle_syncs;    // syncs of the column muscle in the current cycle
   double est;          // last residual estimate
   double normB;        // ||B||_F
   double tol;
@@ -70,6 +70,8 @@ struct BlockPtrs {
 struct SmallWs {
   int s, m, skel, modification;
   int global_ip;       // 1: global block inner product (each s x s Gram block -> tr/s I)
+  int col_muscle;      // 1: BMGS-SVL/LTS with the MGS-SVL/LTS column muscle
+  double* mus;         // the column muscle's work area: R, T, coefficients, status, partials
   int ldH;             // (m+2)*s
   int ldT;             // (m+2)*s
   int ldR;             // (m+1)*s
@@ -177,6 +179,12 @@ void launch_coef_df(cudaStream_t st, int nin, int s, bool two, const double* coe
 // double-float (coefficients after the other inputs'), two outputs, s = 8,
 // 8 nin <= 256 with nin the digit inputs.  dig_out / dexp_out (optional)
 // receive out1's digit planes, as launch_split_digits would write them.
+// Column muscle MGS-SVL / MGS-LTS (kernels_muscle.cu) on one n x s block in
+// place (mode 0 FP64, 1 double-float, 2 FP32); R, T and the status in `area`.
+#define MUS_PARTS 1024
+size_t muscle_area_doubles(int s);
+void launch_col_muscle(cudaStream_t st, void* X, int mode, int64_t n, int s, bool lts,
+                       double* area, Ctl* ctl, int step, int num_sms);
 bool update_tcs_eligible(int s, int nin, bool two);
 void launch_update_tcs(cudaStream_t st, const unsigned char* dig, const int* dexp, int a,
                        const float2* U, const float2* W, const float2* X, int64_t n, float2* out1,

@@ -23,6 +23,7 @@ SKELETONS = {"bcgs": 0, "bcgs_pip": 1, "bcgsi_ls": 2, "bmgs_icwy": 3, "bmgs_cwy"
 MODIFICATIONS = {"fom": 0, "gmres": 1}
 PRECISIONS = {"fp64": 0, "df": 1, "auto": 2, "fp32_ir": 3}
 INNER_PRODUCTS = {"classical": 0, "global": 1}
+MUSCLES = {"cholqr": 0, "mgs": 1}
 
 EXPORTED = ("lsba_default_options", "lsba_create", "lsba_set_options", "lsba_solve",
             "lsba_solve_host", "lsba_get_stats", "lsba_get_history", "lsba_status_string",
@@ -40,7 +41,7 @@ class Options(C.Structure):
                 ("precision", C.c_int32), ("ir_max_outer", C.c_int32),
                 ("ir_inner_tol", C.c_double), ("cuda_graphs", C.c_int32),
                 ("tensor_cores", C.c_int32), ("inner_product", C.c_int32),
-                ("reserved", C.c_int32 * 1)]
+                ("muscle", C.c_int32)]
 
 
 class Stats(C.Structure):
@@ -210,6 +211,8 @@ class Solver:
                 v = PRECISIONS[v]
             if k == "inner_product" and isinstance(v, str):
                 v = INNER_PRODUCTS[v]
+            if k == "muscle" and isinstance(v, str):
+                v = MUSCLES[v]
             if isinstance(v, bool):
                 v = int(v)
             setattr(self.opt, k, v)

@@ -167,7 +167,8 @@ def _compare_solve(lsba, A, B, m, tol, sk, mod, max_restarts=50, first_cycle_tol
                   record_first_cycle=True, inject_flags=inject,
                   adaptive=bool(kw.get("adaptive_restart", 1)),
                   verify_true_residual=bool(kw.get("verify_true_residual", 1)),
-                  inner_product=kw.get("inner_product", "classical"))
+                  inner_product=kw.get("inner_product", "classical"),
+                  muscle=kw.get("muscle", "cholqr"))
     # Same restart decisions.
     assert hist["cycle_m"] == ref.cycle_m, (hist["cycle_m"], ref.cycle_m)
     assert hist["cycle_flag"] == ref.cycle_flag
@@ -252,6 +253,33 @@ def test_global_inner_product(env, sk, precision):
     for c in range(ref.first_cycle["j"]):
         blk = H[c * s:(c + 1) * s, c * s:(c + 1) * s]
         assert np.allclose(blk, blk[0, 0] * np.eye(s), rtol=0, atol=1e-14 * abs(blk[0, 0]))
+
+
+@pytest.mark.parametrize("precision", ["df", "fp64"])
+@pytest.mark.parametrize("mod", ["gmres", "fom"])
+@pytest.mark.parametrize("sk", ["bmgs_svl", "bmgs_lts"])
+def test_column_muscles(env, sk, mod, precision):
+    """BMGS-SVL / BMGS-LTS with the column muscles MGS-SVL / MGS-LTS (the
+    paper's classical configuration): the oracle's restart log, counters
+    (3s - 2 syncs per muscle call, counted on the device), first-cycle Grams
+    and Hessenberg, and X."""
+    torch, lsba = env
+    A = W.laplacian_2d(40, 37)
+    B = W.gaussian_block(A.n, 4, 3)
+    _compare_solve(lsba, A, B, 8, 1e-10, sk, mod, max_restarts=200, precision=precision,
+                   muscle="mgs")
+
+
+def test_column_muscle_injected_flag_and_invalid_use(env):
+    torch, lsba = env
+    A = W.laplacian_2d(30)
+    B = W.gaussian_block(A.n, 3, 4)
+    _compare_solve(lsba, A, B, 8, 1e-9, "bmgs_lts", "gmres", max_restarts=300, muscle="mgs",
+                   inject_flag_cycle=1, inject_flag_relation=5)
+    # the column muscle belongs to BMGS-SVL/LTS under the classical product
+    for sk, ip in (("bcgsi_ls", "classical"), ("bmgs_svl", "global")):
+        with pytest.raises(lsba.LSBAError):
+            lsba.solve(A, B, 8, 1e-9, sk, device=0, muscle="mgs", inner_product=ip)
 
 
 @pytest.mark.parametrize("s", [1, 3, 5, 16])
