@@ -459,7 +459,7 @@ def main():
     suffix = "_df" if is_df else ""
     roofline = {
         "kernel": {"gram": ("k_gram_df_tcs (stored digits, tensor cores, iterations k >= 2) + "
-                            "k_gram_df_tma (start block, k = 1) + k_gram_reduce_df" if is_df
+                            "k_gram_df_tma (start block, k <= 4) + k_gram_reduce_df" if is_df
                             else "k_gram + k_gram_reduce"),
                    "update": ("k_coef_fold + k_update_df_tcs (tensor cores, iterations k >= 2 and "
                               "the cycle end; also writes the new block's digit planes) + k_coef_df + "

@@ -666,7 +666,9 @@ static void enqueue_cycle(lsba_ctx* h, const lsba_csr* A, const double* Rstart, 
         memset(&R, 0, sizeof(R));
         R.p[0] = h->Ub;
         R.p[1] = h->Wb;
-        if (h->use_tcs && gram_tcs_eligible(s, k, 2)) do_gram_tcs(h, k, n, s, ctl);
+        // The stored-digit Gram has a fixed cost of about 90 us (its per-chunk
+        // chain); below k = 5 the FP32-pipe Gram over the few blocks is faster.
+        if (h->use_tcs && k >= 5 && gram_tcs_eligible(s, k, 2)) do_gram_tcs(h, k, n, s, ctl);
         else do_gram(h, L, k, R, 2, n, s, ctl, 1);
         wait_side(h, k - 1);
         PROF(LSBA_K_SMALL, launch_small_step(st, w, k, 0));
