@@ -890,7 +890,8 @@ GramPlan plan_gram_tcs(int64_t n, int s, int a, int b, int num_sms) {
   const int ma = ma8 > 128 ? ma8 : 128;
   const size_t buf = (size_t)(ma / 8) * DIG_GROUP + 12 * 512 + GTC_THREADS * sizeof(int);
   p.smem = 3 * buf + 10 * sizeof(uint64_t) + 16;
-  int64_t gx = num_sms;
+  // one CTA per SM, one SM left for the small side kernel of the iteration
+  int64_t gx = num_sms > 1 ? num_sms - 1 : 1;
   const int64_t chunks = (n + GTC_KC - 1) / GTC_KC;
   if (gx > chunks) gx = chunks;
   if (gx < 1) gx = 1;

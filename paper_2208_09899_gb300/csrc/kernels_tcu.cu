@@ -121,7 +121,9 @@ __device__ __forceinline__ void ut_ld8(uint32_t taddr, float (&v)[8]) {
   for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-__global__ void __launch_bounds__(UT_THREADS, 2) k_update_df_tcs(const __grid_constant__ UpdTcsArgs u) {
+// MINB CTAs per SM: 3 where the shared memory of three fits (K <= 128), else 2.
+template <int MINB>
+__global__ void __launch_bounds__(UT_THREADS, MINB) k_update_df_tcs(const __grid_constant__ UpdTcsArgs u) {
   if (u.step >= 0 && *(volatile const int*)&u.ctl->update_step != u.step) return;
   extern __shared__ __align__(1024) unsigned char sm[];
   // Shared layout: A buffers [2][UT_SUB blocks][12 KB] | B digit stack | exponents | misc.
@@ -583,7 +585,8 @@ void launch_update_tcs(cudaStream_t st, const unsigned char* dig, const int* dex
   k_coef_fold<<<(f.rows + FOLD_ROWS - 1) / FOLD_ROWS, 128, 0, st>>>(f);
   static std::atomic<unsigned long long> attr_done{0};
   once_per_device(attr_done, [] {
-    cudaFuncSetAttribute(k_update_df_tcs, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    cudaFuncSetAttribute(k_update_df_tcs<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    cudaFuncSetAttribute(k_update_df_tcs<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
   });
   UpdTcsArgs u;
   u.dig = dig;
@@ -607,15 +610,22 @@ void launch_update_tcs(cudaStream_t st, const unsigned char* dig, const int* dex
   u.ctl = ctl;
   u.step = step;
   u.err = err;
-  // Two CTAs per SM, two short of filling the GPU: the SMs left with one CTA
-  // have room for the small side kernel of the same iteration (512 threads x
-  // 64 registers), which then runs beside this pass instead of after it,
-  // where it would hold an SM that the next Gram's persistent grid needs.
+  // Three CTAs per SM where their shared memory fits (228 KB per SM, 1 KB of it
+  // reserved per CTA), else two CTAs per SM, two short of filling the GPU: the
+  // SMs left with one CTA have room for the small side kernel of the same
+  // iteration (512 threads x 64 registers), which then runs beside this pass.
+  // With three per SM the side kernel runs after this pass, on the SMs the next
+  // Gram leaves free.
   const int64_t tiles = (n + 127) / 128;
-  int64_t grid = 2LL * num_sms - 2;
+  const size_t smem = update_tcs_smem(nin);
+  const bool three = 3 * (smem + 1024) <= 228 * 1024;
+  int64_t grid = three ? 3LL * num_sms : 2LL * num_sms - 2;
   if (grid > tiles) grid = tiles;
   if (grid < 1) grid = 1;
-  k_update_df_tcs<<<(unsigned)grid, UT_THREADS, update_tcs_smem(nin), st>>>(u);
+  if (three)
+    k_update_df_tcs<3><<<(unsigned)grid, UT_THREADS, smem, st>>>(u);
+  else
+    k_update_df_tcs<2><<<(unsigned)grid, UT_THREADS, smem, st>>>(u);
 }
 
 }  // namespace lsba
