@@ -76,9 +76,53 @@ __global__ void __launch_bounds__(256) k_spmm_df(int64_t n, const int32_t* __res
   W[row * s + c] = df_value(acc);
 }
 
+// s = 8: one thread per row, all eight columns: the row's nonzeros and column
+// indices are read once, each neighbour row of V arrives as four 16-byte
+// loads, and a warp keeps 2 KB of V rows in flight per nonzero (the
+// per-(row, column) kernel: 256 B).  Every output sums its products in the
+// row's order, as the per-(row, column) kernel does.
+__global__ void __launch_bounds__(256) k_spmm_df8(int64_t n, const int32_t* __restrict__ rowptr,
+                                                  const int32_t* __restrict__ colidx,
+                                                  const float2* __restrict__ vals,
+                                                  const float2* __restrict__ V,
+                                                  float2* __restrict__ W, const Ctl* ctl,
+                                                  int guard) {
+  if (guard && !ctl_active_df(ctl)) return;
+  const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (row >= n) return;
+  const int p0 = rowptr[row], p1 = rowptr[row + 1];
+  dfacc acc[8];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) acc[c] = dfacc{0.f, 0.f};
+  for (int p = p0; p < p1; ++p) {
+    const float2 a = vals[p];
+    const float4* v = reinterpret_cast<const float4*>(V + (int64_t)colidx[p] * 8);
+    float4 q[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) q[i] = v[i];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      df_fma(acc[2 * i], a, make_float2(q[i].x, q[i].y));
+      df_fma(acc[2 * i + 1], a, make_float2(q[i].z, q[i].w));
+    }
+  }
+  float4* w = reinterpret_cast<float4*>(W + row * 8);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const float2 lo = df_value(acc[2 * i]), hi = df_value(acc[2 * i + 1]);
+    w[i] = make_float4(lo.x, lo.y, hi.x, hi.y);
+  }
+}
+
 void launch_spmm_df(cudaStream_t st, int64_t n, const int32_t* rowptr, const int32_t* colidx,
                     const float2* vals, const float2* V, float2* W, int s, const Ctl* ctl,
                     int guard) {
+  if (s == 8) {
+    if (n > 0)
+      k_spmm_df8<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, rowptr, colidx, vals, V, W, ctl,
+                                                              guard);
+    return;
+  }
   const int S2 = next_pow2_df(s);
   const int64_t threads = n * S2;
   if (threads == 0) return;
