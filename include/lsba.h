@@ -250,6 +250,25 @@ int lsba_spmm(lsba_handle h, const lsba_csr* A, const double* d_V, double* d_W, 
 int lsba_gram(lsba_handle h, const double* d_L, int a, const double* d_R, int b,
               int64_t n, int s, double* d_G);
 
+/* Autotuner of the kernel choices of the double-float lagged skeletons
+ * (BCGSI+LS, BMGS-CWY/ICWY) at s = 8, where two kernels can run the same step:
+ * for every iteration k = 2..m+1 of a cycle it times, on the handle's stream
+ * with CUDA events (one warm-up and three runs each, on zeroed n x 8 operands),
+ * the stored-digit tensor-core Gram of Alg. 7 line 10 against the FP32-pipe
+ * Gram, and the tensor-core basis update (Alg. 7 lines 16-17) with two against
+ * three CTAs per SM.  Later solves on this handle with the same n and s take
+ * the faster choice at each k (otherwise fixed rules: the tensor-core Gram
+ * from k = 5, three update CTAs per SM wherever they fit).  The two Gram
+ * kernels round differently (both to 48-bit accuracy), so tuned and untuned
+ * solves agree to rounding, not bit for bit.  The workspace is (re)allocated
+ * for (n, 8, m); the basis contents are overwritten.
+ * gram_choice[k] (k < cap): 1 tensor-core Gram, 0 FP32-pipe Gram, -1 no choice;
+ * update_ctas[k]: 2 or 3, 0 no choice.  Host arrays of cap entries (may be
+ * NULL when cap = 0).  Returns LSBA_OK, LSBA_INVALID_ARG (s != 8, n < 1, m < 1
+ * or m too large), LSBA_OUT_OF_MEMORY, LSBA_DEVICE_TIMEOUT or LSBA_CUDA_ERROR. */
+int lsba_autotune(lsba_handle h, int64_t n, int s, int m, int8_t* gram_choice,
+                  int8_t* update_ctas, int cap);
+
 /* The same G as lsba_gram, computed by the double-float Gram kernels of the
  * solver (the block inner product of every skeleton, Sec. 2): L and R are
  * converted to hi + lo FP32 pairs on the device, G is returned in FP64.

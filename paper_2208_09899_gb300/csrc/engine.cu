@@ -88,6 +88,12 @@ struct lsba_ctx {
   uint64_t graph_clock = 0;
   std::vector<uint8_t> side_recorded;  // side events recorded in the current cycle
   bool own_stream = false;     // stream created by the handle (caller passed NULL)
+  // lsba_autotune: measured kernel choices per lagged iteration k for one (n, s)
+  int64_t tune_n = 0;
+  int tune_s = 0;
+  std::vector<int8_t> tune_gram;   // 1: stored-digit tensor-core Gram, 0: FP32-pipe Gram
+  std::vector<int8_t> tune_minb;   // CTAs per SM of the tensor-core update (2 or 3)
+  int tune_gen = 0;
 };
 
 // The launch sequence of one restart cycle is fixed by these values; a cycle
@@ -668,7 +674,9 @@ static void enqueue_cycle(lsba_ctx* h, const lsba_csr* A, const double* Rstart, 
         R.p[1] = h->Wb;
         // The stored-digit Gram has a fixed cost of about 90 us (its per-chunk
         // chain); below k = 5 the FP32-pipe Gram over the few blocks is faster.
-        if (h->use_tcs && k >= 5 && gram_tcs_eligible(s, k, 2)) do_gram_tcs(h, k, n, s, ctl);
+        const bool tuned = h->tune_n == n && h->tune_s == s && k < (int)h->tune_gram.size();
+        if (h->use_tcs && gram_tcs_eligible(s, k, 2) && (tuned ? h->tune_gram[k] == 1 : k >= 5))
+          do_gram_tcs(h, k, n, s, ctl);
         else do_gram(h, L, k, R, 2, n, s, ctl, 1);
         wait_side(h, k - 1);
         PROF(LSBA_K_SMALL, launch_small_step(st, w, k, 0));
@@ -685,7 +693,7 @@ static void enqueue_cycle(lsba_ctx* h, const lsba_csr* A, const double* Rstart, 
                             w.tri1, w.coef2, w.chain, skel == SK_LS ? w.tri2 : nullptr, h->cdf,
                             h->dig + (size_t)(k - 1) * digit_block_bytes(n, s),
                             h->dexp + (size_t)(k - 1) * digit_exp_count(n, s), ctl, k,
-                            &h->d_ctl->error, h->num_sms);
+                            &h->d_ctl->error, h->num_sms, tuned ? h->tune_minb[k] : 0);
           prof_end(h);
         } else {
           do_update(h, in, k + 1, n, s, Vk, w.coef1, w.tri1, h->Ub, w.coef2, w.chain,
@@ -862,6 +870,7 @@ static int run_cycle_body(lsba_handle h, const lsba_csr* A, const double* Rstart
     key.tensor_cores = h->opt.tensor_cores;
     key.global_ip = h->ws.global_ip;
     key.col_muscle = h->ws.col_muscle;
+    key.pad = h->tune_gen;
     key.ws_gen = h->ws_gen;
     for (auto& e : h->graphs)
       if (e.key == key) g = &e;
@@ -1409,6 +1418,98 @@ int lsba_gram(lsba_handle h, const double* d_L, int a, const double* d_R, int b,
   launch_gram(h->stream, p, L, a, R, b, n, s, h->partials, d_G, nullptr, 0);
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(h->stream));
+  return LSBA_OK;
+}
+
+// Measured kernel choices for the double-float lagged skeletons at s = 8: for
+// every iteration k = 2..m+1, the stored-digit tensor-core Gram against the
+// FP32-pipe Gram of [V_1..V_{k-1}, U]^T [U, W], and the tensor-core update with
+// two against three CTAs per SM where three fit.  Each candidate runs once to
+// warm up and three times under CUDA events on the handle's stream, on zeroed
+// operands of the solve's shape.
+int lsba_autotune(lsba_handle h, int64_t n, int s, int m, int8_t* gram_choice,
+                  int8_t* update_ctas, int cap) {
+  if (!h || n < 1 || s != 8 || m < 1 || (int64_t)(m + 1) * s > LSBA_MAX_MS || m + 3 > LSBA_MAXB ||
+      cap < 0 || (cap > 0 && (!gram_choice || !update_ctas)))
+    return LSBA_INVALID_ARG;
+  CK(cudaSetDevice(h->device));
+  int rc = ensure_ws(h, n, s, m);
+  if (rc != LSBA_OK) return rc;
+  if ((rc = ensure_digits(h)) != LSBA_OK) return rc;
+  h->mode = MODE_DF;
+  cudaStream_t st = h->stream;
+  const size_t blk = (size_t)n * s;
+  CK(cudaMemsetAsync(h->basis, 0, sizeof(double) * blk * (m + 1), st));
+  CK(cudaMemsetAsync(h->Ub, 0, sizeof(double) * blk, st));
+  CK(cudaMemsetAsync(h->Wb, 0, sizeof(double) * blk, st));
+  CK(cudaMemsetAsync(h->dig, 0, (size_t)(m + 1) * digit_block_bytes(n, s), st));
+  CK(cudaMemsetAsync(h->dexp, 0, sizeof(int) * (size_t)(m + 1) * digit_exp_count(n, s), st));
+  Ctl* c = h->h_ctl;
+  c->active = 1;
+  c->update_step = -1;
+  c->error = 0;
+  if ((rc = push_ctl(h)) != LSBA_OK) return rc;
+  Ctl* ctl = h->d_ctl;
+  const SmallWs& w = h->ws;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  auto timed = [&](auto&& run) -> float {
+    run();
+    cudaEventRecord(e0, st);
+    for (int r = 0; r < 3; ++r) run();
+    cudaEventRecord(e1, st);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    return ms;
+  };
+  std::vector<int8_t> tg(m + 2, -1), tm(m + 2, 0);
+  for (int k = 2; k <= m + 1; ++k) {
+    BlockPtrs L = basis_list(h, n, s, k - 1);
+    L.p[k - 1] = h->Ub;
+    BlockPtrs R;
+    memset(&R, 0, sizeof(R));
+    R.p[0] = h->Ub;
+    R.p[1] = h->Wb;
+    if (gram_tcs_eligible(s, k, 2)) {
+      const float t_tc = timed([&] { do_gram_tcs(h, k, n, s, ctl); });
+      const float t_fp = timed([&] { do_gram(h, L, k, R, 2, n, s, ctl, 1); });
+      tg[k] = t_tc < t_fp ? 1 : 0;
+    }
+    if (update_tcs_eligible(s, k + 1, true)) {
+      double* Vk = h->basis + (size_t)(k - 1) * blk;
+      auto upd = [&](int minb) {
+        launch_update_tcs(st, h->dig, h->dexp, k - 1, (const float2*)h->Ub, (const float2*)h->Wb,
+                          nullptr, n, (float2*)Vk, (float2*)h->Ub, w.coef1, nullptr, w.coef2,
+                          nullptr, nullptr, h->cdf,
+                          h->dig + (size_t)(k - 1) * digit_block_bytes(n, s),
+                          h->dexp + (size_t)(k - 1) * digit_exp_count(n, s), ctl, -1,
+                          &h->d_ctl->error, h->num_sms, minb);
+      };
+      if (3 * (update_tcs_smem(k + 1) + 1024) <= 228 * 1024) {
+        const float t2 = timed([&] { upd(2); });
+        const float t3 = timed([&] { upd(0); });
+        tm[k] = t2 < t3 ? 2 : 3;
+      } else {
+        tm[k] = 2;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  CK(cudaGetLastError());
+  if ((rc = pull_ctl(h)) != LSBA_OK) return rc;
+  if (c->error) return LSBA_DEVICE_TIMEOUT;
+  h->tune_gram = tg;
+  h->tune_minb = tm;
+  h->tune_n = n;
+  h->tune_s = s;
+  ++h->tune_gen;
+  for (int k = 0; k < cap; ++k) {
+    gram_choice[k] = k < (int)tg.size() ? tg[k] : -1;
+    update_ctas[k] = k < (int)tm.size() ? tm[k] : 0;
+  }
   return LSBA_OK;
 }
 

@@ -568,7 +568,7 @@ void launch_update_tcs(cudaStream_t st, const unsigned char* dig, const int* dex
                        const float2* U, const float2* W, const float2* X, int64_t n, float2* out1,
                        float2* out2, const double* coef1, const double* tri1, const double* coef2,
                        const double* chain, const double* tri2, float2* cdf, unsigned char* dig_out,
-                       int* dexp_out, const Ctl* ctl, int step, int* err, int num_sms) {
+                       int* dexp_out, const Ctl* ctl, int step, int* err, int num_sms, int minb) {
   const int nsplit = U ? 2 : 0;
   const int nin = a + nsplit;
   const int ncoef = nin + (X ? 1 : 0);
@@ -618,7 +618,7 @@ void launch_update_tcs(cudaStream_t st, const unsigned char* dig, const int* dex
   // Gram leaves free.
   const int64_t tiles = (n + 127) / 128;
   const size_t smem = update_tcs_smem(nin);
-  const bool three = 3 * (smem + 1024) <= 228 * 1024;
+  const bool three = 3 * (smem + 1024) <= 228 * 1024 && minb != 2;
   int64_t grid = three ? 3LL * num_sms : 2LL * num_sms - 2;
   if (grid > tiles) grid = tiles;
   if (grid < 1) grid = 1;

@@ -190,7 +190,9 @@ void launch_update_tcs(cudaStream_t st, const unsigned char* dig, const int* dex
                        const float2* U, const float2* W, const float2* X, int64_t n, float2* out1,
                        float2* out2, const double* coef1, const double* tri1, const double* coef2,
                        const double* chain, const double* tri2, float2* cdf, unsigned char* dig_out,
-                       int* dexp_out, const Ctl* ctl, int step, int* err, int num_sms);
+                       int* dexp_out, const Ctl* ctl, int step, int* err, int num_sms,
+                       int minb = 0);   // CTAs per SM: 0 = 3 where they fit, else 2; 2 forces 2
+size_t update_tcs_smem(int nin);
 GramPlan plan_gram_tcs(int64_t n, int s, int a, int b, int num_sms);
 void launch_gram_tcs(cudaStream_t st, const GramPlan& p, const unsigned char* dig,
                      const int* dexp, int64_t n, int s, int a, const float2* U, const float2* W,

@@ -27,6 +27,7 @@ MUSCLES = {"cholqr": 0, "mgs": 1}
 
 EXPORTED = ("lsba_default_options", "lsba_create", "lsba_set_options", "lsba_solve",
             "lsba_solve_host", "lsba_get_stats", "lsba_get_history", "lsba_status_string",
+            "lsba_autotune",
             "lsba_destroy", "lsba_spmm", "lsba_gram", "lsba_combine", "lsba_get_profile",
             "lsba_reset_profile", "lsba_gram_noalloc", "lsba_release_workspace",
             "lsba_workspace_bytes", "lsba_gram_df")
@@ -86,6 +87,7 @@ def load(path: str = LIB_PATH):
     lib.lsba_set_options.argtypes = [vp, C.POINTER(Options)]
     lib.lsba_solve.argtypes = [vp, C.POINTER(CSRDesc), vp, vp, i32, i32, f64, i32]
     lib.lsba_solve_host.argtypes = [vp, i64, i64, vp, vp, vp, vp, vp, i32, i32, f64, i32]
+    lib.lsba_autotune.argtypes = [vp, i64, i32, i32, vp, vp, i32]
     lib.lsba_get_stats.argtypes = [vp, C.POINTER(Stats)]
     lib.lsba_get_history.argtypes = [vp, C.POINTER(History)]
     lib.lsba_status_string.argtypes = [i32]
@@ -270,6 +272,17 @@ class Solver:
                                       tol, SKELETONS[skeleton])
         _check(st, (LSBA_OK, LSBA_NOT_CONVERGED, LSBA_BREAKDOWN))
         return X, st
+
+    def autotune(self, n: int, s: int, m: int) -> dict:
+        """Time the alternative kernels of the double-float lagged skeletons
+        (s = 8) for every iteration of an m-step cycle on n rows; later solves
+        with the same n and s use the faster ones.  Returns {k: (tensor-core
+        Gram?, update CTAs per SM)} for the iterations with a choice."""
+        g = (C.c_int8 * (m + 2))()
+        u = (C.c_int8 * (m + 2))()
+        _check(self.lib.lsba_autotune(self.h, n, s, m, g, u, m + 2))
+        return {k: (g[k] == 1 if g[k] >= 0 else None, u[k] or None) for k in range(2, m + 2)
+                if g[k] >= 0 or u[k]}
 
     def stats(self) -> dict:
         s = Stats()

@@ -498,3 +498,29 @@ def test_tensor_core_gram_in_solves(env, sk, s, m):
     B = W.gaussian_block(A.n, s, 31)
     _compare_solve(lsba, A, B, m, 1e-10, sk, "gmres", max_restarts=200, precision="df",
                    tensor_cores=2)
+
+
+def test_autotune_then_solve(env):
+    """The kernel autotuner (double-float lagged skeletons, s = 8) returns a
+    choice for every iteration of the cycle, and a solve on the tuned handle
+    still matches the oracle (restart log, counters, X)."""
+    torch, lsba = env
+    A = W.laplacian_2d(64, 60)
+    B = W.gaussian_block(A.n, 8, 5)
+    m = 10
+    sv = lsba.Solver(0, modification="gmres", max_restarts=300, record_history=1)
+    ch = sv.autotune(A.n, 8, m)
+    assert set(ch) == set(range(2, m + 2))
+    for g, u in ch.values():
+        assert g in (True, False) and u in (2, 3)
+    X, code = sv.solve_host(A, B, m, 1e-10, "bcgsi_ls")
+    st, h = sv.stats(), sv.history()
+    ref = O.solve(A, B, m, 1e-10, "bcgsi_ls", modification="gmres", max_restarts=300)
+    assert code == 0 and st["status"] == ref.status
+    assert h["cycle_m"] == ref.cycle_m
+    assert (st["cycles"], st["steps"], st["a_calls"], st["syncs"]) == \
+        (ref.cycles, ref.steps, ref.a_calls, ref.syncs)
+    assert _rel(X, ref.X) <= TOL_X
+    with pytest.raises(lsba.LSBAError):
+        sv.autotune(A.n, 4, m)
+    sv.close()
