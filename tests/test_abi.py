@@ -69,3 +69,39 @@ def test_binding_enums_match_header():
               for m in re.finditer(r"LSBA_(\w+)\s*=\s*(\d+)", body)}
     assert header == lsba.SKELETONS
     assert "bmgs" in header and "bcgsi_ls" in header
+
+
+def _header_struct(name):
+    """(type, field) pairs of `typedef struct { ... } name;` in lsba.h."""
+    src = open(os.path.join(ROOT, "include", "lsba.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    body = re.search(r"typedef struct \{([^}]*)\}\s*" + name + ";", src).group(1)
+    out = []
+    for decl in body.split(";"):
+        decl = decl.strip()
+        if not decl:
+            continue
+        m = re.match(r"(.+?)\s*(\**)\s*(\w+)(\[\d+\])?$", decl)
+        out.append((m.group(1).strip() + m.group(2), m.group(3), m.group(4)))
+    return out
+
+
+def test_binding_structs_match_header():
+    """lsba_options, lsba_stats and lsba_history: the ctypes structures of the
+    binding have the header's fields, in order, with the same sizes (a
+    mismatch would shift every later option silently)."""
+    import ctypes as C
+    from paper_2208_09899_gb300 import lsba
+    for cname, pystruct in (("lsba_options", lsba.Options), ("lsba_stats", lsba.Stats),
+                            ("lsba_history", lsba.History)):
+        hdr = _header_struct(cname)
+        py = pystruct._fields_
+        assert [f for _, f, _ in hdr] == [f for f, _ in py], cname
+        for (ctype, field, arr), (pf, pt) in zip(hdr, py):
+            if ctype.endswith("*"):
+                assert C.sizeof(pt) == C.sizeof(C.c_void_p), (cname, field)
+            else:
+                base = ctype.replace("const ", "")
+                n = int(arr[1:-1]) if arr else 1
+                size = {"int32_t": 4, "int64_t": 8, "double": 8}[base] * n
+                assert C.sizeof(pt) == size, (cname, field)
