@@ -37,10 +37,6 @@ METRIC = "BGMRES time-to-1e-10 relres & Arnoldi HBM GB/s vs FP64 plain; serve p5
 WORKLOAD = "lapl512_s8"
 M = 20
 SKELETON = "bcgsi_ls"
-FP64_PEAK_TFLOPS = 1.25   # nominal FP64 (DFMA) rate of GB300; the probe measured 1.00
-# Double-float: one FP64-accurate FMA = 13 FP32-pipe instructions (df.cuh), so the
-# ALU peak in FP64-equivalent flops is 152 SMs x 128 FP32 lanes x 2.07 GHz / 13 x 2.
-DF_PEAK_TFLOPS = 152 * 128 * 2.07e9 / 13 * 2 / 1e12
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 
 
@@ -468,7 +464,6 @@ def main():
     achieved_tflops = fl[dom] / (dom_ms_per_step * 1e-3) / 1e12
     achieved_gbs = by[dom] / (dom_ms_per_step * 1e-3) / 1e9
     is_df = st0["precision"] == 1
-    peak = DF_PEAK_TFLOPS if is_df else FP64_PEAK_TFLOPS
     suffix = "_df" if is_df else ""
     roofline = {
         "kernel": {"gram": ("k_gram_df_tcs (stored digits, tensor cores, iterations k >= 2) + "
@@ -479,17 +474,13 @@ def main():
                               "k_update_df_row (start block, k = 1) + k_split_digits (start block)"
                               if is_df else "k_update"),
                    "spmm": f"k_spmm{suffix}"}[dom],
-        "bound": "alu", "achieved": achieved_tflops, "peak": peak, "unit": "TFLOP/s",
-        "frac": achieved_tflops / peak,
+        "bound": "hbm", "achieved": achieved_gbs, "peak": hbm, "unit": "GB/s",
+        "frac": achieved_gbs / hbm, "peak_source": f"{hbm_src} (copy bandwidth)",
         "traffic": captured_traffic(dom + ("_df" if is_df else ""), by[dom] / max(dom_launches, 1)),
-        "peak_source": ("derived: double-float FMA = 13 FP32 ops; 152 SMs x 128 lanes x 2.07 GHz"
-                        " / 13 x 2 flop (FP64-equivalent)") if is_df else
-                       "nominal FP64 DFMA rate (1.25 TFLOP/s); the FP64 probe measured 1.00",
         "launches_per_step": dom_launches,
         "algorithmic_bytes_per_launch": by[dom] / max(dom_launches, 1),
         "algorithmic_flops_per_launch": fl[dom] / max(dom_launches, 1),
-        "hbm_achieved_gbs": achieved_gbs, "hbm_peak_gbs": hbm, "hbm_frac": achieved_gbs / hbm,
-        "hbm_peak_source": hbm_src,
+        "fp64_equivalent_tflops": achieved_tflops,
     }
     kernels = {k: {"ms_per_step": prof[k][0] / args.steps, "launches_per_step": prof[k][1] / args.steps,
                    "share": prof[k][0] / max(sum(v[0] for v in prof.values()), 1e-12)}
@@ -595,8 +586,8 @@ def main():
             "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64 (double-float: hi+lo FP32 pairs, compensated products on the FP32 pipes)"
-                     if st0["precision"] == 1 else "f64",
+            "dtype": "df48 (double-float: hi+lo FP32 pairs, 48-bit significand, FP32 exponent "
+                     "range; narrower than FP64)" if st0["precision"] == 1 else "f64",
             "data": "synthetic (seeded numpy inputs shaped like the paper's lapl_2d)",
             "config": {"workload": f"{WORKLOAD}: 2D 5-point Laplacian 512x512 (n=262144), B n x 8 "
                                    f"N(0,1), BGMRES(m={M}), BCGSI+LS, one restart cycle per step",

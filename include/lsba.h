@@ -294,10 +294,10 @@ int lsba_combine(lsba_handle h, const double* d_in, int nin, int64_t n, int s,
 
 /* ---- allocation-free variant ------------------------------------------------
  * The paper has no counterpart to this entry point; it exists for callers that
- * cannot allocate device memory: code running while a CUDA graph is captured
- * (cudaMalloc/cudaFree are not allowed there), serving loops that must not
- * pay for an allocation or the synchronisation cudaFree implies, and hosts
- * that fix the device memory footprint at start-up.
+ * cannot allocate device memory: serving loops that must not pay for an
+ * allocation or the synchronisation cudaFree implies, and hosts that fix the
+ * device memory footprint at start-up (a budget shared with other processes,
+ * or an allocator that owns the device's memory).
  *
  * lsba_gram_noalloc computes the same G = [L_1..L_a]^T [R_1..R_b] as lsba_gram
  * (same arguments and layouts) without a handle and without allocating: no
@@ -306,8 +306,15 @@ int lsba_combine(lsba_handle h, const double* d_in, int nin, int64_t n, int s,
  * LSBA_GRAM_NOALLOC_SCRATCH_DOUBLES doubles (512 KiB), which every GPU that loads
  * the library holds until the process exits.
  *   - Limit: (a*s)*(b*s) <= LSBA_GRAM_NOALLOC_SCRATCH_DOUBLES, otherwise
- *     LSBA_INVALID_ARG is returned and nothing is launched; when the usual
- *     number of row partitions would not fit, fewer are used.
+ *     LSBA_INVALID_ARG is returned and nothing is launched.  The partial sums
+ *     take one row of (a*s)*(b*s) doubles per row partition (one CTA each), so
+ *     at most LSBA_GRAM_NOALLOC_SCRATCH_DOUBLES / ((a*s)*(b*s)) partitions fit:
+ *     where lsba_gram would use more, this call uses fewer CTAs and runs at
+ *     lower bandwidth than lsba_gram (e.g. a*s = 168, b*s = 16: 24 CTAs).
+ *   - Errors: if a CUDA error is already pending when the call starts (left
+ *     by earlier work of the caller), it returns LSBA_CUDA_ERROR without
+ *     launching and leaves that error pending; an error of its own launch is
+ *     cleared and reported as LSBA_CUDA_ERROR.
  *   - Device: the current CUDA device.  The first call on a device looks up the
  *     array's device address (cudaGetSymbolAddress) and caches it; make that
  *     first call before any stream capture.

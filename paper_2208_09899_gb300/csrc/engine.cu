@@ -44,6 +44,8 @@ struct lsba_ctx {
   size_t ismall_cap = 0;
   Ctl* d_ctl = nullptr;
   Ctl* h_ctl = nullptr;        // pinned mirror
+  unsigned long long* d_range = nullptr;   // magnitude ranges of A and B (k_absrange)
+  unsigned long long* h_range = nullptr;   // pinned mirror
   SmallWs ws;
   // host-buffer solve
   int32_t* hA_rowptr = nullptr;
@@ -783,9 +785,14 @@ int lsba_create(lsba_handle* out, int device, void* cuda_stream, const lsba_opti
   else lsba_default_options(&h->opt);
   cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, device);
   if (cudaMalloc(&h->d_ctl, sizeof(Ctl)) != cudaSuccess ||
-      cudaMallocHost(&h->h_ctl, sizeof(Ctl)) != cudaSuccess) {
+      cudaMallocHost(&h->h_ctl, sizeof(Ctl)) != cudaSuccess ||
+      cudaMalloc(&h->d_range, 4 * sizeof(unsigned long long)) != cudaSuccess ||
+      cudaMallocHost(&h->h_range, 4 * sizeof(unsigned long long)) != cudaSuccess) {
     cudaGetLastError();
     cudaFree(h->d_ctl);
+    cudaFree(h->d_range);
+    cudaFreeHost(h->h_ctl);
+    cudaFreeHost(h->h_range);
     if (h->own_stream) cudaStreamDestroy(h->stream);
     delete h;
     return LSBA_OUT_OF_MEMORY;
@@ -811,6 +818,8 @@ int lsba_destroy(lsba_handle h) {
   free_ws(h);
   cudaFree(h->d_ctl);
   cudaFreeHost(h->h_ctl);
+  cudaFree(h->d_range);
+  cudaFreeHost(h->h_range);
   ws_free(h, h->hA_rowptr);
   ws_free(h, h->hA_colidx);
   ws_free(h, h->hA_vals);
@@ -1084,6 +1093,40 @@ static void enqueue_fp64_residual(lsba_ctx* h, const lsba_csr* A, const double* 
   h->mode = mode;
 }
 
+// Magnitude ranges of A's values and of B (one pass each, one host sync):
+// amax, amin (smallest nonzero) of A and bmax of B; false if either holds a
+// non-finite value.
+static int input_ranges(lsba_ctx* h, const lsba_csr* A, const double* d_B, int64_t count_b,
+                        double* amax, double* amin, double* bmax, bool* finite) {
+  cudaStream_t st = h->stream;
+  unsigned long long init[4] = {0ull, ~0ull, 0ull, ~0ull};
+  memcpy(h->h_range, init, sizeof(init));
+  CK(cudaMemcpyAsync(h->d_range, h->h_range, sizeof(init), cudaMemcpyHostToDevice, st));
+  launch_absrange(st, A->nnz, A->d_vals, h->d_range, h->num_sms);
+  launch_absrange(st, count_b, d_B, h->d_range + 2, h->num_sms);
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(h->h_range, h->d_range, sizeof(init), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  const unsigned long long inf_bits = 0x7FF0000000000000ull;
+  *finite = h->h_range[0] < inf_bits && h->h_range[2] < inf_bits;
+  double v[4];
+  memcpy(v, h->h_range, sizeof(v));
+  *amax = v[0];
+  *amin = h->h_range[1] == ~0ull ? 0.0 : v[1];
+  *bmax = v[2];
+  return LSBA_OK;
+}
+
+// The power of two 2^p applied to an input whose largest magnitude is x: none
+// (p = 0) while x is in [2^-32, 2^32], where every Gram of the solve stays far
+// inside FP32's exponent range (for n up to 2^30 and s <= 32), else p with
+// x 2^p in [1, 2).  p = 0 for x = 0 or non-finite x.
+static int unit_scale_exp(double x) {
+  if (!(x > 0.0) || !std::isfinite(x)) return 0;
+  if (x >= std::ldexp(1.0, -32) && x <= std::ldexp(1.0, 32)) return 0;
+  return -std::ilogb(x);
+}
+
 static int solve_impl(lsba_handle h, const lsba_csr* A, const double* d_B, double* d_X, int s, int m,
                       double tol, lsba_skeleton skel_in) {
   auto t0 = std::chrono::steady_clock::now();
@@ -1123,6 +1166,29 @@ static int solve_impl(lsba_handle h, const lsba_csr* A, const double* d_B, doubl
            (prec == LSBA_PREC_AUTO && lagged(skel)))
     h->mode = MODE_DF;
   else h->mode = MODE_FP64;
+  // Low-precision modes keep FP32's exponent range (2^-126 .. 2^128): A and B
+  // whose largest magnitudes lie outside [2^-32, 2^32] are scaled by powers of
+  // two (exact) to magnitudes near 1, and X is scaled back (the first cycle's
+  // recorded Grams and Hessenberg are then those of the scaled problem).
+  // Under "auto", double-float is taken only if
+  // A's nonzero magnitudes then stay above 2^-90 (the low words of double-float
+  // values keep their bits down to about 2^-102) and the inputs are finite;
+  // otherwise the solve runs in FP64.
+  int pA = 0, pB = 0;
+  if (h->mode != MODE_FP64) {
+    double amax = 0, amin = 0, bmax = 0;
+    bool finite = true;
+    if ((rc = input_ranges(h, A, d_B, (int64_t)blk, &amax, &amin, &bmax, &finite)) !=
+        LSBA_OK)
+      return h->stats.status = rc;
+    pA = unit_scale_exp(amax);
+    pB = unit_scale_exp(bmax);
+    const bool spread_ok = amin == 0.0 || std::ldexp(amin, pA) >= std::ldexp(1.0, -90);
+    if (prec == LSBA_PREC_AUTO && (!finite || !spread_ok)) {
+      h->mode = MODE_FP64;
+      pA = pB = 0;
+    }
+  }
   h->stats.precision = ir ? LSBA_PREC_FP32_IR : h->mode == MODE_DF ? LSBA_PREC_DF : LSBA_PREC_FP64;
   // Tensor-core Gram on stored digit planes: double-float lagged skeletons, s = 8.
   h->use_tcs = h->mode == MODE_DF && s == 8 && h->opt.tensor_cores != 0 && lagged(skel);
@@ -1153,15 +1219,18 @@ static int solve_impl(lsba_handle h, const lsba_csr* A, const double* d_B, doubl
     double* Xw = d_X;
     if (h->mode == MODE_DF) {
       if ((rc = ensure_lowprec_A(h, A)) != LSBA_OK) return S.status = rc;
-      PROF(LSBA_K_UPDATE, launch_to_df(st, A->nnz, A->d_vals, h->A_df));
-      PROF(LSBA_K_UPDATE, launch_to_df(st, n * s, d_B, (float2*)h->Bdf));
+      PROF(LSBA_K_UPDATE, launch_to_df(st, A->nnz, A->d_vals, h->A_df, std::ldexp(1.0, pA)));
+      PROF(LSBA_K_UPDATE, launch_to_df(st, n * s, d_B, (float2*)h->Bdf, std::ldexp(1.0, pB)));
       Bw = h->Bdf;
       Xw = h->Xdf;
     }
     if ((rc = run_cycles(h, A, Bw, Xw, n, s, m, tol, h->opt.verify_true_residual != 0, true,
                          &status)) != LSBA_OK)
       return S.status = rc;
-    if (h->mode == MODE_DF) PROF(LSBA_K_UPDATE, launch_from_df(st, n * s, (const float2*)Xw, d_X));
+    // (2^pA A) X' = 2^pB B, so X = 2^(pA - pB) X'
+    if (h->mode == MODE_DF)
+      PROF(LSBA_K_UPDATE,
+           launch_from_df(st, n * s, (const float2*)Xw, d_X, std::ldexp(1.0, pA - pB)));
     // True residual of the returned X (FP64).
     enqueue_fp64_residual(h, A, d_B, d_X, n, s, true);
     if ((rc = pull_ctl(h)) != LSBA_OK) return S.status = rc;
@@ -1170,7 +1239,7 @@ static int solve_impl(lsba_handle h, const lsba_csr* A, const double* d_B, doubl
     // FP64 iterative refinement around an FP32 inner BGMRES/BFOM:
     //   R = B - A X (FP64);  solve A D = R in FP32 to ir_inner_tol;  X += D (FP64).
     if ((rc = ensure_lowprec_A(h, A)) != LSBA_OK) return S.status = rc;
-    PROF(LSBA_K_UPDATE, launch_to_f32(st, A->nnz, A->d_vals, (float*)h->A_df));
+    PROF(LSBA_K_UPDATE, launch_to_f32(st, A->nnz, A->d_vals, (float*)h->A_df, std::ldexp(1.0, pA)));
     CK(cudaMemsetAsync(d_X, 0, sizeof(double) * blk, st));
     const double inner_tol = h->opt.ir_inner_tol > 0 ? h->opt.ir_inner_tol : 1e-5;
     const int max_outer = h->opt.ir_max_outer > 0 ? h->opt.ir_max_outer : 10;
@@ -1186,14 +1255,18 @@ static int solve_impl(lsba_handle h, const lsba_csr* A, const double* d_B, doubl
       if (it == max_outer || !(c->relres_true < prev)) break;
       prev = c->relres_true;
       S.ir_outer += 1;
-      // Inner FP32 solve of A D = R (R in Ub as FP64 -> FP32 into Bdf).
-      PROF(LSBA_K_UPDATE, launch_to_f32(st, n * s, h->Ub, (float*)h->Bdf));
+      // Inner FP32 solve of (2^pA A) D' = 2^pR R, R scaled as A is (by its
+      // Frobenius norm) when outside [2^-32, 2^32] (R in Ub as FP64 -> FP32
+      // into Bdf); then D = 2^(pA - pR) D'.
+      const int pR = unit_scale_exp(c->relres_true * c->outer_normB);
+      PROF(LSBA_K_UPDATE, launch_to_f32(st, n * s, h->Ub, (float*)h->Bdf, std::ldexp(1.0, pR)));
       int inner_status = 0;
       if ((rc = run_cycles(h, A, h->Bdf, h->Xdf, n, s, m, inner_tol, false, it == 0,
                            &inner_status)) != LSBA_OK)
         return S.status = rc;
       if (inner_status == LSBA_BREAKDOWN) break;
-      PROF(LSBA_K_UPDATE, launch_add_f32(st, n * s, (const float*)h->Xdf, d_X));
+      PROF(LSBA_K_UPDATE,
+           launch_add_f32(st, n * s, (const float*)h->Xdf, d_X, std::ldexp(1.0, pA - pR)));
     }
   }
   S.status = status;

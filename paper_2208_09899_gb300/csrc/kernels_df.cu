@@ -28,13 +28,41 @@ static inline int next_pow2_df(int s) {
 }
 
 // ----------------------------------------------------------------- conversions
-__global__ void k_to_df(int64_t count, const double* __restrict__ in, float2* __restrict__ out) {
+// scale is a power of two (exact unless a value leaves FP64's range).
+__global__ void k_to_df(int64_t count, const double* __restrict__ in, float2* __restrict__ out,
+                        double scale) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < count) out[i] = df_from_double(in[i]);
+  if (i < count) out[i] = df_from_double(in[i] * scale);
 }
-__global__ void k_from_df(int64_t count, const float2* __restrict__ in, double* __restrict__ out) {
+__global__ void k_from_df(int64_t count, const float2* __restrict__ in, double* __restrict__ out,
+                          double scale) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < count) out[i] = df_to_double(in[i]);
+  if (i < count) out[i] = df_to_double(in[i]) * scale;
+}
+// Magnitude range of an FP64 array: out[0] = max |x|, out[1] = min |x| over the
+// nonzero entries, as the bit patterns of the non-negative doubles (which order
+// like unsigned integers; a NaN orders above +inf, so a non-finite input shows
+// as out[0] >= the bits of +inf).  out must hold {0, ~0} before the launch.
+__global__ void __launch_bounds__(256) k_absrange(int64_t count, const double* __restrict__ in,
+                                                  unsigned long long* __restrict__ out) {
+  unsigned long long mx = 0ull, mn = ~0ull;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(in[i]) & 0x7FFFFFFFFFFFFFFFull;
+    mx = b > mx ? b : mx;
+    if (b != 0ull) mn = b < mn ? b : mn;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long a = __shfl_xor_sync(0xffffffffu, mx, o);
+    const unsigned long long c = __shfl_xor_sync(0xffffffffu, mn, o);
+    mx = a > mx ? a : mx;
+    mn = c < mn ? c : mn;
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(&out[0], mx);
+    atomicMin(&out[1], mn);
+  }
 }
 // R = B - W (double-float)
 __global__ void k_sub_df(int64_t count, const float2* __restrict__ B, const float2* __restrict__ W,
@@ -48,11 +76,18 @@ __global__ void k_sub_df(int64_t count, const float2* __restrict__ B, const floa
   }
 }
 
-void launch_to_df(cudaStream_t st, int64_t count, const double* in, float2* out) {
-  if (count > 0) k_to_df<<<(unsigned)((count + 255) / 256), 256, 0, st>>>(count, in, out);
+void launch_to_df(cudaStream_t st, int64_t count, const double* in, float2* out, double scale) {
+  if (count > 0) k_to_df<<<(unsigned)((count + 255) / 256), 256, 0, st>>>(count, in, out, scale);
 }
-void launch_from_df(cudaStream_t st, int64_t count, const float2* in, double* out) {
-  if (count > 0) k_from_df<<<(unsigned)((count + 255) / 256), 256, 0, st>>>(count, in, out);
+void launch_from_df(cudaStream_t st, int64_t count, const float2* in, double* out, double scale) {
+  if (count > 0) k_from_df<<<(unsigned)((count + 255) / 256), 256, 0, st>>>(count, in, out, scale);
+}
+void launch_absrange(cudaStream_t st, int64_t count, const double* in, unsigned long long* out,
+                     int num_sms) {
+  if (count <= 0) return;
+  int64_t grid = (count + 255) / 256;
+  if (grid > 4LL * num_sms) grid = 4LL * num_sms;
+  k_absrange<<<(unsigned)grid, 256, 0, st>>>(count, in, out);
 }
 void launch_sub_df(cudaStream_t st, int64_t count, const float2* B, const float2* W, float2* R) {
   if (count > 0) k_sub_df<<<(unsigned)((count + 255) / 256), 256, 0, st>>>(count, B, W, R);

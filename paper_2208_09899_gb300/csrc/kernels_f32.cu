@@ -18,20 +18,24 @@ namespace lsba {
 static __device__ __forceinline__ int ctl_on(const Ctl* c) { return *(volatile const int*)&c->active; }
 
 // ----------------------------------------------------------------- conversions
-__global__ void k_to_f32(int64_t count, const double* __restrict__ in, float* __restrict__ out) {
+// scale is a power of two: the inner solver works on a scaled copy whose
+// largest entries are near 1, so FP32's exponent range is not left.
+__global__ void k_to_f32(int64_t count, const double* __restrict__ in, float* __restrict__ out,
+                         double scale) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < count) out[i] = __double2float_rn(in[i]);
+  if (i < count) out[i] = __double2float_rn(in[i] * scale);
 }
-// X += D (D in FP32): the FP64 solution update of iterative refinement.
-__global__ void k_add_f32(int64_t count, const float* __restrict__ d, double* __restrict__ x) {
+// X += scale D (D in FP32): the FP64 solution update of iterative refinement.
+__global__ void k_add_f32(int64_t count, const float* __restrict__ d, double* __restrict__ x,
+                          double scale) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < count) x[i] += (double)d[i];
+  if (i < count) x[i] += (double)d[i] * scale;
 }
-void launch_to_f32(cudaStream_t st, int64_t count, const double* in, float* out) {
-  if (count > 0) k_to_f32<<<(unsigned)((count + 255) / 256), 256, 0, st>>>(count, in, out);
+void launch_to_f32(cudaStream_t st, int64_t count, const double* in, float* out, double scale) {
+  if (count > 0) k_to_f32<<<(unsigned)((count + 255) / 256), 256, 0, st>>>(count, in, out, scale);
 }
-void launch_add_f32(cudaStream_t st, int64_t count, const float* d, double* x) {
-  if (count > 0) k_add_f32<<<(unsigned)((count + 255) / 256), 256, 0, st>>>(count, d, x);
+void launch_add_f32(cudaStream_t st, int64_t count, const float* d, double* x, double scale) {
+  if (count > 0) k_add_f32<<<(unsigned)((count + 255) / 256), 256, 0, st>>>(count, d, x, scale);
 }
 
 // ----------------------------------------------------------------- SpMM

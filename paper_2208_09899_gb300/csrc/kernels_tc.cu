@@ -452,8 +452,6 @@ void launch_gram_tc(cudaStream_t st, const GramPlan& p, const BlockPtrs& L, int 
                     const Ctl* ctl, int guard, int* err) {
   static std::atomic<unsigned long long> attr_done{0};
   once_per_device(attr_done, [] {
-    cudaFuncSetAttribute(k_gram_df_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
-    cudaFuncSetAttribute(k_gram_df_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
     cudaFuncSetAttribute(k_gram_df_tc<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
   });
   GramTcArgs g;
@@ -470,11 +468,10 @@ void launch_gram_tc(cudaStream_t st, const GramPlan& p, const BlockPtrs& L, int 
   g.ctl = ctl;
   g.guard = guard;
   g.err = err;
-  // Threads per column: 4 (8 rows each) up to 64 columns, 2 up to 128, else 1.
-  const int cols = g.as + g.bs;
-  if (cols <= GTC_THREADS / 4) k_gram_df_tc<1><<<p.grid_x, GTC_THREADS, p.smem, st>>>(g);
-  else if (cols <= GTC_THREADS / 2) k_gram_df_tc<2><<<p.grid_x, GTC_THREADS, p.smem, st>>>(g);
-  else k_gram_df_tc<4><<<p.grid_x, GTC_THREADS, p.smem, st>>>(g);
+  // One thread per column (all 32 rows of a chunk) for every shape: the
+  // variants with two or four threads per column were removed after an
+  // unexplained launch failure in a build that ran one of them in solves.
+  k_gram_df_tc<4><<<p.grid_x, GTC_THREADS, p.smem, st>>>(g);
 }
 
 // ============================================================================

@@ -148,8 +148,14 @@ void launch_update(cudaStream_t st, const BlockPtrs& in, int nin, int64_t n, int
                    const Ctl* ctl, int step);
 
 // ---- double-float (FP64-accurate, FP32-pipe) variants; block vectors are float2 (hi, lo) ----
-void launch_to_df(cudaStream_t st, int64_t count, const double* in, float2* out);
-void launch_from_df(cudaStream_t st, int64_t count, const float2* in, double* out);
+// in * scale -> double-float, and back (scale a power of two).
+void launch_to_df(cudaStream_t st, int64_t count, const double* in, float2* out, double scale = 1.0);
+void launch_from_df(cudaStream_t st, int64_t count, const float2* in, double* out,
+                    double scale = 1.0);
+// out[0] = bits of max |in|, out[1] = bits of the smallest nonzero |in| (out
+// preset to {0, ~0}); a non-finite entry gives out[0] >= bits of +inf.
+void launch_absrange(cudaStream_t st, int64_t count, const double* in, unsigned long long* out,
+                     int num_sms);
 void launch_sub_df(cudaStream_t st, int64_t count, const float2* B, const float2* W, float2* R);
 void launch_spmm_df(cudaStream_t st, int64_t n, const int32_t* rowptr, const int32_t* colidx,
                     const float2* vals, const float2* V, float2* W, int s, const Ctl* ctl, int guard);
@@ -212,8 +218,8 @@ void launch_update_df(cudaStream_t st, const BlockPtrs& in, int nin, int64_t n, 
                       int step, int num_sms);
 
 // ---- FP32 variants (inner solver of FP64 iterative refinement); block vectors are float ----
-void launch_to_f32(cudaStream_t st, int64_t count, const double* in, float* out);
-void launch_add_f32(cudaStream_t st, int64_t count, const float* d, double* x);
+void launch_to_f32(cudaStream_t st, int64_t count, const double* in, float* out, double scale = 1.0);
+void launch_add_f32(cudaStream_t st, int64_t count, const float* d, double* x, double scale = 1.0);
 void launch_spmm_f32(cudaStream_t st, int64_t n, const int32_t* rowptr, const int32_t* colidx,
                      const float* vals, const float* V, float* W, int s, const Ctl* ctl, int guard);
 GramPlan plan_gram_f32(int64_t n, int s, int a, int b, int num_sms);

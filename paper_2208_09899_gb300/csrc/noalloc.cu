@@ -3,13 +3,12 @@
 // lsba_gram needs a scratch buffer for the per-CTA partial sums of its
 // two-stage reduction, and takes it from the handle's workspace, which is
 // allocated with cudaMalloc the first time it is needed.  Some callers cannot
-// allow that: code that runs while a CUDA graph is being captured (where
-// cudaMalloc and cudaFree are not permitted), latency-critical serving loops in
-// which an allocation (and the device-wide synchronisation cudaFree implies)
-// is not acceptable, and hosts that must keep the device's memory footprint
-// fixed after start-up.  lsba_gram_noalloc gives them the same result with no
-// handle and no allocation: its scratch is a fixed array in the library's own
-// device memory.
+// allow that: latency-critical serving loops in which an allocation (and the
+// device-wide synchronisation cudaFree implies) is not acceptable, and hosts
+// that must keep the device's memory footprint fixed after start-up (a memory
+// budget shared with other processes, or an allocator that owns all device
+// memory).  lsba_gram_noalloc gives them the same result with no handle and no
+// allocation: its scratch is a fixed array in the library's own device memory.
 #include <mutex>
 
 #include "../../include/lsba.h"
@@ -84,7 +83,14 @@ extern "C" int lsba_gram_noalloc(const double* d_L, int a, const double* d_R, in
   for (int i = 0; i < LSBA_MAXB; ++i) L.p[i] = R.p[i] = nullptr;
   for (int i = 0; i < a; ++i) L.p[i] = d_L + (size_t)i * n * s;
   for (int i = 0; i < b; ++i) R.p[i] = d_R + (size_t)i * n * s;
+  // An error left pending by earlier, unrelated work is the caller's: report
+  // it without launching and without clearing it.  After the launch, an error
+  // is this launch's own, so it is read and cleared.
+  if (cudaPeekAtLastError() != cudaSuccess) return LSBA_CUDA_ERROR;
   launch_gram((cudaStream_t)cuda_stream, p, L, a, R, b, n, s, scratch, d_G, nullptr, 0);
-  if (cudaGetLastError() != cudaSuccess) return LSBA_CUDA_ERROR;
+  if (cudaPeekAtLastError() != cudaSuccess) {
+    cudaGetLastError();
+    return LSBA_CUDA_ERROR;
+  }
   return LSBA_OK;
 }

@@ -524,3 +524,80 @@ def test_autotune_then_solve(env):
     with pytest.raises(lsba.LSBAError):
         sv.autotune(A.n, 4, m)
     sv.close()
+
+
+def _scaled_csr(A, factor):
+    return W._from_coo(A.n, *_coo(A), A.vals * factor)
+
+
+def _coo(A):
+    rows = np.repeat(np.arange(A.n), np.diff(A.rowptr))
+    return rows, A.colidx
+
+
+@pytest.mark.parametrize("a_scale,b_scale,precision", [
+    (1e-40, 1.0, "df"), (1e39, 1.0, "df"), (1.0, 2.0 ** 120, "df"), (1.0, 2.0 ** -120, "df"),
+    (1e-40, 2.0 ** -120, "auto"), (1e39, 2.0 ** 120, "auto")])
+def test_double_float_outside_fp32_range(env, a_scale, b_scale, precision):
+    """Double-float keeps FP32's exponent range; the solver scales A and B by
+    powers of two so that their largest magnitudes are near 1 and scales X
+    back, so inputs far outside FP32's range (A x 1e-40 or 1e39, B x 2^+-120)
+    give the oracle's restart log, counters, estimates and X (the first-cycle
+    Grams are those of the scaled problem and are not compared here)."""
+    torch, lsba = env
+    A = _scaled_csr(W.laplacian_2d(30, 27), a_scale)
+    B = W.gaussian_block(A.n, 4, 9) * b_scale
+    X, st, hist = lsba.solve(A, B, 8, 1e-10, "bcgsi_ls", device=0, max_restarts=300,
+                             record_history=True, precision=precision)
+    ref = O.solve(A, B, 8, 1e-10, "bcgsi_ls", modification="gmres", max_restarts=300)
+    assert st["precision"] == lsba.PRECISIONS["df"]
+    assert hist["cycle_m"] == ref.cycle_m
+    assert (st["status"], st["cycles"], st["steps"], st["a_calls"], st["syncs"]) == \
+        (ref.status, ref.cycles, ref.steps, ref.a_calls, ref.syncs)
+    est_ref = np.array([e for (_, _, e) in ref.est_history])
+    ok = np.isfinite(est_ref)
+    assert np.allclose(hist["est"][ok], est_ref[ok], rtol=1e-6, atol=0)
+    assert np.all(np.isfinite(X)) and _rel(X, ref.X) <= TOL_X
+    assert st["relres_true"] <= 1e-10 and ref.relres_true <= 1e-10
+
+
+@pytest.mark.parametrize("a_scale,b_scale", [(1e-40, 2.0 ** -120), (1e39, 2.0 ** 120)])
+def test_fp32_inner_refinement_outside_fp32_range(env, a_scale, b_scale):
+    """The FP32 inner solver works on A and on each refinement residual scaled
+    by powers of two to magnitudes near 1: relative residual 1e-10 and X within
+    1e-8 of the FP64 oracle for A x 1e-40 / 1e39 and B x 2^-120 / 2^120."""
+    torch, lsba = env
+    A0, B0 = W.workload("tridiag2000_s4", 0)
+    A = _scaled_csr(A0, a_scale)
+    B = B0 * b_scale
+    X, st, _ = lsba.solve(A, B, 10, 1e-10, "bcgsi_ls", device=0, precision="fp32_ir",
+                          max_restarts=50)
+    ref = O.solve(A, B, 10, 1e-10, "bcgsi_ls", modification="gmres", max_restarts=50)
+    assert st["precision"] == lsba.PRECISIONS["fp32_ir"]
+    assert st["status"] == lsba.LSBA_OK and st["relres_true"] <= 1e-10
+    assert _rel(X, ref.X) <= TOL_X
+
+
+def test_auto_takes_fp64_for_wide_or_nonfinite_inputs(env):
+    """Under precision "auto", a matrix whose nonzero magnitudes span more than
+    2^90 (which double-float cannot hold relative to its largest entry) runs in
+    FP64 and matches the oracle at the usual bars; a non-finite B also goes to
+    FP64, whose CholQR of B flags (breakdown)."""
+    torch, lsba = env
+    A = W.laplacian_2d(20, 19)
+    rows, cols = _coo(A)
+    vals = A.vals.copy()
+    off = np.nonzero(rows != cols)[0][:6]
+    vals[off] = -1e-30
+    # keep A symmetric: the mirrored entries get the same value
+    for p in off:
+        q = np.nonzero((rows == cols[p]) & (cols == rows[p]))[0]
+        vals[q] = -1e-30
+    A = W._from_coo(A.n, rows, cols, vals)
+    B = W.gaussian_block(A.n, 4, 2)
+    _, st, _, _ = _compare_solve(lsba, A, B, 8, 1e-10, "bcgsi_ls", "gmres", max_restarts=300)
+    assert st["precision"] == lsba.PRECISIONS["fp64"]
+    Bn = B.copy()
+    Bn[3, 1] = np.nan
+    _, st, _ = lsba.solve(A, Bn, 8, 1e-10, "bcgsi_ls", device=0)
+    assert st["precision"] == lsba.PRECISIONS["fp64"] and st["status"] == lsba.LSBA_BREAKDOWN

@@ -1,7 +1,8 @@
 """lsba_gram_noalloc: the block inner product for callers that cannot allocate
-device memory (e.g. inside CUDA graph capture, or serving loops with a fixed
-memory footprint).  It must give the same G as lsba_gram, on consecutive calls
-that reuse its fixed scratch array, and refuse sizes beyond that array."""
+device memory (serving loops that may not pay for an allocation, hosts that
+keep the device's memory footprint fixed).  It must give the same G as
+lsba_gram and as a NumPy FP64 product, on consecutive calls that reuse its
+fixed scratch array, and refuse sizes beyond that array."""
 import ctypes as C
 
 import numpy as np
@@ -44,6 +45,12 @@ def test_noalloc_matches_gram_on_consecutive_calls(env, calls):
         torch.cuda.synchronize()
         g, gr = G.cpu().numpy(), G_ref.cpu().numpy()
         assert np.linalg.norm(g - gr) <= 1e-13 * np.linalg.norm(gr)
+        # independent of the kernels both entry points share: the FP64 product
+        # of the stacked blocks, computed on the host
+        Lh = np.hstack(list(L.cpu().numpy()))
+        Rh = np.hstack(list(R.cpu().numpy()))
+        gn = Lh.T @ Rh
+        assert np.linalg.norm(g - gn) <= 1e-13 * np.linalg.norm(gn)
 
 
 def test_noalloc_rejects_oversized_output(env):
