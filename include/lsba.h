@@ -153,6 +153,8 @@ typedef struct {
   double solve_ms;         /* wall time of lsba_solve                            */
   int32_t precision;       /* precision the solve ran in (LSBA_PREC_*)           */
   int32_t ir_outer;        /* FP32_IR: refinement steps (inner solves) taken     */
+  int32_t tensor_cores;    /* 1: the Gram and update passes of the Arnoldi steps
+                              ran on the tensor-core digit kernels               */
 } lsba_stats;
 
 /* Host-side copies kept by the handle when record_history = 1; valid until the
@@ -291,6 +293,30 @@ int lsba_gram_df(lsba_handle h, const double* d_L, int a, const double* d_R, int
  *   is C_i); d_T: s x s upper-triangular (row-major) or NULL for no solve. */
 int lsba_combine(lsba_handle h, const double* d_in, int nin, int64_t n, int s,
                  const double* d_C, const double* d_T, double* d_out);
+
+/* FP64 on the tensor cores (exact digit products; the Gram and update passes
+ * the solver runs for BCGSI+LS and BMGS-CWY/ICWY at s = 8 in FP64).
+ * Every FP64 value is split, relative to the maximum of its (128-row tile,
+ * column) group, into seven 8-bit digits carrying 53 bits (F = trunc(x
+ * 2^(54 - E)) for max |x| < 2^E); the bf16 tensor cores sum the digit products
+ * by level exactly in FP32 over windows of at most 128 products, and each
+ * window's levels 0..7 are combined in 64-bit integers and added into FP64
+ * accumulators.  Error per product term about 2^-53 (max|x| |y| + |x| max|y|).
+ *
+ * lsba_gram_fp64tc: G = [L_1..L_a]^T [R_1..R_b], the Gram of lsba_gram (same
+ *   layouts), s = 8, a*s <= 256, b <= 2, a + b <= 24; deterministic (fixed
+ *   reduction order).
+ * lsba_combine_fp64tc: out1 = ([in_1..in_nin] C1) T^{-1} (d_T: s x s upper,
+ *   row-major, or NULL) and, if d_out2, out2 = [in_1..in_nin] C2; C1, C2 are
+ *   nin*s x s row-major (block i of rows multiplies in_i); s = 8, nin <= 24.
+ * Both return LSBA_OK, LSBA_INVALID_ARG (shape outside these limits),
+ * LSBA_OUT_OF_MEMORY, LSBA_CUDA_ERROR or LSBA_DEVICE_TIMEOUT (a bounded wait
+ * inside the kernel gave up). */
+int lsba_gram_fp64tc(lsba_handle h, const double* d_L, int a, const double* d_R, int b,
+                     int64_t n, int s, double* d_G);
+int lsba_combine_fp64tc(lsba_handle h, const double* d_in, int nin, int64_t n, int s,
+                        const double* d_C1, const double* d_T, const double* d_C2,
+                        double* d_out1, double* d_out2);
 
 /* ---- allocation-free variant ------------------------------------------------
  * The paper has no counterpart to this entry point; it exists for callers that

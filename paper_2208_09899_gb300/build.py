@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "liblsba.so")
 SOURCES = ["engine.cu", "kernels_big.cu", "kernels_small.cu", "kernels_df.cu", "kernels_f32.cu",
-           "kernels_tc.cu", "kernels_tcu.cu", "kernels_muscle.cu", "noalloc.cu"]
+           "kernels_tc.cu", "kernels_tcu.cu", "kernels_f64tc.cu", "kernels_muscle.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

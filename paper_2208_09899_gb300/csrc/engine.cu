@@ -82,6 +82,16 @@ struct lsba_ctx {
   unsigned char* dig = nullptr;
   int* dexp = nullptr;
   bool use_tcs = false;
+  // FP64 on the tensor cores (exact digit products, kernels_f64tc.cu): lagged
+  // skeletons, s = 8.  Per-(tile, column) exponents of the basis blocks
+  // (block i at fexp + i * f64tc_exp_count(n, s)), of U, W and the cycle's
+  // start block, and the folded FP64 update coefficients.
+  bool use_ftc = false;
+  int* fexp = nullptr;
+  int* fexp_U = nullptr;
+  int* fexp_W = nullptr;
+  int* fexp_R0 = nullptr;
+  double* cf64 = nullptr;
   double prof_ms[LSBA_K_NCLASS] = {0, 0, 0, 0};
   int64_t prof_n[LSBA_K_NCLASS] = {0, 0, 0, 0};
   // captured restart cycles (see run_cycle_body)
@@ -185,6 +195,10 @@ static void free_ws(lsba_ctx* h) {
   ws_free(h, h->dexp);
   h->dig = nullptr;
   h->dexp = nullptr;
+  ws_free(h, h->fexp);
+  ws_free(h, h->cf64);
+  h->fexp = h->fexp_U = h->fexp_W = h->fexp_R0 = nullptr;
+  h->cf64 = nullptr;
   ws_free(h, h->basis);
   ws_free(h, h->Wb);
   ws_free(h, h->Ub);
@@ -220,6 +234,11 @@ static size_t max_partials(int64_t n, int s, int mmax, int sms, size_t* qmax_out
       }
       if (gram_tcs_eligible(s, a, b)) {
         GramPlan pt = plan_gram_tcs(n, s, a, b, sms);
+        v = (size_t)pt.grid_x * pt.q;
+        if (v > best) best = v;
+      }
+      if (gram_f64tc_eligible(s, a, b, false)) {
+        GramPlan pt = plan_gram_f64tc(n, s, a, b, sms);
         v = (size_t)pt.grid_x * pt.q;
         if (v > best) best = v;
       }
@@ -421,6 +440,27 @@ static int ensure_digits(lsba_ctx* h) {
   return LSBA_OK;
 }
 
+// Exponent arrays and FP64 coefficient buffer of the FP64 tensor-core path
+// (allocated on first use, within the workspace's capacity).
+static int ensure_f64tc(lsba_ctx* h) {
+  if (h->fexp) return LSBA_OK;
+  const size_t ec = f64tc_exp_count(h->cap_n, h->cap_s);
+  const size_t nb = (size_t)h->cap_m + 1 + 3;
+  if (ws_alloc(h, &h->fexp, sizeof(int) * nb * ec) != cudaSuccess ||
+      ws_alloc(h, &h->cf64, sizeof(double) * 2 * 8 * (size_t)(h->cap_m + 3) * 8) != cudaSuccess) {
+    cudaGetLastError();
+    ws_free(h, h->fexp);
+    ws_free(h, h->cf64);
+    h->fexp = nullptr;
+    h->cf64 = nullptr;
+    return LSBA_OUT_OF_MEMORY;
+  }
+  h->fexp_U = h->fexp + (size_t)(h->cap_m + 1) * ec;
+  h->fexp_W = h->fexp_U + ec;
+  h->fexp_R0 = h->fexp_W + ec;
+  return LSBA_OK;
+}
+
 static BlockPtrs basis_list(const lsba_ctx* h, int64_t n, int s, int count) {
   BlockPtrs p;
   memset(&p, 0, sizeof(p));
@@ -518,6 +558,35 @@ static void split_basis(lsba_ctx* h, int i, int64_t n, int s, const Ctl* ctl, in
   prof_end(h);
 }
 
+// FP64 tensor-core passes.  Block i of the basis and its exponents:
+static const int* basis_exp(const lsba_ctx* h, int64_t n, int s, int i) {
+  return h->fexp + (size_t)i * f64tc_exp_count(n, s);
+}
+static void do_block_exp(lsba_ctx* h, const double* V, int* ex, int64_t n, int s, const Ctl* ctl,
+                         int guard) {
+  prof_begin(h, LSBA_K_SPMM);
+  launch_block_exp(h->stream, V, n, s, ex, ctl, guard);
+  prof_end(h);
+}
+static void do_gram_ftc(lsba_ctx* h, const double* const* L, const int* const* Le, int a,
+                        const double* const* R, const int* const* Re, int b, bool shared, int64_t n,
+                        int s, const Ctl* ctl, int guard) {
+  prof_begin(h, LSBA_K_GRAM);
+  GramPlan p = plan_gram_f64tc(n, s, a, b, h->num_sms);
+  launch_gram_f64tc(h->stream, p, L, Le, a, R, Re, b, shared, n, h->partials, h->Gbuf, ctl, guard,
+                    &h->d_ctl->error);
+  prof_end(h);
+}
+static void do_update_ftc(lsba_ctx* h, const double* const* in, const int* const* ein, int nin,
+                          const double* X, int64_t n, double* out1, int* e1, double* out2, int* e2,
+                          const double* coef1, const double* tri1, const double* coef2,
+                          const double* chain, const double* tri2, const Ctl* ctl, int step) {
+  prof_begin(h, LSBA_K_UPDATE);
+  launch_update_f64tc(h->stream, in, ein, nin, X, n, out1, e1, out2, e2, coef1, tri1, coef2, chain,
+                      tri2, h->cf64, ctl, step, &h->d_ctl->error, h->num_sms);
+  prof_end(h);
+}
+
 // After the small kernel of loop iteration k: run its side kernel on the side
 // stream (it overlaps the next iteration's SpMM and Gram).  The next small
 // kernel, and the end of the batch, wait for it.
@@ -535,6 +604,69 @@ static void wait_side(lsba_ctx* h, int k) {
   if (k >= 1 && h->side_recorded[k]) cudaStreamWaitEvent(h->stream, h->ev_side[k], 0);
 }
 
+// One cycle of a lagged skeleton (Alg. 6, 7) on the FP64 tensor-core passes
+// (s = 8): CholQR of R_start, iteration 1, iterations k = 2..kmax.  The same
+// launches as the generic path, with every block's per-tile exponents written
+// after the pass that writes the block.
+static void enqueue_cycle_ftc(lsba_ctx* h, const lsba_csr* A, const double* Rstart, int64_t n,
+                              int s, int kmax, int start_flags) {
+  cudaStream_t st = h->stream;
+  const SmallWs& w = h->ws;
+  const int skel = w.skel;
+  Ctl* ctl = h->d_ctl;
+  const size_t blk = (size_t)n * s;
+  const double* L[LSBA_MAXB];
+  const int* Le[LSBA_MAXB];
+  const double* R[2];
+  const int* Re[2];
+  do_block_exp(h, Rstart, h->fexp_R0, n, s, ctl, 0);
+  L[0] = Rstart;
+  Le[0] = h->fexp_R0;
+  do_gram_ftc(h, L, Le, 1, L, Le, 1, true, n, s, ctl, 0);
+  PROF(LSBA_K_SMALL, launch_small_start(st, w, start_flags));
+  do_update_ftc(h, L, Le, 1, nullptr, n, h->basis, h->fexp, nullptr, nullptr, w.coef1, w.tri1,
+                nullptr, nullptr, nullptr, ctl, 0);
+  for (int k = 1; k <= kmax; ++k) {
+    const double* U = (k == 1) ? h->basis : h->Ub;
+    const int* Ue = (k == 1) ? h->fexp : h->fexp_U;
+    do_spmm(h, A, U, h->Wb, s, ctl, 1);
+    do_block_exp(h, h->Wb, h->fexp_W, n, s, ctl, 1);
+    if (k == 1) {
+      L[0] = h->basis;
+      Le[0] = h->fexp;
+      R[0] = h->Wb;
+      Re[0] = h->fexp_W;
+      do_gram_ftc(h, L, Le, 1, R, Re, 1, false, n, s, ctl, 1);
+      PROF(LSBA_K_SMALL, launch_small_step(st, w, 1, 0));
+      L[1] = h->Wb;
+      Le[1] = h->fexp_W;
+      do_update_ftc(h, L, Le, 2, nullptr, n, h->Ub, h->fexp_U, nullptr, nullptr, w.coef1, nullptr,
+                    nullptr, nullptr, nullptr, ctl, 1);
+    } else {
+      for (int i = 0; i < k - 1; ++i) {
+        L[i] = h->basis + (size_t)i * blk;
+        Le[i] = basis_exp(h, n, s, i);
+      }
+      L[k - 1] = h->Ub;
+      Le[k - 1] = h->fexp_U;
+      R[0] = h->Ub;
+      Re[0] = h->fexp_U;
+      R[1] = h->Wb;
+      Re[1] = h->fexp_W;
+      do_gram_ftc(h, L, Le, k, R, Re, 2, true, n, s, ctl, 1);
+      wait_side(h, k - 1);
+      PROF(LSBA_K_SMALL, launch_small_step(st, w, k, 0));
+      enqueue_side(h, k);
+      L[k] = h->Wb;
+      Le[k] = h->fexp_W;
+      do_update_ftc(h, L, Le, k + 1, nullptr, n, h->basis + (size_t)(k - 1) * blk,
+                    h->fexp + (size_t)(k - 1) * f64tc_exp_count(n, s), h->Ub, h->fexp_U, w.coef1,
+                    w.tri1, w.coef2, w.chain, skel == SK_LS ? w.tri2 : nullptr, ctl, k);
+    }
+  }
+  wait_side(h, kmax);
+}
+
 // Enqueue the CholQR of R_start and every loop iteration of one cycle.
 static void enqueue_cycle(lsba_ctx* h, const lsba_csr* A, const double* Rstart, int64_t n, int s,
                           int m_cur, int start_flags) {
@@ -543,6 +675,10 @@ static void enqueue_cycle(lsba_ctx* h, const lsba_csr* A, const double* Rstart, 
   const int skel = w.skel;
   Ctl* ctl = h->d_ctl;
   h->side_recorded.assign(h->ev_side.size(), 0);
+  if (h->use_ftc) {
+    enqueue_cycle_ftc(h, A, Rstart, n, s, m_cur + 1, start_flags);
+    return;
+  }
   BlockPtrs one;
   memset(&one, 0, sizeof(one));
   one.p[0] = Rstart;
@@ -1016,7 +1152,17 @@ static int run_cycles(lsba_handle h, const lsba_csr* A, const double* Bw, double
     }
     // Cycle end: X += V_j Xi C, U = V_{j+1} [M; -H], C <- c C.
     PROF(LSBA_K_SMALL, launch_small_end(st, w));
-    if (h->use_tcs && update_tcs_eligible(s, j + 1, true)) {
+    if (h->use_ftc) {
+      // on the FP64 tensor-core update; X's own term in FP64
+      const double* L[LSBA_MAXB];
+      const int* Le[LSBA_MAXB];
+      for (int i = 0; i <= j; ++i) {
+        L[i] = h->basis + (size_t)i * n * s;
+        Le[i] = h->fexp + (size_t)i * f64tc_exp_count(n, s);
+      }
+      do_update_ftc(h, L, Le, j + 1, Xw, n, Xw, nullptr, h->Ub, h->fexp_U, w.coef1, nullptr,
+                    w.coef2, nullptr, nullptr, h->d_ctl, LSBA_END_STEP);
+    } else if (h->use_tcs && update_tcs_eligible(s, j + 1, true)) {
       // on the stored digit planes of V_1..V_{j+1}; X's own term in double-float
       prof_begin(h, LSBA_K_UPDATE);
       launch_update_tcs(st, h->dig, h->dexp, j + 1, nullptr, nullptr, (const float2*)Xw, n,
@@ -1193,6 +1339,12 @@ static int solve_impl(lsba_handle h, const lsba_csr* A, const double* d_B, doubl
   // Tensor-core Gram on stored digit planes: double-float lagged skeletons, s = 8.
   h->use_tcs = h->mode == MODE_DF && s == 8 && h->opt.tensor_cores != 0 && lagged(skel);
   if (h->use_tcs && ensure_digits(h) != LSBA_OK) h->use_tcs = false;
+  // FP64 on the tensor cores: lagged skeletons, s = 8, m <= 22 (classical inner
+  // product and CholQR, the paths whose passes it covers).
+  h->use_ftc = h->mode == MODE_FP64 && s == 8 && h->opt.tensor_cores != 0 && lagged(skel) &&
+               gram_f64tc_eligible(s, m + 1, 2, true) && update_f64tc_eligible(s, m + 2);
+  if (h->use_ftc && ensure_f64tc(h) != LSBA_OK) h->use_ftc = false;
+  h->stats.tensor_cores = (h->use_tcs || h->use_ftc) ? 1 : 0;
 
   Ctl* c = h->h_ctl;
   const int hist_cap = c->hist_cap, gram_cap = c->gram_hist_cap;
@@ -1401,8 +1553,12 @@ int64_t lsba_workspace_bytes(int64_t n, int64_t nnz, int s, int m) {
   bytes += (int64_t)((partials + qmax) * sizeof(double));
   bytes += (int64_t)(coef_df_count(m + 3, s, true) * sizeof(float2));
   bytes += (int64_t)((2 * L.hist_cap + 2 * (m + 4)) * sizeof(int));
-  if (s == 8)  // stored digit planes of the basis (tensor-core Gram)
+  if (s == 8) {  // stored digit planes of the basis (double-float tensor-core Gram)
     bytes += (int64_t)((m + 1) * (digit_block_bytes(n, s) + sizeof(int) * digit_exp_count(n, s)));
+    // exponents and FP64 coefficients of the FP64 tensor-core passes
+    bytes += (int64_t)(sizeof(int) * (size_t)(m + 4) * f64tc_exp_count(n, s) +
+                       sizeof(double) * 2 * 8 * (size_t)(m + 3) * 8);
+  }
   return bytes;
 }
 
@@ -1662,6 +1818,97 @@ int lsba_gram_df(lsba_handle h, const double* d_L, int a, const double* d_R, int
   prof_collect(h);
   err = h->h_ctl->error;
   return err ? LSBA_DEVICE_TIMEOUT : LSBA_OK;
+}
+
+int lsba_gram_fp64tc(lsba_handle h, const double* d_L, int a, const double* d_R, int b, int64_t n,
+                     int s, double* d_G) {
+  if (!h || !d_L || !d_R || !d_G || n < 1 || !gram_f64tc_eligible(s, a, b, false))
+    return LSBA_INVALID_ARG;
+  CK(cudaSetDevice(h->device));
+  cudaStream_t st = h->stream;
+  GramPlan p = plan_gram_f64tc(n, s, a, b, h->num_sms);
+  const size_t need = (size_t)p.grid_x * p.q;
+  if (need > h->partials_cap) {
+    ws_free(h, h->partials);
+    h->partials = nullptr;
+    h->partials_cap = 0;
+    if (ws_alloc(h, &h->partials, sizeof(double) * need) != cudaSuccess) {
+      cudaGetLastError();
+      return LSBA_OUT_OF_MEMORY;
+    }
+    h->partials_cap = need;
+  }
+  const size_t ec = f64tc_exp_count(n, s);
+  int* ex = nullptr;
+  if (ws_alloc(h, &ex, sizeof(int) * ec * (a + b)) != cudaSuccess) {
+    cudaGetLastError();
+    return LSBA_OUT_OF_MEMORY;
+  }
+  const double* L[LSBA_MAXB];
+  const int* Le[LSBA_MAXB];
+  const double* R[2];
+  const int* Re[2];
+  for (int i = 0; i < a + b; ++i) {
+    const double* blk = i < a ? d_L + (size_t)i * n * s : d_R + (size_t)(i - a) * n * s;
+    launch_block_exp(st, blk, n, s, ex + (size_t)i * ec, nullptr, 0);
+    if (i < a) {
+      L[i] = blk;
+      Le[i] = ex + (size_t)i * ec;
+    } else {
+      R[i - a] = blk;
+      Re[i - a] = ex + (size_t)i * ec;
+    }
+  }
+  CK(cudaMemsetAsync(&h->d_ctl->error, 0, sizeof(int), st));
+  prof_begin(h, LSBA_K_GRAM);
+  launch_gram_f64tc(st, p, L, Le, a, R, Re, b, false, n, h->partials, d_G, nullptr, 0,
+                    &h->d_ctl->error);
+  prof_end(h);
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(&h->h_ctl->error, &h->d_ctl->error, sizeof(int), cudaMemcpyDeviceToHost, st));
+  ws_free(h, ex);
+  CK(cudaStreamSynchronize(st));
+  prof_collect(h);
+  return h->h_ctl->error ? LSBA_DEVICE_TIMEOUT : LSBA_OK;
+}
+
+int lsba_combine_fp64tc(lsba_handle h, const double* d_in, int nin, int64_t n, int s,
+                        const double* d_C1, const double* d_T, const double* d_C2, double* d_out1,
+                        double* d_out2) {
+  if (!h || !d_in || !d_C1 || !d_out1 || n < 1 || !update_f64tc_eligible(s, nin) ||
+      (d_out2 && !d_C2))
+    return LSBA_INVALID_ARG;
+  CK(cudaSetDevice(h->device));
+  cudaStream_t st = h->stream;
+  const size_t ec = f64tc_exp_count(n, s);
+  int* ex = nullptr;
+  double* cf = nullptr;
+  if (ws_alloc(h, &ex, sizeof(int) * ec * nin) != cudaSuccess ||
+      ws_alloc(h, &cf, sizeof(double) * 2 * 8 * (size_t)nin * 8) != cudaSuccess) {
+    cudaGetLastError();
+    ws_free(h, ex);
+    ws_free(h, cf);
+    return LSBA_OUT_OF_MEMORY;
+  }
+  const double* in[LSBA_MAXB];
+  const int* ein[LSBA_MAXB];
+  for (int i = 0; i < nin; ++i) {
+    in[i] = d_in + (size_t)i * n * s;
+    ein[i] = ex + (size_t)i * ec;
+    launch_block_exp(st, in[i], n, s, ex + (size_t)i * ec, nullptr, 0);
+  }
+  CK(cudaMemsetAsync(&h->d_ctl->error, 0, sizeof(int), st));
+  prof_begin(h, LSBA_K_UPDATE);
+  launch_update_f64tc(st, in, ein, nin, nullptr, n, d_out1, nullptr, d_out2, nullptr, d_C1, d_T,
+                      d_C2, nullptr, nullptr, cf, nullptr, -1, &h->d_ctl->error, h->num_sms);
+  prof_end(h);
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(&h->h_ctl->error, &h->d_ctl->error, sizeof(int), cudaMemcpyDeviceToHost, st));
+  ws_free(h, ex);
+  ws_free(h, cf);
+  CK(cudaStreamSynchronize(st));
+  prof_collect(h);
+  return h->h_ctl->error ? LSBA_DEVICE_TIMEOUT : LSBA_OK;
 }
 
 int lsba_combine(lsba_handle h, const double* d_in, int nin, int64_t n, int s, const double* d_C,

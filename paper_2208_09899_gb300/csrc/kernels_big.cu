@@ -189,7 +189,12 @@ void launch_gram(cudaStream_t st, const GramPlan& p, const BlockPtrs& L, int a, 
   });
   dim3 grid(p.grid_x, p.grid_y);
   k_gram<<<grid, GRAM_THREADS, p.smem, st>>>(g);
-  k_gram_reduce<<<(p.q + 255) / 256, 256, 0, st>>>(partials, p.grid_x, p.q, G, ctl, guard);
+  launch_gram_reduce(st, partials, p.grid_x, p.q, G, ctl, guard);
+}
+
+void launch_gram_reduce(cudaStream_t st, const double* partials, int nparts, int q, double* G,
+                        const Ctl* ctl, int guard) {
+  if (q > 0) k_gram_reduce<<<(q + 255) / 256, 256, 0, st>>>(partials, nparts, q, G, ctl, guard);
 }
 
 // ----------------------------------------------------------------- Update

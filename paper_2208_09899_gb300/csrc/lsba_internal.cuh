@@ -233,6 +233,35 @@ void launch_update_f32(cudaStream_t st, const BlockPtrs& in, int nin, int64_t n,
                        const double* chain, const double* tri2, float* cf, const Ctl* ctl, int step,
                        int num_sms);
 
+// ---- FP64 on the tensor cores by exact digit products (kernels_f64tc.cu), s = 8 ----
+// Per-(128-row tile, column) exponents E (max |x| < 2^E) of an n x s block:
+// ex[tile * s + c]; f64tc_exp_count(n, s) ints per block.
+size_t f64tc_exp_count(int64_t n, int s);
+void launch_block_exp(cudaStream_t st, const double* V, int64_t n, int s, int* ex, const Ctl* ctl,
+                      int guard);
+// Gram [L_1..L_a]^T [R_1..R_b] (FP64 blocks with exponents), reduced into G.
+// shared: R_1 is L_a (split once).
+bool gram_f64tc_eligible(int s, int a, int b, bool shared);
+GramPlan plan_gram_f64tc(int64_t n, int s, int a, int b, int num_sms);
+void launch_gram_f64tc(cudaStream_t st, const GramPlan& p, const double* const* L, const int* const* Le,
+                       int a, const double* const* R, const int* const* Re, int b, bool shared,
+                       int64_t n, double* partials, double* G, const Ctl* ctl, int guard, int* err);
+// out1 = (sum_i in_i C1_i (+ X C1_X)) T1^{-1},
+// out2 = (sum_i in_i C2_i (+ X C2_X) + out1 Chain) T2^{-1}  (out2 optional),
+// with the triangular factors and the chain folded into the coefficients
+// first (into cf: 2 x 8 ncoef x 8 doubles, ncoef = nin (+1 with X)); the
+// outputs' per-tile exponents go to e_out1 / e_out2 (optional).
+bool update_f64tc_eligible(int s, int nin);
+size_t update_f64tc_smem(int nin);
+void launch_update_f64tc(cudaStream_t st, const double* const* in, const int* const* ein, int nin,
+                         const double* X, int64_t n, double* out1, int* e_out1, double* out2,
+                         int* e_out2, const double* coef1, const double* tri1, const double* coef2,
+                         const double* chain, const double* tri2, double* cf, const Ctl* ctl,
+                         int step, int* err, int num_sms);
+// Fixed-order (CTA-order) sum of FP64 Gram partials [nparts][q] into G.
+void launch_gram_reduce(cudaStream_t st, const double* partials, int nparts, int q, double* G,
+                        const Ctl* ctl, int guard);
+
 // Small single-CTA kernels (skeleton logic, Cholesky, least squares, estimate).
 void launch_small_start(cudaStream_t st, const SmallWs& w, int flags);
 void launch_true_relres(cudaStream_t st, const double* G, int s, Ctl* ctl);

@@ -30,7 +30,7 @@ EXPORTED = ("lsba_default_options", "lsba_create", "lsba_set_options", "lsba_sol
             "lsba_autotune",
             "lsba_destroy", "lsba_spmm", "lsba_gram", "lsba_combine", "lsba_get_profile",
             "lsba_reset_profile", "lsba_gram_noalloc", "lsba_release_workspace",
-            "lsba_workspace_bytes", "lsba_gram_df")
+            "lsba_workspace_bytes", "lsba_gram_df", "lsba_gram_fp64tc", "lsba_combine_fp64tc")
 KERNEL_CLASSES = ("spmm", "gram", "update", "small")
 
 
@@ -50,7 +50,7 @@ class Stats(C.Structure):
                 ("a_calls", C.c_int32), ("syncs", C.c_int32), ("v_apps", C.c_int32),
                 ("flags", C.c_int32), ("m_final", C.c_int32), ("relres_est", C.c_double),
                 ("relres_true", C.c_double), ("solve_ms", C.c_double),
-                ("precision", C.c_int32), ("ir_outer", C.c_int32)]
+                ("precision", C.c_int32), ("ir_outer", C.c_int32), ("tensor_cores", C.c_int32)]
 
 
 class History(C.Structure):
@@ -102,6 +102,8 @@ def load(path: str = LIB_PATH):
     lib.lsba_release_workspace.argtypes = [vp]
     lib.lsba_workspace_bytes.argtypes = [i64, i64, i32, i32]
     lib.lsba_gram_df.argtypes = [vp, vp, i32, vp, i32, i64, i32, vp, i32]
+    lib.lsba_gram_fp64tc.argtypes = [vp, vp, i32, vp, i32, i64, i32, vp]
+    lib.lsba_combine_fp64tc.argtypes = [vp, vp, i32, i64, i32, vp, vp, vp, vp, vp]
     for name in EXPORTED:
         if name not in ("lsba_default_options", "lsba_status_string"):
             getattr(lib, name).restype = C.c_int
@@ -357,6 +359,24 @@ class Solver:
         mode = 3 if tensor_cores == "stored" else int(bool(tensor_cores))
         _check(self.lib.lsba_gram_df(self.h, C.c_void_p(_ptr(L)), a, C.c_void_p(_ptr(R)), b, n, s,
                                      C.c_void_p(_ptr(G)), mode))
+
+    def gram_fp64tc(self, L, R, G):
+        """FP64 Gram on the tensor cores (exact digit products): L (a, n, 8),
+        R (b, n, 8) CUDA FP64 -> G (a*8, b*8)."""
+        a, n, s = L.shape
+        b = R.shape[0]
+        _check(self.lib.lsba_gram_fp64tc(self.h, C.c_void_p(_ptr(L)), a, C.c_void_p(_ptr(R)), b, n,
+                                         s, C.c_void_p(_ptr(G))))
+
+    def combine_fp64tc(self, inputs, coef1, tri, out1, coef2=None, out2=None):
+        """FP64 update on the tensor cores: out1 = ([inputs] coef1) tri^{-1} and
+        out2 = [inputs] coef2; inputs (nin, n, 8), coefs (nin*8, 8), tri (8, 8)
+        upper or None, outputs (n, 8) -- all CUDA FP64."""
+        nin, n, s = inputs.shape
+        opt = lambda t: C.c_void_p(_ptr(t)) if t is not None else None  # noqa: E731
+        _check(self.lib.lsba_combine_fp64tc(self.h, C.c_void_p(_ptr(inputs)), nin, n, s,
+                                            C.c_void_p(_ptr(coef1)), opt(tri), opt(coef2),
+                                            C.c_void_p(_ptr(out1)), opt(out2)))
 
     def combine(self, inputs, coef, tri, out):
         """inputs: (nin, n, s); coef: (nin*s, s); tri: (s, s) upper or None; out: (n, s)."""
