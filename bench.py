@@ -37,6 +37,10 @@ METRIC = "BGMRES time-to-1e-10 relres & Arnoldi HBM GB/s vs FP64 plain; serve p5
 WORKLOAD = "lapl512_s8"
 M = 20
 SKELETON = "bcgsi_ls"
+# The headline runs at the paper's precision: FP64 storage, with the Gram and
+# update passes as exact 8-bit digit products on the tensor cores (FP64-grade
+# results) and the SpMM and small kernels in native FP64.
+HEADLINE_PRECISION = "fp64"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 
 
@@ -384,6 +388,30 @@ def run_reference(args, world, rank):
     return 0
 
 
+def profile_cycle(precision):
+    """One restart cycle of the headline workload (the launch sequence an ncu
+    capture selects its kernels from): lapl512_s8, BGMRES(20), BCGSI+LS."""
+    import torch
+    from paper_2208_09899_gb300 import build, lsba
+    build.build()
+    lsba.load()
+    A, B = W.workload(WORKLOAD, 0)
+    dA = lsba.DeviceCSR.from_host(A, "cuda:0")
+    dB = torch.from_numpy(B).to("cuda:0")
+    dX = torch.empty_like(dB)
+    extra = {"tensor_cores": 0} if precision == "fp64-plain" else {}
+    prec = "fp64" if precision == "fp64-plain" else precision
+    sv = lsba.Solver(0, modification="gmres", max_restarts=0, verify_true_residual=0,
+                     precision=prec, cuda_graphs=0, **extra)
+    sv.solve(dA, dB, dX, M, 1e-30, SKELETON)
+    torch.cuda.synchronize()
+    st = sv.stats()
+    print(json.dumps({"profile_cycle": precision, "cycles": st["cycles"], "steps": st["steps"],
+                      "tensor_cores": st["tensor_cores"]}))
+    sv.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -396,11 +424,16 @@ def main():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-gram-kernels", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=32)
+    ap.add_argument("--profile-cycle", default=None,
+                    help="run one restart cycle of the workload in this precision (fp64, df, "
+                         "fp64-plain) and exit: the launch list that ncu captures")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     world, rank, local = dist_setup()
     if args.impl == "reference":
         return run_reference(args, world, rank)
+    if args.profile_cycle:
+        return profile_cycle(args.profile_cycle)
 
     import torch
     from paper_2208_09899_gb300 import build, lsba
@@ -420,7 +453,7 @@ def main():
     dB = torch.from_numpy(B).to(f"cuda:{dev}")
     dX = torch.empty_like(dB)
     sv = lsba.Solver(dev, modification="gmres", max_restarts=0, verify_true_residual=0,
-                     profile=1)
+                     profile=1, precision=HEADLINE_PRECISION)
     stream = torch.cuda.current_stream(dev)
 
     def step():
@@ -464,23 +497,31 @@ def main():
     achieved_tflops = fl[dom] / (dom_ms_per_step * 1e-3) / 1e12
     achieved_gbs = by[dom] / (dom_ms_per_step * 1e-3) / 1e9
     is_df = st0["precision"] == 1
-    suffix = "_df" if is_df else ""
+    is_ftc = st0["precision"] == 0 and st0["tensor_cores"] == 1
+    kernel_names = {
+        "gram": ("k_gram_df_tcs (stored digits, tensor cores, iterations k >= 2) + k_gram_df_tma "
+                 "(start block, k <= 4) + k_gram_reduce_df" if is_df else
+                 "k_gram_f64tc (FP64 digit products on tcgen05) + k_gram_reduce" if is_ftc else
+                 "k_gram + k_gram_reduce"),
+        "update": ("k_coef_fold + k_update_df_tcs (tensor cores, iterations k >= 2 and the cycle "
+                   "end; also writes the new block's digit planes) + k_coef_df + k_update_df_row "
+                   "(start block, k = 1) + k_split_digits (start block)" if is_df else
+                   "k_coef_fold64 + k_update_f64tc (FP64 digit products on tcgen05, every update "
+                   "of the cycle and its end)" if is_ftc else "k_update"),
+        "spmm": ("k_spmm_df8" if is_df else
+                 "k_spmm (FP64) + k_block_exp (tile exponents of W)" if is_ftc else "k_spmm"),
+    }
+    traffic_key = dom + ("_df" if is_df else "_f64tc" if is_ftc else "")
     roofline = {
-        "kernel": {"gram": ("k_gram_df_tcs (stored digits, tensor cores, iterations k >= 2) + "
-                            "k_gram_df_tma (start block, k <= 4) + k_gram_reduce_df" if is_df
-                            else "k_gram + k_gram_reduce"),
-                   "update": ("k_coef_fold + k_update_df_tcs (tensor cores, iterations k >= 2 and "
-                              "the cycle end; also writes the new block's digit planes) + k_coef_df + "
-                              "k_update_df_row (start block, k = 1) + k_split_digits (start block)"
-                              if is_df else "k_update"),
-                   "spmm": f"k_spmm{suffix}"}[dom],
+        "kernel": kernel_names[dom],
         "bound": "hbm", "achieved": achieved_gbs, "peak": hbm, "unit": "GB/s",
         "frac": achieved_gbs / hbm, "peak_source": f"{hbm_src} (copy bandwidth)",
-        "traffic": captured_traffic(dom + ("_df" if is_df else ""), by[dom] / max(dom_launches, 1)),
+        "traffic": captured_traffic(traffic_key, by[dom] / max(dom_launches, 1)),
         "launches_per_step": dom_launches,
         "algorithmic_bytes_per_launch": by[dom] / max(dom_launches, 1),
         "algorithmic_flops_per_launch": fl[dom] / max(dom_launches, 1),
         "fp64_equivalent_tflops": achieved_tflops,
+        "dominant_by_device_time": max(prof, key=lambda k: prof[k][0]),
     }
     kernels = {k: {"ms_per_step": prof[k][0] / args.steps, "launches_per_step": prof[k][1] / args.steps,
                    "share": prof[k][0] / max(sum(v[0] for v in prof.values()), 1e-12)}
@@ -489,7 +530,7 @@ def main():
 
     # The same steps with native FP64 (DFMA) Gram/update/SpMM kernels.
     sv64 = lsba.Solver(dev, modification="gmres", max_restarts=0, verify_true_residual=0,
-                       precision="fp64")
+                       precision="fp64", tensor_cores=0)
     for _ in range(2):
         sv64.solve(dA, dB, dX, M, 1e-30, SKELETON)
     k64 = max(1, min(args.steps, 3))
@@ -503,8 +544,24 @@ def main():
     torch.cuda.synchronize(dev)
     ms64 = f0.elapsed_time(f1) / k64
     fp64_plain = {"value": step_bytes / (ms64 * 1e-3) / 1e9, "unit": "GB/s", "ms_per_step": ms64,
-                  "speedup_of_value": ms64 / ms_step}
+                  "speedup_of_value": ms64 / ms_step,
+                  "note": "native FP64 (DFMA) SpMM, Gram and update kernels (tensor_cores = 0)"}
     sv64.close()
+    # The same steps in double-float (hi + lo FP32 pairs, 48-bit significand).
+    svdf = lsba.Solver(dev, modification="gmres", max_restarts=0, verify_true_residual=0,
+                       precision="df")
+    for _ in range(2):
+        svdf.solve(dA, dB, dX, M, 1e-30, SKELETON)
+    torch.cuda.synchronize(dev)
+    f0.record(stream)
+    for _ in range(k64):
+        svdf.solve(dA, dB, dX, M, 1e-30, SKELETON)
+    f1.record(stream)
+    torch.cuda.synchronize(dev)
+    msdf = f0.elapsed_time(f1) / k64
+    df48 = {"value": step_bytes / (msdf * 1e-3) / 1e9, "unit": "GB/s", "ms_per_step": msdf,
+            "note": "double-float (48-bit significand, FP32 exponent range; narrower than FP64)"}
+    svdf.close()
 
     # End to end through the C ABI with host buffers (copies inside the timed region).
     # Inputs and the result live in pinned host memory.
@@ -528,7 +585,7 @@ def main():
     dA1 = lsba.DeviceCSR.from_host(A1, f"cuda:{dev}")
     dB1 = torch.from_numpy(B1).to(f"cuda:{dev}")
     dX1 = torch.empty_like(dB1)
-    sv1 = lsba.Solver(dev, modification="gmres", max_restarts=50)
+    sv1 = lsba.Solver(dev, modification="gmres", max_restarts=50, precision=HEADLINE_PRECISION)
     for _ in range(3):
         sv1.solve(dA1, dB1, dX1, 10, 1e-10, SKELETON)
     tts = []
@@ -542,7 +599,8 @@ def main():
         torch.cuda.synchronize(dev)
         tts.append(a.elapsed_time(b))
     st1 = sv1.stats()
-    sv0 = lsba.Solver(dev, modification="gmres", max_restarts=50, cuda_graphs=0)
+    sv0 = lsba.Solver(dev, modification="gmres", max_restarts=50, cuda_graphs=0,
+                      precision=HEADLINE_PRECISION)
     for _ in range(3):
         sv0.solve(dA1, dB1, dX1, 10, 1e-10, SKELETON)
     tts0 = []
@@ -586,8 +644,11 @@ def main():
             "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": "df48 (double-float: hi+lo FP32 pairs, 48-bit significand, FP32 exponent "
-                     "range; narrower than FP64)" if st0["precision"] == 1 else "f64",
+            "dtype": ("df48 (double-float: hi+lo FP32 pairs, 48-bit significand, FP32 exponent "
+                      "range; narrower than FP64)" if is_df else
+                      "f64 (FP64 storage; Gram and update as exact products of 8-bit digits "
+                      "carrying 53 bits, on the tcgen05 tensor cores, FP64 accumulation; SpMM "
+                      "and small kernels native FP64)" if is_ftc else "f64"),
             "data": "synthetic (seeded numpy inputs shaped like the paper's lapl_2d)",
             "config": {"workload": f"{WORKLOAD}: 2D 5-point Laplacian 512x512 (n=262144), B n x 8 "
                                    f"N(0,1), BGMRES(m={M}), BCGSI+LS, one restart cycle per step",
@@ -597,7 +658,8 @@ def main():
                        "algorithmic_bytes_per_step": step_bytes},
             "roofline": roofline, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": gpu_launches, "clocks": clocks, "time_to_tol": time_to_tol,
-            "fp64_plain": fp64_plain, "mixed_precision": mixed, "graph_workload": rgg,
+            "fp64_plain": fp64_plain, "df48": df48, "mixed_precision": mixed,
+            "graph_workload": rgg,
             "serving": served, "gram_kernels": gk,
         }
         print(json.dumps(line))

@@ -5,7 +5,7 @@
 // basis update (Alg. 6 lines 17-18, Alg. 7 lines 16-17, the cycle end of
 // Thm. 1) are contractions of FP64 blocks stored in HBM as FP64.  GB300 runs
 // FP64 arithmetic at about 1 TFLOP/s, which leaves plain FP64 kernels 10-20x
-// below the HBM roofline; the bf16 tensor cores can carry the same products
+// below the HBM roofline; the fp16 tensor cores can carry the same products
 // exactly on integer digits (a splitting of each operand into small integers
 // in the manner of Ozaki's error-free scheme for matrix products):
 //
@@ -15,8 +15,9 @@
 //     to the group maximum, the precision of FP64 at that maximum), and F is
 //     written as seven signed 8-bit digits, F = sum_t d_t 2^(8(6 - t)),
 //     t = 0 the most significant: the bytes of F + 0x0080808080808080 minus
-//     128, so |d_0| <= 64 and |d_t| <= 128.  Every digit is exact in bf16.
-//   * The tensor core sums digit products by level l = t + u in FP32:
+//     128, so |d_0| <= 64 and |d_t| <= 128.  Every digit is exact in fp16.
+//   * The fp16 tensor cores (kind::f16) sum digit products by level
+//     l = t + u in FP32:
 //     S_l = sum_k sum_{t+u=l} dL_t dR_u.  Per k every level is bounded by
 //     98304 (level 6: 2 64 128 + 5 128^2; level 7: 6 128^2), so over a window
 //     of at most 128 values of k every partial sum is an integer below 2^24
@@ -38,7 +39,7 @@
 // levels and starts each window (accumulate = 0).
 #include <cstring>
 
-#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include "lsba_internal.cuh"
 #include "tc.cuh"
@@ -69,16 +70,20 @@ __device__ __forceinline__ unsigned long long ft_biased(double x, int E, bool& n
   return (bits >> 63) ? FT_BIAS - F : FT_BIAS + F;
 }
 
-// Digit t (0 = most significant) of two values in biased form, as a bf16 pair
-// (element 0 in the low half): byte 6 - t minus 128, exact.
+// Digit t (0 = most significant) of two values in biased form, as an fp16
+// pair (element 0 in the low half), exact: the half word 0x6400 | b is
+// 1024 + b, so one byte permutation, one mask-and-or and one packed
+// subtraction of 1152 give (b0 - 128, b1 - 128).
 __device__ __forceinline__ uint32_t ft_pair(unsigned long long g0, unsigned long long g1, int t) {
   const int byte = 6 - t;
   const uint32_t w0 = byte >= 4 ? (uint32_t)(g0 >> 32) : (uint32_t)g0;
   const uint32_t w1 = byte >= 4 ? (uint32_t)(g1 >> 32) : (uint32_t)g1;
-  const uint32_t sel = 0x7440u | (uint32_t)(byte & 3);   // 0x4B0000bb = 2^23 + bb
-  const float f0 = __fadd_rn(__uint_as_float(__byte_perm(w0, 0x4B000000u, sel)), -8388736.0f);
-  const float f1 = __fadd_rn(__uint_as_float(__byte_perm(w1, 0x4B000000u, sel)), -8388736.0f);
-  return __byte_perm(__float_as_uint(f0), __float_as_uint(f1), 0x7632u);
+  const uint32_t sel = (uint32_t)(byte & 3) | ((uint32_t)(4 + (byte & 3)) << 8);
+  const uint32_t h = (__byte_perm(w0, w1, sel) & 0x00FF00FFu) | 0x64006400u;
+  __half2 v = *reinterpret_cast<const __half2*>(&h);
+  v = __hsub2(v, __halves2half2(__ushort_as_half((unsigned short)0x6480u),
+                                __ushort_as_half((unsigned short)0x6480u)));
+  return *reinterpret_cast<const uint32_t*>(&v);
 }
 
 // Seven 16-byte core-matrix rows (one per digit) of eight values.
@@ -97,6 +102,16 @@ __device__ __forceinline__ void ft_digits8(const unsigned long long (&g)[8], uin
 __device__ __forceinline__ double ft_fma_pow2(double t, int x, double acc) {
   if (x >= -1022 && x <= 1023) return fma(t, __longlong_as_double((long long)(x + 1023) << 52), acc);
   return acc + scalbn(t, x);
+}
+
+// c 2^dx for dx <= 0 by the exponent field (integer arithmetic, exact) while
+// the result stays normal; scalbn's rounding into the subnormal range below.
+__device__ __forceinline__ double ft_scale_down(double c, int dx) {
+  const long long b = __double_as_longlong(c);
+  const int eb = (int)((b >> 52) & 0x7FF);
+  if (eb == 0 || eb == 0x7FF) return eb == 0 && dx == 0 ? c : (eb == 0x7FF ? c : scalbn(c, dx));
+  if (eb + dx >= 1) return __longlong_as_double(b + ((long long)dx << 52));
+  return scalbn(c, dx);
 }
 
 // Level sums S_0..S_7 of 16 outputs, read level by level from tensor memory
@@ -184,24 +199,37 @@ size_t f64tc_exp_count(int64_t n, int s) { return (size_t)((n + 127) / 128) * s;
 
 // ---------------------------------------------------------------- Gram
 // G = L^T R with L = [L_1..L_a], R = [R_1..R_b] (s = 8), the partial sums of
-// one CTA's row range into partials[blockIdx.x][a s][b s].  With `shared`,
-// R_1 is L_a (the lagged skeletons' [V_1..V_{k-1}, U]^T [U, W]) and is split
-// once.
+// one CTA's row range (whole 128-row tiles) into partials[blockIdx.x][a s][b s].
+// With `shared`, R_1 is L_a (the lagged skeletons' [V_1..V_{k-1}, U]^T [U, W])
+// and is split once.
 //
-// Roles (256 threads, 8 warps: two per scheduler partition, so up to 255
-// registers a thread): every warp splits 32-row chunks of the blocks into the
-// digit operands of shared-memory buffer c & 1 (warp w takes blocks w, w + 8,
-// w + 16; lane = column (lane & 7) x 8-row group (lane >> 3)) and, one window
-// later, runs the epilogue of a 128-row window (warps 0-3, and 4-7 for the
-// second M tile: tensor-memory lanes = L columns); lane 0 of warp 0 issues the
-// MMAs of a chunk once every warp has split it.  Barriers (parity = use count & 1):
-//   sfull[b]  warps -> MMA issue: chunk's digits are in buffer b;
-//   mmad[b]   MMA commit -> warps: buffer b may be rewritten;
-//   wdone[w]  MMA commit at a window's last chunk -> epilogue warps;
-//   tfree[w]  epilogue warps -> MMA issue: accumulator buffer w may be reused.
-#define GF_THREADS 256
-#define GF_SPLIT_WARPS 8
-#define GF_MAXT 3          // split tasks (blocks) per warp and chunk: a + b - shared <= 24
+// Rows go in slabs of 16 (one MMA K step) and windows of 128 (one tile: the
+// exponents' group and the exact accumulation window).  Roles (512 threads,
+// 16 warps, so up to 128 registers a thread):
+//   warps 0-9: split a slab's values from its stage into the digit operands
+//     of slab buffer q % ndb (task = block slot x 8-row group);
+//   warp 10: bulk copies (cp.async.bulk, the TMA engine) of every block's 16
+//     rows of a slab (1 KB each, contiguous) into a ring of nst FP64 stages,
+//     one block per lane, up to nst slabs ahead;
+//   warp 11 (one lane): the MMAs of a slab once it is split;
+//   warps 12-15: the epilogue of each 128-row window (tensor-memory lanes =
+//     L columns; with two M tiles, tile 0 then tile 1), overlapping the
+//     next window's splits and MMAs.
+// Barriers (parity = use count & 1):
+//   full[st]  bulk copies -> split warps        empty[st] split warps -> copies
+//   dfull[b]  split warps -> MMA issue          dfree[b]  MMA commit -> split warps
+//   wdone[w]  MMA commit at a window's end -> epilogue warps
+//   tfree[w]  epilogue warps -> MMA issue (accumulator buffer w reusable)
+#define GF_THREADS 512
+#define GF_SPLIT_WARPS 10
+#define GF_TMA_WARP 10
+#define GF_MMA_WARP 11
+#define GF_EPI_WARP0 12
+#define GF_MAXSPLIT 24     // blocks split per slab: a + b - shared
+#define GF_BSTRIDE 1088    // bytes per block in a stage: 16 rows x 64 B + 64 (bank offset)
+#define GF_MAXST 6
+#define GF_MAXDB 3         // digit slab buffers
+#define GF_MAXTASK 5       // split tasks per warp and slab: 2 GF_MAXSPLIT / 10, rounded up
 
 struct F64Blocks {
   const double* p[LSBA_MAXB];
@@ -212,7 +240,8 @@ struct GramF64Args {
   F64Blocks L, R;
   int a, b, as, bs, shared, nsplit;
   int ma, ntile, tile1;
-  uint32_t a_bytes, buf_bytes, tcols, acc_bytes;
+  uint32_t dbuf_bytes, acc_bytes, stage_bytes, tcols;
+  int nst, ndb;
   int64_t n;
   int tiles_per_cta;
   int q;
@@ -230,29 +259,54 @@ __device__ __forceinline__ void gf_wait(uint64_t* bar, unsigned parity, bool& fa
   failed = __any_sync(0xffffffffu, failed);
 }
 
+// Source block of split slot i (0 .. nsplit-1): L blocks, then the R blocks not shared.
+__device__ __forceinline__ void gf_slot(const GramF64Args& g, int i, const double** p, const int** e,
+                                        int* lblk, int* rblk) {
+  if (i < g.a) {
+    *p = g.L.p[i];
+    *e = g.L.e[i];
+    *lblk = i;
+    *rblk = (g.shared && i == g.a - 1) ? 0 : -1;
+  } else {
+    const int r = i - g.a + (g.shared ? 1 : 0);
+    *p = g.R.p[r];
+    *e = g.R.e[r];
+    *lblk = -1;
+    *rblk = r;
+  }
+}
+
 __global__ void __launch_bounds__(GF_THREADS, 1) k_gram_f64tc(const __grid_constant__ GramF64Args g) {
   if (g.guard && !*(volatile const int*)&g.ctl->active) return;
   extern __shared__ __align__(1024) unsigned char sm[];
-  // FP64 accumulators of the epilogue, [16][ma] (output j of L column m at j ma + m)
-  double* accs = reinterpret_cast<double*>(sm + 2 * (size_t)g.buf_bytes);
-  uint64_t* bars = reinterpret_cast<uint64_t*>(sm + 2 * (size_t)g.buf_bytes + g.acc_bytes);
-  uint64_t* sfull = bars;
-  uint64_t* mmad = bars + 2;
-  uint64_t* wdone = bars + 4;
-  uint64_t* tfree = bars + 6;
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 8);
+  unsigned char* dbuf = sm;                                                   // [ndb] digit slabs
+  double* accs = reinterpret_cast<double*>(sm + (size_t)g.ndb * g.dbuf_bytes);  // [16][ma]
+  unsigned char* stage = sm + (size_t)g.ndb * g.dbuf_bytes + g.acc_bytes;     // [nst] FP64 stages
+  uint64_t* bars = reinterpret_cast<uint64_t*>(stage + (size_t)g.nst * g.stage_bytes);
+  uint64_t* full = bars;                    // [GF_MAXST]
+  uint64_t* empty = bars + GF_MAXST;        // [GF_MAXST]
+  uint64_t* dfull = bars + 2 * GF_MAXST;    // [GF_MAXDB]
+  uint64_t* dfree = dfull + GF_MAXDB;       // [GF_MAXDB]
+  uint64_t* wdone = dfree + GF_MAXDB;       // [2]
+  uint64_t* tfree = wdone + 2;              // [2]
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(tfree + 2);
   int* bad = reinterpret_cast<int*>(tslot + 1);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int nepi = 4 * g.ntile;
 
-  for (uint32_t i = (uint32_t)tid * 16; i < 2 * g.buf_bytes + g.acc_bytes; i += GF_THREADS * 16)
+  for (uint32_t i = (uint32_t)tid * 16; i < (uint32_t)g.ndb * g.dbuf_bytes + g.acc_bytes; i += GF_THREADS * 16)
     *reinterpret_cast<uint4*>(sm + i) = make_uint4(0u, 0u, 0u, 0u);
   if (tid == 0) {
+    for (int i = 0; i < g.nst; ++i) {
+      mbar_init(&full[i], 1);
+      mbar_init(&empty[i], GF_SPLIT_WARPS);
+    }
+    for (int i = 0; i < g.ndb; ++i) {
+      mbar_init(&dfull[i], GF_SPLIT_WARPS);
+      mbar_init(&dfree[i], 1);
+    }
     for (int b2 = 0; b2 < 2; ++b2) {
-      mbar_init(&sfull[b2], GF_SPLIT_WARPS);
-      mbar_init(&mmad[b2], 1);
       mbar_init(&wdone[b2], 1);
-      mbar_init(&tfree[b2], nepi);
+      mbar_init(&tfree[b2], 4);
     }
     *bad = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -267,177 +321,199 @@ __global__ void __launch_bounds__(GF_THREADS, 1) k_gram_f64tc(const __grid_const
   const int64_t tile0 = (int64_t)blockIdx.x * g.tiles_per_cta;
   const int64_t r_begin = tile0 * 128;
   const int64_t r_end = min(g.n, r_begin + (int64_t)g.tiles_per_cta * 128);
-  const int nch = r_end > r_begin ? (int)((r_end - r_begin + 31) / 32) : 0;
+  const int nslab = r_end > r_begin ? (int)((r_end - r_begin + 15) / 16) : 0;
   bool failed = false;
 
-  // MMAs of chunk c (lane 0 of warp 0): every warp has split it; at a window
-  // start the epilogue of the window two back has released its accumulators.
-  auto issue = [&](int c) {
-    const int w = c >> 2, wb = w & 1, b = c & 1;
-    bool f = false;
-    if ((c & 3) == 0 && w >= 2 && !mbar_wait_bounded(&tfree[wb], (unsigned)(((w - 2) >> 1) & 1)))
-      f = true;
-    if (!f && !mbar_wait_bounded(&sfull[b], (unsigned)((c >> 1) & 1))) f = true;
-    if (f) {
-      if (g.err) atomicExch(g.err, 1);
-      return true;
+  if (warp == GF_TMA_WARP) {
+    // ---- bulk copies of the slabs into the stage ring: lane i copies block
+    // slot i (the copies of a slab are issued in parallel)
+    for (int q = 0; q < nslab && !failed; ++q) {
+      const int st = q % g.nst;
+      bool f = false;
+      if (lane == 0 && q >= g.nst && !mbar_wait_bounded(&empty[st], (unsigned)((q / g.nst - 1) & 1)))
+        f = true;
+      const int64_t r0 = r_begin + (int64_t)q * 16;
+      const unsigned bytes = (unsigned)(min((int64_t)16, r_end - r0) * 64);
+      if (lane == 0 && !f) mbar_expect_tx(&full[st], bytes * (unsigned)g.nsplit);
+      failed = __any_sync(0xffffffffu, f);
+      if (failed) break;
+      unsigned char* dst = stage + (size_t)st * g.stage_bytes;
+      for (int i = lane; i < g.nsplit; i += 32) {
+        const double* p;
+        const int* e;
+        int lb, rb;
+        gf_slot(g, i, &p, &e, &lb, &rb);
+        bulk_copy_g2s(dst + (size_t)i * GF_BSTRIDE, p + r0 * 8, bytes, &full[st]);
+      }
     }
-    tc_fence_after();
-    const uint32_t pa = smem_addr(sm + (size_t)b * g.buf_bytes);
-    const uint32_t pb = pa + g.a_bytes;
-    for (int T = 0; T < g.ntile; ++T) {
-      const uint32_t aoff = T ? (uint32_t)(g.tile1 >> 3) * 256u : 0u;
-      const uint32_t dcol = tmem + (uint32_t)((wb * g.ntile + T) * 128);
+    if (failed && lane == 0 && g.err) atomicExch(g.err, 1);
+  } else if (warp == GF_MMA_WARP) {
+    // ---- MMA issue
+    if (lane == 0) {
+      for (int q = 0; q < nslab && !failed; ++q) {
+        const int w = q >> 3, wb = w & 1, b = q % g.ndb;
+        if ((q & 7) == 0 && w >= 2 && !mbar_wait_bounded(&tfree[wb], (unsigned)(((w - 2) >> 1) & 1)))
+          failed = true;
+        if (!failed && !mbar_wait_bounded(&dfull[b], (unsigned)((q / g.ndb) & 1))) failed = true;
+        if (failed) break;
+        tc_fence_after();
+        const uint32_t pa = smem_addr(dbuf + (size_t)b * g.dbuf_bytes);
+        const uint32_t pb = pa + 224u * (uint32_t)g.ma;
+        for (int T = 0; T < g.ntile; ++T) {
+          const uint32_t aoff = T ? (uint32_t)(g.tile1 >> 3) * 256u : 0u;
+          const uint32_t dcol = tmem + (uint32_t)((wb * g.ntile + T) * 128);
 #pragma unroll
-      for (int j = 0; j < 2; ++j) {
-#pragma unroll
-        for (int t = 0; t < 7; ++t) {
-          const uint64_t ad = tc_smem_desc(pa + (uint32_t)t * 64u * g.ma + (uint32_t)j * 32u * g.ma + aoff, 128, 256);
-          const uint64_t bd = tc_smem_desc(pb + (uint32_t)j * 4096u, 128, 256);
-          const uint32_t accum = ((c & 3) || j || t) ? 1u : 0u;
-          tc_mma_bf16(dcol + (uint32_t)(16 * t), ad, bd, tc_idesc_bf16_f32(128, 16 * (8 - t)), accum);
+          for (int t = 0; t < 7; ++t) {
+            const uint64_t ad = tc_smem_desc(pa + (uint32_t)t * 32u * g.ma + aoff, 128, 256);
+            const uint64_t bd = tc_smem_desc(pb, 128, 256);
+            const uint32_t accum = ((q & 7) || t) ? 1u : 0u;
+            tc_mma_bf16(dcol + (uint32_t)(16 * t), ad, bd, tc_idesc_f16_f32(128, 16 * (8 - t)), accum);
+          }
         }
+        tc_commit(&dfree[b]);
+        if ((q & 7) == 7 || q == nslab - 1) tc_commit(&wdone[wb]);
       }
+      if (failed && g.err) atomicExch(g.err, 1);
     }
-    tc_commit(&mmad[b]);
-    if ((c & 3) == 3 || c == nch - 1) tc_commit(&wdone[wb]);
-    return false;
-  };
-
-  const int col = lane & 7, rg = lane >> 3;
-  const double* src[GF_MAXT];
-  const int* esrc[GF_MAXT];
-  uint32_t dstA[GF_MAXT], dstB[GF_MAXT];   // byte offsets in a buffer (digit 0), or ~0u
+  } else if (warp >= GF_EPI_WARP0) {
+    // ---- epilogue warps: lanes 32 (warp % 4) .. of each M tile = L columns
+    for (int w = 0; w <= (nslab - 1) >> 3 && nslab > 0 && !failed; ++w) {
+      const int wb = w & 1;
+      gf_wait(&wdone[wb], (unsigned)((w >> 1) & 1), failed, g.err);
+      tc_fence_after();
+      if (!failed) {
+        const int64_t tile = tile0 + w;
+        for (int T = 0; T < g.ntile; ++T) {
+          const int m = (T ? g.tile1 : 0) + 32 * (warp & 3) + lane;
+          const bool valid = m < g.as && (T == 0 || m >= 128);
+          const int EL = valid ? g.L.e[m >> 3][tile * 8 + (m & 7)] : 0;
+          const uint32_t ta = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)((wb * g.ntile + T) * 128);
 #pragma unroll
-  for (int i = 0; i < GF_MAXT; ++i) {
-    const int task = warp + GF_SPLIT_WARPS * i;
-    src[i] = nullptr;
-    esrc[i] = nullptr;
-    dstA[i] = dstB[i] = ~0u;
-    if (task < g.nsplit) {
-      int rblk = -1;
-      if (task < g.a) {
-        src[i] = g.L.p[task] + col;
-        esrc[i] = g.L.e[task] + col;
-        dstA[i] = (uint32_t)(rg >> 1) * 32u * g.ma + (uint32_t)task * 256u + (uint32_t)(rg & 1) * 128u +
-                  (uint32_t)col * 16u;
-        if (g.shared && task == g.a - 1) rblk = 0;
-      } else {
-        rblk = task - g.a + (g.shared ? 1 : 0);
-        src[i] = g.R.p[rblk] + col;
-        esrc[i] = g.R.e[rblk] + col;
-      }
-      if (rblk >= 0)   // N row u * 16 + 8 rblk + col of the R digit stack, u = 0
-        dstB[i] = g.a_bytes + (uint32_t)(rg >> 1) * 4096u + (uint32_t)rblk * 256u +
-                  (uint32_t)(rg & 1) * 128u + (uint32_t)col * 16u;
-    }
-  }
-  const bool epi = warp < nepi;
-  const int T = warp >> 2;
-  const int m = (T ? g.tile1 : 0) + 32 * (warp & 3) + lane;
-  const bool valid = epi && m < g.as && (T == 0 || m >= 128);
-
-  auto load = [&](int c, double (&x)[GF_MAXT][8]) {
-    const int64_t r0 = r_begin + (int64_t)c * 32 + rg * 8;
+          for (int h = 0; h < 2; ++h) {
+            long long Tv[8];
+            ft_levels8(ta + (uint32_t)(8 * h), Tv);
+            if (valid && 8 * h < g.bs) {
+              const int* er = g.R.e[h] + tile * 8;
 #pragma unroll
-    for (int i = 0; i < GF_MAXT; ++i)
-#pragma unroll
-      for (int k = 0; k < 8; ++k) {
-        const int64_t row = r0 + k;
-        x[i][k] = (src[i] && row < r_end) ? src[i][row * 8] : 0.0;
-      }
-  };
-  auto split = [&](int c, const double (&x)[GF_MAXT][8]) {
-    unsigned char* B = sm + (size_t)(c & 1) * g.buf_bytes;
-    const int64_t tile = tile0 + (c >> 2);
-    bool nf = false;
-#pragma unroll
-    for (int i = 0; i < GF_MAXT; ++i) {
-      if (!src[i]) continue;
-      const int E = esrc[i][tile * 8];
-      unsigned long long gv[8];
-#pragma unroll
-      for (int k = 0; k < 8; ++k) gv[k] = ft_biased(x[i][k], E, nf);
-#pragma unroll
-      for (int t = 0; t < 7; ++t) {
-        uint4 d;
-        d.x = ft_pair(gv[0], gv[1], t);
-        d.y = ft_pair(gv[2], gv[3], t);
-        d.z = ft_pair(gv[4], gv[5], t);
-        d.w = ft_pair(gv[6], gv[7], t);
-        if (dstA[i] != ~0u) *reinterpret_cast<uint4*>(B + dstA[i] + (uint32_t)t * 64u * g.ma) = d;
-        // digit u = t of the R stack: N rows 16 u.. are 2 u core groups further
-        if (dstB[i] != ~0u) *reinterpret_cast<uint4*>(B + dstB[i] + (uint32_t)t * 512u) = d;
-      }
-    }
-    if (nf) *bad = 1;
-  };
-  auto epilogue = [&](int w) {
-    const int wb = w & 1;
-    gf_wait(&wdone[wb], (unsigned)((w >> 1) & 1), failed, g.err);
-    tc_fence_after();
-    if (!failed) {
-      const int64_t tile = tile0 + w;
-      const int EL = valid ? g.L.e[m >> 3][tile * 8 + (m & 7)] : 0;
-      const uint32_t ta = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)((wb * g.ntile + T) * 128);
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        long long Tv[8];
-        ft_levels8(ta + (uint32_t)(8 * h), Tv);
-        if (valid && 8 * h < g.bs) {
-          const int* er = g.R.e[h] + tile * 8;
-#pragma unroll
-          for (int j = 0; j < 8; ++j) {
-            double* a = accs + (size_t)(8 * h + j) * g.ma + m;
-            *a = ft_fma_pow2((double)Tv[j], EL + er[j] - 55, *a);
+              for (int j = 0; j < 8; ++j) {
+                double* a = accs + (size_t)(8 * h + j) * g.ma + m;
+                *a = ft_fma_pow2((double)Tv[j], EL + er[j] - 55, *a);
+              }
+            }
           }
         }
       }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&tfree[wb]);
     }
-    tc_fence_before();
-    __syncwarp();
-    if (lane == 0) mbar_arrive(&tfree[wb]);
-  };
-  auto step = [&](int c, const double (&x)[GF_MAXT][8]) {
-    if (c >= 2) gf_wait(&mmad[c & 1], (unsigned)(((c - 2) >> 1) & 1), failed, g.err);
-    if (!failed) split(c, x);
-    tc_fence_smem();
-    __syncwarp();
-    if (lane == 0) mbar_arrive(&sfull[c & 1]);
-    if (warp == 0) {
-      bool f = failed;
-      if (lane == 0 && !f) f = issue(c);
-      failed = __any_sync(0xffffffffu, f);
-    }
-    if ((c & 3) == 0 && c >= 4 && epi) epilogue((c >> 2) - 1);
-  };
-
-  double xa[GF_MAXT][8], xb[GF_MAXT][8];
-  if (nch > 0) load(0, xa);
-  for (int c = 0; c < nch && !failed; c += 2) {
-    if (c + 1 < nch) load(c + 1, xb);
-    step(c, xa);
-    if (c + 1 >= nch || failed) break;
-    if (c + 2 < nch) load(c + 2, xa);
-    step(c + 1, xb);
-  }
-  if (nch > 0 && epi && !failed) epilogue((nch - 1) >> 2);
-  if (valid && !failed) {
-    double* out = g.partials + (int64_t)blockIdx.x * g.q + (int64_t)m * g.bs;
-    const bool nan_out = *(volatile int*)bad != 0;
+    if (!failed) {
+      for (int T = 0; T < g.ntile; ++T) {
+        const int m = (T ? g.tile1 : 0) + 32 * (warp & 3) + lane;
+        if (m < g.as && (T == 0 || m >= 128)) {
+          double* out = g.partials + (int64_t)blockIdx.x * g.q + (int64_t)m * g.bs;
+          const bool nan_out = *(volatile int*)bad != 0;
 #pragma unroll
-    for (int j = 0; j < 16; ++j)
-      if (j < g.bs) out[j] = nan_out ? __longlong_as_double(0x7FF8000000000000ll) : accs[(size_t)j * g.ma + m];
+          for (int j = 0; j < 16; ++j)
+            if (j < g.bs) out[j] = nan_out ? __longlong_as_double(0x7FF8000000000000ll) : accs[(size_t)j * g.ma + m];
+        }
+      }
+    }
+  } else {
+    // ---- split warps.  Task = (block slot, 8-row group kg) of a slab:
+    // lane = column (lane & 7) x row pair r2 = lane >> 3, the rows r2 and
+    // r2 + 4 of the group, whose digits form fp16 pair r2 of the column's
+    // 16-byte core-matrix row (the same order of the K values in both
+    // operands, so the contraction is unchanged).
+    const int col = lane & 7, r2 = lane >> 3;
+    const int ntask = 2 * g.nsplit;
+    // Exponents of the warp's tasks (task = warp + 10 i, the same every slab)
+    // for the current window, and the next window's loaded one window ahead.
+    int ecur[GF_MAXTASK], enext[GF_MAXTASK];
+    auto load_exps = [&](int w, int (&ev)[GF_MAXTASK]) {
+      const int64_t tile = tile0 + w;
+#pragma unroll
+      for (int i = 0; i < GF_MAXTASK; ++i) {
+        const int task = warp + GF_SPLIT_WARPS * i;
+        ev[i] = 0;
+        if (task < ntask && tile * 128 < r_end) {
+          const double* p;
+          const int* e;
+          int lb, rb;
+          gf_slot(g, task >> 1, &p, &e, &lb, &rb);
+          ev[i] = e[tile * 8 + col];
+        }
+      }
+    };
+    load_exps(0, ecur);
+    load_exps(1, enext);
+    for (int q = 0; q < nslab && !failed; ++q) {
+      const int st = q % g.nst, b = q % g.ndb;
+      const int64_t r0 = r_begin + (int64_t)q * 16;
+      if ((q & 7) == 0 && q > 0) {
+#pragma unroll
+        for (int i = 0; i < GF_MAXTASK; ++i) ecur[i] = enext[i];
+        load_exps((q >> 3) + 1, enext);
+      }
+      gf_wait(&full[st], (unsigned)((q / g.nst) & 1), failed, g.err);
+      const unsigned char* S = stage + (size_t)st * g.stage_bytes;
+      if (q >= g.ndb) gf_wait(&dfree[b], (unsigned)((q / g.ndb - 1) & 1), failed, g.err);
+      unsigned char* D = dbuf + (size_t)b * g.dbuf_bytes;
+      bool nf = false;
+#pragma unroll
+      for (int i = 0; i < GF_MAXTASK; ++i) {
+        const int task = warp + GF_SPLIT_WARPS * i;
+        if (task >= ntask || failed) break;
+        const int sl = task >> 1, kg = task & 1;
+        const int64_t row = r0 + kg * 8 + r2;
+        const unsigned char* src = S + (size_t)sl * GF_BSTRIDE + (size_t)(kg * 8 + r2) * 64 + (size_t)col * 8;
+        const double x0 = row < r_end ? *reinterpret_cast<const double*>(src) : 0.0;
+        const double x1 = row + 4 < r_end ? *reinterpret_cast<const double*>(src + 256) : 0.0;
+        const int E = ecur[i];
+        const unsigned long long g0 = ft_biased(x0, E, nf), g1 = ft_biased(x1, E, nf);
+        int lb, rb;
+        if (sl < g.a) {
+          lb = sl;
+          rb = (g.shared && sl == g.a - 1) ? 0 : -1;
+        } else {
+          lb = -1;
+          rb = sl - g.a + (g.shared ? 1 : 0);
+        }
+        const uint32_t dA = lb >= 0 ? (uint32_t)lb * 256u + (uint32_t)kg * 128u + (uint32_t)col * 16u +
+                                          (uint32_t)r2 * 4u
+                                    : ~0u;
+        const uint32_t dB = rb >= 0 ? 224u * (uint32_t)g.ma + (uint32_t)rb * 256u + (uint32_t)kg * 128u +
+                                          (uint32_t)col * 16u + (uint32_t)r2 * 4u
+                                    : ~0u;
+#pragma unroll
+        for (int t = 0; t < 7; ++t) {
+          const uint32_t d = ft_pair(g0, g1, t);
+          if (dA != ~0u) *reinterpret_cast<uint32_t*>(D + dA + (uint32_t)t * 32u * g.ma) = d;
+          // digit u = t of the R stack: N rows 16 u.. are 2 u core groups further
+          if (dB != ~0u) *reinterpret_cast<uint32_t*>(D + dB + (uint32_t)t * 512u) = d;
+        }
+      }
+      if (nf) *bad = 1;
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[st]);
+      tc_fence_smem();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&dfull[b]);
+    }
   }
   tc_fence_before();
   const bool any_failed = __syncthreads_or(failed);
   tc_fence_after();
   if (any_failed && tid == 0) {
     if (g.err) atomicExch(g.err, 1);
-    // let this CTA's MMAs drain before its tensor memory is released
-    for (int b2 = 0; b2 < 2; ++b2) {
-      mbar_wait_bounded(&mmad[b2], 0);
-      mbar_wait_bounded(&mmad[b2], 1);
+    // let this CTA's MMAs and copies drain before its memory is released
+    for (int i = 0; i < g.ndb; ++i) {
+      mbar_wait_bounded(&dfree[i], 0);
+      mbar_wait_bounded(&dfree[i], 1);
+    }
+    for (int i = 0; i < g.nst; ++i) {
+      mbar_wait_bounded(&full[i], 0);
+      mbar_wait_bounded(&full[i], 1);
     }
   }
   __syncthreads();
@@ -446,7 +522,7 @@ __global__ void __launch_bounds__(GF_THREADS, 1) k_gram_f64tc(const __grid_const
 
 bool gram_f64tc_eligible(int s, int a, int b, bool shared) {
   return s == 8 && a >= 1 && b >= 1 && b <= 2 && a * s <= 256 &&
-         a + b - (shared ? 1 : 0) <= GF_SPLIT_WARPS * GF_MAXT;
+         a + b - (shared ? 1 : 0) <= GF_MAXSPLIT;
 }
 
 static void gram_f64tc_shape(int a, int* ma, int* ntile, int* tile1) {
@@ -456,18 +532,33 @@ static void gram_f64tc_shape(int a, int* ma, int* ntile, int* tile1) {
   *tile1 = *ma - 128;
 }
 
+// Shared memory: ndb digit slabs, the accumulators, nst FP64 stages, barriers.
+static size_t gram_f64tc_smem(int ma, int nsplit, int nst, int ndb) {
+  return (size_t)ndb * ((size_t)224 * ma + 4096) + (size_t)16 * ma * 8 +
+         (size_t)nst * nsplit * GF_BSTRIDE + (2 * GF_MAXST + 2 * GF_MAXDB + 4) * 8 + 16;
+}
+// Three digit slabs where at least three stages fit beside them, else two;
+// then as many stages (<= 6) as fit.
+static void gram_f64tc_buffers(int ma, int nsplit, int* nst, int* ndb) {
+  *ndb = gram_f64tc_smem(ma, nsplit, 3, 3) <= 227 * 1024 ? 3 : 2;
+  *nst = GF_MAXST;
+  while (*nst > 2 && gram_f64tc_smem(ma, nsplit, *nst, *ndb) > 227 * 1024) --*nst;
+}
+
 GramPlan plan_gram_f64tc(int64_t n, int s, int a, int b, int num_sms) {
   GramPlan p{};
   p.q = a * s * b * s;
   p.tile = 128;
   p.grid_y = 1;
-  p.rows_per_chunk = 32;
+  p.rows_per_chunk = 16;
   p.nl_max = a;
   p.tc = 3;
   int ma, nt, t1;
   gram_f64tc_shape(a, &ma, &nt, &t1);
-  const size_t buf = (size_t)7 * 64 * ma + 8192;
-  p.smem = 2 * buf + (size_t)16 * ma * sizeof(double) + 8 * sizeof(uint64_t) + 16;
+  const int nsplit = a + b;   // upper bound (shared splits one fewer)
+  int nst, ndb;
+  gram_f64tc_buffers(ma, nsplit, &nst, &ndb);
+  p.smem = gram_f64tc_smem(ma, nsplit, nst, ndb);
   // one CTA per SM, one SM left for the small side kernel of the iteration
   const int64_t tiles = (n + 127) / 128;
   int64_t gx = num_sms > 1 ? num_sms - 1 : 1;
@@ -504,10 +595,11 @@ void launch_gram_f64tc(cudaStream_t st, const GramPlan& p, const double* const* 
   g.shared = shared ? 1 : 0;
   g.nsplit = a + b - (shared ? 1 : 0);
   gram_f64tc_shape(a, &g.ma, &g.ntile, &g.tile1);
-  g.a_bytes = 7u * 64u * (uint32_t)g.ma;
-  g.buf_bytes = g.a_bytes + 8192u;
-  g.tcols = g.ntile == 2 ? 512u : 256u;
+  g.dbuf_bytes = 224u * (uint32_t)g.ma + 4096u;
   g.acc_bytes = 16u * (uint32_t)g.ma * (uint32_t)sizeof(double);
+  g.stage_bytes = (uint32_t)g.nsplit * GF_BSTRIDE;
+  gram_f64tc_buffers(g.ma, g.nsplit, &g.nst, &g.ndb);
+  g.tcols = g.ntile == 2 ? 512u : 256u;
   g.n = n;
   g.tiles_per_cta = (int)(p.rows_per_cta / 128);
   g.q = p.q;
@@ -515,7 +607,7 @@ void launch_gram_f64tc(cudaStream_t st, const GramPlan& p, const double* const* 
   g.ctl = ctl;
   g.guard = guard;
   g.err = err;
-  k_gram_f64tc<<<p.grid_x, GF_THREADS, p.smem, st>>>(g);
+  k_gram_f64tc<<<p.grid_x, GF_THREADS, gram_f64tc_smem(g.ma, g.nsplit, g.nst, g.ndb), st>>>(g);
   launch_gram_reduce(st, partials, p.grid_x, p.q, G, ctl, guard);
 }
 
@@ -635,8 +727,7 @@ __global__ void __launch_bounds__(UF_THREADS, MINB) k_update_f64tc(const __grid_
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
           const double c = cp[q * 8];
-          const int dx = ex[blk * 8 + q] - emax;
-          cs[q] = ft_fma_pow2(c, dx, 0.0);
+          cs[q] = ft_scale_down(c, ex[blk * 8 + q] - emax);
           const unsigned long long b = (unsigned long long)__double_as_longlong(cs[q]) & 0x7FFFFFFFFFFFFFFFull;
           bmax = b > bmax ? b : bmax;
           nf |= !(fabs(c) <= 1.79769313486231570e308);
@@ -704,7 +795,7 @@ __global__ void __launch_bounds__(UF_THREADS, MINB) k_update_f64tc(const __grid_
           const uint64_t ad = tc_smem_desc(pa + (uint32_t)t * UF_APLANE, 128, 256);
           const uint64_t bd = tc_smem_desc(pb, 128, 256);
           const uint32_t accum = ((ks % UF_FLUSH) || t) ? 1u : 0u;
-          tc_mma_bf16(tmem + (uint32_t)(16 * t), ad, bd, tc_idesc_bf16_f32(128, 16 * (8 - t)), accum);
+          tc_mma_bf16(tmem + (uint32_t)(16 * t), ad, bd, tc_idesc_f16_f32(128, 16 * (8 - t)), accum);
         }
         tc_commit(&mmad[b]);
       }

@@ -1,6 +1,6 @@
 // Fifth-generation tensor core (tcgen05) building blocks, written from the PTX
 // ISA: tensor-memory allocation, shared-memory matrix descriptors, the
-// kind::f16 MMA (bf16 x bf16 -> f32 accumulators in tensor memory), its
+// kind::f16 MMA (bf16 x bf16 or f16 x f16 -> f32 accumulators in tensor memory), its
 // commit to an mbarrier, and tensor-memory loads.
 //
 // Operands use the no-swizzle K-major canonical layout: a "core matrix" is 8
@@ -35,6 +35,11 @@ __host__ __device__ constexpr uint32_t tc_idesc_bf16_f32(int M, int N) {
          ((uint32_t)(M >> 4) << 24);
 }
 
+// The same with fp16 A and B (formats 0).
+__host__ __device__ constexpr uint32_t tc_idesc_f16_f32(int M, int N) {
+  return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
 // Warp-wide: allocate ncols (a power of two, 32..512) tensor-memory columns;
 // the base address is written to *slot (shared memory).
 __device__ __forceinline__ void tc_alloc(uint32_t* slot, uint32_t ncols) {
@@ -57,7 +62,8 @@ __device__ __forceinline__ void tc_fence_smem() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
-// D[tmem] (+)= A * B, M = 128, issued by one thread.
+// D[tmem] (+)= A * B, M = 128, kind::f16 (bf16 or f16 operands, as the
+// instruction descriptor says), issued by one thread.
 __device__ __forceinline__ void tc_mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
                                             uint32_t idesc, uint32_t accumulate) {
   asm volatile(
