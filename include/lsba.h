@@ -45,7 +45,8 @@ enum {
   LSBA_INVALID_ARG = 3,
   LSBA_OUT_OF_MEMORY = 4,
   LSBA_CUDA_ERROR = 5,
-  LSBA_DEVICE_TIMEOUT = 6   /* reserved */
+  LSBA_DEVICE_TIMEOUT = 6   /* a kernel's bounded wait (mbarrier, one second at
+                               most) gave up; the kernel recorded it and returned */
 };
 
 /* Block Arnoldi skeletons (names as in the paper, Sec. 3). */
@@ -132,6 +133,14 @@ typedef struct {
                                     muscles); any other skeleton or the global
                                     product with LSBA_MUSCLE_COLUMN is
                                     LSBA_INVALID_ARG.                                  */
+  int32_t inject_stall;          /* test hook (0 in normal use): 1 makes the start
+                                    kernel of the first cycle wait, boundedly, on an
+                                    mbarrier that nothing arrives at; the wait gives
+                                    up after one second, the kernel records the
+                                    error, the remaining kernels of the cycle skip
+                                    their work and the solve returns
+                                    LSBA_DEVICE_TIMEOUT (X undefined).  The handle
+                                    stays usable.                                      */
 } lsba_options;
 
 enum { LSBA_PREC_FP64 = 0, LSBA_PREC_DF = 1, LSBA_PREC_AUTO = 2, LSBA_PREC_FP32_IR = 3 };

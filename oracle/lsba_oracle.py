@@ -130,16 +130,22 @@ def block_inner_product(name: str, s: int):
     raise ValueError(name)
 
 
-def chol_flag(G: np.ndarray):
+def chol_flag(G: np.ndarray, pivots: list | None = None):
     """Upper Cholesky factor R (G = R^T R) read from the upper triangle of G,
-    with the NaN-flag of Sec. 4 (reading R1).  Returns (R, flag)."""
+    with the NaN-flag of Sec. 4 (reading R1).  Returns (R, flag).  If
+    ``pivots`` is a list, the pivots d_j computed are appended to it (the last
+    one is the failing pivot of a flag)."""
     G = np.asarray(G, dtype=np.float64)
     s = G.shape[0]
     R = np.zeros((s, s))
     if not np.all(np.isfinite(np.triu(G))):
+        if pivots is not None:
+            pivots.append(float("nan"))
         return R, True
     for j in range(s):
         d = G[j, j] - np.dot(R[:j, j], R[:j, j])
+        if pivots is not None:
+            pivots.append(float(d))
         if not np.isfinite(d) or d <= 0.0:
             return R, True
         R[j, j] = np.sqrt(d)
@@ -240,6 +246,7 @@ class _Arnoldi:
         self.k = 0
         self.counts = counts
         self.grams = grams
+        self.pivot_log = None   # BCGS-PIP: (k, smallest relative Cholesky pivot) per step
 
     def _blk(self, i, j):
         s = self.s
@@ -334,7 +341,12 @@ class BCGS_PIP(_Arnoldi):
         self._sync()
         self._record(G)
         Hc, Om = G[:k * s], G[k * s:]
-        R, flag = chol_flag(Om - Hc.T @ Hc)
+        piv = [] if self.pivot_log is not None else None
+        R, flag = chol_flag(Om - Hc.T @ Hc, piv)
+        if piv is not None:
+            # smallest pivot relative to <W, W>'s diagonal: how far the
+            # Pythagorean difference Omega - H^T H is from cancelling out
+            self.pivot_log.append((k, min(p / Om[i, i] for i, p in enumerate(piv))))
         if flag or force_flag:
             return ("flag", k)
         self.set_Hcol(1, k, k, Hc)
@@ -619,12 +631,17 @@ def solve(A, B: np.ndarray, m: int, tol: float, skeleton: str = "bcgsi_ls",
           modification: str = "gmres", max_restarts: int = 50, adaptive: bool = True,
           verify_true_residual: bool = True, inject_flags=(), record_first_cycle: bool = False,
           true_residual_each_cycle: bool = False, X_star: np.ndarray | None = None,
-          inner_product: str = "classical", muscle: str = "cholqr") -> Result:
+          inner_product: str = "classical", muscle: str = "cholqr",
+          pivot_trace: list | None = None) -> Result:
     """Restarted, adaptively restarted modified BFOM (BFOM or BGMRES) for A X = B
     with the given block Arnoldi skeleton; X_0 = 0.
 
     ``inject_flags`` is a set of (cycle, relation) pairs at which the chol flag
     is forced (test hook: a host-decided input, reading R8 applies).
+    ``pivot_trace`` (a list, BCGS-PIP only) receives (cycle, relation, r) for
+    every step, r the smallest Cholesky pivot of Omega - H^T H relative to
+    Omega's diagonal: the margin by which the step's flag decision was taken,
+    which decides whether another rounding order may decide differently.
     """
     if skeleton not in _CLASSES:
         raise ValueError(skeleton)
@@ -656,6 +673,8 @@ def solve(A, B: np.ndarray, m: int, tol: float, skeleton: str = "bcgsi_ls",
             break
         grams = [] if (record_first_cycle and cycle == 1) else None
         ar = _CLASSES[skeleton](A, V1, m_cur, counts, grams, ip=ip, **extra)
+        if pivot_trace is not None:
+            ar.pivot_log = []
         res.m_cur.append(m_cur)
         j, converged, flagged = 0, False, 0
         coeffs = None
@@ -690,6 +709,8 @@ def solve(A, B: np.ndarray, m: int, tol: float, skeleton: str = "bcgsi_ls",
                 converged = True
                 break
         res.cycles = cycle
+        if pivot_trace is not None and ar.pivot_log is not None:
+            pivot_trace.extend((cycle, k, r) for k, r in ar.pivot_log)
         res.cycle_m.append(j)
         res.cycle_flag.append(flagged)
         res.steps += j

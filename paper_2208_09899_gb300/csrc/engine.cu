@@ -1104,7 +1104,8 @@ static int run_cycles(lsba_handle h, const lsba_csr* A, const double* Bw, double
     c->m_cur = m_cur;
     c->inject_relation = (cycle == h->opt.inject_flag_cycle) ? h->opt.inject_flag_relation : -1;
     c->muscle_syncs = 0;
-    if ((rc = run_cycle_body(h, A, Rstart, n, s, m_cur, start_flags)) != LSBA_OK) return rc;
+    const int stall = (cycle == 1 && h->opt.inject_stall) ? 4 : 0;
+    if ((rc = run_cycle_body(h, A, Rstart, n, s, m_cur, start_flags | stall)) != LSBA_OK) return rc;
     if (c->error) return LSBA_DEVICE_TIMEOUT;
     // the start block's muscle: CholQR one sync; the column muscle counts its
     // own syncs on the device (the start's and every step's)

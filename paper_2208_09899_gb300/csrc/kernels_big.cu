@@ -133,14 +133,32 @@ __global__ void __launch_bounds__(GRAM_THREADS) k_gram(const __grid_constant__ G
   }
 }
 
-__global__ void k_gram_reduce(const double* __restrict__ partials, int nparts, int q,
-                              double* __restrict__ G, const Ctl* ctl, int guard) {
+// Sum of the per-CTA partials in a fixed order: a CTA of 8 warps handles 32
+// consecutive outputs (lane = output); warp w sums the partials of CTAs
+// [w P / 8, (w + 1) P / 8) in CTA order, four independent running sums per
+// lane (partial x goes to sum x % 4, combined 0 + 1 + 2 + 3), and the eight
+// warp sums are added in warp order.  The order depends only on the number of
+// partials, so results are bitwise reproducible.
+__global__ void __launch_bounds__(256) k_gram_reduce(const double* __restrict__ partials, int nparts,
+                                                     int q, double* __restrict__ G, const Ctl* ctl,
+                                                     int guard) {
   if (guard && !ctl_active(ctl)) return;
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= q) return;
-  double v = 0.0;
-  for (int x = 0; x < nparts; ++x) v += partials[(int64_t)x * q + e];
-  G[e] = v;
+  __shared__ double part[8][32];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int e = blockIdx.x * 32 + lane;
+  const int x0 = (int)((int64_t)warp * nparts / 8), x1 = (int)((int64_t)(warp + 1) * nparts / 8);
+  double a[4] = {0.0, 0.0, 0.0, 0.0};
+  if (e < q) {
+    for (int x = x0; x < x1; ++x) a[(x - x0) & 3] += partials[(int64_t)x * q + e];
+  }
+  part[warp][lane] = (a[0] + a[1]) + (a[2] + a[3]);
+  __syncthreads();
+  if (warp == 0 && e < q) {
+    double v = 0.0;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) v += part[w][lane];
+    G[e] = v;
+  }
 }
 
 GramPlan plan_gram(int64_t n, int s, int a, int b, int num_sms) {
@@ -194,7 +212,7 @@ void launch_gram(cudaStream_t st, const GramPlan& p, const BlockPtrs& L, int a, 
 
 void launch_gram_reduce(cudaStream_t st, const double* partials, int nparts, int q, double* G,
                         const Ctl* ctl, int guard) {
-  if (q > 0) k_gram_reduce<<<(q + 255) / 256, 256, 0, st>>>(partials, nparts, q, G, ctl, guard);
+  if (q > 0) k_gram_reduce<<<(q + 31) / 32, 256, 0, st>>>(partials, nparts, q, G, ctl, guard);
 }
 
 // ----------------------------------------------------------------- Update

@@ -24,6 +24,7 @@
 #include <cmath>
 
 #include "lsba_internal.cuh"
+#include "tma.cuh"
 
 namespace lsba {
 
@@ -608,6 +609,24 @@ __global__ void __launch_bounds__(NT) k_small_start(SmallWs w, int flags) {
   __shared__ Shared sh;
   const int s = w.s;
   Ctl* ctl = w.ctl;
+  if (flags & 4) {
+    // Test hook: a bounded wait on an mbarrier that nothing arrives at (no
+    // copies or MMAs in flight).  It gives up, the error is recorded, and the
+    // cycle ends as after a flagged start (every later kernel skips its work).
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) mbar_init(&bar, 1);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      if (!mbar_wait_bounded(&bar, 0)) atomicExch(&ctl->error, 1);
+      ctl->start_flag = 1;
+      ctl->active = 0;
+      ctl->j = 0;
+      ctl->flagged = 0;
+      ctl->converged = 0;
+      ctl->update_step = -1;
+    }
+    return;
+  }
   // G = R_start^T R_start (s x s row-major == col-major since symmetric in exact
   // arithmetic; the upper triangle read as G[a*s + c], a <= c).
   int flag;

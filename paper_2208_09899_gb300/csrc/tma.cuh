@@ -1,6 +1,6 @@
 // One-dimensional bulk copies global -> shared memory (cp.async.bulk, the TMA
 // engine) completing on mbarriers, written from the PTX ISA.  Every wait is
-// bounded (TMA_WAIT_LIMIT polls of mbarrier.try_wait).
+// bounded (TMA_WAIT_LIMIT polls of mbarrier.try_wait, or one second).
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -8,6 +8,7 @@
 namespace lsba {
 
 #define TMA_WAIT_LIMIT (1u << 22)
+#define TMA_WAIT_NS 1000000000ull
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -39,9 +40,21 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
       " selp.u32 %0, 1, 0, p;\n}" : "=r"(ok) : "r"(smem_addr(bar)), "r"(parity) : "memory");
   return ok != 0;
 }
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// false once TMA_WAIT_LIMIT polls or TMA_WAIT_NS nanoseconds have passed
+// without the phase completing (the clock is read every 256 polls, and not at
+// all when the first poll succeeds).
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity) {
-  for (unsigned it = 0; it < TMA_WAIT_LIMIT; ++it)
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = global_ns();
+  for (unsigned it = 1; it < TMA_WAIT_LIMIT; ++it) {
     if (mbar_try_wait(bar, parity)) return true;
+    if ((it & 255u) == 0 && global_ns() - t0 > TMA_WAIT_NS) return false;
+  }
   return false;
 }
 

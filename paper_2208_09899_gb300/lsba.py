@@ -42,7 +42,7 @@ class Options(C.Structure):
                 ("precision", C.c_int32), ("ir_max_outer", C.c_int32),
                 ("ir_inner_tol", C.c_double), ("cuda_graphs", C.c_int32),
                 ("tensor_cores", C.c_int32), ("inner_product", C.c_int32),
-                ("muscle", C.c_int32)]
+                ("muscle", C.c_int32), ("inject_stall", C.c_int32)]
 
 
 class Stats(C.Structure):

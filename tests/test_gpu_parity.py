@@ -601,3 +601,60 @@ def test_auto_takes_fp64_for_wide_or_nonfinite_inputs(env):
     Bn[3, 1] = np.nan
     _, st, _ = lsba.solve(A, Bn, 8, 1e-10, "bcgsi_ls", device=0)
     assert st["precision"] == lsba.PRECISIONS["fp64"] and st["status"] == lsba.LSBA_BREAKDOWN
+
+
+def test_natural_flag_decision_replay(env):
+    """A natural NaN-flag (no injection): BCGS-PIP on the paper's tridiag
+    (n = 300, B = [1/sqrt(n), 1..n], Sec. 5), BGMRES(30).  The flag fires once
+    the basis has lost orthogonality (Table 2: PIP's O(eps) kappa^2 bound), and
+    from there the computed trajectory depends on the rounding order (Sec. 4
+    shows the flag step moving with the thread count; the oracle itself moves
+    it by up to 5 relations under 1e-14 perturbations of B, and a rounding
+    order may not flag in that cycle at all).  So: at least one side flags in
+    the first cycle; where the two first-cycle decisions differ, the oracle's
+    basis must have lost orthogonality (>= 1e-3) before the earlier flag, and
+    that decision is replayed on the other side (the oracle's injection, or
+    the GPU's); after that the restart logs, counters and X agree (later cycles
+    run with m = flag - 1 and do not flag), except that the last cycle may stop
+    one step apart when the later side's estimate there is within 1.5 tol."""
+    torch, lsba = env
+    A, B = W.paper_tridiag(300)
+    s, m, tol = B.shape[1], 30, 1e-10
+    kw = dict(modification="gmres", max_restarts=60)
+    X, st, hist = lsba.solve(A, B, m, tol, "bcgs_pip", device=0, record_history=True,
+                             precision="fp64", **kw)
+    ref = O.solve(A, B, m, tol, "bcgs_pip", record_first_cycle=True, **kw)
+    rg, ro = hist["cycle_flag"][0], ref.cycle_flag[0]
+    print(f"PIP tridiag300: first-cycle flag relation gpu {rg} oracle {ro} (0: none); "
+          f"logs gpu {hist['cycle_m'][:4]} oracle {ref.cycle_m[:4]}")
+    assert rg > 0 or ro > 0
+    if rg != ro:
+        r = min(x for x in (rg, ro) if x > 0)
+        loo = O.loss_of_orthogonality(ref.first_cycle["V"][:, :(r - 1) * s])
+        print(f"  replayed at relation {r}; oracle loss of orthogonality there {loo:.1e}")
+        assert loo >= 1e-3
+        if rg == r:
+            ref = O.solve(A, B, m, tol, "bcgs_pip", inject_flags=[(1, rg)], **kw)
+        else:
+            X, st, hist = lsba.solve(A, B, m, tol, "bcgs_pip", device=0, record_history=True,
+                                     precision="fp64", inject_flag_cycle=1,
+                                     inject_flag_relation=ro, **kw)
+    assert hist["cycle_m"][:-1] == ref.cycle_m[:-1] and hist["cycle_flag"] == ref.cycle_flag
+    assert hist["cycle_mcur"] == ref.m_cur
+    jg, jo = hist["cycle_m"][-1], ref.cycle_m[-1]
+    if jg != jo:
+        # The stopping step of the last cycle: the one side's estimate at the
+        # other side's stopping step sits just above the tolerance (a few
+        # rounding-order ulps of a basis that has lost orthogonality).
+        c, k = len(ref.cycle_m), min(jg, jo)
+        eg = {(int(a), int(b)): e for a, b, e in zip(hist["est_cycle"], hist["est_j"], hist["est"])}
+        eo = {(a, b): e for a, b, e in ref.est_history}
+        late = eg[(c, k)] if jg > jo else eo[(c, k)]
+        print(f"  last-cycle stop gpu {jg} oracle {jo}; late side's estimate at {k}: {late:.3e}")
+        assert abs(jg - jo) == 1 and tol < late <= 1.5 * tol
+    else:
+        assert (st["cycles"], st["steps"], st["a_calls"], st["syncs"]) == \
+            (ref.cycles, ref.steps, ref.a_calls, ref.syncs)
+    assert st["status"] == ref.status == 0 and st["cycles"] == ref.cycles
+    assert _rel(X, ref.X) <= TOL_X
+    assert st["relres_true"] <= tol and ref.relres_true <= tol

@@ -15,7 +15,7 @@ SRC = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
 
 MUTATIONS = {
     # sign of the Pythagorean correction in PIP (Alg. 3)
-    "pip_sign": ("R, flag = chol_flag(Om - Hc.T @ Hc)", "R, flag = chol_flag(Om + Hc.T @ Hc)"),
+    "pip_sign": ("R, flag = chol_flag(Om - Hc.T @ Hc, piv)", "R, flag = chol_flag(Om + Hc.T @ Hc, piv)"),
     # dropped Y^T Z term in BCGSI+LS (Alg. 7)
     "ls_drop_term": ("P = left_solve_upper_T(R, Pt - Y.T @ Z)", "P = left_solve_upper_T(R, Pt)"),
     # ICWY uses T instead of T^{-T} (Alg. 6, blue)

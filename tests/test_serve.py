@@ -169,3 +169,55 @@ def test_served_results_equal_solo():
 def _spmm(A, X):
     import scipy.sparse as sp
     return sp.csr_matrix((A.vals, A.colidx, A.rowptr), shape=(A.n, A.n)) @ X
+
+
+def _lapl3d_kappa(A):
+    """kappa of the 3D 7-point Laplacian + delta I of a served request."""
+    N = round(A.n ** (1 / 3))
+    d = np.repeat(np.arange(A.n), np.diff(A.rowptr)) == A.colidx
+    delta = float(A.vals[d][0] - 6.0)
+    c = np.cos(np.pi / (N + 1))
+    return (delta + 6 * (1 + c)) / (delta + 6 * (1 - c))
+
+
+@pytest.mark.gpu
+def test_served_results_match_oracle():
+    """Every served request against the CPU oracle on the same (A, B, m, tol,
+    skeleton, modification, restarts): FP64, double-float and auto requests
+    have the oracle's status, cycles, relations, A-calls and syncs and X within
+    1e-8; FP32-inner requests reach tol and their error against the oracle is
+    within kappa(A) (relres_gpu + relres_oracle) (iterative refinement reaches
+    the same solution to the conditioning of the problem)."""
+    from oracle import lsba_oracle as O
+    reqs = serve.serving_requests(8, seed=17, side_range=(10, 18), m_range=(6, 12),
+                                  s_choices=(1, 4, 8, 16), tol=1e-8)
+    precisions = ("auto", "fp64", "df", "fp32_ir")
+    skeletons = ("bcgsi_ls", "bcgs_pip", "bmgs_icwy", "bcgsi_ls")
+    for i, r in enumerate(reqs):
+        r.precision = precisions[i % 4]
+        r.skeleton = skeletons[i % 4]
+    # one request on the FP64 tensor-core passes (lagged skeleton, s = 8)
+    reqs[1].skeleton, reqs[1].precision = "bcgsi_ls", "fp64"
+    reqs[1].B = np.ascontiguousarray(
+        np.random.default_rng(5).standard_normal((reqs[1].A.n, 8)))
+    srv = serve.SolveServer(slots=4, hbm_cap_bytes=40e9, device=0)
+    try:
+        out = srv.run(reqs)
+    finally:
+        srv.close()
+    for r, res in zip(reqs, out):
+        assert "error" not in res.stats, res.stats
+        ref = O.solve(r.A, r.B, r.m, r.tol, r.skeleton, modification=r.modification,
+                      max_restarts=r.max_restarts)
+        st = res.stats
+        err = np.linalg.norm(res.X - ref.X) / np.linalg.norm(ref.X)
+        print(f"SERVED rid={r.rid} n={r.n} s={r.s} m={r.m} {r.skeleton} {r.precision}: "
+              f"cycles {st['cycles']}/{ref.cycles} relres {st['relres_true']:.2e} error {err:.2e}")
+        assert st["status"] == ref.status == 0
+        assert st["relres_true"] <= r.tol and ref.relres_true <= r.tol
+        if r.precision == "fp32_ir":
+            assert err <= _lapl3d_kappa(r.A) * (st["relres_true"] + ref.relres_true)
+        else:
+            assert (st["cycles"], st["steps"], st["a_calls"], st["syncs"]) == \
+                (ref.cycles, ref.steps, ref.a_calls, ref.syncs)
+            assert err <= 1e-8
