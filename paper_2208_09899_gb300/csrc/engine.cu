@@ -85,12 +85,17 @@ struct lsba_ctx {
   // FP64 on the tensor cores (exact digit products, kernels_f64tc.cu): lagged
   // skeletons, s = 8.  Per-(tile, column) exponents of the basis blocks
   // (block i at fexp + i * f64tc_exp_count(n, s)), of U, W and the cycle's
-  // start block, and the folded FP64 update coefficients.
+  // start block, their digit planes (block i at fpl + i * f64tc_plane_bytes(n),
+  // then U, W, the start block), and the folded FP64 update coefficients.
   bool use_ftc = false;
   int* fexp = nullptr;
   int* fexp_U = nullptr;
   int* fexp_W = nullptr;
   int* fexp_R0 = nullptr;
+  unsigned char* fpl = nullptr;
+  unsigned char* fpl_U = nullptr;
+  unsigned char* fpl_W = nullptr;
+  unsigned char* fpl_R0 = nullptr;
   double* cf64 = nullptr;
   double prof_ms[LSBA_K_NCLASS] = {0, 0, 0, 0};
   int64_t prof_n[LSBA_K_NCLASS] = {0, 0, 0, 0};
@@ -197,7 +202,9 @@ static void free_ws(lsba_ctx* h) {
   h->dexp = nullptr;
   ws_free(h, h->fexp);
   ws_free(h, h->cf64);
+  ws_free(h, h->fpl);
   h->fexp = h->fexp_U = h->fexp_W = h->fexp_R0 = nullptr;
+  h->fpl = h->fpl_U = h->fpl_W = h->fpl_R0 = nullptr;
   h->cf64 = nullptr;
   ws_free(h, h->basis);
   ws_free(h, h->Wb);
@@ -446,18 +453,25 @@ static int ensure_f64tc(lsba_ctx* h) {
   if (h->fexp) return LSBA_OK;
   const size_t ec = f64tc_exp_count(h->cap_n, h->cap_s);
   const size_t nb = (size_t)h->cap_m + 1 + 3;
+  const size_t pb = f64tc_plane_bytes(h->cap_n);
   if (ws_alloc(h, &h->fexp, sizeof(int) * nb * ec) != cudaSuccess ||
-      ws_alloc(h, &h->cf64, sizeof(double) * 2 * 8 * (size_t)(h->cap_m + 3) * 8) != cudaSuccess) {
+      ws_alloc(h, &h->cf64, sizeof(double) * 2 * 8 * (size_t)(h->cap_m + 3) * 8) != cudaSuccess ||
+      ws_alloc(h, &h->fpl, pb * nb) != cudaSuccess) {
     cudaGetLastError();
     ws_free(h, h->fexp);
     ws_free(h, h->cf64);
+    ws_free(h, h->fpl);
     h->fexp = nullptr;
     h->cf64 = nullptr;
+    h->fpl = nullptr;
     return LSBA_OUT_OF_MEMORY;
   }
   h->fexp_U = h->fexp + (size_t)(h->cap_m + 1) * ec;
   h->fexp_W = h->fexp_U + ec;
   h->fexp_R0 = h->fexp_W + ec;
+  h->fpl_U = h->fpl + (size_t)(h->cap_m + 1) * pb;
+  h->fpl_W = h->fpl_U + pb;
+  h->fpl_R0 = h->fpl_W + pb;
   return LSBA_OK;
 }
 
@@ -559,13 +573,16 @@ static void split_basis(lsba_ctx* h, int i, int64_t n, int s, const Ctl* ctl, in
 }
 
 // FP64 tensor-core passes.  Block i of the basis and its exponents:
-static const int* basis_exp(const lsba_ctx* h, int64_t n, int s, int i) {
+static int* basis_exp(const lsba_ctx* h, int64_t n, int s, int i) {
   return h->fexp + (size_t)i * f64tc_exp_count(n, s);
 }
-static void do_block_exp(lsba_ctx* h, const double* V, int* ex, int64_t n, int s, const Ctl* ctl,
-                         int guard) {
+static unsigned char* basis_planes(const lsba_ctx* h, int64_t n, int i) {
+  return h->fpl + (size_t)i * f64tc_plane_bytes(n);
+}
+static void do_block_digits(lsba_ctx* h, const double* V, int* ex, unsigned char* planes, int64_t n,
+                            const Ctl* ctl, int guard) {
   prof_begin(h, LSBA_K_SPMM);
-  launch_block_exp(h->stream, V, n, s, ex, ctl, guard);
+  launch_block_digits(h->stream, V, n, ex, planes, ctl, guard);
   prof_end(h);
 }
 static void do_gram_ftc(lsba_ctx* h, const double* const* L, const int* const* Le, int a,
@@ -577,13 +594,14 @@ static void do_gram_ftc(lsba_ctx* h, const double* const* L, const int* const* L
                     &h->d_ctl->error);
   prof_end(h);
 }
-static void do_update_ftc(lsba_ctx* h, const double* const* in, const int* const* ein, int nin,
-                          const double* X, int64_t n, double* out1, int* e1, double* out2, int* e2,
+static void do_update_ftc(lsba_ctx* h, const unsigned char* const* in, const int* const* ein,
+                          int nin, const double* X, int64_t n, double* out1, int* e1,
+                          unsigned char* p1, double* out2, int* e2, unsigned char* p2,
                           const double* coef1, const double* tri1, const double* coef2,
                           const double* chain, const double* tri2, const Ctl* ctl, int step) {
   prof_begin(h, LSBA_K_UPDATE);
-  launch_update_f64tc(h->stream, in, ein, nin, X, n, out1, e1, out2, e2, coef1, tri1, coef2, chain,
-                      tri2, h->cf64, ctl, step, &h->d_ctl->error, h->num_sms);
+  launch_update_f64tc(h->stream, in, ein, nin, X, n, out1, e1, p1, out2, e2, p2, coef1, tri1, coef2,
+                      chain, tri2, h->cf64, ctl, step, &h->d_ctl->error, h->num_sms);
   prof_end(h);
 }
 
@@ -606,8 +624,9 @@ static void wait_side(lsba_ctx* h, int k) {
 
 // One cycle of a lagged skeleton (Alg. 6, 7) on the FP64 tensor-core passes
 // (s = 8): CholQR of R_start, iteration 1, iterations k = 2..kmax.  The same
-// launches as the generic path, with every block's per-tile exponents written
-// after the pass that writes the block.
+// launches as the generic path; every block's per-tile exponents and digit
+// planes are written by the pass that writes the block (the update for the
+// basis blocks and U, the digit kernel after the SpMM for W).
 static void enqueue_cycle_ftc(lsba_ctx* h, const lsba_csr* A, const double* Rstart, int64_t n,
                               int s, int kmax, int start_flags) {
   cudaStream_t st = h->stream;
@@ -617,38 +636,43 @@ static void enqueue_cycle_ftc(lsba_ctx* h, const lsba_csr* A, const double* Rsta
   const size_t blk = (size_t)n * s;
   const double* L[LSBA_MAXB];
   const int* Le[LSBA_MAXB];
+  const unsigned char* Lp[LSBA_MAXB];
   const double* R[2];
   const int* Re[2];
-  do_block_exp(h, Rstart, h->fexp_R0, n, s, ctl, 0);
+  do_block_digits(h, Rstart, h->fexp_R0, h->fpl_R0, n, ctl, 0);
   L[0] = Rstart;
   Le[0] = h->fexp_R0;
+  Lp[0] = h->fpl_R0;
   do_gram_ftc(h, L, Le, 1, L, Le, 1, true, n, s, ctl, 0);
   PROF(LSBA_K_SMALL, launch_small_start(st, w, start_flags));
-  do_update_ftc(h, L, Le, 1, nullptr, n, h->basis, h->fexp, nullptr, nullptr, w.coef1, w.tri1,
-                nullptr, nullptr, nullptr, ctl, 0);
+  do_update_ftc(h, Lp, Le, 1, nullptr, n, h->basis, h->fexp, h->fpl, nullptr, nullptr, nullptr,
+                w.coef1, w.tri1, nullptr, nullptr, nullptr, ctl, 0);
   for (int k = 1; k <= kmax; ++k) {
     const double* U = (k == 1) ? h->basis : h->Ub;
-    const int* Ue = (k == 1) ? h->fexp : h->fexp_U;
     do_spmm(h, A, U, h->Wb, s, ctl, 1);
-    do_block_exp(h, h->Wb, h->fexp_W, n, s, ctl, 1);
+    do_block_digits(h, h->Wb, h->fexp_W, h->fpl_W, n, ctl, 1);
     if (k == 1) {
       L[0] = h->basis;
       Le[0] = h->fexp;
+      Lp[0] = h->fpl;
       R[0] = h->Wb;
       Re[0] = h->fexp_W;
       do_gram_ftc(h, L, Le, 1, R, Re, 1, false, n, s, ctl, 1);
       PROF(LSBA_K_SMALL, launch_small_step(st, w, 1, 0));
       L[1] = h->Wb;
       Le[1] = h->fexp_W;
-      do_update_ftc(h, L, Le, 2, nullptr, n, h->Ub, h->fexp_U, nullptr, nullptr, w.coef1, nullptr,
-                    nullptr, nullptr, nullptr, ctl, 1);
+      Lp[1] = h->fpl_W;
+      do_update_ftc(h, Lp, Le, 2, nullptr, n, h->Ub, h->fexp_U, h->fpl_U, nullptr, nullptr, nullptr,
+                    w.coef1, nullptr, nullptr, nullptr, nullptr, ctl, 1);
     } else {
       for (int i = 0; i < k - 1; ++i) {
         L[i] = h->basis + (size_t)i * blk;
         Le[i] = basis_exp(h, n, s, i);
+        Lp[i] = basis_planes(h, n, i);
       }
       L[k - 1] = h->Ub;
       Le[k - 1] = h->fexp_U;
+      Lp[k - 1] = h->fpl_U;
       R[0] = h->Ub;
       Re[0] = h->fexp_U;
       R[1] = h->Wb;
@@ -659,9 +683,10 @@ static void enqueue_cycle_ftc(lsba_ctx* h, const lsba_csr* A, const double* Rsta
       enqueue_side(h, k);
       L[k] = h->Wb;
       Le[k] = h->fexp_W;
-      do_update_ftc(h, L, Le, k + 1, nullptr, n, h->basis + (size_t)(k - 1) * blk,
-                    h->fexp + (size_t)(k - 1) * f64tc_exp_count(n, s), h->Ub, h->fexp_U, w.coef1,
-                    w.tri1, w.coef2, w.chain, skel == SK_LS ? w.tri2 : nullptr, ctl, k);
+      Lp[k] = h->fpl_W;
+      do_update_ftc(h, Lp, Le, k + 1, nullptr, n, h->basis + (size_t)(k - 1) * blk,
+                    basis_exp(h, n, s, k - 1), basis_planes(h, n, k - 1), h->Ub, h->fexp_U, h->fpl_U,
+                    w.coef1, w.tri1, w.coef2, w.chain, skel == SK_LS ? w.tri2 : nullptr, ctl, k);
     }
   }
   wait_side(h, kmax);
@@ -1155,14 +1180,14 @@ static int run_cycles(lsba_handle h, const lsba_csr* A, const double* Bw, double
     PROF(LSBA_K_SMALL, launch_small_end(st, w));
     if (h->use_ftc) {
       // on the FP64 tensor-core update; X's own term in FP64
-      const double* L[LSBA_MAXB];
+      const unsigned char* Lp[LSBA_MAXB];
       const int* Le[LSBA_MAXB];
       for (int i = 0; i <= j; ++i) {
-        L[i] = h->basis + (size_t)i * n * s;
-        Le[i] = h->fexp + (size_t)i * f64tc_exp_count(n, s);
+        Lp[i] = basis_planes(h, n, i);
+        Le[i] = basis_exp(h, n, s, i);
       }
-      do_update_ftc(h, L, Le, j + 1, Xw, n, Xw, nullptr, h->Ub, h->fexp_U, w.coef1, nullptr,
-                    w.coef2, nullptr, nullptr, h->d_ctl, LSBA_END_STEP);
+      do_update_ftc(h, Lp, Le, j + 1, Xw, n, Xw, nullptr, nullptr, h->Ub, h->fexp_U, h->fpl_U,
+                    w.coef1, nullptr, w.coef2, nullptr, nullptr, h->d_ctl, LSBA_END_STEP);
     } else if (h->use_tcs && update_tcs_eligible(s, j + 1, true)) {
       // on the stored digit planes of V_1..V_{j+1}; X's own term in double-float
       prof_begin(h, LSBA_K_UPDATE);
@@ -1556,8 +1581,9 @@ int64_t lsba_workspace_bytes(int64_t n, int64_t nnz, int s, int m) {
   bytes += (int64_t)((2 * L.hist_cap + 2 * (m + 4)) * sizeof(int));
   if (s == 8) {  // stored digit planes of the basis (double-float tensor-core Gram)
     bytes += (int64_t)((m + 1) * (digit_block_bytes(n, s) + sizeof(int) * digit_exp_count(n, s)));
-    // exponents and FP64 coefficients of the FP64 tensor-core passes
+    // exponents, digit planes and FP64 coefficients of the FP64 tensor-core passes
     bytes += (int64_t)(sizeof(int) * (size_t)(m + 4) * f64tc_exp_count(n, s) +
+                       (size_t)(m + 4) * f64tc_plane_bytes(n) +
                        sizeof(double) * 2 * 8 * (size_t)(m + 3) * 8);
   }
   return bytes;
@@ -1881,32 +1907,38 @@ int lsba_combine_fp64tc(lsba_handle h, const double* d_in, int nin, int64_t n, i
     return LSBA_INVALID_ARG;
   CK(cudaSetDevice(h->device));
   cudaStream_t st = h->stream;
-  const size_t ec = f64tc_exp_count(n, s);
+  const size_t ec = f64tc_exp_count(n, s), pb = f64tc_plane_bytes(n);
   int* ex = nullptr;
   double* cf = nullptr;
+  unsigned char* pl = nullptr;
   if (ws_alloc(h, &ex, sizeof(int) * ec * nin) != cudaSuccess ||
-      ws_alloc(h, &cf, sizeof(double) * 2 * 8 * (size_t)nin * 8) != cudaSuccess) {
+      ws_alloc(h, &cf, sizeof(double) * 2 * 8 * (size_t)nin * 8) != cudaSuccess ||
+      ws_alloc(h, &pl, pb * nin) != cudaSuccess) {
     cudaGetLastError();
     ws_free(h, ex);
     ws_free(h, cf);
+    ws_free(h, pl);
     return LSBA_OUT_OF_MEMORY;
   }
-  const double* in[LSBA_MAXB];
+  const unsigned char* in[LSBA_MAXB];
   const int* ein[LSBA_MAXB];
   for (int i = 0; i < nin; ++i) {
-    in[i] = d_in + (size_t)i * n * s;
+    in[i] = pl + (size_t)i * pb;
     ein[i] = ex + (size_t)i * ec;
-    launch_block_exp(st, in[i], n, s, ex + (size_t)i * ec, nullptr, 0);
+    launch_block_digits(st, d_in + (size_t)i * n * s, n, ex + (size_t)i * ec, pl + (size_t)i * pb,
+                        nullptr, 0);
   }
   CK(cudaMemsetAsync(&h->d_ctl->error, 0, sizeof(int), st));
   prof_begin(h, LSBA_K_UPDATE);
-  launch_update_f64tc(st, in, ein, nin, nullptr, n, d_out1, nullptr, d_out2, nullptr, d_C1, d_T,
-                      d_C2, nullptr, nullptr, cf, nullptr, -1, &h->d_ctl->error, h->num_sms);
+  launch_update_f64tc(st, in, ein, nin, nullptr, n, d_out1, nullptr, nullptr, d_out2, nullptr,
+                      nullptr, d_C1, d_T, d_C2, nullptr, nullptr, cf, nullptr, -1, &h->d_ctl->error,
+                      h->num_sms);
   prof_end(h);
   CK(cudaGetLastError());
   CK(cudaMemcpyAsync(&h->h_ctl->error, &h->d_ctl->error, sizeof(int), cudaMemcpyDeviceToHost, st));
   ws_free(h, ex);
   ws_free(h, cf);
+  ws_free(h, pl);
   CK(cudaStreamSynchronize(st));
   prof_collect(h);
   return h->h_ctl->error ? LSBA_DEVICE_TIMEOUT : LSBA_OK;

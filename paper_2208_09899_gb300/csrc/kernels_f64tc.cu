@@ -197,6 +197,110 @@ void launch_block_exp(cudaStream_t st, const double* V, int64_t n, int s, int* e
 
 size_t f64tc_exp_count(int64_t n, int s) { return (size_t)((n + 127) / 128) * s; }
 
+// ---------------------------------------------------------------- digit planes
+// The stored digits of an n x 8 FP64 block: for tile tau (rows 128 tau ..),
+// digit t (0 = most significant) and tile row r, the 8 bytes at
+//   planes + ((tau * 7 + t) * 128 + r) * 8 + c,  c = 0..7 (the columns),
+// are the biased digits d_t + 128 of F = trunc(x 2^(54 - E)) (x the value in
+// row 128 tau + r, column c; E the tile column's exponent).  Rows past n hold
+// digit 0 (byte 128).  7 KB a tile: 7 bytes a value, read by the update
+// instead of the FP64 block, so the digits of a block are formed once, by the
+// pass that writes it.  A tile column holding a non-finite value has E = 1025
+// (the exponent of its maximum's bits), and its digits are meaningless.
+#define FT_PLANE_TILE 7168
+#define FT_EXP_NONFINITE 1025
+
+size_t f64tc_plane_bytes(int64_t n) { return (size_t)((n + 127) / 128) * FT_PLANE_TILE; }
+
+// Byte p (0..7) of each of eight 64-bit words, packed in order (word c -> byte c).
+__device__ __forceinline__ uint2 ft_gather_byte(const unsigned long long (&g)[8], int p) {
+  const uint32_t b = (uint32_t)(p & 3), sel = b | ((4u + b) << 4);
+  uint32_t w[8];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) w[c] = p >= 4 ? (uint32_t)(g[c] >> 32) : (uint32_t)g[c];
+  const uint32_t p01 = __byte_perm(w[0], w[1], sel), p23 = __byte_perm(w[2], w[3], sel);
+  const uint32_t p45 = __byte_perm(w[4], w[5], sel), p67 = __byte_perm(w[6], w[7], sel);
+  return make_uint2(__byte_perm(p01, p23, 0x5410), __byte_perm(p45, p67, 0x5410));
+}
+
+// Eight biased digit bytes (d + 128) to eight fp16 digits d, exact: the half
+// word 0x64 << 8 | b is 1024 + b, and 1024 + b - 1152 = d.
+__device__ __forceinline__ uint4 ft_expand8(uint2 w) {
+  const uint32_t k = 0x64646464u;
+  uint32_t h[4] = {__byte_perm(w.x, k, 0x4140), __byte_perm(w.x, k, 0x4342),
+                   __byte_perm(w.y, k, 0x4140), __byte_perm(w.y, k, 0x4342)};
+  const __half2 off = __halves2half2(__ushort_as_half((unsigned short)0x6480u),
+                                     __ushort_as_half((unsigned short)0x6480u));
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const __half2 v = __hsub2(*reinterpret_cast<const __half2*>(&h[i]), off);
+    h[i] = *reinterpret_cast<const uint32_t*>(&v);
+  }
+  return make_uint4(h[0], h[1], h[2], h[3]);
+}
+
+// Exponent of a tile column from the maximum of the high words of |x|.
+__device__ __forceinline__ int ft_exp_of_hi(uint32_t hi) { return max((int)(hi >> 20) - 1022, FT_EXP_MIN); }
+
+// The biased digit planes of 8 values (one row of a tile) with exponents e[c],
+// stored at dst (the row's 8 bytes of digit plane 0; planes 1024 bytes apart).
+__device__ __forceinline__ void ft_store_row_digits(const double (&x)[8], const int* e,
+                                                    unsigned char* dst) {
+  unsigned long long g[8];
+  bool nf = false;
+#pragma unroll
+  for (int c = 0; c < 8; ++c) g[c] = ft_biased(x[c], e[c], nf);
+#pragma unroll
+  for (int t = 0; t < 7; ++t) *reinterpret_cast<uint2*>(dst + t * 1024) = ft_gather_byte(g, 6 - t);
+}
+
+// Exponents and digit planes of an n x 8 FP64 block: one CTA of 128 threads
+// per tile, thread r owns row r.
+__global__ void __launch_bounds__(128) k_block_digits(const double* __restrict__ V, int64_t n,
+                                                      int* __restrict__ ex,
+                                                      unsigned char* __restrict__ planes,
+                                                      const Ctl* ctl, int guard) {
+  if (guard && !*(volatile const int*)&ctl->active) return;
+  __shared__ uint32_t red[4][8];
+  __shared__ int es[8];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int64_t tile = blockIdx.x, row = tile * 128 + tid;
+  double x[8];
+  if (row < n) {
+    const double2* p = reinterpret_cast<const double2*>(V + row * 8);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const double2 v = p[i];
+      x[2 * i] = v.x;
+      x[2 * i + 1] = v.y;
+    }
+  } else {
+#pragma unroll
+    for (int c = 0; c < 8; ++c) x[c] = 0.0;
+  }
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    const uint32_t hi = (uint32_t)((unsigned long long)__double_as_longlong(x[c]) >> 32) & 0x7FFFFFFFu;
+    const uint32_t m = __reduce_max_sync(0xffffffffu, hi);
+    if (lane == 0) red[warp][c] = m;
+  }
+  __syncthreads();
+  if (tid < 8) {
+    const uint32_t m = max(max(red[0][tid], red[1][tid]), max(red[2][tid], red[3][tid]));
+    const int e = ft_exp_of_hi(m);
+    es[tid] = e;
+    ex[tile * 8 + tid] = e;
+  }
+  __syncthreads();
+  ft_store_row_digits(x, es, planes + (size_t)tile * FT_PLANE_TILE + (size_t)tid * 8);
+}
+
+void launch_block_digits(cudaStream_t st, const double* V, int64_t n, int* ex, unsigned char* planes,
+                         const Ctl* ctl, int guard) {
+  const int64_t tiles = (n + 127) / 128;
+  if (tiles > 0) k_block_digits<<<(unsigned)tiles, 128, 0, st>>>(V, n, ex, planes, ctl, guard);
+}
+
 // ---------------------------------------------------------------- Gram
 // G = L^T R with L = [L_1..L_a], R = [R_1..R_b] (s = 8), the partial sums of
 // one CTA's row range (whole 128-row tiles) into partials[blockIdx.x][a s][b s].
@@ -614,36 +718,76 @@ void launch_gram_f64tc(cudaStream_t st, const GramPlan& p, const double* const* 
 
 // ---------------------------------------------------------------- update
 // out1 = sum_b in_b C1'_b (+ X C1'_X), out2 = sum_b in_b C2'_b (+ X C2'_X) for
-// n x 8 FP64 blocks in_1..in_nin with per-tile exponents, coefficients folded
-// beforehand (k_coef_fold64).  One CTA of 128 threads per 128-row tile at a
-// time, thread r owning row r (the MMA's M = 128 rows, K = the 8 nin input
-// columns, N = levels x 16 outputs):
-//   * the tile's input exponents e_kk give E = max_kk e_kk; coefficient row kk
-//     is scaled by 2^(e_kk - E) (exact) and split with one exponent f_n per
-//     output column n, so sum_kk in[r][kk] C[kk][n] = 2^(E + f_n - 55) T[r][n];
-//   * k-steps of 16 columns (two input blocks): each thread splits its row's
-//     16 values into the digit planes of buffer ks & 1 (the 8 values of one
-//     block are one 16-byte core-matrix row), thread 0 issues 7 MMAs against
-//     the tile's coefficient digit stack; the accumulators are flushed into
-//     FP64 every 8 k-steps (128 columns keep the level sums exact);
-//   * X's own term is added in FP64 (X is much larger than its correction late
-//     in a solve, so it does not go through the digits), the outputs are
-//     stored, and the tile maxima of the output columns give their exponents.
-#define UF_THREADS 128
+// n x 8 blocks in_1..in_nin given by their exponents and digit planes, with
+// the coefficients folded beforehand (k_coef_fold64); the outputs are written
+// in FP64 together with their own exponents and digit planes.  For a 128-row
+// tile (the MMA's M) with input exponents e_kk and E = max_kk e_kk,
+// coefficient row kk is scaled by 2^(e_kk - E) and split with one exponent
+// f_n per output column n, so sum_kk in[r][kk] C[kk][n] = 2^(E + f_n - 55)
+// T[r][n]; K = 8 nin columns go in k-steps of 16 (two input blocks), and the
+// level sums are flushed into FP64 every 8 k-steps (a window: 128 columns
+// keep them exact).  X's own term is added in FP64 (late in a solve X is much
+// larger than its correction, so it does not go through the digits).
+//
+// One persistent CTA an SM, 18 warps in four roles joined by mbarriers:
+//   warps 0-7 (expansion): per k-step, thread (row r, block h) expands its
+//     row's 7 digit rows (8 bytes -> 8 fp16) from the ring into the A operand
+//     buffer g % 3, which lives in tensor memory (lane = row, 8 columns a
+//     digit plane: tcgen05.st, so the A digits never pass through shared
+//     memory), and thread (cq, cn, ckb) splits one coefficient value into the
+//     B stack in shared memory (N = 8 digit slots x 16 outputs, slot 7 zero)
+//     from the launch's significand table; at a tile's start they form E and
+//     the f_n (parameter slot j % 8);
+//   warp 16, lane 0: bulk copies (the TMA engine) of the plane sets (7 KB,
+//     one block's tile) into a ring of UF_NST stages, across tiles;
+//   warp 17, lane 0: the 7 MMAs of a k-step (digit t of A against slots
+//     0..7-t, into accumulator column 16 t, so pair (t, u) lands on level
+//     t + u) into accumulator buffer (window % 2);
+//   warps 8-15 (epilogue; tensor-memory lanes = rows, warp 8 + 4 o + i for
+//     lane quarter i and output half o): each window's levels into 8 FP64
+//     accumulators a row, then X's term, the outputs, their exponents and
+//     digit planes, while the next tile's k-steps run.
+// Tensor memory: accumulators in columns [0, 256), A buffers of 56 columns
+// from column 256.
+// Barriers (parity = use count & 1): full/empty (ring), afull/afree (operand
+// buffers), accfull/accfree (accumulators), pready/pfree (tile parameters).
+// A wait that gives up sets the CTA's abort flag; from then on every wait
+// returns at once and no copy or MMA is issued, so every role runs out its
+// loops and the CTA ends after its copies and MMAs in flight have landed.
+// A non-finite input (exponent 1025) or coefficient makes the tile's outputs
+// NaN.
+#define UF_THREADS 576
+#define UF_EWARP0 8
+#define UF_PWARP 16
+#define UF_MWARP 17
 #define UF_MAXIN 24
 #define UF_FLUSH 8
-#define UF_APLANE 4096
-#define UF_ABUF (7 * UF_APLANE)
+#define UF_NST 12
+#define UF_ND 3
+#define UF_ACOL 256        // tensor-memory column of A buffer 0 (56 columns each)
+#define UF_PSLOTS 8
+#define UF_PSTRIDE 20
+#define UF_OFF_B (UF_NST * FT_PLANE_TILE)
+#define UF_OFF_CM (UF_OFF_B + UF_ND * 4096)
+#define UF_OFF_CS (UF_OFF_CM + 8 * UF_MAXIN * 16 * 8)
+#define UF_OFF_EX (UF_OFF_CS + 8 * UF_MAXIN * 16 * 2)
+#define UF_OFF_PAR (UF_OFF_EX + 8 * UF_MAXIN * 4)
+#define UF_OFF_RED (UF_OFF_PAR + UF_PSLOTS * UF_PSTRIDE * 4)
+#define UF_OFF_BAR (UF_OFF_RED + 1024)
+#define UF_SMEM (UF_OFF_BAR + 512)
 
 struct UpdF64Args {
-  F64Blocks in;
-  int nin, nks;
+  const unsigned char* ip[UF_MAXIN];   // input digit planes
+  const int* ie[UF_MAXIN];             // input exponents
+  int nin, nks, nw;                    // inputs, k-steps and windows a tile
   const double* X;
   int64_t n;
   double* out1;
   double* out2;
   int* e_out1;
   int* e_out2;
+  unsigned char* p_out1;
+  unsigned char* p_out2;
   const double* cf;      // C1' [ncoef * 8][8] row-major, then C2' likewise
   int ncoef;
   const Ctl* ctl;
@@ -651,250 +795,393 @@ struct UpdF64Args {
   int* err;
 };
 
-template <int MINB>
-__global__ void __launch_bounds__(UF_THREADS, MINB) k_update_f64tc(const __grid_constant__ UpdF64Args u) {
+__device__ __forceinline__ void uf_bar(int id, int count) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+
+// A bounded wait that honours the CTA's abort flag (see above).
+__device__ __forceinline__ bool uf_wait(uint64_t* bar, unsigned parity, volatile int* abortf, int* err) {
+  if (*abortf) return false;
+  if (mbar_wait_bounded(bar, parity)) return true;
+  *abortf = 1;
+  if (err) atomicExch(err, 1);
+  return false;
+}
+
+// Tensor-memory stores of 4 columns (32-bit) for the warp's 32 lanes, and
+// the MMA with the A operand in tensor memory (kind::f16, issued by one thread).
+__device__ __forceinline__ void uf_st4(uint32_t taddr, uint4 v) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};" ::"r"(taddr), "r"(v.x),
+               "r"(v.y), "r"(v.z), "r"(v.w)
+               : "memory");
+}
+__device__ __forceinline__ void uf_mma_ta(uint32_t d_tmem, uint32_t a_tmem, uint64_t bdesc, uint32_t idesc,
+                                          uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "r"(a_tmem), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+// Levels 0..7 of 8 outputs (8 columns a level at taddr + 16 l): all eight
+// loads issued before one wait, then combined into T as in ft_levels16.
+__device__ __forceinline__ void uf_levels8(uint32_t taddr, long long (&T)[8]) {
+  uint32_t r[8][8];
+#pragma unroll
+  for (int l = 0; l < 8; ++l)
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[l][0]), "=r"(r[l][1]), "=r"(r[l][2]), "=r"(r[l][3]), "=r"(r[l][4]),
+                   "=r"(r[l][5]), "=r"(r[l][6]), "=r"(r[l][7])
+                 : "r"(taddr + (uint32_t)(16 * l))
+                 : "memory");
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    long long t = 0;
+    int s6 = 0;
+#pragma unroll
+    for (int l = 0; l < 8; ++l) {
+      const int si = __float2int_rn(__uint_as_float(r[l][j]));
+      if (l == 0) t = si;
+      else if (l <= 5) t = (t << 8) + si;
+      else if (l == 6) s6 = si;
+      else t = (t << 3) + (((long long)s6 * 256 + si) >> 13);
+    }
+    T[j] = t;
+  }
+}
+
+__global__ void __launch_bounds__(UF_THREADS, 1) k_update_f64tc(const __grid_constant__ UpdF64Args u) {
   if (u.step >= 0 && *(volatile const int*)&u.ctl->update_step != u.step) return;
   extern __shared__ __align__(1024) unsigned char sm[];
-  unsigned char* Abuf = sm;                                   // [2][7][4096]
-  unsigned char* Bst = sm + 2 * UF_ABUF;                      // [nks][4096]
-  int* ex = reinterpret_cast<int*>(Bst + (size_t)u.nks * 4096);   // [8 UF_MAXIN]
-  int* fexp = ex + 8 * UF_MAXIN;                              // [16]
-  unsigned long long* red = reinterpret_cast<unsigned long long*>(fexp + 16);  // [4][16]
-  int* misc = reinterpret_cast<int*>(red + 64);               // [0] bad coefficients
-  uint64_t* mmad = reinterpret_cast<uint64_t*>(misc + 4);     // [2]
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(mmad + 2);
+  unsigned char* ring = sm;                                            // [UF_NST][7168] plane sets
+  unsigned char* bst = sm + UF_OFF_B;                                  // [UF_ND][4096] fp16 B stacks
+  unsigned long long* cm = reinterpret_cast<unsigned long long*>(sm + UF_OFF_CM);  // [8 nin][16]
+  short* cs = reinterpret_cast<short*>(sm + UF_OFF_CS);                // [8 nin][16]
+  int* exs = reinterpret_cast<int*>(sm + UF_OFF_EX);                   // [8 nin]
+  int* par = reinterpret_cast<int*>(sm + UF_OFF_PAR);                  // [UF_PSLOTS][UF_PSTRIDE]
+  int* redx = reinterpret_cast<int*>(sm + UF_OFF_RED);                 // [8][16] + [8]
+  uint32_t* rede = reinterpret_cast<uint32_t*>(sm + UF_OFF_RED + 576); // [8 warps][8]
+  int* eo = reinterpret_cast<int*>(sm + UF_OFF_RED + 832);             // [16]
+  volatile int* abortf = reinterpret_cast<volatile int*>(sm + UF_OFF_RED + 960);
+  int* badc = reinterpret_cast<int*>(sm + UF_OFF_RED + 964);
+  uint64_t* full = reinterpret_cast<uint64_t*>(sm + UF_OFF_BAR);
+  uint64_t* empty = full + UF_NST;
+  uint64_t* afull = empty + UF_NST;
+  uint64_t* afree = afull + UF_ND;
+  uint64_t* accfull = afree + UF_ND;
+  uint64_t* accfree = accfull + 2;
+  uint64_t* pready = accfree + 2;
+  uint64_t* pfree = pready + UF_PSLOTS;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + UF_OFF_BAR + 448);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int nin = u.nin, K = 8 * nin;
+  const int nin = u.nin, K = 8 * nin, nks = u.nks, nw = u.nw;
   const bool two = u.out2 != nullptr;
   const int64_t ntile = (u.n + 127) / 128;
+  const int64_t ntl = (int64_t)blockIdx.x < ntile ? (ntile - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  const int64_t nq = ntl * nin;   // plane sets this CTA consumes, in (tile, block) order
 
-  for (uint32_t i = (uint32_t)tid * 16; i < (uint32_t)u.nks * 4096u; i += UF_THREADS * 16)
-    *reinterpret_cast<uint4*>(Bst + i) = make_uint4(0u, 0u, 0u, 0u);
+  for (int i = tid * 16; i < UF_ND * 4096; i += UF_THREADS * 16)
+    *reinterpret_cast<uint4*>(bst + i) = make_uint4(0u, 0u, 0u, 0u);
   if (tid == 0) {
-    mbar_init(&mmad[0], 1);
-    mbar_init(&mmad[1], 1);
+    *abortf = 0;
+    *badc = 0;
+    for (int i = 0; i < UF_NST; ++i) {
+      mbar_init(&full[i], 1);
+      mbar_init(&empty[i], 4);
+    }
+    for (int i = 0; i < UF_ND; ++i) {
+      mbar_init(&afull[i], 8);
+      mbar_init(&afree[i], 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&accfull[i], 1);
+      mbar_init(&accfree[i], 8);
+    }
+    for (int i = 0; i < UF_PSLOTS; ++i) {
+      mbar_init(&pready[i], 1);
+      mbar_init(&pfree[i], 8);
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 0) tc_alloc(tslot, 128);
+  if (warp == 0) tc_alloc(tslot, 512);
   tc_fence_smem();
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tslot;
-  const uint32_t tlane = tmem + ((uint32_t)(32 * warp) << 16);
-  bool failed = false;
-  int gks = 0;   // k-steps issued by this CTA (mbarrier phases)
-
-  auto load = [&](int64_t tile, int ks, double (&x)[16]) {
-    const int64_t row = tile * 128 + tid;
-#pragma unroll
-    for (int kb = 0; kb < 2; ++kb) {
-      const int blk = 2 * ks + kb;
-      if (blk < nin && row < u.n) {
-        const double2* p = reinterpret_cast<const double2*>(u.in.p[blk] + row * 8);
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          const double2 v = p[i];
-          x[8 * kb + 2 * i] = v.x;
-          x[8 * kb + 2 * i + 1] = v.y;
+  // The coefficients' significand table (tile-independent): for (kk, n),
+  // cm = 2 m | sign << 63 (m the 53-bit significand, 52 bits for subnormals)
+  // and cs = 1022 - max(eb, 1), so that digit integer of C[kk][n] 2^(e_kk - E)
+  // against group exponent F is (2 m) >> (F + E - e_kk + cs).
+  for (int e = tid; e < 16 * K; e += UF_THREADS) {
+    const int n = e & 15, kk = e >> 4;
+    unsigned long long mv = 0ull;
+    int sh = 1021;
+    if (n < 8 || two) {
+      const double c = u.cf[(n < 8 ? 0 : (size_t)u.ncoef * 64) + (size_t)kk * 8 + (n & 7)];
+      const unsigned long long b = (unsigned long long)__double_as_longlong(c);
+      const int eb = (int)((b >> 52) & 0x7FF);
+      if (eb == 0x7FF) *badc = 1;
+      const unsigned long long m = (b & 0x000FFFFFFFFFFFFFull) | (eb ? 0x0010000000000000ull : 0ull);
+      mv = (m << 1) | (b & 0x8000000000000000ull);
+      sh = 1022 - max(eb, 1);
+    }
+    cm[kk * 16 + n] = mv;
+    cs[kk * 16 + n] = (short)sh;
+  }
+  __syncthreads();
+  if (warp < UF_EWARP0) {
+    // ================= expansion warps (256 threads)
+    const int r = tid & 127, h = tid >> 7;                        // A: row r of block 2 ks + h
+    const int cq = tid & 7, cn = (tid >> 3) & 15, ckb = tid >> 7;  // B: value (8 (2 ks + ckb) + cq, cn)
+    int ne = (tid < K && ntl > 0) ? u.ie[tid >> 3][(int64_t)blockIdx.x * 8 + (tid & 7)] : 0;
+    int64_t q = 0;
+    int g = 0;
+    for (int64_t j = 0; j < ntl; ++j) {
+      const int64_t tile = blockIdx.x + j * gridDim.x;
+      const int slot = (int)(j % UF_PSLOTS);
+      int* pr = par + slot * UF_PSTRIDE;
+      uf_bar(1, 256);   // the previous tile's reads of exs and redx are done
+      if (tid == 0 && j >= UF_PSLOTS)
+        uf_wait(&pfree[slot], (unsigned)(((j / UF_PSLOTS) - 1) & 1), abortf, u.err);
+      if (tid < K) exs[tid] = ne;
+      if (tid < K && j + 1 < ntl) ne = u.ie[tid >> 3][(tile + gridDim.x) * 8 + (tid & 7)];
+      uf_bar(1, 256);
+      {
+        const int n = tid & 15;
+        int mE = FT_EXP_MIN, mF = -100000;
+        for (int kk = tid >> 4; kk < K; kk += 16) {
+          const int e = exs[kk];
+          mE = max(mE, e);
+          mF = max(mF, 1022 - (int)cs[kk * 16 + n] + e);
         }
-      } else {
+        mF = max(mF, __shfl_xor_sync(0xffffffffu, mF, 16));
+        mE = __reduce_max_sync(0xffffffffu, mE);
+        if (lane < 16) redx[warp * 16 + lane] = mF;
+        if (lane == 0) redx[128 + warp] = mE;
+      }
+      uf_bar(1, 256);
+      if (tid < 16) {
+        int mF = redx[tid], mE = redx[128];
+        for (int w = 1; w < 8; ++w) {
+          mF = max(mF, redx[w * 16 + tid]);
+          mE = max(mE, redx[128 + w]);
+        }
+        pr[2 + tid] = max(mF - mE - 1022, FT_EXP_MIN);
+        if (tid == 0) {
+          pr[0] = mE;
+          pr[1] = mE >= FT_EXP_NONFINITE ? 1 : 0;
+        }
+      }
+      uf_bar(1, 256);
+      if (tid == 0) mbar_arrive(&pready[slot]);
+      const int E = pr[0];
+      const int fn = pr[2 + cn];
+      for (int ks = 0; ks < nks; ++ks, ++g) {
+        const int d = g % UF_ND, v = g / UF_ND;
+        const int nb = (2 * ks + 1 < nin) ? 2 : 1;
+        bool ok = true;
+        if (h < nb) {
+          const int64_t qq = q + h;
+          ok = uf_wait(&full[qq % UF_NST], (unsigned)((qq / UF_NST) & 1), abortf, u.err);
+        }
+        if (v >= 1) ok = uf_wait(&afree[d], (unsigned)((v - 1) & 1), abortf, u.err) && ok;
+        ok = __all_sync(0xffffffffu, ok);   // the tensor-memory stores are warp-wide
+        if (ok) {
+          // A: digit plane t of block h -> columns UF_ACOL + 56 d + 8 t + 4 h, lane r
+          const uint32_t ta = tmem + ((uint32_t)(32 * (warp & 3)) << 16) +
+                              (uint32_t)(UF_ACOL + 56 * d + 4 * h);
+          if (h < nb) {
+            const unsigned char* S = ring + (size_t)((q + h) % UF_NST) * FT_PLANE_TILE + (size_t)r * 8;
+            uint2 w[7];
 #pragma unroll
-        for (int i = 0; i < 8; ++i) x[8 * kb + i] = 0.0;
+            for (int t = 0; t < 7; ++t) w[t] = *reinterpret_cast<const uint2*>(S + t * 1024);
+#pragma unroll
+            for (int t = 0; t < 7; ++t) uf_st4(ta + (uint32_t)(8 * t), ft_expand8(w[t]));
+          } else {
+#pragma unroll
+            for (int t = 0; t < 7; ++t) uf_st4(ta + (uint32_t)(8 * t), make_uint4(0u, 0u, 0u, 0u));
+          }
+          asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+          const int blk = 2 * ks + ckb;
+          unsigned long long gv = FT_BIAS;
+          if (blk < nin) {
+            const int kk = blk * 8 + cq;
+            const unsigned long long mv = cm[kk * 16 + cn];
+            const int rs = fn + E - exs[kk] + (int)cs[kk * 16 + cn];
+            const unsigned long long F = rs > 63 ? 0ull : ((mv & 0x7FFFFFFFFFFFFFFFull) >> rs);
+            gv = (mv >> 63) ? FT_BIAS - F : FT_BIAS + F;
+          }
+          unsigned short* Bd = reinterpret_cast<unsigned short*>(
+                                   bst + (size_t)d * 4096 + (size_t)(cn >> 3) * 256 + (size_t)ckb * 128 +
+                                   (size_t)(cn & 7) * 16) + cq;
+#pragma unroll
+          for (int t = 0; t < 7; ++t) {
+            const int p = 6 - t;
+            const uint32_t wd = p >= 4 ? (uint32_t)(gv >> 32) : (uint32_t)gv;
+            const uint32_t hw = __byte_perm(wd, 0x64646464u, 0x40u | (uint32_t)(p & 3));
+            const __half dg = __hsub(__ushort_as_half((unsigned short)(hw & 0xFFFFu)),
+                                     __ushort_as_half((unsigned short)0x6480u));
+            Bd[t * 256] = __half_as_ushort(dg);
+          }
+        }
+        tc_fence_smem();
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) {
+          mbar_arrive(&afull[d]);
+          if (h < nb) mbar_arrive(&empty[(q + h) % UF_NST]);
+        }
+        q += nb;
       }
     }
-  };
-
-  for (int64_t tile = blockIdx.x; tile < ntile && !failed; tile += gridDim.x) {
-    const int64_t row = tile * 128 + tid;
-    // ---- input exponents and their maximum
-    for (int kk = tid; kk < K; kk += UF_THREADS) ex[kk] = u.in.e[kk >> 3][tile * 8 + (kk & 7)];
-    if (tid < 16) fexp[tid] = -100000;
-    if (tid == 0) misc[0] = 0;
-    __syncthreads();
-    int emax = FT_EXP_MIN;
-    for (int kk = 0; kk < K; ++kk) emax = max(emax, ex[kk]);
-    // ---- coefficient digits: unit = (output n, input block) -> 8 K values of one N row
-    const int nunits = 16 * nin;
-    for (int pass = 0; pass < 2; ++pass) {
-      for (int un = tid; un < nunits; un += UF_THREADS) {
-        const int n = un & 15, blk = un >> 4;
-        if (n >= 8 && !two) continue;
-        const double* cp = u.cf + (n < 8 ? 0 : (size_t)u.ncoef * 64) + (size_t)blk * 64 + (n & 7);
-        double cs[8];
-        bool nf = false;
-        unsigned long long bmax = 0ull;
+  } else if (warp < UF_PWARP) {
+    // ================= epilogue warps (256 threads): lane quarter i = warp & 3,
+    // output half o (out1 / out2), row er of each tile
+    const int ew = warp - UF_EWARP0, o = ew >> 2, qd = ew & 3, er = 32 * qd + lane;
+    const uint32_t tl = tmem + ((uint32_t)(32 * qd) << 16) + (uint32_t)(8 * o);
+    const bool olive = o == 0 || two;
+    double* outp = o ? u.out2 : u.out1;
+    int* eout = o ? u.e_out2 : u.e_out1;
+    unsigned char* pout = o ? u.p_out2 : u.p_out1;
+    const double* cx = u.cf + (o ? (size_t)u.ncoef * 64 : 0) + (size_t)nin * 64;   // X's coefficient rows
+    int wi = 0;
+    for (int64_t j = 0; j < ntl; ++j) {
+      const int64_t tile = blockIdx.x + j * gridDim.x;
+      const int slot = (int)(j % UF_PSLOTS);
+      const int* pr = par + slot * UF_PSTRIDE;
+      bool ok = uf_wait(&pready[slot], (unsigned)((j / UF_PSLOTS) & 1), abortf, u.err);
+      double acc[8];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          const double c = cp[q * 8];
-          cs[q] = ft_scale_down(c, ex[blk * 8 + q] - emax);
-          const unsigned long long b = (unsigned long long)__double_as_longlong(cs[q]) & 0x7FFFFFFFFFFFFFFFull;
-          bmax = b > bmax ? b : bmax;
-          nf |= !(fabs(c) <= 1.79769313486231570e308);
-        }
-        if (pass == 0) {
-          atomicMax(&fexp[n], ft_exp_of_bits(bmax));
-          if (nf) misc[0] = 1;
-        } else {
-          const int F = fexp[n];
-          unsigned long long gv[8];
-          bool nf2 = false;
+      for (int c = 0; c < 8; ++c) acc[c] = 0.0;
+      const int E = pr[0];
+      const bool tnan = pr[1] != 0;
+      for (int wl = 0; wl < nw; ++wl, ++wi) {
+        const int a = wi & 1, z = wi >> 1;
+        const bool got = __all_sync(0xffffffffu, uf_wait(&accfull[a], (unsigned)(z & 1), abortf, u.err) && ok);
+        if (got && olive) {
+          tc_fence_after();
+          long long T[8];
+          uf_levels8(tl + (uint32_t)(128 * a), T);
 #pragma unroll
-          for (int q = 0; q < 8; ++q) gv[q] = ft_biased(cs[q], F, nf2);
-          uint4 d[7];
-          ft_digits8(gv, d);
-          unsigned char* dst = Bst + (size_t)(blk >> 1) * 4096 + (size_t)(n >> 3) * 256 +
-                               (size_t)(blk & 1) * 128 + (size_t)(n & 7) * 16;
-#pragma unroll
-          for (int t = 0; t < 7; ++t) *reinterpret_cast<uint4*>(dst + (size_t)t * 512) = d[t];
-        }
-      }
-      __syncthreads();
-    }
-    // ---- k-steps
-    double acc[16];
-#pragma unroll
-    for (int j = 0; j < 16; ++j) acc[j] = 0.0;
-    bool rowbad = false;
-    double xa[16], xb[16];
-    load(tile, 0, xa);
-    for (int ks = 0; ks < u.nks; ++ks) {
-      const int b = gks & 1;
-      if (ks + 1 < u.nks) load(tile, ks + 1, xb);
-      if (gks >= 2 && !mbar_wait_bounded(&mmad[b], (unsigned)(((gks - 2) >> 1) & 1))) failed = true;
-      unsigned char* A = Abuf + (size_t)b * UF_ABUF;
-#pragma unroll
-      for (int kb = 0; kb < 2; ++kb) {
-        const int blk = 2 * ks + kb;
-        unsigned char* dst = A + (size_t)(tid >> 3) * 256 + (size_t)kb * 128 + (size_t)(tid & 7) * 16;
-        if (blk < nin) {
-          unsigned long long gv[8];
-#pragma unroll
-          for (int c = 0; c < 8; ++c) gv[c] = ft_biased(xa[8 * kb + c], ex[blk * 8 + c], rowbad);
-          uint4 d[7];
-          ft_digits8(gv, d);
-#pragma unroll
-          for (int t = 0; t < 7; ++t) *reinterpret_cast<uint4*>(dst + (size_t)t * UF_APLANE) = d[t];
-        } else {
-#pragma unroll
-          for (int t = 0; t < 7; ++t)
-            *reinterpret_cast<uint4*>(dst + (size_t)t * UF_APLANE) = make_uint4(0u, 0u, 0u, 0u);
-        }
-      }
-      tc_fence_smem();
-      tc_fence_before();
-      if (__syncthreads_or(failed)) {
-        failed = true;
-        break;
-      }
-      tc_fence_after();
-      if (tid == 0) {
-        const uint32_t pa = smem_addr(A), pb = smem_addr(Bst + (size_t)ks * 4096);
-#pragma unroll
-        for (int t = 0; t < 7; ++t) {
-          const uint64_t ad = tc_smem_desc(pa + (uint32_t)t * UF_APLANE, 128, 256);
-          const uint64_t bd = tc_smem_desc(pb, 128, 256);
-          const uint32_t accum = ((ks % UF_FLUSH) || t) ? 1u : 0u;
-          tc_mma_bf16(tmem + (uint32_t)(16 * t), ad, bd, tc_idesc_f16_f32(128, 16 * (8 - t)), accum);
-        }
-        tc_commit(&mmad[b]);
-      }
-      if ((ks % UF_FLUSH) == UF_FLUSH - 1 || ks + 1 == u.nks) {
-        if (!mbar_wait_bounded(&mmad[b], (unsigned)((gks >> 1) & 1))) failed = true;
-        tc_fence_after();
-        if (!__syncthreads_or(failed)) {
-          long long Tv[16];
-          ft_levels16(tlane, Tv);
-#pragma unroll
-          for (int j = 0; j < 16; ++j) acc[j] = ft_fma_pow2((double)Tv[j], emax + fexp[j] - 55, acc[j]);
-        } else {
-          failed = true;
+          for (int c = 0; c < 8; ++c) acc[c] = ft_fma_pow2((double)T[c], E + pr[2 + 8 * o + c] - 55, acc[c]);
         }
         tc_fence_before();
-        __syncthreads();
-        tc_fence_after();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&accfree[a]);
       }
-      ++gks;
-      if (failed) break;
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&pfree[slot]);
+      // X's own term (FP64), the outputs, their exponents and digit planes
+      const int64_t row = tile * 128 + er;
+      bool rowbad = false;
+      if (u.X && row < u.n && olive) {
+        const double* xr = u.X + row * 8;
+        double xv[8];
 #pragma unroll
-      for (int i = 0; i < 16; ++i) xa[i] = xb[i];
-    }
-    if (__syncthreads_or(failed)) {
-      failed = true;
-      break;
-    }
-    // ---- X's own term (FP64), outputs, output exponents
-    if (u.X && row < u.n) {
-      const double* xr = u.X + row * 8;   // read before out1 (which may be X) is written
-      double xv[8];
+        for (int qv = 0; qv < 8; ++qv) xv[qv] = xr[qv];
 #pragma unroll
-      for (int q = 0; q < 8; ++q) xv[q] = xr[q];
-      const double* c1 = u.cf + (size_t)nin * 64;
-      const double* c2 = u.cf + (size_t)u.ncoef * 64 + (size_t)nin * 64;
+        for (int qv = 0; qv < 8; ++qv) {
+          rowbad |= !(fabs(xv[qv]) <= 1.79769313486231570e308);
 #pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        rowbad |= !(fabs(xv[q]) <= 1.79769313486231570e308);
-#pragma unroll
-        for (int c = 0; c < 8; ++c) {
-          acc[c] = fma(xv[q], c1[q * 8 + c], acc[c]);
-          if (two) acc[8 + c] = fma(xv[q], c2[q * 8 + c], acc[8 + c]);
+          for (int c = 0; c < 8; ++c) acc[c] = fma(xv[qv], cx[qv * 8 + c], acc[c]);
         }
       }
+      if (rowbad || tnan || *badc) {
+#pragma unroll
+        for (int c = 0; c < 8; ++c) acc[c] = __longlong_as_double(0x7FF8000000000000ll);
+      }
+      uf_bar(2, 256);   // every read of X (out1 may be X) before the stores
+      if (olive && row < u.n) {
+        double2* dp = reinterpret_cast<double2*>(outp + row * 8);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) dp[i] = make_double2(acc[2 * i], acc[2 * i + 1]);
+      }
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        const uint32_t hi = (uint32_t)((unsigned long long)__double_as_longlong(acc[c]) >> 32) & 0x7FFFFFFFu;
+        const uint32_t m = __reduce_max_sync(0xffffffffu, hi);
+        if (lane == 0) rede[ew * 8 + c] = m;
+      }
+      uf_bar(2, 256);
+      if (qd == 0 && lane < 8) {
+        const uint32_t* rm = rede + o * 32 + lane;   // warps 4 o .. 4 o + 3
+        const uint32_t m = max(max(rm[0], rm[8]), max(rm[16], rm[24]));
+        const int e = ft_exp_of_hi(m);
+        eo[8 * o + lane] = e;
+        if (eout && olive) eout[tile * 8 + lane] = e;
+      }
+      uf_bar(2, 256);
+      if (olive && pout) ft_store_row_digits(acc, eo + 8 * o, pout + (size_t)tile * FT_PLANE_TILE + (size_t)er * 8);
     }
-    if (rowbad || misc[0]) {
-#pragma unroll
-      for (int j = 0; j < 16; ++j) acc[j] = __longlong_as_double(0x7FF8000000000000ll);
-    }
-    if (row < u.n) {
-      double2* d1 = reinterpret_cast<double2*>(u.out1 + row * 8);
-#pragma unroll
-      for (int i = 0; i < 4; ++i) d1[i] = make_double2(acc[2 * i], acc[2 * i + 1]);
-      if (two) {
-        double2* d2 = reinterpret_cast<double2*>(u.out2 + row * 8);
-#pragma unroll
-        for (int i = 0; i < 4; ++i) d2[i] = make_double2(acc[8 + 2 * i], acc[8 + 2 * i + 1]);
+  } else if (warp == UF_PWARP) {
+    // ================= bulk copies of the plane sets, in (tile, block) order
+    if (lane == 0) {
+      int64_t issued = 0, tl2 = blockIdx.x;
+      int blk = 0, st = 0;
+      unsigned ph = 0;   // parity of the stage's previous use
+      for (int64_t qq = 0; qq < nq; ++qq) {
+        if (qq >= UF_NST && !uf_wait(&empty[st], ph, abortf, u.err)) break;
+        if (*abortf) break;
+        mbar_expect_tx(&full[st], FT_PLANE_TILE);
+        bulk_copy_g2s(ring + (size_t)st * FT_PLANE_TILE, u.ip[blk] + tl2 * FT_PLANE_TILE, FT_PLANE_TILE,
+                      &full[st]);
+        issued = qq + 1;
+        if (++blk == nin) {
+          blk = 0;
+          tl2 += gridDim.x;
+        }
+        if (++st == UF_NST) {
+          st = 0;
+          if (qq >= UF_NST) ph ^= 1u;
+        }
+      }
+      if (*abortf) {
+        // the last copy issued into each stage lands before the CTA ends
+        for (int64_t qq = issued > UF_NST ? issued - UF_NST : 0; qq < issued; ++qq)
+          mbar_wait_bounded(&full[qq % UF_NST], (unsigned)((qq / UF_NST) & 1));
       }
     }
+  } else {
+    // ================= MMA issue (A from tensor memory, B from shared memory)
+    if (lane == 0) {
+      int g = 0, wi = 0, last = -1;
+      for (int64_t j = 0; j < ntl; ++j) {
+        for (int ks = 0; ks < nks; ++ks, ++g) {
+          const int d = g % UF_ND, v = g / UF_ND;
+          const int a = wi & 1, z = wi >> 1;
+          bool ok = true;
+          if ((ks % UF_FLUSH) == 0 && z >= 1) ok = uf_wait(&accfree[a], (unsigned)((z - 1) & 1), abortf, u.err);
+          ok = uf_wait(&afull[d], (unsigned)(v & 1), abortf, u.err) && ok;
+          const bool wend = (ks % UF_FLUSH) == UF_FLUSH - 1 || ks + 1 == nks;
+          if (ok) {
+            tc_fence_after();
+            const uint64_t bd = tc_smem_desc(smem_addr(bst + (size_t)d * 4096), 128, 256);
 #pragma unroll
-    for (int j = 0; j < 16; ++j) {
-      unsigned long long b =
-          row < u.n ? ((unsigned long long)__double_as_longlong(acc[j]) & 0x7FFFFFFFFFFFFFFFull) : 0ull;
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        const unsigned long long y = __shfl_xor_sync(0xffffffffu, b, o);
-        b = y > b ? y : b;
+            for (int t = 0; t < 7; ++t) {
+              const uint32_t accum = ((ks % UF_FLUSH) || t) ? 1u : 0u;
+              uf_mma_ta(tmem + (uint32_t)(128 * a + 16 * t), tmem + (uint32_t)(UF_ACOL + 56 * d + 8 * t), bd,
+                        tc_idesc_f16_f32(128, 16 * (8 - t)), accum);
+            }
+            tc_commit(&afree[d]);
+            if (wend) tc_commit(&accfull[a]);
+            last = g;
+          }
+          if (wend) ++wi;
+        }
       }
-      if (lane == 0) red[warp * 16 + j] = b;
-    }
-    __syncthreads();
-    if (tid < 16) {
-      unsigned long long b = red[tid];
-      for (int w = 1; w < 4; ++w) b = red[w * 16 + tid] > b ? red[w * 16 + tid] : b;
-      int* eo = tid < 8 ? u.e_out1 : u.e_out2;
-      if (eo && (tid < 8 || two)) eo[tile * 8 + (tid & 7)] = ft_exp_of_bits(b);
-    }
-    __syncthreads();
-  }
-  if (failed) {
-    if (tid == 0) {
-      if (u.err) atomicExch(u.err, 1);
-      for (int b2 = 0; b2 < 2; ++b2) {
-        mbar_wait_bounded(&mmad[b2], 0);
-        mbar_wait_bounded(&mmad[b2], 1);
-      }
+      // the last MMAs complete before the CTA ends
+      if (*abortf && last >= 0) mbar_wait_bounded(&afree[last % UF_ND], (unsigned)((last / UF_ND) & 1));
     }
   }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  if (warp == 0) tc_dealloc(tmem, 128);
+  if (warp == 0) tc_dealloc(tmem, 512);
 }
 
-size_t update_f64tc_smem(int nin) {
-  const int nks = (nin + 1) / 2;
-  return 2 * (size_t)UF_ABUF + (size_t)nks * 4096 + 8 * UF_MAXIN * 4 + 16 * 4 + 64 * 8 + 4 * 4 +
-         2 * 8 + 16;
-}
+size_t update_f64tc_smem(int) { return UF_SMEM; }
 
 bool update_f64tc_eligible(int s, int nin) { return s == 8 && nin >= 1 && nin <= UF_MAXIN; }
 
@@ -956,9 +1243,10 @@ __global__ void __launch_bounds__(128) k_coef_fold64(const __grid_constant__ Coe
   }
 }
 
-void launch_update_f64tc(cudaStream_t st, const double* const* in, const int* const* ein, int nin,
-                         const double* X, int64_t n, double* out1, int* e_out1, double* out2,
-                         int* e_out2, const double* coef1, const double* tri1, const double* coef2,
+void launch_update_f64tc(cudaStream_t st, const unsigned char* const* in, const int* const* ein,
+                         int nin, const double* X, int64_t n, double* out1, int* e_out1,
+                         unsigned char* p_out1, double* out2, int* e_out2, unsigned char* p_out2,
+                         const double* coef1, const double* tri1, const double* coef2,
                          const double* chain, const double* tri2, double* cf, const Ctl* ctl,
                          int step, int* err, int num_sms) {
   const int ncoef = nin + (X ? 1 : 0);
@@ -975,34 +1263,37 @@ void launch_update_f64tc(cudaStream_t st, const double* const* in, const int* co
   k_coef_fold64<<<(f.rows + 15) / 16, 128, 0, st>>>(f);
   static std::atomic<unsigned long long> attr_done{0};
   once_per_device(attr_done, [] {
-    cudaFuncSetAttribute(k_update_f64tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    cudaFuncSetAttribute(k_update_f64tc, cudaFuncAttributeMaxDynamicSharedMemorySize, UF_SMEM);
   });
   UpdF64Args u;
   memset(&u, 0, sizeof(u));
   for (int i = 0; i < nin; ++i) {
-    u.in.p[i] = in[i];
-    u.in.e[i] = ein[i];
+    u.ip[i] = in[i];
+    u.ie[i] = ein[i];
   }
   u.nin = nin;
   u.nks = (nin + 1) / 2;
+  u.nw = (u.nks + UF_FLUSH - 1) / UF_FLUSH;
   u.X = X;
   u.n = n;
   u.out1 = out1;
   u.out2 = out2;
   u.e_out1 = e_out1;
   u.e_out2 = e_out2;
+  u.p_out1 = p_out1;
+  u.p_out2 = p_out2;
   u.cf = cf;
   u.ncoef = ncoef;
   u.ctl = ctl;
   u.step = step;
   u.err = err;
-  // Two CTAs per SM, two short of filling the GPU: the SMs left with one CTA
-  // have room for the iteration's small side kernel.
+  // One CTA an SM, one short of filling the GPU: the SM left free takes the
+  // iteration's small side kernel.
   const int64_t tiles = (n + 127) / 128;
-  int64_t grid = 2LL * num_sms - 2;
+  int64_t grid = num_sms - 1;
   if (grid > tiles) grid = tiles;
   if (grid < 1) grid = 1;
-  k_update_f64tc<2><<<(unsigned)grid, UF_THREADS, update_f64tc_smem(nin), st>>>(u);
+  k_update_f64tc<<<(unsigned)grid, UF_THREADS, UF_SMEM, st>>>(u);
 }
 
 }  // namespace lsba

@@ -239,6 +239,12 @@ void launch_update_f32(cudaStream_t st, const BlockPtrs& in, int nin, int64_t n,
 size_t f64tc_exp_count(int64_t n, int s);
 void launch_block_exp(cudaStream_t st, const double* V, int64_t n, int s, int* ex, const Ctl* ctl,
                       int guard);
+// Exponents and digit planes (7 bytes a value, f64tc_plane_bytes(n) a block)
+// of an n x 8 FP64 block, written by the pass that writes the block and read
+// by the update in place of its FP64 values.
+size_t f64tc_plane_bytes(int64_t n);
+void launch_block_digits(cudaStream_t st, const double* V, int64_t n, int* ex, unsigned char* planes,
+                         const Ctl* ctl, int guard);
 // Gram [L_1..L_a]^T [R_1..R_b] (FP64 blocks with exponents), reduced into G.
 // shared: R_1 is L_a (split once).
 bool gram_f64tc_eligible(int s, int a, int b, bool shared);
@@ -248,14 +254,16 @@ void launch_gram_f64tc(cudaStream_t st, const GramPlan& p, const double* const* 
                        int64_t n, double* partials, double* G, const Ctl* ctl, int guard, int* err);
 // out1 = (sum_i in_i C1_i (+ X C1_X)) T1^{-1},
 // out2 = (sum_i in_i C2_i (+ X C2_X) + out1 Chain) T2^{-1}  (out2 optional),
-// with the triangular factors and the chain folded into the coefficients
-// first (into cf: 2 x 8 ncoef x 8 doubles, ncoef = nin (+1 with X)); the
-// outputs' per-tile exponents go to e_out1 / e_out2 (optional).
+// with the inputs given by their exponents and digit planes, X (optional) in
+// FP64, and the triangular factors and the chain folded into the
+// coefficients first (into cf: 2 x 8 ncoef x 8 doubles, ncoef = nin (+1 with
+// X)); the outputs' exponents and digit planes go to e_out / p_out (optional).
 bool update_f64tc_eligible(int s, int nin);
 size_t update_f64tc_smem(int nin);
-void launch_update_f64tc(cudaStream_t st, const double* const* in, const int* const* ein, int nin,
-                         const double* X, int64_t n, double* out1, int* e_out1, double* out2,
-                         int* e_out2, const double* coef1, const double* tri1, const double* coef2,
+void launch_update_f64tc(cudaStream_t st, const unsigned char* const* in, const int* const* ein,
+                         int nin, const double* X, int64_t n, double* out1, int* e_out1,
+                         unsigned char* p_out1, double* out2, int* e_out2, unsigned char* p_out2,
+                         const double* coef1, const double* tri1, const double* coef2,
                          const double* chain, const double* tri2, double* cf, const Ctl* ctl,
                          int step, int* err, int num_sms);
 // Fixed-order (CTA-order) sum of FP64 Gram partials [nparts][q] into G.
