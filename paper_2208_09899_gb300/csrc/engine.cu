@@ -585,9 +585,9 @@ static void do_block_digits(lsba_ctx* h, const double* V, int* ex, unsigned char
   launch_block_digits(h->stream, V, n, ex, planes, ctl, guard);
   prof_end(h);
 }
-static void do_gram_ftc(lsba_ctx* h, const double* const* L, const int* const* Le, int a,
-                        const double* const* R, const int* const* Re, int b, bool shared, int64_t n,
-                        int s, const Ctl* ctl, int guard) {
+static void do_gram_ftc(lsba_ctx* h, const unsigned char* const* L, const int* const* Le, int a,
+                        const unsigned char* const* R, const int* const* Re, int b, bool shared,
+                        int64_t n, int s, const Ctl* ctl, int guard) {
   prof_begin(h, LSBA_K_GRAM);
   GramPlan p = plan_gram_f64tc(n, s, a, b, h->num_sms);
   launch_gram_f64tc(h->stream, p, L, Le, a, R, Re, b, shared, n, h->partials, h->Gbuf, ctl, guard,
@@ -634,16 +634,14 @@ static void enqueue_cycle_ftc(lsba_ctx* h, const lsba_csr* A, const double* Rsta
   const int skel = w.skel;
   Ctl* ctl = h->d_ctl;
   const size_t blk = (size_t)n * s;
-  const double* L[LSBA_MAXB];
   const int* Le[LSBA_MAXB];
   const unsigned char* Lp[LSBA_MAXB];
-  const double* R[2];
+  const unsigned char* Rp[2];
   const int* Re[2];
   do_block_digits(h, Rstart, h->fexp_R0, h->fpl_R0, n, ctl, 0);
-  L[0] = Rstart;
   Le[0] = h->fexp_R0;
   Lp[0] = h->fpl_R0;
-  do_gram_ftc(h, L, Le, 1, L, Le, 1, true, n, s, ctl, 0);
+  do_gram_ftc(h, Lp, Le, 1, Lp, Le, 1, true, n, s, ctl, 0);
   PROF(LSBA_K_SMALL, launch_small_start(st, w, start_flags));
   do_update_ftc(h, Lp, Le, 1, nullptr, n, h->basis, h->fexp, h->fpl, nullptr, nullptr, nullptr,
                 w.coef1, w.tri1, nullptr, nullptr, nullptr, ctl, 0);
@@ -652,36 +650,31 @@ static void enqueue_cycle_ftc(lsba_ctx* h, const lsba_csr* A, const double* Rsta
     do_spmm(h, A, U, h->Wb, s, ctl, 1);
     do_block_digits(h, h->Wb, h->fexp_W, h->fpl_W, n, ctl, 1);
     if (k == 1) {
-      L[0] = h->basis;
       Le[0] = h->fexp;
       Lp[0] = h->fpl;
-      R[0] = h->Wb;
+      Rp[0] = h->fpl_W;
       Re[0] = h->fexp_W;
-      do_gram_ftc(h, L, Le, 1, R, Re, 1, false, n, s, ctl, 1);
+      do_gram_ftc(h, Lp, Le, 1, Rp, Re, 1, false, n, s, ctl, 1);
       PROF(LSBA_K_SMALL, launch_small_step(st, w, 1, 0));
-      L[1] = h->Wb;
       Le[1] = h->fexp_W;
       Lp[1] = h->fpl_W;
       do_update_ftc(h, Lp, Le, 2, nullptr, n, h->Ub, h->fexp_U, h->fpl_U, nullptr, nullptr, nullptr,
                     w.coef1, nullptr, nullptr, nullptr, nullptr, ctl, 1);
     } else {
       for (int i = 0; i < k - 1; ++i) {
-        L[i] = h->basis + (size_t)i * blk;
         Le[i] = basis_exp(h, n, s, i);
         Lp[i] = basis_planes(h, n, i);
       }
-      L[k - 1] = h->Ub;
       Le[k - 1] = h->fexp_U;
       Lp[k - 1] = h->fpl_U;
-      R[0] = h->Ub;
+      Rp[0] = h->fpl_U;
       Re[0] = h->fexp_U;
-      R[1] = h->Wb;
+      Rp[1] = h->fpl_W;
       Re[1] = h->fexp_W;
-      do_gram_ftc(h, L, Le, k, R, Re, 2, true, n, s, ctl, 1);
+      do_gram_ftc(h, Lp, Le, k, Rp, Re, 2, true, n, s, ctl, 1);
       wait_side(h, k - 1);
       PROF(LSBA_K_SMALL, launch_small_step(st, w, k, 0));
       enqueue_side(h, k);
-      L[k] = h->Wb;
       Le[k] = h->fexp_W;
       Lp[k] = h->fpl_W;
       do_update_ftc(h, Lp, Le, k + 1, nullptr, n, h->basis + (size_t)(k - 1) * blk,
@@ -1865,24 +1858,28 @@ int lsba_gram_fp64tc(lsba_handle h, const double* d_L, int a, const double* d_R,
     }
     h->partials_cap = need;
   }
-  const size_t ec = f64tc_exp_count(n, s);
+  const size_t ec = f64tc_exp_count(n, s), pb = f64tc_plane_bytes(n);
   int* ex = nullptr;
-  if (ws_alloc(h, &ex, sizeof(int) * ec * (a + b)) != cudaSuccess) {
+  unsigned char* pl = nullptr;
+  if (ws_alloc(h, &ex, sizeof(int) * ec * (a + b)) != cudaSuccess ||
+      ws_alloc(h, &pl, pb * (a + b)) != cudaSuccess) {
     cudaGetLastError();
+    ws_free(h, ex);
+    ws_free(h, pl);
     return LSBA_OUT_OF_MEMORY;
   }
-  const double* L[LSBA_MAXB];
+  const unsigned char* L[LSBA_MAXB];
   const int* Le[LSBA_MAXB];
-  const double* R[2];
+  const unsigned char* R[2];
   const int* Re[2];
   for (int i = 0; i < a + b; ++i) {
     const double* blk = i < a ? d_L + (size_t)i * n * s : d_R + (size_t)(i - a) * n * s;
-    launch_block_exp(st, blk, n, s, ex + (size_t)i * ec, nullptr, 0);
+    launch_block_digits(st, blk, n, ex + (size_t)i * ec, pl + (size_t)i * pb, nullptr, 0);
     if (i < a) {
-      L[i] = blk;
+      L[i] = pl + (size_t)i * pb;
       Le[i] = ex + (size_t)i * ec;
     } else {
-      R[i - a] = blk;
+      R[i - a] = pl + (size_t)i * pb;
       Re[i - a] = ex + (size_t)i * ec;
     }
   }
@@ -1894,6 +1891,7 @@ int lsba_gram_fp64tc(lsba_handle h, const double* d_L, int a, const double* d_R,
   CK(cudaGetLastError());
   CK(cudaMemcpyAsync(&h->h_ctl->error, &h->d_ctl->error, sizeof(int), cudaMemcpyDeviceToHost, st));
   ws_free(h, ex);
+  ws_free(h, pl);
   CK(cudaStreamSynchronize(st));
   prof_collect(h);
   return h->h_ctl->error ? LSBA_DEVICE_TIMEOUT : LSBA_OK;

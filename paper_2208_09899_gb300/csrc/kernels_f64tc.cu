@@ -162,6 +162,34 @@ __device__ __forceinline__ void ft_levels8(uint32_t taddr, long long (&T)[8]) {
   }
 }
 
+// Levels 0..7 of 8 outputs (8 columns a level at taddr + 16 l): all eight
+// loads issued before one wait, then combined into T as in ft_levels16.
+__device__ __forceinline__ void ft_levels8b(uint32_t taddr, long long (&T)[8]) {
+  uint32_t r[8][8];
+#pragma unroll
+  for (int l = 0; l < 8; ++l)
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[l][0]), "=r"(r[l][1]), "=r"(r[l][2]), "=r"(r[l][3]), "=r"(r[l][4]),
+                   "=r"(r[l][5]), "=r"(r[l][6]), "=r"(r[l][7])
+                 : "r"(taddr + (uint32_t)(16 * l))
+                 : "memory");
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    long long t = 0;
+    int s6 = 0;
+#pragma unroll
+    for (int l = 0; l < 8; ++l) {
+      const int si = __float2int_rn(__uint_as_float(r[l][j]));
+      if (l == 0) t = si;
+      else if (l <= 5) t = (t << 8) + si;
+      else if (l == 6) s6 = si;
+      else t = (t << 3) + (((long long)s6 * 256 + si) >> 13);
+    }
+    T[j] = t;
+  }
+}
+
 // ---------------------------------------------------------------- exponents
 // Per-(128-row tile, column) exponents of an n x s FP64 block (s <= 32): one
 // CTA of 128 threads per tile, thread r owns row r of the tile.
@@ -199,15 +227,18 @@ size_t f64tc_exp_count(int64_t n, int s) { return (size_t)((n + 127) / 128) * s;
 
 // ---------------------------------------------------------------- digit planes
 // The stored digits of an n x 8 FP64 block: for tile tau (rows 128 tau ..),
-// digit t (0 = most significant) and tile row r, the 8 bytes at
-//   planes + ((tau * 7 + t) * 128 + r) * 8 + c,  c = 0..7 (the columns),
+// tile row r = 16 j + i (slab j of 16 rows, row i in it) and digit t (0 =
+// most significant), the 8 bytes at
+//   planes + tau * 7168 + j * 896 + t * 128 + i * 8 + c,  c = 0..7 (columns),
 // are the biased digits d_t + 128 of F = trunc(x 2^(54 - E)) (x the value in
 // row 128 tau + r, column c; E the tile column's exponent).  Rows past n hold
-// digit 0 (byte 128).  7 KB a tile: 7 bytes a value, read by the update
-// instead of the FP64 block, so the digits of a block are formed once, by the
-// pass that writes it.  A tile column holding a non-finite value has E = 1025
+// digit 0 (byte 128).  7 KB a tile (7 bytes a value), a 16-row slab's 7
+// digit rows contiguous (896 bytes): the update reads a tile's planes, the
+// Gram a slab's, instead of the FP64 block, so the digits of a block are
+// formed once, by the pass that writes it.  A tile column holding a non-finite value has E = 1025
 // (the exponent of its maximum's bits), and its digits are meaningless.
 #define FT_PLANE_TILE 7168
+#define FT_PLANE_SLAB 896
 #define FT_EXP_NONFINITE 1025
 
 size_t f64tc_plane_bytes(int64_t n) { return (size_t)((n + 127) / 128) * FT_PLANE_TILE; }
@@ -243,7 +274,10 @@ __device__ __forceinline__ uint4 ft_expand8(uint2 w) {
 __device__ __forceinline__ int ft_exp_of_hi(uint32_t hi) { return max((int)(hi >> 20) - 1022, FT_EXP_MIN); }
 
 // The biased digit planes of 8 values (one row of a tile) with exponents e[c],
-// stored at dst (the row's 8 bytes of digit plane 0; planes 1024 bytes apart).
+// stored at dst (the row's 8 bytes of digit plane 0; planes 128 bytes apart).
+// Offset of tile row r's digit-0 bytes in a tile's plane set.
+__device__ __forceinline__ size_t ft_row_off(int r) { return (size_t)(r >> 4) * FT_PLANE_SLAB + (size_t)(r & 15) * 8; }
+
 __device__ __forceinline__ void ft_store_row_digits(const double (&x)[8], const int* e,
                                                     unsigned char* dst) {
   unsigned long long g[8];
@@ -251,7 +285,7 @@ __device__ __forceinline__ void ft_store_row_digits(const double (&x)[8], const 
 #pragma unroll
   for (int c = 0; c < 8; ++c) g[c] = ft_biased(x[c], e[c], nf);
 #pragma unroll
-  for (int t = 0; t < 7; ++t) *reinterpret_cast<uint2*>(dst + t * 1024) = ft_gather_byte(g, 6 - t);
+  for (int t = 0; t < 7; ++t) *reinterpret_cast<uint2*>(dst + t * 128) = ft_gather_byte(g, 6 - t);
 }
 
 // Exponents and digit planes of an n x 8 FP64 block: one CTA of 128 threads
@@ -292,7 +326,7 @@ __global__ void __launch_bounds__(128) k_block_digits(const double* __restrict__
     ex[tile * 8 + tid] = e;
   }
   __syncthreads();
-  ft_store_row_digits(x, es, planes + (size_t)tile * FT_PLANE_TILE + (size_t)tid * 8);
+  ft_store_row_digits(x, es, planes + (size_t)tile * FT_PLANE_TILE + ft_row_off(tid));
 }
 
 void launch_block_digits(cudaStream_t st, const double* V, int64_t n, int* ex, unsigned char* planes,
@@ -302,49 +336,59 @@ void launch_block_digits(cudaStream_t st, const double* V, int64_t n, int* ex, u
 }
 
 // ---------------------------------------------------------------- Gram
-// G = L^T R with L = [L_1..L_a], R = [R_1..R_b] (s = 8), the partial sums of
-// one CTA's row range (whole 128-row tiles) into partials[blockIdx.x][a s][b s].
-// With `shared`, R_1 is L_a (the lagged skeletons' [V_1..V_{k-1}, U]^T [U, W])
-// and is split once.
+// G = L^T R with L = [L_1..L_a], R = [R_1..R_b] (s = 8) given by their
+// exponents and digit planes, the partial sums of one CTA's rows (whole
+// 128-row tiles) into partials[blockIdx.x][a s][b s].  With `shared`, R_1 is
+// L_a (the lagged skeletons' [V_1..V_{k-1}, U]^T [U, W]), read once.
 //
 // Rows go in slabs of 16 (one MMA K step) and windows of 128 (one tile: the
-// exponents' group and the exact accumulation window).  Roles (512 threads,
-// 16 warps, so up to 128 registers a thread):
-//   warps 0-9: split a slab's values from its stage into the digit operands
-//     of slab buffer q % ndb (task = block slot x 8-row group);
-//   warp 10: bulk copies (cp.async.bulk, the TMA engine) of every block's 16
-//     rows of a slab (1 KB each, contiguous) into a ring of nst FP64 stages,
-//     one block per lane, up to nst slabs ahead;
-//   warp 11 (one lane): the MMAs of a slab once it is split;
+// exponents' group and the exact accumulation window).  The A operand is
+// L^T's digit plane t (M = L columns, K-major: the core-matrix row of column
+// c holds its 8 rows of the group), the B operand the stack of R's digits
+// u = 0..7 (N = 16 u + R column, slot 7 zero); the MMA of digit t writes from
+// tensor-memory column 16 t, so pair (t, u) lands on level t + u.  Roles
+// (512 threads, 16 warps, up to 128 registers a thread):
+//   warps 0-9: expand a slab's digit bytes from its stage into the operands
+//     of slab buffer q % ndb, warps 0-4 the even slabs and warps 5-9 the odd
+//     ones (two slabs in flight).  Task = (digit t, 8-row group kg, block slot):
+//     the 8 x 8 bytes of the group's rows and the block's columns are read
+//     (64 contiguous bytes) and written column by column as fp16 (the byte
+//     pair of rows 2i, 2i + 1 of a column is one fp16 pair, so the K order
+//     is the row order in both operands);
+//   warp 10: bulk copies (cp.async.bulk, the TMA engine) of every block's two
+//     slabs of a stage (1792 contiguous bytes) into a ring of nst stages, one
+//     block per lane;
+//   warp 11 (one lane): the MMAs of a slab once it is expanded;
 //   warps 12-15: the epilogue of each 128-row window (tensor-memory lanes =
 //     L columns; with two M tiles, tile 0 then tile 1), overlapping the
-//     next window's splits and MMAs.
+//     next window's expansion and MMAs.
 // Barriers (parity = use count & 1):
-//   full[st]  bulk copies -> split warps        empty[st] split warps -> copies
-//   dfull[b]  split warps -> MMA issue          dfree[b]  MMA commit -> split warps
+//   full[st]  bulk copies -> expansion warps     empty[st] expansion warps -> copies
+//   dfull[b]  expansion warps -> MMA issue       dfree[b]  MMA commit -> expansion warps
 //   wdone[w]  MMA commit at a window's end -> epilogue warps
 //   tfree[w]  epilogue warps -> MMA issue (accumulator buffer w reusable)
+// A tile column with a non-finite value (exponent 1025) makes G NaN.
 #define GF_THREADS 512
 #define GF_SPLIT_WARPS 10
 #define GF_TMA_WARP 10
 #define GF_MMA_WARP 11
 #define GF_EPI_WARP0 12
-#define GF_MAXSPLIT 24     // blocks split per slab: a + b - shared
-#define GF_BSTRIDE 1088    // bytes per block in a stage: 16 rows x 64 B + 64 (bank offset)
+#define GF_MAXSPLIT 24     // blocks read per slab: a + b - shared
+#define GF_SSTRIDE 1808    // bytes per block in a stage: 2 slabs (1792) + 16 (bank offset)
+#define GF_ASBO 272        // A operand: bytes from one 8-column group to the next (256 + 16)
 #define GF_MAXST 6
 #define GF_MAXDB 3         // digit slab buffers
-#define GF_MAXTASK 5       // split tasks per warp and slab: 2 GF_MAXSPLIT / 10, rounded up
 
-struct F64Blocks {
-  const double* p[LSBA_MAXB];
-  const int* e[LSBA_MAXB];   // per-(tile, column) exponents: e[i][tile * s + c]
+struct F64Planes {
+  const unsigned char* p[LSBA_MAXB];   // digit planes
+  const int* e[LSBA_MAXB];             // per-(tile, column) exponents: e[i][tile * 8 + c]
 };
 
 struct GramF64Args {
-  F64Blocks L, R;
+  F64Planes L, R;
   int a, b, as, bs, shared, nsplit;
   int ma, ntile, tile1;
-  uint32_t dbuf_bytes, acc_bytes, stage_bytes, tcols;
+  uint32_t aplane_bytes, dbuf_bytes, acc_bytes, stage_bytes, tcols;
   int nst, ndb;
   int64_t n;
   int tiles_per_cta;
@@ -363,21 +407,36 @@ __device__ __forceinline__ void gf_wait(uint64_t* bar, unsigned parity, bool& fa
   failed = __any_sync(0xffffffffu, failed);
 }
 
-// Source block of split slot i (0 .. nsplit-1): L blocks, then the R blocks not shared.
-__device__ __forceinline__ void gf_slot(const GramF64Args& g, int i, const double** p, const int** e,
-                                        int* lblk, int* rblk) {
+// Source block of slot i (0 .. nsplit-1): L blocks, then the R blocks not shared.
+__device__ __forceinline__ void gf_slot(const GramF64Args& g, int i, const unsigned char** p, int* lblk,
+                                        int* rblk) {
   if (i < g.a) {
     *p = g.L.p[i];
-    *e = g.L.e[i];
     *lblk = i;
     *rblk = (g.shared && i == g.a - 1) ? 0 : -1;
   } else {
     const int r = i - g.a + (g.shared ? 1 : 0);
     *p = g.R.p[r];
-    *e = g.R.e[r];
     *lblk = -1;
     *rblk = r;
   }
+}
+
+// fp16 digit pairs of column c (bytes c of rows 2i and 2i + 1, i = 0..3) of an
+// 8 x 8 byte block held as rows w[0..7] (lo, hi words), as one 16-byte row.
+__device__ __forceinline__ uint4 gf_column(const uint2 (&w)[8], int c) {
+  const uint32_t b = (uint32_t)(c & 3), sel = b | ((4u + b) << 8);
+  const __half2 off = __halves2half2(__ushort_as_half((unsigned short)0x6480u),
+                                     __ushort_as_half((unsigned short)0x6480u));
+  uint32_t h[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const uint32_t x0 = c >= 4 ? w[2 * i].y : w[2 * i].x, x1 = c >= 4 ? w[2 * i + 1].y : w[2 * i + 1].x;
+    const uint32_t v = (__byte_perm(x0, x1, sel) & 0x00FF00FFu) | 0x64006400u;
+    const __half2 d = __hsub2(*reinterpret_cast<const __half2*>(&v), off);
+    h[i] = *reinterpret_cast<const uint32_t*>(&d);
+  }
+  return make_uint4(h[0], h[1], h[2], h[3]);
 }
 
 __global__ void __launch_bounds__(GF_THREADS, 1) k_gram_f64tc(const __grid_constant__ GramF64Args g) {
@@ -385,7 +444,7 @@ __global__ void __launch_bounds__(GF_THREADS, 1) k_gram_f64tc(const __grid_const
   extern __shared__ __align__(1024) unsigned char sm[];
   unsigned char* dbuf = sm;                                                   // [ndb] digit slabs
   double* accs = reinterpret_cast<double*>(sm + (size_t)g.ndb * g.dbuf_bytes);  // [16][ma]
-  unsigned char* stage = sm + (size_t)g.ndb * g.dbuf_bytes + g.acc_bytes;     // [nst] FP64 stages
+  unsigned char* stage = sm + (size_t)g.ndb * g.dbuf_bytes + g.acc_bytes;     // [nst] plane stages
   uint64_t* bars = reinterpret_cast<uint64_t*>(stage + (size_t)g.nst * g.stage_bytes);
   uint64_t* full = bars;                    // [GF_MAXST]
   uint64_t* empty = bars + GF_MAXST;        // [GF_MAXST]
@@ -405,7 +464,7 @@ __global__ void __launch_bounds__(GF_THREADS, 1) k_gram_f64tc(const __grid_const
       mbar_init(&empty[i], GF_SPLIT_WARPS);
     }
     for (int i = 0; i < g.ndb; ++i) {
-      mbar_init(&dfull[i], GF_SPLIT_WARPS);
+      mbar_init(&dfull[i], GF_SPLIT_WARPS / 2);
       mbar_init(&dfree[i], 1);
     }
     for (int b2 = 0; b2 < 2; ++b2) {
@@ -422,86 +481,119 @@ __global__ void __launch_bounds__(GF_THREADS, 1) k_gram_f64tc(const __grid_const
   tc_fence_after();
   const uint32_t tmem = *tslot;
 
+  const int64_t ntile_all = (g.n + 127) / 128;
   const int64_t tile0 = (int64_t)blockIdx.x * g.tiles_per_cta;
-  const int64_t r_begin = tile0 * 128;
-  const int64_t r_end = min(g.n, r_begin + (int64_t)g.tiles_per_cta * 128);
-  const int nslab = r_end > r_begin ? (int)((r_end - r_begin + 15) / 16) : 0;
+  const int64_t tile_end = min(ntile_all, tile0 + (int64_t)g.tiles_per_cta);
+  const int nslab = tile_end > tile0 ? (int)(tile_end - tile0) * 8 : 0;   // 16-row slabs
+  const int nstg = nslab / 2;                                               // stages of two slabs
   bool failed = false;
 
   if (warp == GF_TMA_WARP) {
-    // ---- bulk copies of the slabs into the stage ring: lane i copies block
-    // slot i (the copies of a slab are issued in parallel)
-    for (int q = 0; q < nslab && !failed; ++q) {
-      const int st = q % g.nst;
+    // ---- bulk copies: stage qs holds slabs 2 qs, 2 qs + 1 of every block,
+    // lane i copying block slot i
+    for (int qs = 0; qs < nstg && !failed; ++qs) {
+      const int st = qs % g.nst;
       bool f = false;
-      if (lane == 0 && q >= g.nst && !mbar_wait_bounded(&empty[st], (unsigned)((q / g.nst - 1) & 1)))
+      if (lane == 0 && qs >= g.nst && !mbar_wait_bounded(&empty[st], (unsigned)((qs / g.nst - 1) & 1)))
         f = true;
-      const int64_t r0 = r_begin + (int64_t)q * 16;
-      const unsigned bytes = (unsigned)(min((int64_t)16, r_end - r0) * 64);
-      if (lane == 0 && !f) mbar_expect_tx(&full[st], bytes * (unsigned)g.nsplit);
+      if (lane == 0 && !f) mbar_expect_tx(&full[st], 2u * FT_PLANE_SLAB * (unsigned)g.nsplit);
       failed = __any_sync(0xffffffffu, f);
       if (failed) break;
+      const int64_t tile = tile0 + (qs >> 2);
+      const size_t off = (size_t)tile * FT_PLANE_TILE + (size_t)(qs & 3) * 2 * FT_PLANE_SLAB;
       unsigned char* dst = stage + (size_t)st * g.stage_bytes;
       for (int i = lane; i < g.nsplit; i += 32) {
-        const double* p;
-        const int* e;
+        const unsigned char* p;
         int lb, rb;
-        gf_slot(g, i, &p, &e, &lb, &rb);
-        bulk_copy_g2s(dst + (size_t)i * GF_BSTRIDE, p + r0 * 8, bytes, &full[st]);
+        gf_slot(g, i, &p, &lb, &rb);
+        bulk_copy_g2s(dst + (size_t)i * GF_SSTRIDE, p + off, 2u * FT_PLANE_SLAB, &full[st]);
       }
     }
     if (failed && lane == 0 && g.err) atomicExch(g.err, 1);
   } else if (warp == GF_MMA_WARP) {
-    // ---- MMA issue
+    // ---- MMA issue.  Descriptors are formed once: the start-address field
+    // (address >> 4, 14 bits) of a base descriptor is advanced by adding
+    // (byte offset >> 4), which cannot carry out of the field (shared memory
+    // is below 256 KB).
     if (lane == 0) {
+      const uint32_t pa0 = smem_addr(dbuf);
+      const uint64_t adesc0 = tc_smem_desc(pa0, 128, GF_ASBO);
+      const uint64_t bdesc0 = tc_smem_desc(pa0 + 7u * g.aplane_bytes, 128, 256);
+      const uint64_t bstep = g.dbuf_bytes >> 4;   // one slab buffer further
+      const uint64_t astep = g.aplane_bytes >> 4, a1 = (uint64_t)(((g.tile1 >> 3) * GF_ASBO) >> 4);
+      int b = 0, bu = 0;   // slab buffer and its use count
       for (int q = 0; q < nslab && !failed; ++q) {
-        const int w = q >> 3, wb = w & 1, b = q % g.ndb;
+        const int w = q >> 3, wb = w & 1;
         if ((q & 7) == 0 && w >= 2 && !mbar_wait_bounded(&tfree[wb], (unsigned)(((w - 2) >> 1) & 1)))
           failed = true;
-        if (!failed && !mbar_wait_bounded(&dfull[b], (unsigned)((q / g.ndb) & 1))) failed = true;
+        if (!failed && !mbar_wait_bounded(&dfull[b], (unsigned)(bu & 1))) failed = true;
         if (failed) break;
         tc_fence_after();
-        const uint32_t pa = smem_addr(dbuf + (size_t)b * g.dbuf_bytes);
-        const uint32_t pb = pa + 224u * (uint32_t)g.ma;
+        const uint64_t ab = adesc0 + (uint64_t)b * bstep, bd = bdesc0 + (uint64_t)b * bstep;
+        const uint32_t first = (q & 7) ? 1u : 0u;
         for (int T = 0; T < g.ntile; ++T) {
-          const uint32_t aoff = T ? (uint32_t)(g.tile1 >> 3) * 256u : 0u;
+          const uint64_t at = ab + (T ? a1 : 0ull);
           const uint32_t dcol = tmem + (uint32_t)((wb * g.ntile + T) * 128);
 #pragma unroll
-          for (int t = 0; t < 7; ++t) {
-            const uint64_t ad = tc_smem_desc(pa + (uint32_t)t * 32u * g.ma + aoff, 128, 256);
-            const uint64_t bd = tc_smem_desc(pb, 128, 256);
-            const uint32_t accum = ((q & 7) || t) ? 1u : 0u;
-            tc_mma_bf16(dcol + (uint32_t)(16 * t), ad, bd, tc_idesc_f16_f32(128, 16 * (8 - t)), accum);
-          }
+          for (int t = 0; t < 7; ++t)
+            tc_mma_bf16(dcol + (uint32_t)(16 * t), at + (uint64_t)t * astep, bd, tc_idesc_f16_f32(128, 16 * (8 - t)),
+                        t ? 1u : first);
         }
         tc_commit(&dfree[b]);
         if ((q & 7) == 7 || q == nslab - 1) tc_commit(&wdone[wb]);
+        if (++b == g.ndb) {
+          b = 0;
+          ++bu;
+        }
       }
       if (failed && g.err) atomicExch(g.err, 1);
     }
   } else if (warp >= GF_EPI_WARP0) {
-    // ---- epilogue warps: lanes 32 (warp % 4) .. of each M tile = L columns
-    for (int w = 0; w <= (nslab - 1) >> 3 && nslab > 0 && !failed; ++w) {
+    // ---- epilogue warps: lanes 32 (warp % 4) .. of each M tile = L columns.
+    // The exponents of a window are loaded one window ahead.
+    const int nwin = nslab > 0 ? ((nslab - 1) >> 3) + 1 : 0;
+    int mcol[2];
+    bool mvalid[2];
+    for (int T = 0; T < 2; ++T) {
+      mcol[T] = (T ? g.tile1 : 0) + 32 * (warp & 3) + lane;
+      mvalid[T] = T < g.ntile && mcol[T] < g.as && (T == 0 || mcol[T] >= 128);
+    }
+    int ELn[2], ERn[16];
+    auto load_exps = [&](int w) {
+      const int64_t tile = tile0 + w;
+#pragma unroll
+      for (int T = 0; T < 2; ++T) ELn[T] = mvalid[T] ? g.L.e[mcol[T] >> 3][tile * 8 + (mcol[T] & 7)] : 0;
+#pragma unroll
+      for (int j = 0; j < 16; ++j) ERn[j] = j < g.bs ? g.R.e[j >> 3][tile * 8 + (j & 7)] : 0;
+    };
+    if (nwin > 0) load_exps(0);
+    for (int w = 0; w < nwin && !failed; ++w) {
       const int wb = w & 1;
+      int EL[2], ER[16];
+#pragma unroll
+      for (int T = 0; T < 2; ++T) EL[T] = ELn[T];
+#pragma unroll
+      for (int j = 0; j < 16; ++j) ER[j] = ERn[j];
+      if (w + 1 < nwin) load_exps(w + 1);
       gf_wait(&wdone[wb], (unsigned)((w >> 1) & 1), failed, g.err);
       tc_fence_after();
       if (!failed) {
-        const int64_t tile = tile0 + w;
         for (int T = 0; T < g.ntile; ++T) {
-          const int m = (T ? g.tile1 : 0) + 32 * (warp & 3) + lane;
-          const bool valid = m < g.as && (T == 0 || m >= 128);
-          const int EL = valid ? g.L.e[m >> 3][tile * 8 + (m & 7)] : 0;
+          const int m = mcol[T];
+          const bool valid = mvalid[T];
+          if (valid && EL[T] >= FT_EXP_NONFINITE) *bad = 1;
           const uint32_t ta = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)((wb * g.ntile + T) * 128);
 #pragma unroll
           for (int h = 0; h < 2; ++h) {
             long long Tv[8];
-            ft_levels8(ta + (uint32_t)(8 * h), Tv);
+            ft_levels8b(ta + (uint32_t)(8 * h), Tv);
             if (valid && 8 * h < g.bs) {
-              const int* er = g.R.e[h] + tile * 8;
 #pragma unroll
               for (int j = 0; j < 8; ++j) {
+                const int Ej = ER[8 * h + j];
+                if (Ej >= FT_EXP_NONFINITE) *bad = 1;
                 double* a = accs + (size_t)(8 * h + j) * g.ma + m;
-                *a = ft_fma_pow2((double)Tv[j], EL + er[j] - 55, *a);
+                *a = ft_fma_pow2((double)Tv[j], EL[T] + Ej - 55, *a);
               }
             }
           }
@@ -511,12 +603,14 @@ __global__ void __launch_bounds__(GF_THREADS, 1) k_gram_f64tc(const __grid_const
       __syncwarp();
       if (lane == 0) mbar_arrive(&tfree[wb]);
     }
+    // every epilogue warp's NaN marks before the outputs
+    asm volatile("bar.sync 1, 128;" ::: "memory");
     if (!failed) {
+      const bool nan_out = *(volatile int*)bad != 0;
       for (int T = 0; T < g.ntile; ++T) {
         const int m = (T ? g.tile1 : 0) + 32 * (warp & 3) + lane;
         if (m < g.as && (T == 0 || m >= 128)) {
           double* out = g.partials + (int64_t)blockIdx.x * g.q + (int64_t)m * g.bs;
-          const bool nan_out = *(volatile int*)bad != 0;
 #pragma unroll
           for (int j = 0; j < 16; ++j)
             if (j < g.bs) out[j] = nan_out ? __longlong_as_double(0x7FF8000000000000ll) : accs[(size_t)j * g.ma + m];
@@ -524,80 +618,52 @@ __global__ void __launch_bounds__(GF_THREADS, 1) k_gram_f64tc(const __grid_const
       }
     }
   } else {
-    // ---- split warps.  Task = (block slot, 8-row group kg) of a slab:
-    // lane = column (lane & 7) x row pair r2 = lane >> 3, the rows r2 and
-    // r2 + 4 of the group, whose digits form fp16 pair r2 of the column's
-    // 16-byte core-matrix row (the same order of the K values in both
-    // operands, so the contraction is unchanged).
-    const int col = lane & 7, r2 = lane >> 3;
-    const int ntask = 2 * g.nsplit;
-    // Exponents of the warp's tasks (task = warp + 10 i, the same every slab)
-    // for the current window, and the next window's loaded one window ahead.
-    int ecur[GF_MAXTASK], enext[GF_MAXTASK];
-    auto load_exps = [&](int w, int (&ev)[GF_MAXTASK]) {
-      const int64_t tile = tile0 + w;
-#pragma unroll
-      for (int i = 0; i < GF_MAXTASK; ++i) {
-        const int task = warp + GF_SPLIT_WARPS * i;
-        ev[i] = 0;
-        if (task < ntask && tile * 128 < r_end) {
-          const double* p;
-          const int* e;
-          int lb, rb;
-          gf_slot(g, task >> 1, &p, &e, &lb, &rb);
-          ev[i] = e[tile * 8 + col];
-        }
-      }
-    };
-    load_exps(0, ecur);
-    load_exps(1, enext);
-    for (int q = 0; q < nslab && !failed; ++q) {
-      const int st = q % g.nst, b = q % g.ndb;
-      const int64_t r0 = r_begin + (int64_t)q * 16;
-      if ((q & 7) == 0 && q > 0) {
-#pragma unroll
-        for (int i = 0; i < GF_MAXTASK; ++i) ecur[i] = enext[i];
-        load_exps((q >> 3) + 1, enext);
-      }
-      gf_wait(&full[st], (unsigned)((q / g.nst) & 1), failed, g.err);
-      const unsigned char* S = stage + (size_t)st * g.stage_bytes;
+    // ---- expansion warps.  Task index k = (t * 2 + kg) * nsplit + slot, so
+    // the lanes of a warp mostly share (t, kg) and take consecutive slots
+    // (their shared-memory rows GF_SSTRIDE and GF_ASBO apart fall in
+    // different banks).
+    const int ntask = 14 * g.nsplit;
+    const int grp = warp >= GF_SPLIT_WARPS / 2 ? 1 : 0, gtid = tid - grp * (GF_SPLIT_WARPS / 2) * 32;
+    for (int q = grp; q < nslab && !failed; q += 2) {
+      const int qs = q >> 1, st = qs % g.nst, b = q % g.ndb;
+      gf_wait(&full[st], (unsigned)((qs / g.nst) & 1), failed, g.err);
+      const unsigned char* S = stage + (size_t)st * g.stage_bytes + (size_t)(q & 1) * FT_PLANE_SLAB;
       if (q >= g.ndb) gf_wait(&dfree[b], (unsigned)((q / g.ndb - 1) & 1), failed, g.err);
       unsigned char* D = dbuf + (size_t)b * g.dbuf_bytes;
-      bool nf = false;
+      if (!failed) {
+        for (int k = gtid; k < ntask; k += (GF_SPLIT_WARPS / 2) * 32) {
+          const int slot = k % g.nsplit, tk = k / g.nsplit, t = tk >> 1, kg = tk & 1;
+          int lb, rb;
+          if (slot < g.a) {
+            lb = slot;
+            rb = (g.shared && slot == g.a - 1) ? 0 : -1;
+          } else {
+            lb = -1;
+            rb = slot - g.a + (g.shared ? 1 : 0);
+          }
+          const uint4* src = reinterpret_cast<const uint4*>(S + (size_t)slot * GF_SSTRIDE + (size_t)t * 128 +
+                                                            (size_t)kg * 64);
+          uint2 w[8];
 #pragma unroll
-      for (int i = 0; i < GF_MAXTASK; ++i) {
-        const int task = warp + GF_SPLIT_WARPS * i;
-        if (task >= ntask || failed) break;
-        const int sl = task >> 1, kg = task & 1;
-        const int64_t row = r0 + kg * 8 + r2;
-        const unsigned char* src = S + (size_t)sl * GF_BSTRIDE + (size_t)(kg * 8 + r2) * 64 + (size_t)col * 8;
-        const double x0 = row < r_end ? *reinterpret_cast<const double*>(src) : 0.0;
-        const double x1 = row + 4 < r_end ? *reinterpret_cast<const double*>(src + 256) : 0.0;
-        const int E = ecur[i];
-        const unsigned long long g0 = ft_biased(x0, E, nf), g1 = ft_biased(x1, E, nf);
-        int lb, rb;
-        if (sl < g.a) {
-          lb = sl;
-          rb = (g.shared && sl == g.a - 1) ? 0 : -1;
-        } else {
-          lb = -1;
-          rb = sl - g.a + (g.shared ? 1 : 0);
-        }
-        const uint32_t dA = lb >= 0 ? (uint32_t)lb * 256u + (uint32_t)kg * 128u + (uint32_t)col * 16u +
-                                          (uint32_t)r2 * 4u
-                                    : ~0u;
-        const uint32_t dB = rb >= 0 ? 224u * (uint32_t)g.ma + (uint32_t)rb * 256u + (uint32_t)kg * 128u +
-                                          (uint32_t)col * 16u + (uint32_t)r2 * 4u
-                                    : ~0u;
+          for (int i = 0; i < 4; ++i) {
+            const uint4 v = src[i];
+            w[2 * i] = make_uint2(v.x, v.y);
+            w[2 * i + 1] = make_uint2(v.z, v.w);
+          }
+          unsigned char* dA = lb >= 0 ? D + (size_t)t * g.aplane_bytes + (size_t)lb * GF_ASBO + (size_t)kg * 128
+                                      : nullptr;
+          // digit u = t of the R stack: N rows 16 u + 8 rb .. are 2 u + rb core groups further
+          unsigned char* dB = rb >= 0 ? D + 7 * (size_t)g.aplane_bytes + (size_t)(2 * t + rb) * 256 + (size_t)kg * 128
+                                      : nullptr;
+          // digit plane t of the stored bytes is digit t (0 = most significant)
 #pragma unroll
-        for (int t = 0; t < 7; ++t) {
-          const uint32_t d = ft_pair(g0, g1, t);
-          if (dA != ~0u) *reinterpret_cast<uint32_t*>(D + dA + (uint32_t)t * 32u * g.ma) = d;
-          // digit u = t of the R stack: N rows 16 u.. are 2 u core groups further
-          if (dB != ~0u) *reinterpret_cast<uint32_t*>(D + dB + (uint32_t)t * 512u) = d;
+          for (int c = 0; c < 8; ++c) {
+            const uint4 row = gf_column(w, c);
+            if (dA) *reinterpret_cast<uint4*>(dA + c * 16) = row;
+            if (dB) *reinterpret_cast<uint4*>(dB + c * 16) = row;
+          }
         }
       }
-      if (nf) *bad = 1;
       __syncwarp();
       if (lane == 0) mbar_arrive(&empty[st]);
       tc_fence_smem();
@@ -636,10 +702,12 @@ static void gram_f64tc_shape(int a, int* ma, int* ntile, int* tile1) {
   *tile1 = *ma - 128;
 }
 
-// Shared memory: ndb digit slabs, the accumulators, nst FP64 stages, barriers.
+static uint32_t gram_f64tc_aplane(int ma) { return (uint32_t)(ma / 8) * GF_ASBO; }
+
+// Shared memory: ndb digit slabs, the accumulators, nst plane stages, barriers.
 static size_t gram_f64tc_smem(int ma, int nsplit, int nst, int ndb) {
-  return (size_t)ndb * ((size_t)224 * ma + 4096) + (size_t)16 * ma * 8 +
-         (size_t)nst * nsplit * GF_BSTRIDE + (2 * GF_MAXST + 2 * GF_MAXDB + 4) * 8 + 16;
+  return (size_t)ndb * (7 * (size_t)gram_f64tc_aplane(ma) + 4096) + (size_t)16 * ma * 8 +
+         (size_t)nst * nsplit * GF_SSTRIDE + (2 * GF_MAXST + 2 * GF_MAXDB + 4) * 8 + 16;
 }
 // Three digit slabs where at least three stages fit beside them, else two;
 // then as many stages (<= 6) as fit.
@@ -659,7 +727,7 @@ GramPlan plan_gram_f64tc(int64_t n, int s, int a, int b, int num_sms) {
   p.tc = 3;
   int ma, nt, t1;
   gram_f64tc_shape(a, &ma, &nt, &t1);
-  const int nsplit = a + b;   // upper bound (shared splits one fewer)
+  const int nsplit = a + b;   // upper bound (shared reads one fewer)
   int nst, ndb;
   gram_f64tc_buffers(ma, nsplit, &nst, &ndb);
   p.smem = gram_f64tc_smem(ma, nsplit, nst, ndb);
@@ -675,9 +743,10 @@ GramPlan plan_gram_f64tc(int64_t n, int s, int a, int b, int num_sms) {
   return p;
 }
 
-void launch_gram_f64tc(cudaStream_t st, const GramPlan& p, const double* const* L, const int* const* Le,
-                       int a, const double* const* R, const int* const* Re, int b, bool shared,
-                       int64_t n, double* partials, double* G, const Ctl* ctl, int guard, int* err) {
+void launch_gram_f64tc(cudaStream_t st, const GramPlan& p, const unsigned char* const* L,
+                       const int* const* Le, int a, const unsigned char* const* R, const int* const* Re,
+                       int b, bool shared, int64_t n, double* partials, double* G, const Ctl* ctl,
+                       int guard, int* err) {
   static std::atomic<unsigned long long> attr_done{0};
   once_per_device(attr_done, [] {
     cudaFuncSetAttribute(k_gram_f64tc, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
@@ -699,9 +768,10 @@ void launch_gram_f64tc(cudaStream_t st, const GramPlan& p, const double* const* 
   g.shared = shared ? 1 : 0;
   g.nsplit = a + b - (shared ? 1 : 0);
   gram_f64tc_shape(a, &g.ma, &g.ntile, &g.tile1);
-  g.dbuf_bytes = 224u * (uint32_t)g.ma + 4096u;
+  g.aplane_bytes = gram_f64tc_aplane(g.ma);
+  g.dbuf_bytes = 7u * g.aplane_bytes + 4096u;
   g.acc_bytes = 16u * (uint32_t)g.ma * (uint32_t)sizeof(double);
-  g.stage_bytes = (uint32_t)g.nsplit * GF_BSTRIDE;
+  g.stage_bytes = (uint32_t)g.nsplit * GF_SSTRIDE;
   gram_f64tc_buffers(g.ma, g.nsplit, &g.nst, &g.ndb);
   g.tcols = g.ntile == 2 ? 512u : 256u;
   g.n = n;
@@ -730,14 +800,15 @@ void launch_gram_f64tc(cudaStream_t st, const GramPlan& p, const double* const* 
 // larger than its correction, so it does not go through the digits).
 //
 // One persistent CTA an SM, 18 warps in four roles joined by mbarriers:
-//   warps 0-7 (expansion): per k-step, thread (row r, block h) expands its
-//     row's 7 digit rows (8 bytes -> 8 fp16) from the ring into the A operand
-//     buffer g % 3, which lives in tensor memory (lane = row, 8 columns a
-//     digit plane: tcgen05.st, so the A digits never pass through shared
-//     memory), and thread (cq, cn, ckb) splits one coefficient value into the
-//     B stack in shared memory (N = 8 digit slots x 16 outputs, slot 7 zero)
-//     from the launch's significand table; at a tile's start they form E and
-//     the f_n (parameter slot j % 8);
+//   warps 0-7 (expansion), two groups of four taking alternate k-steps (two
+//     k-steps in flight): per k-step, thread r of the group expands row r's 7
+//     digit rows (8 bytes -> 8 fp16) of both blocks from the ring into the A
+//     operand buffer g % 3, which lives in tensor memory (lane = row, 8
+//     columns a digit plane: tcgen05.st, so the A digits never pass through
+//     shared memory), and splits two coefficient values into the B stack in
+//     shared memory (N = 8 digit slots x 16 outputs, slot 7 zero) from the
+//     launch's significand table; at a tile's start all eight form E and the
+//     f_n (parameter slot j % 8);
 //   warp 16, lane 0: bulk copies (the TMA engine) of the plane sets (7 KB,
 //     one block's tile) into a ring of UF_NST stages, across tiles;
 //   warp 17, lane 0: the 7 MMAs of a k-step (digit t of A against slots
@@ -823,33 +894,6 @@ __device__ __forceinline__ void uf_mma_ta(uint32_t d_tmem, uint32_t a_tmem, uint
       "r"(a_tmem), "l"(bdesc), "r"(idesc), "r"(accumulate)
       : "memory");
 }
-// Levels 0..7 of 8 outputs (8 columns a level at taddr + 16 l): all eight
-// loads issued before one wait, then combined into T as in ft_levels16.
-__device__ __forceinline__ void uf_levels8(uint32_t taddr, long long (&T)[8]) {
-  uint32_t r[8][8];
-#pragma unroll
-  for (int l = 0; l < 8; ++l)
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                 : "=r"(r[l][0]), "=r"(r[l][1]), "=r"(r[l][2]), "=r"(r[l][3]), "=r"(r[l][4]),
-                   "=r"(r[l][5]), "=r"(r[l][6]), "=r"(r[l][7])
-                 : "r"(taddr + (uint32_t)(16 * l))
-                 : "memory");
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int j = 0; j < 8; ++j) {
-    long long t = 0;
-    int s6 = 0;
-#pragma unroll
-    for (int l = 0; l < 8; ++l) {
-      const int si = __float2int_rn(__uint_as_float(r[l][j]));
-      if (l == 0) t = si;
-      else if (l <= 5) t = (t << 8) + si;
-      else if (l == 6) s6 = si;
-      else t = (t << 3) + (((long long)s6 * 256 + si) >> 13);
-    }
-    T[j] = t;
-  }
-}
 
 __global__ void __launch_bounds__(UF_THREADS, 1) k_update_f64tc(const __grid_constant__ UpdF64Args u) {
   if (u.step >= 0 && *(volatile const int*)&u.ctl->update_step != u.step) return;
@@ -891,7 +935,7 @@ __global__ void __launch_bounds__(UF_THREADS, 1) k_update_f64tc(const __grid_con
       mbar_init(&empty[i], 4);
     }
     for (int i = 0; i < UF_ND; ++i) {
-      mbar_init(&afull[i], 8);
+      mbar_init(&afull[i], 4);
       mbar_init(&afree[i], 1);
     }
     for (int i = 0; i < 2; ++i) {
@@ -933,8 +977,10 @@ __global__ void __launch_bounds__(UF_THREADS, 1) k_update_f64tc(const __grid_con
   __syncthreads();
   if (warp < UF_EWARP0) {
     // ================= expansion warps (256 threads)
-    const int r = tid & 127, h = tid >> 7;                        // A: row r of block 2 ks + h
-    const int cq = tid & 7, cn = (tid >> 3) & 15, ckb = tid >> 7;  // B: value (8 (2 ks + ckb) + cq, cn)
+    // group grp (warps 4 grp .. 4 grp + 3) takes the k-steps g = grp (mod 2);
+    // thread gr of a group: row r = gr of both blocks (A) and coefficient
+    // values gr, gr + 128 (B)
+    const int grp = warp >> 2, gr = tid & 127, r = gr;
     int ne = (tid < K && ntl > 0) ? u.ie[tid >> 3][(int64_t)blockIdx.x * 8 + (tid & 7)] : 0;
     int64_t q = 0;
     int g = 0;
@@ -977,53 +1023,68 @@ __global__ void __launch_bounds__(UF_THREADS, 1) k_update_f64tc(const __grid_con
       uf_bar(1, 256);
       if (tid == 0) mbar_arrive(&pready[slot]);
       const int E = pr[0];
-      const int fn = pr[2 + cn];
+      int fnv[2];
+#pragma unroll
+      for (int i = 0; i < 2; ++i) fnv[i] = pr[2 + ((gr + 128 * i) >> 3 & 15)];
       for (int ks = 0; ks < nks; ++ks, ++g) {
-        const int d = g % UF_ND, v = g / UF_ND;
         const int nb = (2 * ks + 1 < nin) ? 2 : 1;
+        if ((g & 1) != grp) {   // the other group's k-step
+          q += nb;
+          continue;
+        }
+        const int d = g % UF_ND, v = g / UF_ND;
         bool ok = true;
-        if (h < nb) {
-          const int64_t qq = q + h;
-          ok = uf_wait(&full[qq % UF_NST], (unsigned)((qq / UF_NST) & 1), abortf, u.err);
+        for (int hh = 0; hh < nb; ++hh) {
+          const int64_t qq = q + hh;
+          ok = uf_wait(&full[qq % UF_NST], (unsigned)((qq / UF_NST) & 1), abortf, u.err) && ok;
         }
         if (v >= 1) ok = uf_wait(&afree[d], (unsigned)((v - 1) & 1), abortf, u.err) && ok;
         ok = __all_sync(0xffffffffu, ok);   // the tensor-memory stores are warp-wide
         if (ok) {
-          // A: digit plane t of block h -> columns UF_ACOL + 56 d + 8 t + 4 h, lane r
-          const uint32_t ta = tmem + ((uint32_t)(32 * (warp & 3)) << 16) +
-                              (uint32_t)(UF_ACOL + 56 * d + 4 * h);
-          if (h < nb) {
-            const unsigned char* S = ring + (size_t)((q + h) % UF_NST) * FT_PLANE_TILE + (size_t)r * 8;
-            uint2 w[7];
 #pragma unroll
-            for (int t = 0; t < 7; ++t) w[t] = *reinterpret_cast<const uint2*>(S + t * 1024);
+          for (int hh = 0; hh < 2; ++hh) {
+            // A: digit plane t of block hh -> columns UF_ACOL + 56 d + 8 t + 4 hh, lane r
+            const uint32_t ta = tmem + ((uint32_t)(32 * (warp & 3)) << 16) +
+                                (uint32_t)(UF_ACOL + 56 * d + 4 * hh);
+            if (hh < nb) {
+              const unsigned char* S = ring + (size_t)((q + hh) % UF_NST) * FT_PLANE_TILE + ft_row_off(r);
+              uint2 w[7];
 #pragma unroll
-            for (int t = 0; t < 7; ++t) uf_st4(ta + (uint32_t)(8 * t), ft_expand8(w[t]));
-          } else {
+              for (int t = 0; t < 7; ++t) w[t] = *reinterpret_cast<const uint2*>(S + t * 128);
 #pragma unroll
-            for (int t = 0; t < 7; ++t) uf_st4(ta + (uint32_t)(8 * t), make_uint4(0u, 0u, 0u, 0u));
+              for (int t = 0; t < 7; ++t) uf_st4(ta + (uint32_t)(8 * t), ft_expand8(w[t]));
+            } else {
+#pragma unroll
+              for (int t = 0; t < 7; ++t) uf_st4(ta + (uint32_t)(8 * t), make_uint4(0u, 0u, 0u, 0u));
+            }
           }
           asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-          const int blk = 2 * ks + ckb;
-          unsigned long long gv = FT_BIAS;
-          if (blk < nin) {
-            const int kk = blk * 8 + cq;
-            const unsigned long long mv = cm[kk * 16 + cn];
-            const int rs = fn + E - exs[kk] + (int)cs[kk * 16 + cn];
-            const unsigned long long F = rs > 63 ? 0ull : ((mv & 0x7FFFFFFFFFFFFFFFull) >> rs);
-            gv = (mv >> 63) ? FT_BIAS - F : FT_BIAS + F;
-          }
-          unsigned short* Bd = reinterpret_cast<unsigned short*>(
-                                   bst + (size_t)d * 4096 + (size_t)(cn >> 3) * 256 + (size_t)ckb * 128 +
-                                   (size_t)(cn & 7) * 16) + cq;
+          // B: coefficient values v2 = gr + 128 i: (kk = 8 (2 ks + ckb) + cq, n = cn)
 #pragma unroll
-          for (int t = 0; t < 7; ++t) {
-            const int p = 6 - t;
-            const uint32_t wd = p >= 4 ? (uint32_t)(gv >> 32) : (uint32_t)gv;
-            const uint32_t hw = __byte_perm(wd, 0x64646464u, 0x40u | (uint32_t)(p & 3));
-            const __half dg = __hsub(__ushort_as_half((unsigned short)(hw & 0xFFFFu)),
-                                     __ushort_as_half((unsigned short)0x6480u));
-            Bd[t * 256] = __half_as_ushort(dg);
+          for (int i = 0; i < 2; ++i) {
+            const int v2 = gr + 128 * i;
+            const int cq = v2 & 7, cn = (v2 >> 3) & 15, ckb = v2 >> 7;
+            const int blk = 2 * ks + ckb;
+            unsigned long long gv = FT_BIAS;
+            if (blk < nin) {
+              const int kk = blk * 8 + cq;
+              const unsigned long long mv = cm[kk * 16 + cn];
+              const int rs = fnv[i] + E - exs[kk] + (int)cs[kk * 16 + cn];
+              const unsigned long long F = rs > 63 ? 0ull : ((mv & 0x7FFFFFFFFFFFFFFFull) >> rs);
+              gv = (mv >> 63) ? FT_BIAS - F : FT_BIAS + F;
+            }
+            unsigned short* Bd = reinterpret_cast<unsigned short*>(
+                                     bst + (size_t)d * 4096 + (size_t)(cn >> 3) * 256 + (size_t)ckb * 128 +
+                                     (size_t)(cn & 7) * 16) + cq;
+#pragma unroll
+            for (int t = 0; t < 7; ++t) {
+              const int p = 6 - t;
+              const uint32_t wd = p >= 4 ? (uint32_t)(gv >> 32) : (uint32_t)gv;
+              const uint32_t hw = __byte_perm(wd, 0x64646464u, 0x40u | (uint32_t)(p & 3));
+              const __half dg = __hsub(__ushort_as_half((unsigned short)(hw & 0xFFFFu)),
+                                       __ushort_as_half((unsigned short)0x6480u));
+              Bd[t * 256] = __half_as_ushort(dg);
+            }
           }
         }
         tc_fence_smem();
@@ -1031,7 +1092,7 @@ __global__ void __launch_bounds__(UF_THREADS, 1) k_update_f64tc(const __grid_con
         __syncwarp();
         if (lane == 0) {
           mbar_arrive(&afull[d]);
-          if (h < nb) mbar_arrive(&empty[(q + h) % UF_NST]);
+          for (int hh = 0; hh < nb; ++hh) mbar_arrive(&empty[(q + hh) % UF_NST]);
         }
         q += nb;
       }
@@ -1063,7 +1124,7 @@ __global__ void __launch_bounds__(UF_THREADS, 1) k_update_f64tc(const __grid_con
         if (got && olive) {
           tc_fence_after();
           long long T[8];
-          uf_levels8(tl + (uint32_t)(128 * a), T);
+          ft_levels8b(tl + (uint32_t)(128 * a), T);
 #pragma unroll
           for (int c = 0; c < 8; ++c) acc[c] = ft_fma_pow2((double)T[c], E + pr[2 + 8 * o + c] - 55, acc[c]);
         }
@@ -1113,7 +1174,8 @@ __global__ void __launch_bounds__(UF_THREADS, 1) k_update_f64tc(const __grid_con
         if (eout && olive) eout[tile * 8 + lane] = e;
       }
       uf_bar(2, 256);
-      if (olive && pout) ft_store_row_digits(acc, eo + 8 * o, pout + (size_t)tile * FT_PLANE_TILE + (size_t)er * 8);
+      if (olive && pout)
+        ft_store_row_digits(acc, eo + 8 * o, pout + (size_t)tile * FT_PLANE_TILE + ft_row_off(er));
     }
   } else if (warp == UF_PWARP) {
     // ================= bulk copies of the plane sets, in (tile, block) order

@@ -241,17 +241,18 @@ void launch_block_exp(cudaStream_t st, const double* V, int64_t n, int s, int* e
                       int guard);
 // Exponents and digit planes (7 bytes a value, f64tc_plane_bytes(n) a block)
 // of an n x 8 FP64 block, written by the pass that writes the block and read
-// by the update in place of its FP64 values.
+// by the Gram and the update in place of its FP64 values.
 size_t f64tc_plane_bytes(int64_t n);
 void launch_block_digits(cudaStream_t st, const double* V, int64_t n, int* ex, unsigned char* planes,
                          const Ctl* ctl, int guard);
-// Gram [L_1..L_a]^T [R_1..R_b] (FP64 blocks with exponents), reduced into G.
-// shared: R_1 is L_a (split once).
+// Gram [L_1..L_a]^T [R_1..R_b] (blocks given by exponents and digit planes),
+// reduced into G.  shared: R_1 is L_a (read once).
 bool gram_f64tc_eligible(int s, int a, int b, bool shared);
 GramPlan plan_gram_f64tc(int64_t n, int s, int a, int b, int num_sms);
-void launch_gram_f64tc(cudaStream_t st, const GramPlan& p, const double* const* L, const int* const* Le,
-                       int a, const double* const* R, const int* const* Re, int b, bool shared,
-                       int64_t n, double* partials, double* G, const Ctl* ctl, int guard, int* err);
+void launch_gram_f64tc(cudaStream_t st, const GramPlan& p, const unsigned char* const* L,
+                       const int* const* Le, int a, const unsigned char* const* R, const int* const* Re,
+                       int b, bool shared, int64_t n, double* partials, double* G, const Ctl* ctl,
+                       int guard, int* err);
 // out1 = (sum_i in_i C1_i (+ X C1_X)) T1^{-1},
 // out2 = (sum_i in_i C2_i (+ X C2_X) + out1 Chain) T2^{-1}  (out2 optional),
 // with the inputs given by their exponents and digit planes, X (optional) in
