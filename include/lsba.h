@@ -93,12 +93,20 @@ typedef struct {
                                     LSBA_PREC_DF: double-float (hi + lo FP32 pairs, 48
                                     significand bits, 8 bytes per entry) on the FP32
                                     pipes; LSBA_PREC_FP64: native FP64 (DFMA);
-                                    LSBA_PREC_AUTO (default): DF for BCGSI+LS and
-                                    BMGS-CWY/ICWY, FP64 for BCGS and BCGS-PIP, whose
-                                    O(eps) kappa^2 loss of orthogonality (Table 2)
-                                    amplifies the 2^-48 representation error.  The
-                                    small s x s / ks x s kernels are FP64 in all modes.
-                                    DF takes every s <= 32 and m.
+                                    LSBA_PREC_AUTO (default): for BCGSI+LS and
+                                    BMGS-CWY/ICWY FP64 on the tensor cores where
+                                    those passes take the shape (s = 8, m <= 22,
+                                    tensor_cores != 0), else DF; FP64 for BCGS and
+                                    BCGS-PIP, whose O(eps) kappa^2 loss of
+                                    orthogonality (Table 2) amplifies the 2^-48
+                                    representation error.  The small s x s / ks x s
+                                    kernels are FP64 in all modes.  DF takes every
+                                    s <= 32 and m.  FP64 runs the Gram and the
+                                    update of the lagged skeletons at s = 8,
+                                    m <= 22 as exact products of 8-bit digits on
+                                    the tensor cores (53 bits per value relative to
+                                    its 128-row tile and column, FP64
+                                    accumulation; tensor_cores = 0 turns this off).
                                     LSBA_PREC_FP32_IR: FP64 iterative refinement
                                     (residual B - A X and X += D in FP64) around an
                                     FP32 inner solve of A D = R (FP32 SpMM, Gram and
@@ -113,12 +121,15 @@ typedef struct {
                                     occurrences replay it (same kernels, same
                                     results); 0: every launch is issued directly.
                                     Off while profile = 1.                            */
-  int32_t tensor_cores;          /* 1 (default): the double-float Gram passes whose
-                                    shape the tensor-core digit kernel runs faster
-                                    (b s = 16 and a s >= 160, a s + b s <= 256) use
-                                    it (exact digit products, 48-bit accuracy); 2:
-                                    every pass whose shape it allows; 0: FP32-pipe
-                                    kernels only.                                      */
+  int32_t tensor_cores;          /* 1 (default): the tensor-core digit kernels run
+                                    where they are faster: in FP64 the Gram and
+                                    update of the lagged skeletons at s = 8, m <= 22;
+                                    in DF the passes of those skeletons at s = 8 and
+                                    other Grams with b s = 16, a s >= 160,
+                                    a s + b s <= 256 (exact digit products, 48-bit
+                                    accuracy); 2: also every DF pass whose shape the
+                                    kernel allows; 0: FP64 and FP32-pipe kernels
+                                    only.                                              */
   int32_t inner_product;         /* block inner product (Sec. 2.2, Table 1):
                                     LSBA_IP_CLASSICAL (default): <X, Y> = X^T Y, muscle
                                     CholQR; LSBA_IP_GLOBAL: <X, Y> = tr(X^T Y)/s I_s,

@@ -1326,9 +1326,14 @@ static int solve_impl(lsba_handle h, const lsba_csr* A, const double* d_B, doubl
   // row kernels for s = 4, 8, 16 only and otherwise runs in double-float.
   const bool fits_f32 = (s == 4 || s == 8 || s == 16) && update_f32_smem(m + 3, s, true) <= 200 * 1024;
   const bool ir = prec == LSBA_PREC_FP32_IR && fits_f32;
+  // Shapes the FP64 tensor-core passes take (lagged skeletons, s = 8, m <= 22):
+  // under "auto" they run there, in FP64, rather than in double-float (they
+  // are faster on GB300 and keep 53 bits).
+  const bool ftc_shape = s == 8 && h->opt.tensor_cores != 0 && lagged(skel) &&
+                         gram_f64tc_eligible(s, m + 1, 2, true) && update_f64tc_eligible(s, m + 2);
   if (ir) h->mode = MODE_F32;
   else if (prec == LSBA_PREC_DF || prec == LSBA_PREC_FP32_IR ||
-           (prec == LSBA_PREC_AUTO && lagged(skel)))
+           (prec == LSBA_PREC_AUTO && lagged(skel) && !ftc_shape))
     h->mode = MODE_DF;
   else h->mode = MODE_FP64;
   // Low-precision modes keep FP32's exponent range (2^-126 .. 2^128): A and B
@@ -1360,8 +1365,7 @@ static int solve_impl(lsba_handle h, const lsba_csr* A, const double* d_B, doubl
   if (h->use_tcs && ensure_digits(h) != LSBA_OK) h->use_tcs = false;
   // FP64 on the tensor cores: lagged skeletons, s = 8, m <= 22 (classical inner
   // product and CholQR, the paths whose passes it covers).
-  h->use_ftc = h->mode == MODE_FP64 && s == 8 && h->opt.tensor_cores != 0 && lagged(skel) &&
-               gram_f64tc_eligible(s, m + 1, 2, true) && update_f64tc_eligible(s, m + 2);
+  h->use_ftc = h->mode == MODE_FP64 && ftc_shape;
   if (h->use_ftc && ensure_f64tc(h) != LSBA_OK) h->use_ftc = false;
   h->stats.tensor_cores = (h->use_tcs || h->use_ftc) ? 1 : 0;
 

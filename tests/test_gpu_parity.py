@@ -404,6 +404,49 @@ def test_lapl512_first_cycle_full_size(env, sk, precision):
     assert _rel(X, ref.X) <= TOL_X
 
 
+def test_lapl512_icwy_m32_auto_first_cycle(env):
+    """BMGS-ICWY with a longer basis (m = 32, 264 columns) on the 512x512
+    Laplacian under precision "auto" (double-float at this m): the first
+    cycle's Gram outputs and Hessenberg stay within 1e-11 of the oracle."""
+    torch, lsba = env
+    A, B = W.workload("lapl512_s8", 0)
+    X, st, hist = lsba.solve(A, B, 32, 1e-30, "bmgs_icwy", device=0, max_restarts=0,
+                             verify_true_residual=0, record_history=True)
+    ref = O.solve(A, B, 32, 1e-30, "bmgs_icwy", modification="gmres", max_restarts=0,
+                  verify_true_residual=False, record_first_cycle=True)
+    fc = ref.first_cycle
+    assert hist["cycle_m"] == ref.cycle_m
+    errs = [_rel(g_gpu, g_ref) for g_gpu, g_ref in zip(hist["grams"], fc["grams"])]
+    print(f"ICWY32 precision {st['precision']} Gram max {max(errs):.3e} "
+          f"H {_rel(hist['first_H'], fc['H']):.3e}")
+    assert max(errs) <= TOL_GRAM
+    assert _rel(hist["first_H"], fc["H"]) <= TOL_GRAM
+
+
+@pytest.mark.parametrize("sk", ["bcgsi_ls", "bcgs_pip"])
+def test_rgg1M_first_cycle_full_size(env, sk):
+    """The ill-conditioned graph workload at its full size: random geometric
+    graph Laplacian, n = 2^20 (weights 10^U(-3,3), shift 1e-6 max diag), B n x 16,
+    BGMRES(16), FP64: the first cycle's restart decision, every Gram output and
+    the Hessenberg within 1e-11 of the oracle (Sec. 5's measures at the
+    largest single-GPU configuration)."""
+    torch, lsba = env
+    A, B = W.workload("rgg1M_s16", 0)
+    X, st, hist = lsba.solve(A, B, 16, 1e-30, sk, device=0, max_restarts=0,
+                             verify_true_residual=0, record_history=True, precision="fp64")
+    ref = O.solve(A, B, 16, 1e-30, sk, modification="gmres", max_restarts=0,
+                  verify_true_residual=False, record_first_cycle=True)
+    fc = ref.first_cycle
+    assert hist["cycle_m"] == ref.cycle_m and hist["cycle_flag"] == ref.cycle_flag
+    errs = [_rel(g_gpu, g_ref) for g_gpu, g_ref in zip(hist["grams"], fc["grams"])]
+    assert len(errs) == len(fc["grams"])
+    print(f"RGG1M {sk} cycle {hist['cycle_m']} flags {hist['cycle_flag']} Gram max {max(errs):.3e} "
+          f"H {_rel(hist['first_H'], fc['H']):.3e} X {_rel(X, ref.X):.3e}")
+    assert max(errs) <= TOL_GRAM
+    assert _rel(hist["first_H"], fc["H"]) <= TOL_GRAM
+    assert _rel(X, ref.X) <= TOL_X
+
+
 @pytest.mark.parametrize("sk", ["bcgsi_ls", "bcgs_pip", "bmgs_icwy"])
 def test_fp32_inner_fp64_refinement_well_conditioned(env, sk):
     """FP64 iterative refinement around an FP32 inner BGMRES: relative residual
