@@ -275,7 +275,8 @@ int lsba_gram(lsba_handle h, const double* d_L, int a, const double* d_R, int b,
 /* Autotuner of the kernel choices of the double-float lagged skeletons
  * (BCGSI+LS, BMGS-CWY/ICWY) at s = 8, where two kernels can run the same step:
  * for every iteration k = 2..m+1 of a cycle it times, on the handle's stream
- * with CUDA events (one warm-up and three runs each, on zeroed n x 8 operands),
+ * with CUDA events (one warm-up and three runs each, on pseudo-random n x 8
+ * operands whose digits are all busy, and their stored digit planes),
  * the stored-digit tensor-core Gram of Alg. 7 line 10 against the FP32-pipe
  * Gram, and the tensor-core basis update (Alg. 7 lines 16-17) with two against
  * three CTAs per SM.  Later solves on this handle with the same n and s take

@@ -265,7 +265,7 @@ static size_t max_partials(int64_t n, int s, int mmax, int sms, size_t* qmax_out
 #define LSBA_HIST_RESTARTS 4096
 struct SmallLayout {
   size_t oH, oT, oJ, oc1, oc2, och, ot1, ot2, oRb, orf, otau, otw, og, oTf, ogf, ocf, ouf, oC,
-      oBc, oXi, oMv, owk, osz, osy, osr, ohe, ogh, omu;
+      oBc, oXi, oMv, owk, osz, osy, osr, ohe, ogh, omu, opr;
   size_t hist_cap, gram_hist_cap, total;
 };
 
@@ -310,6 +310,7 @@ static SmallLayout small_layout(int s, int m, int max_restarts) {
   L.ohe = take(L.hist_cap);
   L.ogh = take(L.gram_hist_cap);
   L.omu = take(muscle_area_doubles(s));
+  L.opr = take((size_t)LSBA_LS_PROD_CTAS * 2 * ss);
   L.total = off;
   return L;
 }
@@ -397,6 +398,7 @@ static int ensure_ws(lsba_ctx* h, int64_t n, int s, int m) {
   w.hist_est = b + ohe;
   w.gram_hist = b + ogh;
   w.mus = b + L.omu;
+  w.prod = b + L.opr;
   w.hist_cycle = h->ismall;
   w.hist_j = h->ismall + hist_cap;
   w.gram_dims = h->ismall + 2 * hist_cap;
@@ -1678,8 +1680,9 @@ int lsba_gram(lsba_handle h, const double* d_L, int a, const double* d_R, int b,
 // every iteration k = 2..m+1, the stored-digit tensor-core Gram against the
 // FP32-pipe Gram of [V_1..V_{k-1}, U]^T [U, W], and the tensor-core update with
 // two against three CTAs per SM where three fit.  Each candidate runs once to
-// warm up and three times under CUDA events on the handle's stream, on zeroed
-// operands of the solve's shape.
+// warm up and three times under CUDA events on the handle's stream, on
+// pseudo-random operands of the solve's shape (every digit busy) and their
+// stored digit planes.
 int lsba_autotune(lsba_handle h, int64_t n, int s, int m, int8_t* gram_choice,
                   int8_t* update_ctas, int cap) {
   if (!h || n < 1 || s != 8 || m < 1 || (int64_t)(m + 1) * s > LSBA_MAX_MS || m + 3 > LSBA_MAXB ||
@@ -1692,16 +1695,17 @@ int lsba_autotune(lsba_handle h, int64_t n, int s, int m, int8_t* gram_choice,
   h->mode = MODE_DF;
   cudaStream_t st = h->stream;
   const size_t blk = (size_t)n * s;
-  CK(cudaMemsetAsync(h->basis, 0, sizeof(double) * blk * (m + 1), st));
-  CK(cudaMemsetAsync(h->Ub, 0, sizeof(double) * blk, st));
-  CK(cudaMemsetAsync(h->Wb, 0, sizeof(double) * blk, st));
-  CK(cudaMemsetAsync(h->dig, 0, (size_t)(m + 1) * digit_block_bytes(n, s), st));
-  CK(cudaMemsetAsync(h->dexp, 0, sizeof(int) * (size_t)(m + 1) * digit_exp_count(n, s), st));
+  // Operands with every digit busy (not zeros): pseudo-random blocks and
+  // their stored digit planes.
+  launch_fill_df(st, (int64_t)(blk * (m + 1)), 0x5EED0001ull, (float2*)h->basis);
+  launch_fill_df(st, (int64_t)blk, 0x5EED0002ull, (float2*)h->Ub);
+  launch_fill_df(st, (int64_t)blk, 0x5EED0003ull, (float2*)h->Wb);
   Ctl* c = h->h_ctl;
   c->active = 1;
   c->update_step = -1;
   c->error = 0;
   if ((rc = push_ctl(h)) != LSBA_OK) return rc;
+  for (int i = 0; i <= m; ++i) split_basis(h, i, n, s, h->d_ctl, -1);
   Ctl* ctl = h->d_ctl;
   const SmallWs& w = h->ws;
   cudaEvent_t e0, e1;

@@ -76,6 +76,26 @@ __global__ void k_sub_df(int64_t count, const float2* __restrict__ B, const floa
   }
 }
 
+// Pseudo-random double-float values for timing runs: entry i is u_i + v_i 2^-24
+// with u_i, v_i uniform in [-1, 1) from a counter hash (SplitMix64's output
+// function of seed + i), so every digit a kernel forms from them is busy.
+__global__ void k_fill_df(int64_t count, uint64_t seed, float2* __restrict__ out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    uint64_t z = seed + (uint64_t)i * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    const float u = (float)(int32_t)(uint32_t)z * 0x1p-31f;
+    const float v = (float)(int32_t)(uint32_t)(z >> 32) * 0x1p-31f;
+    out[i] = make_float2(u, v * 0x1p-24f);
+  }
+}
+
+void launch_fill_df(cudaStream_t st, int64_t count, uint64_t seed, float2* out) {
+  if (count > 0) k_fill_df<<<1024, 256, 0, st>>>(count, seed, out);
+}
+
 void launch_to_df(cudaStream_t st, int64_t count, const double* in, float2* out, double scale) {
   if (count > 0) k_to_df<<<(unsigned)((count + 255) / 256), 256, 0, st>>>(count, in, out, scale);
 }

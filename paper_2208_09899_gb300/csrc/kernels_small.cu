@@ -124,9 +124,9 @@ __device__ int cta_chol(const double* S, int lds, int s, double* R, int* sflag) 
   // Right-looking: pivot p reads the updated row p of the working matrix (in
   // R's lower-left free space is not used: the work copy lives in the strict
   // upper triangle of R itself and row p is finalised in place).  Each pivot
-  // takes one reciprocal square root (computed redundantly by every thread)
-  // and one barrier: the row-p scaling and the trailing update of rows > p use
-  // the unscaled row p, so they need no barrier between them.
+  // takes one reciprocal square root and two barriers: the row-p scaling and
+  // the trailing update of rows > p use the unscaled row p, so they need no
+  // barrier between them.
   __shared__ double wrk[LSBA_MAX_S * LSBA_MAX_S];
   if (threadIdx.x == 0) *sflag = 0;
   __syncthreads();
@@ -142,11 +142,21 @@ __device__ int cta_chol(const double* S, int lds, int s, double* R, int* sflag) 
   }
   __syncthreads();
   if (*sflag) return 1;
+  // The pivot's reciprocal square root is formed once, by thread 0, and
+  // shared: on GB300 an FP64 rsqrt costs ~430 cycles, and 512 threads forming
+  // it redundantly queue ~1800 cycles on the SM's FP64 pipe.
+  __shared__ double piv[2];
   for (int p = 0; p < s; ++p) {
     const double d = wrk[p + p * s];
     if (!(d > 0.0) || !isfinite(d)) return 1;   // uniform: every thread reads the same d
-    const double ri = rsqrt(d);
-    const double id = ri * ri;
+    if (threadIdx.x == 0) {
+      const double r0 = rsqrt(d);
+      piv[0] = r0;
+      piv[1] = r0 * r0;
+    }
+    __syncthreads();
+    const double ri = piv[0];
+    const double id = piv[1];
     const int nt = s - p;                        // row p (c >= p) and rows a in (p, c]
     for (int e = threadIdx.x; e < nt * nt; e += NT) {
       const int a = p + e % nt, c = p + e / nt;
@@ -997,9 +1007,11 @@ __device__ void step_cwy(const SmallWs& w, int k, bool inverse, Shared& sh) {
   // Coefficients: out1 = V_k = U R^{-1};
   // out2 = W R^{-1} - V_{1:k-1} Hc_{1:k-1} - V_k Hc_k.
   cta_tri_inverse(sh.R, s, sh.B);
-  for (int b = 0; b < k - 1; ++b) {
-    put_zero_coef(w.coef1, b, s);
-    put_coef(w.coef2, b, s, ZP + b * s, ks, -1.0);
+  // (coefficient block b, row a, column c: all blocks in one pass)
+  for (int e = threadIdx.x; e < (k - 1) * s * s; e += NT) {
+    const int b = e / (s * s), a = (e / s) % s, c = e % s;
+    w.coef1[e] = 0.0;
+    w.coef2[e] = -ZP[b * s + a + c * ks];
   }
   put_coef(w.coef1, k - 1, s, nullptr, 0, 1.0);
   put_zero_coef(w.coef2, k - 1, s);
@@ -1017,13 +1029,54 @@ __device__ void step_cwy(const SmallWs& w, int k, bool inverse, Shared& sh) {
 }
 
 // BCGSI+LS iteration k >= 2 (Alg. 7).  Inputs [V_1..V_{k-1}, U, W]; out1 = V_k, out2 = U.
+// BCGSI+LS, s <= 16: the step's two s x s products Y^T Y and Y^T Z (Alg. 7
+// lines 11 and 13; Y, Z the first (k-1)s rows of the reduced Gram [Y Z; Omega~
+// P~]) split by row ranges over LSBA_LS_PROD_CTAS CTAs, one output a thread:
+// on one SM the FP64 pipe (~1.7 FMA a clock) would take ~2 s^2 (k-1) s / 1.7
+// cycles.  The small step adds the CTAs' partial sums in CTA order.
+__global__ void __launch_bounds__(512) k_ls_products(SmallWs w, int k) {
+  if (!*(volatile const int*)&w.ctl->active) return;
+  const int s = w.s, ss = s * s, cols = 2 * s, K = (k - 1) * s;
+  const int t = threadIdx.x;
+  if (t >= 2 * ss) return;
+  const int o = t % ss, which = t / ss, i = o % s, j = o / s;
+  const int q0 = (int)((int64_t)blockIdx.x * K / LSBA_LS_PROD_CTAS);
+  const int q1 = (int)((int64_t)(blockIdx.x + 1) * K / LSBA_LS_PROD_CTAS);
+  const double* G = w.G;
+  double a0 = 0.0, a1 = 0.0;
+  int q = q0;
+  for (; q + 1 < q1; q += 2) {
+    a0 = fma(G[q * cols + i], G[q * cols + which * s + j], a0);
+    a1 = fma(G[(q + 1) * cols + i], G[(q + 1) * cols + which * s + j], a1);
+  }
+  if (q < q1) a0 = fma(G[q * cols + i], G[q * cols + which * s + j], a0);
+  w.prod[(size_t)blockIdx.x * 2 * ss + t] = a0 + a1;
+}
+
 __device__ void step_ls(const SmallWs& w, int k, Shared& sh) {
   const int s = w.s, ldH = w.ldH;
   const int k1s = (k - 1) * s, ks = k * s, cols = 2 * s;
   const double* G = w.G;
   record_gram(w, G, ks, cols);
   // Omega = Omega~ - Y^T Y.  Y(i,c) = G[i*cols + c] is Y^T col-major with ld cols.
-  cta_gemm_s(s, s, k1s, -1.0, G, cols, false, G, cols, true, 0.0, sh.A, s);
+  // sh.B = Y^T Z for P below.  For s <= 16 (classical inner product) both come
+  // as k_ls_products' partial sums (output i + j s); under the global product
+  // the Gram is projected in this kernel first, so they are formed here.
+  if (s <= 16 && !w.global_ip) {
+    for (int e = threadIdx.x; e < s * s; e += NT) {
+      double v1 = 0.0, v2 = 0.0;
+      for (int p = 0; p < LSBA_LS_PROD_CTAS; ++p) {
+        v1 += w.prod[(size_t)p * 2 * s * s + e];
+        v2 += w.prod[(size_t)p * 2 * s * s + s * s + e];
+      }
+      sh.A[e] = -v1;
+      sh.B[e] = v2;
+    }
+    __syncthreads();
+  } else {
+    cta_gemm_s(s, s, k1s, -1.0, G, cols, false, G, cols, true, 0.0, sh.A, s);
+    cta_gemm_s(s, s, k1s, 1.0, G, cols, false, G + s, cols, true, 0.0, sh.B, s);
+  }
   for (int e = threadIdx.x; e < s * s; e += NT) {
     const int a = e % s, c = e / s;
     sh.A[a + c * s] += G[(k1s + a) * cols + c];
@@ -1044,8 +1097,7 @@ __device__ void step_ls(const SmallWs& w, int k, Shared& sh) {
     const int i = e % k1s, c = e / k1s;
     Hkm1[i + c * ldH] = w.J[i + c * ldH] + G[i * cols + c];
   }
-  // P = R^{-T} (P~ - Y^T Z):  sh.B = Y^T Z  (Y^T as col-major (s x k1s) from G, Z likewise)
-  cta_gemm_s(s, s, k1s, 1.0, G, cols, false, G + s, cols, true, 0.0, sh.B, s);
+  // P = R^{-T} (P~ - Y^T Z), sh.B = Y^T Z (above)
   double* ZP = w.work;                // ks x s, ld ks
   for (int e = threadIdx.x; e < s * s; e += NT) {
     const int a = e % s, c = e / s;
@@ -1067,14 +1119,11 @@ __device__ void step_ls(const SmallWs& w, int k, Shared& sh) {
   }
   for (int e = threadIdx.x; e < s * s; e += NT) w.saveR[e] = sh.R[e];
   // out1 = V_k = (U - V_{1:k-1} Y) R^{-1};  out2 = (W - V_{1:k-1} Z - V_k P) R^{-1}
-  for (int b = 0; b < k - 1; ++b) {
-    double* c1 = w.coef1 + (size_t)b * s * s;
-    double* c2 = w.coef2 + (size_t)b * s * s;
-    for (int e = threadIdx.x; e < s * s; e += NT) {
-      const int a = e / s, c = e % s;
-      c1[a * s + c] = -G[(b * s + a) * cols + c];
-      c2[a * s + c] = -G[(b * s + a) * cols + s + c];
-    }
+  // (coefficient block b, row a, column c: all blocks in one pass)
+  for (int e = threadIdx.x; e < (k - 1) * s * s; e += NT) {
+    const int b = e / (s * s), a = (e / s) % s, c = e % s;
+    w.coef1[e] = -G[(b * s + a) * cols + c];
+    w.coef2[e] = -G[(b * s + a) * cols + s + c];
   }
   put_coef(w.coef1, k - 1, s, nullptr, 0, 1.0);
   put_zero_coef(w.coef2, k - 1, s);
@@ -1357,6 +1406,8 @@ void launch_outer_norm(cudaStream_t st, const double* G, int s, Ctl* ctl, int mo
   k_outer_norm<<<1, 32, 0, st>>>(G, s, ctl, mode);
 }
 void launch_small_step(cudaStream_t st, const SmallWs& w, int k, int phase) {
+  if (w.skel == SK_LS && k >= 2 && w.s <= 16 && !w.global_ip)
+    k_ls_products<<<LSBA_LS_PROD_CTAS, 2 * w.s * w.s, 0, st>>>(w, k);
   k_small_step<<<1, NT, SMALL_ARENA_DOUBLES * sizeof(double), st>>>(w, k, phase);
 }
 void launch_small_side(cudaStream_t st, const SmallWs& w, int k) {

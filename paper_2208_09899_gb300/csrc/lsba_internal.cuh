@@ -67,6 +67,9 @@ struct BlockPtrs {
 };
 
 // Device workspace of the small kernels (all device pointers).
+// CTAs that share the s x s products of a BCGSI+LS step (k_ls_products).
+#define LSBA_LS_PROD_CTAS 16
+
 struct SmallWs {
   int s, m, skel, modification;
   int global_ip;       // 1: global block inner product (each s x s Gram block -> tr/s I)
@@ -101,6 +104,8 @@ struct SmallWs {
   double* saveZP;      // BCGSI+LS: [Z; P] of the last iteration, (m+1)s x s
   double* saveY;       // BCGSI+LS: Y of the last iteration, (m+1)s x s
   double* saveR;       // BCGSI+LS: R = H_{k,k-1} of the last iteration, s x s
+  double* prod;        // BCGSI+LS, s <= 16: per-CTA partial sums of Y^T Y and Y^T Z,
+                       // [LSBA_LS_PROD_CTAS][2][s x s] (k_ls_products)
   double* hist_est;    // [hist_cap]
   int* hist_cycle;
   int* hist_j;
@@ -173,6 +178,8 @@ void launch_gram_reduce_df(cudaStream_t st, const float2* partials, int nparts, 
 // [V_1..V_{a-1} (stored), U] x [U, W] (s = 8, b = 2, a s <= 168).
 size_t digit_block_bytes(int64_t n, int s);
 size_t digit_exp_count(int64_t n, int s);
+// Pseudo-random double-float values (timing runs only).
+void launch_fill_df(cudaStream_t st, int64_t count, uint64_t seed, float2* out);
 void launch_split_digits(cudaStream_t st, const float2* V, int64_t n, int s, unsigned char* dig,
                          int* dexp, const Ctl* ctl, int step, int num_sms);
 bool gram_tcs_eligible(int s, int a, int b);
