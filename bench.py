@@ -509,7 +509,7 @@ def main():
                    "k_coef_fold64 + k_update_f64tc (FP64 digit products on tcgen05, every update "
                    "of the cycle and its end)" if is_ftc else "k_update"),
         "spmm": ("k_spmm_df8" if is_df else
-                 "k_spmm (FP64) + k_block_digits (tile exponents and digit planes of W)" if is_ftc else "k_spmm"),
+                 "k_spmm_digits (FP64 SpMM writing W with its tile exponents and digit planes)" if is_ftc else "k_spmm"),
     }
     traffic_key = dom + ("_df" if is_df else "_f64tc" if is_ftc else "")
     roofline = {

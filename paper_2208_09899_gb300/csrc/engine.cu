@@ -649,8 +649,10 @@ static void enqueue_cycle_ftc(lsba_ctx* h, const lsba_csr* A, const double* Rsta
                 w.coef1, w.tri1, nullptr, nullptr, nullptr, ctl, 0);
   for (int k = 1; k <= kmax; ++k) {
     const double* U = (k == 1) ? h->basis : h->Ub;
-    do_spmm(h, A, U, h->Wb, s, ctl, 1);
-    do_block_digits(h, h->Wb, h->fexp_W, h->fpl_W, n, ctl, 1);
+    prof_begin(h, LSBA_K_SPMM);
+    launch_spmm_digits(st, A->n, A->d_rowptr, A->d_colidx, A->d_vals, U, h->Wb, h->fexp_W, h->fpl_W,
+                       ctl, 1);
+    prof_end(h);
     if (k == 1) {
       Le[0] = h->fexp;
       Lp[0] = h->fpl;

@@ -335,6 +335,61 @@ void launch_block_digits(cudaStream_t st, const double* V, int64_t n, int* ex, u
   if (tiles > 0) k_block_digits<<<(unsigned)tiles, 128, 0, st>>>(V, n, ex, planes, ctl, guard);
 }
 
+// W = A V for s = 8 in FP64 (CSR, one thread per (row, column): the same
+// summation as the plain SpMM), fused with W's tile exponents and digit
+// planes: one CTA of 1024 threads per 128-row tile stages the tile's W in
+// shared memory, reduces its column maxima and writes the digits, so W is not
+// read back by a separate pass.
+__global__ void __launch_bounds__(1024) k_spmm_digits(int64_t n, const int32_t* __restrict__ rowptr,
+                                                      const int32_t* __restrict__ colidx,
+                                                      const double* __restrict__ vals,
+                                                      const double* __restrict__ V, double* __restrict__ W,
+                                                      int* __restrict__ ex, unsigned char* __restrict__ planes,
+                                                      const Ctl* ctl, int guard) {
+  if (guard && !*(volatile const int*)&ctl->active) return;
+  __shared__ double wt[128][9];   // the tile's W (padded rows)
+  __shared__ uint32_t red[32][8];
+  __shared__ int es[8];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int r = tid >> 3, c = tid & 7;
+  const int64_t tile = blockIdx.x, row = tile * 128 + r;
+  double acc = 0.0;
+  if (row < n) {
+    const int p0 = rowptr[row], p1 = rowptr[row + 1];
+    for (int p = p0; p < p1; ++p) acc = fma(vals[p], V[(int64_t)colidx[p] * 8 + c], acc);
+    W[row * 8 + c] = acc;
+  }
+  wt[r][c] = acc;
+  // column maxima (high words of |x|): lanes c, c + 8, c + 16, c + 24 share a column
+  uint32_t hi = (uint32_t)((unsigned long long)__double_as_longlong(acc) >> 32) & 0x7FFFFFFFu;
+  hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, 8));
+  hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, 16));
+  if (lane < 8) red[warp][lane] = hi;
+  __syncthreads();
+  if (tid < 8) {
+    uint32_t m = 0;
+    for (int w = 0; w < 32; ++w) m = max(m, red[w][tid]);
+    const int e = ft_exp_of_hi(m);
+    es[tid] = e;
+    ex[tile * 8 + tid] = e;
+  }
+  __syncthreads();
+  if (tid < 128) {
+    double x[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) x[q] = wt[tid][q];
+    ft_store_row_digits(x, es, planes + (size_t)tile * FT_PLANE_TILE + ft_row_off(tid));
+  }
+}
+
+void launch_spmm_digits(cudaStream_t st, int64_t n, const int32_t* rowptr, const int32_t* colidx,
+                        const double* vals, const double* V, double* W, int* ex, unsigned char* planes,
+                        const Ctl* ctl, int guard) {
+  const int64_t tiles = (n + 127) / 128;
+  if (tiles > 0)
+    k_spmm_digits<<<(unsigned)tiles, 1024, 0, st>>>(n, rowptr, colidx, vals, V, W, ex, planes, ctl, guard);
+}
+
 // ---------------------------------------------------------------- Gram
 // G = L^T R with L = [L_1..L_a], R = [R_1..R_b] (s = 8) given by their
 // exponents and digit planes, the partial sums of one CTA's rows (whole

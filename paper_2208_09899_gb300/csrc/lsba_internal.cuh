@@ -252,6 +252,10 @@ void launch_block_exp(cudaStream_t st, const double* V, int64_t n, int s, int* e
 size_t f64tc_plane_bytes(int64_t n);
 void launch_block_digits(cudaStream_t st, const double* V, int64_t n, int* ex, unsigned char* planes,
                          const Ctl* ctl, int guard);
+// W = A V (FP64, s = 8) with W's exponents and digit planes, in one pass.
+void launch_spmm_digits(cudaStream_t st, int64_t n, const int32_t* rowptr, const int32_t* colidx,
+                        const double* vals, const double* V, double* W, int* ex, unsigned char* planes,
+                        const Ctl* ctl, int guard);
 // Gram [L_1..L_a]^T [R_1..R_b] (blocks given by exponents and digit planes),
 // reduced into G.  shared: R_1 is L_a (read once).
 bool gram_f64tc_eligible(int s, int a, int b, bool shared);
