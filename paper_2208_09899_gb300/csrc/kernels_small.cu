@@ -1274,18 +1274,31 @@ __global__ void __launch_bounds__(256) k_side_J_glob(SmallWs w, int k, int S2) {
 // coefficients of the pass over [V_1..V_{j+1}, X]:
 //   out1 = X + V_{1:j} (Xi C),   out2 = U = V_{1:j+1} [M; -H_{j+1,j}];
 // then C <- c C.
+// The cycle end runs as three kernels:
+//   k_small_end (one CTA): Xi's right-hand side (BGMRES: g; BFOM: the last
+//     block c_fom and g_{1:j-1} - u c_fom) and, for BGMRES, Y_last =
+//     T^{-T} S with S = H_{j+1,j}^T H_{j+1,j};
+//   k_end_cols (one CTA per right-hand-side column): the block back
+//     substitution with Rbar and, for BGMRES, M = Q_{1..j-1} [0; Y_last], both
+//     column by column (the columns are independent; on one SM the FP64 pipe
+//     made this the longest part of a cycle);
+//   k_end_tail (one CTA): the coefficients of X += V Xi C and U = V [M; -H],
+//     and C <- c C.
+__device__ __forceinline__ bool end_skip(const SmallWs& w, const Ctl* ctl) {
+  return ctl->j == 0 || (w.modification == 0 && ctl->fom_singular);
+}
+
 __global__ void __launch_bounds__(NT) k_small_end(SmallWs w) {
   __shared__ Shared sh;
   Ctl* ctl = w.ctl;
   const int j = ctl->j;
-  const int s = w.s, ldH = w.ldH, ldR = w.ldR, ldg = w.ldH;
-  if (j == 0 || (w.modification == 0 && ctl->fom_singular)) {
+  const int s = w.s, ldH = w.ldH, ldg = w.ldH;
+  if (end_skip(w, ctl)) {
     if (threadIdx.x == 0) ctl->update_step = -2;
     return;
   }
   const int js = j * s;
   double* Xi = w.Xi;     // js x s, ld ldH
-  double* Mv = w.Mvec;   // js x s, ld ldH
   // Xi_j (last block)
   if (w.modification == 1) {
     cta_copy(Xi, ldH, w.g, ldg, js, s);
@@ -1295,12 +1308,12 @@ __global__ void __launch_bounds__(NT) k_small_end(SmallWs w) {
     // g_{1:j-1} - u c
     cta_gemm_s((j - 1) * s, s, s, -1.0, w.ufom, ldH, false, w.cfom, s, false, 1.0, Xi, ldH);
   }
-  // Block back substitution with Rbar (BGMRES: blocks 1..j; BFOM: blocks 1..j-1).
-  // The inverses of the upper-triangular diagonal blocks are formed first, all
-  // blocks at once (one thread per block column: back substitution for R_ii x = e_c),
-  // so that each block step is two small products.
+  // Inverses of Rbar's upper-triangular diagonal blocks (BGMRES: blocks 1..j;
+  // BFOM: blocks 1..j-1), one thread per block column (back substitution for
+  // R_ii z = e_c with the diagonal's reciprocals), for k_end_cols.
   const int top = (w.modification == 1) ? j : j - 1;
-  double* Rinv = w.work + (size_t)4 * w.ldH * s;  // top blocks of s x s (clear of Ylast/XiC/w1/w2)
+  const int ldR = w.ldR;
+  double* Rinv = w.work + (size_t)4 * w.ldH * s;  // top blocks of s x s (clear of Ylast/XiC)
   for (int e = threadIdx.x; e < top * s; e += NT) {
     const int i = e / s, c = e % s;  // block i (0-based), column c
     const double* Rii = w.Rbar + (size_t)i * s + (size_t)i * s * ldR;
@@ -1314,20 +1327,9 @@ __global__ void __launch_bounds__(NT) k_small_end(SmallWs w) {
     }
   }
   __syncthreads();
-  for (int i = top; i >= 1; --i) {
-    double* Xii = Xi + (i - 1) * s;
-    const int rest = top - i;  // blocks i+1..top already known
-    if (rest > 0)
-      cta_gemm_s(s, s, rest * s, -1.0, w.Rbar + (i - 1) * s + (size_t)i * s * ldR, ldR, false,
-               Xi + i * s, ldH, false, 1.0, Xii, ldH);
-    cta_gemm_s(s, s, s, 1.0, Rinv + (size_t)(i - 1) * s * s, s, false, Xii, ldH, false, 0.0, sh.B, s);
-    cta_copy(Xii, ldH, sh.B, s, s, s);
-  }
-  // c = Xi_j (s x s) -> sh.A
-  cta_copy(sh.A, s, Xi + (j - 1) * s, ldH, s, s);
-  // M (BGMRES): Q_{1..j-1} [0; T^{-T} S], S = H_{j+1,j}^T H_{j+1,j}
-  const double* Hsub = w.H + js + (size_t)(j - 1) * s * ldH;
+  // M (BGMRES): Q_{1..j-1} [0; T^{-T} S], S = H_{j+1,j}^T H_{j+1,j}; here Y_last = T^{-T} S
   if (w.modification == 1) {
+    const double* Hsub = w.H + js + (size_t)(j - 1) * s * ldH;
     cta_gemm_s(s, s, s, 1.0, Hsub, ldH, true, Hsub, ldH, false, 0.0, sh.B, s);
     // T^{-T} S: solve T^T Y = S  -> LU solve with T^T.
     for (int e = threadIdx.x; e < s * s; e += NT) {
@@ -1337,24 +1339,103 @@ __global__ void __launch_bounds__(NT) k_small_end(SmallWs w) {
     __syncthreads();
     double* Ylast = w.work;  // s x s
     warp_lu_solve(sh.R, sh.B, s, Ylast, w.work + s * s, &sh.piv, &sh.flag2);
-    for (int e = threadIdx.x; e < js * s; e += NT) {
-      const int r = e % js, c = e / js;
-      Mv[r + c * ldH] = (r >= (j - 1) * s) ? Ylast[(r - (j - 1) * s) + c * s] : 0.0;
+  }
+}
+
+// Shared memory of k_end_cols.
+static size_t end_cols_smem(int s, int m) {
+  const size_t js = (size_t)(m + 1) * s;
+  return sizeof(double) * (2 * js + 2 * (size_t)s);
+}
+
+__global__ void __launch_bounds__(256) k_end_cols(SmallWs w) {
+  const Ctl* ctl = w.ctl;
+  if (end_skip(w, ctl)) return;
+  const int j = ctl->j;
+  const int s = w.s, ldH = w.ldH, ldR = w.ldR, js = j * s, c = blockIdx.x, t = threadIdx.x;
+  const int top = (w.modification == 1) ? j : j - 1;
+  extern __shared__ double se[];
+  double* x = se;                         // [js] column c of Xi
+  double* mv = x + js;                    // [js] column c of M
+  double* w1 = mv + js;                   // [s]
+  double* w2 = w1 + s;                    // [s]
+  const double* Ri = w.work + (size_t)4 * ldH * s;   // R_ii^{-1}, from k_small_end
+  for (int r = t; r < js; r += 256) x[r] = w.Xi[r + (size_t)c * ldH];
+  __syncthreads();
+  // block back substitution, right-looking: x_i <- Ri_i x_i, then the rows
+  // above drop R_{l,i} x_i
+  for (int i = top; i >= 1; --i) {
+    const int r0 = (i - 1) * s;
+    if (t < s) {
+      const double* Rb = Ri + (size_t)(i - 1) * s * s;
+      double acc = 0.0;
+      for (int q = 0; q < s; ++q) acc = fma(Rb[t + q * s], x[r0 + q], acc);
+      w1[t] = acc;
     }
     __syncthreads();
-    double* w1 = w.work + (size_t)2 * w.ldH * s + 2 * (size_t)s * s;
-    double* w2 = w1 + (size_t)s * s;
-    for (int i = j - 1; i >= 1; --i)
-      apply_set_wy(w.refl + (size_t)(i - 1) * 2 * s * s, w.Twy + (size_t)(i - 1) * s * s, s, Mv,
-                   ldH, (i - 1) * s, s, 0, w1, w2);
+    if (t < s) x[r0 + t] = w1[t];
+    __syncthreads();
+    for (int r = t; r < r0; r += 256) {
+      double acc = x[r];
+      for (int q = 0; q < s; ++q) acc = fma(-w.Rbar[r + (size_t)(r0 + q) * ldR], x[r0 + q], acc);
+      x[r] = acc;
+    }
+    __syncthreads();
   }
+  for (int r = t; r < js; r += 256) w.Xi[r + (size_t)c * ldH] = x[r];
+  if (w.modification == 1) {
+    // M = Q_{1..j-1} [0; Y_last]: reflector sets j-1 .. 1, Q_i = I - V T V^T on rows (i-1)s .. (i+1)s
+    const double* Ylast = w.work;
+    for (int r = t; r < js; r += 256)
+      mv[r] = (r >= (j - 1) * s) ? Ylast[(r - (j - 1) * s) + c * s] : 0.0;
+    __syncthreads();
+    const int h = 2 * s;
+    for (int i = j - 1; i >= 1; --i) {
+      const double* V = w.refl + (size_t)(i - 1) * 2 * s * s;
+      const double* T = w.Twy + (size_t)(i - 1) * s * s;
+      const int r0 = (i - 1) * s;
+      if (t < s) {
+        double acc = 0.0;
+        for (int q = 0; q < h; ++q) acc = fma(V[q + t * h], mv[r0 + q], acc);
+        w1[t] = acc;
+      }
+      __syncthreads();
+      if (t < s) {
+        double acc = 0.0;
+        for (int q = 0; q < s; ++q) acc = fma(T[t + q * s], w1[q], acc);
+        w2[t] = acc;
+      }
+      __syncthreads();
+      if (t < h) {
+        double acc = 0.0;
+        for (int l = 0; l < s; ++l) acc = fma(V[t + l * h], w2[l], acc);
+        mv[r0 + t] -= acc;
+      }
+      __syncthreads();
+    }
+    for (int r = t; r < js; r += 256) w.Mvec[r + (size_t)c * ldH] = mv[r];
+  }
+}
+
+__global__ void __launch_bounds__(NT) k_end_tail(SmallWs w) {
+  __shared__ Shared sh;
+  Ctl* ctl = w.ctl;
+  if (end_skip(w, ctl)) return;
+  const int j = ctl->j;
+  const int s = w.s, ldH = w.ldH, js = j * s, ss = s * s;
+  double* Xi = w.Xi;
+  const double* Mv = w.Mvec;
+  const double* Hsub = w.H + js + (size_t)(j - 1) * s * ldH;
+  // c = Xi_j (s x s) -> sh.A
+  cta_copy(sh.A, s, Xi + (j - 1) * s, ldH, s, s);
   // Coefficients.  Xi C -> coef1 blocks 0..j-1; coef1 block j = 0; block j+1 (X) = I.
   double* XiC = w.work + 2 * s * s;  // js x s, ld js
   cta_gemm_s(js, s, s, 1.0, Xi, ldH, false, w.Cfac, s, false, 0.0, XiC, js);
-  for (int b = 0; b < j; ++b) {
-    put_coef(w.coef1, b, s, XiC + b * s, js, 1.0);
-    if (w.modification == 1) put_coef(w.coef2, b, s, Mv + b * s, ldH, 1.0);
-    else put_zero_coef(w.coef2, b, s);
+  // coefficient block b, row a, column cc: all blocks in one pass
+  for (int e = threadIdx.x; e < j * ss; e += NT) {
+    const int b = e / ss, a = (e / s) % s, cc = e % s;
+    w.coef1[e] = XiC[b * s + a + cc * js];
+    w.coef2[e] = (w.modification == 1) ? Mv[b * s + a + cc * ldH] : 0.0;
   }
   put_zero_coef(w.coef1, j, s);
   put_coef(w.coef2, j, s, Hsub, ldH, -1.0);
@@ -1383,6 +1464,7 @@ static void small_attrs() {
     cudaFuncSetAttribute(k_small_step, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     cudaFuncSetAttribute(k_small_side, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     cudaFuncSetAttribute(k_small_end, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaFuncSetAttribute(k_end_tail, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   });
 }
 
@@ -1431,7 +1513,10 @@ void launch_small_side(cudaStream_t st, const SmallWs& w, int k) {
   k_small_side<<<1, NT, SMALL_ARENA_DOUBLES * sizeof(double), st>>>(w, k);
 }
 void launch_small_end(cudaStream_t st, const SmallWs& w) {
+  small_attrs();
   k_small_end<<<1, NT, SMALL_ARENA_DOUBLES * sizeof(double), st>>>(w);
+  k_end_cols<<<w.s, 256, end_cols_smem(w.s, w.m), st>>>(w);
+  k_end_tail<<<1, NT, SMALL_ARENA_DOUBLES * sizeof(double), st>>>(w);
 }
 
 }  // namespace lsba
