@@ -260,6 +260,32 @@ def rgg_cycles(torch, lsba, dev, stream):
     return out
 
 
+def skeleton_table(torch, lsba, dev, stream):
+    """The 512x512 Laplacian configuration skeleton by skeleton: BGMRES(20) and
+    BFOM(20) with BCGS, BCGS-PIP, BCGSI+LS and BMGS-ICWY under precision auto
+    (adaptive restart on, tol 1e-8), three restart cycles each: time per cycle,
+    sync points and A-calls per cycle, the precision taken and the estimate
+    reached."""
+    A, B = W.workload(WORKLOAD, 0)
+    dA = lsba.DeviceCSR.from_host(A, f"cuda:{dev}")
+    dB = torch.from_numpy(B).to(f"cuda:{dev}")
+    dX = torch.empty_like(dB)
+    out = {"workload": f"{WORKLOAD}, m = 20, tol 1e-8, precision auto, 3 cycles per run", "runs": {}}
+    for mod in ("gmres", "fom"):
+        for sk in ("bcgs", "bcgs_pip", "bcgsi_ls", "bmgs_icwy"):
+            sv = lsba.Solver(dev, modification=mod, max_restarts=2, verify_true_residual=0)
+            sv.solve(dA, dB, dX, M, 1e-8, sk)
+            ms = _timed(torch, stream, lambda: sv.solve(dA, dB, dX, M, 1e-8, sk), 1)
+            st = sv.stats()
+            cyc = max(st["cycles"], 1)
+            out["runs"][f"{sk}/{mod}"] = {
+                "ms_per_cycle": ms / cyc, "cycles": st["cycles"], "syncs_per_cycle": st["syncs"] / cyc,
+                "a_calls_per_cycle": st["a_calls"] / cyc, "precision": st["precision"],
+                "tensor_cores": st["tensor_cores"], "relres_est": st["relres_est"]}
+            sv.close()
+    return out
+
+
 def gram_kernels(torch, lsba, dev, n=262144, s=8, b=2, reps=5):
     """Double-float Gram kernels alone (CUDA events around each launch):
     the tensor-core digit kernel vs the FP32-pipe kernel, L = a blocks and
@@ -423,6 +449,7 @@ def main():
     ap.add_argument("--no-rgg", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-gram-kernels", action="store_true")
+    ap.add_argument("--no-skeletons", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=32)
     ap.add_argument("--profile-cycle", default=None,
                     help="run one restart cycle of the workload in this precision (fp64, df, "
@@ -626,6 +653,7 @@ def main():
     rgg = None if args.no_rgg else rgg_cycles(torch, lsba, dev, stream)
     served = None if args.no_serving else serving(torch, lsba, dev, args.serve_requests)
     gk = None if args.no_gram_kernels else gram_kernels(torch, lsba, dev)
+    skt = None if args.no_skeletons else skeleton_table(torch, lsba, dev, stream)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -660,7 +688,7 @@ def main():
             "gpu_launches": gpu_launches, "clocks": clocks, "time_to_tol": time_to_tol,
             "fp64_plain": fp64_plain, "df48": df48, "mixed_precision": mixed,
             "graph_workload": rgg,
-            "serving": served, "gram_kernels": gk,
+            "serving": served, "gram_kernels": gk, "skeletons": skt,
         }
         print(json.dumps(line))
     if pg:
