@@ -524,6 +524,69 @@ __device__ void record_gram(const SmallWs& w, const double* G, int rows, int col
 }
 
 // Relation j of the current cycle is complete: H(1:j+1, j) is final.
+// The dot product of cta_gemm_s's inner loop (four running sums over q, q+1,
+// q+2, q+3, the rest into the first, combined (a0 + a1) + (a2 + a3)), on
+// strided shared-memory operands.
+__device__ __forceinline__ double dot4(const double* x, int sx, const double* y, int sy, int K) {
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+  int q = 0;
+  for (; q + 3 < K; q += 4) {
+    a0 = fma(x[q * sx], y[q * sy], a0);
+    a1 = fma(x[(q + 1) * sx], y[(q + 1) * sy], a1);
+    a2 = fma(x[(q + 2) * sx], y[(q + 2) * sy], a2);
+    a3 = fma(x[(q + 3) * sx], y[(q + 3) * sy], a3);
+  }
+  for (; q < K; ++q) a0 = fma(x[q * sx], y[q * sy], a0);
+  return (a0 + a1) + (a2 + a3);
+}
+
+// Q_1^T .. Q_{j-1}^T applied to col ((j+1)s x s, ld ldc, global), the
+// reflector sets' V and T and col itself staged once in the shared-memory
+// arena: the same products as apply_set_wy (transpose = 1) in the same order,
+// without a global round trip per product.  Returns false (nothing done) if
+// they do not fit the arena.
+__device__ bool apply_sets_T_staged(const SmallWs& w, int j, double* col, int ldc) {
+  const int s = w.s, h = 2 * s, ss = s * s, rows = (j + 1) * s;
+  const size_t need = (size_t)(j - 1) * 3 * ss + (size_t)rows * s + 2 * (size_t)ss;
+  if (j < 2 || need > SMALL_ARENA_DOUBLES) return false;
+  double* Vs = small_arena;                          // [(j-1)][2s x s]
+  double* Ts = Vs + (size_t)(j - 1) * 2 * ss;        // [(j-1)][s x s]
+  double* cs = Ts + (size_t)(j - 1) * ss;            // rows x s, ld rows
+  double* w1 = cs + (size_t)rows * s;                // s x s
+  double* w2 = w1 + ss;                              // s x s
+  for (int e = threadIdx.x; e < (j - 1) * 2 * ss; e += NT) Vs[e] = w.refl[e];
+  for (int e = threadIdx.x; e < (j - 1) * ss; e += NT) Ts[e] = w.Twy[e];
+  for (int e = threadIdx.x; e < rows * s; e += NT) cs[e] = col[(e % rows) + (size_t)(e / rows) * ldc];
+  __syncthreads();
+  for (int i = 1; i < j; ++i) {
+    const double* V = Vs + (size_t)(i - 1) * 2 * ss;
+    const double* T = Ts + (size_t)(i - 1) * ss;
+    double* x = cs + (i - 1) * s;
+    // w1 = V^T x  (s x s, K = 2s)
+    for (int e = threadIdx.x; e < ss; e += NT) {
+      const int l = e % s, c = e / s;
+      w1[l + c * s] = dot4(V + l * h, 1, x + c * rows, 1, h);
+    }
+    __syncthreads();
+    // w2 = T^T w1
+    for (int e = threadIdx.x; e < ss; e += NT) {
+      const int l = e % s, c = e / s;
+      w2[l + c * s] = dot4(T + l * s, 1, w1 + c * s, 1, s);
+    }
+    __syncthreads();
+    // x -= V w2  (2s x s)
+    for (int e = threadIdx.x; e < h * s; e += NT) {
+      const int r = e % h, c = e / h;
+      const double v = dot4(V + r, h, w2 + c * s, 1, s);
+      x[r + c * rows] = -1.0 * v + 1.0 * x[r + c * rows];
+    }
+    __syncthreads();
+  }
+  for (int e = threadIdx.x; e < rows * s; e += NT) col[(e % rows) + (size_t)(e / rows) * ldc] = cs[e];
+  __syncthreads();
+  return true;
+}
+
 __device__ void relation_complete(const SmallWs& w, int j, Shared& sh) {
   const int s = w.s, ldH = w.ldH, ldg = w.ldH, ldR = w.ldR;
   Ctl* ctl = w.ctl;
@@ -532,9 +595,10 @@ __device__ void relation_complete(const SmallWs& w, int j, Shared& sh) {
   cta_copy(col, ldH, Hj, ldH, (j + 1) * s, s);
   double* w1 = w.work + (size_t)2 * w.ldH * s;   // s x s scratch (clear of col and of J's)
   double* w2 = w1 + (size_t)s * s;
-  for (int i = 1; i < j; ++i)
-    apply_set_wy(w.refl + (size_t)(i - 1) * 2 * s * s, w.Twy + (size_t)(i - 1) * s * s, s, col,
-                 ldH, (i - 1) * s, s, 1, w1, w2);
+  if (!apply_sets_T_staged(w, j, col, ldH))
+    for (int i = 1; i < j; ++i)
+      apply_set_wy(w.refl + (size_t)(i - 1) * 2 * s * s, w.Twy + (size_t)(i - 1) * s * s, s, col,
+                   ldH, (i - 1) * s, s, 1, w1, w2);
   // BFOM pieces (before reflector set j).
   cta_copy(w.Tfom, s, col + (j - 1) * s, ldH, s, s);
   cta_copy(w.ufom, ldH, col, ldH, (j - 1) * s, s);
