@@ -286,6 +286,40 @@ def skeleton_table(torch, lsba, dev, stream):
     return out
 
 
+def autotune_table(torch, lsba, dev, stream):
+    """The autotuner on the 2D Laplacian 512x512 in double-float, BGMRES(16),
+    BCGSI+LS, for s = 4, 8, 16 (B n x s N(0,1)): the chosen Gram and update
+    shape of every iteration k, and one restart cycle timed with the fixed
+    rules and with the tuned shapes."""
+    A = W.laplacian_2d(512)
+    dA = lsba.DeviceCSR.from_host(A, f"cuda:{dev}")
+    m = 16
+    out = {"workload": "lapl512: 2D Laplacian 512x512, B n x s N(0,1), BGMRES(16), BCGSI+LS, "
+                       "double-float, one restart cycle", "by_s": {}}
+    for s in (4, 8, 16):
+        dB = torch.from_numpy(W.gaussian_block(A.n, s, 0)).to(f"cuda:{dev}")
+        dX = torch.empty_like(dB)
+        cyc = {}
+        for tuned in (False, True):
+            sv = lsba.Solver(dev, modification="gmres", max_restarts=0, verify_true_residual=0,
+                             precision="df")
+            if tuned:
+                sv.autotune(A.n, s, m)
+                table = sv.tune_table()
+            sv.solve(dA, dB, dX, m, 1e-30, "bcgsi_ls")
+            cyc["tuned" if tuned else "rules"] = _timed(
+                torch, stream, lambda: sv.solve(dA, dB, dX, m, 1e-30, "bcgsi_ls"), 3)
+            sv.close()
+        out["by_s"][str(s)] = {
+            "ms_per_cycle": cyc,
+            "shapes": [{"k": e["k"], "gram": [e["gram_kernel"], e["gram_ctas_per_sm"], e["gram_rows"]],
+                        "gram_us": round(e["gram_us"], 1), "gram_rule_us": round(e["gram_default_us"], 1),
+                        "update": [e["update_kernel"], e["update_ctas_per_sm"]],
+                        "update_us": round(e["update_us"], 1),
+                        "update_rule_us": round(e["update_default_us"], 1)} for e in table]}
+    return out
+
+
 def gram_kernels(torch, lsba, dev, n=262144, s=8, b=2, reps=5):
     """Double-float Gram kernels alone (CUDA events around each launch):
     the tensor-core digit kernel vs the FP32-pipe kernel, L = a blocks and
@@ -450,6 +484,7 @@ def main():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-gram-kernels", action="store_true")
     ap.add_argument("--no-skeletons", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=32)
     ap.add_argument("--profile-cycle", default=None,
                     help="run one restart cycle of the workload in this precision (fp64, df, "
@@ -654,6 +689,7 @@ def main():
     served = None if args.no_serving else serving(torch, lsba, dev, args.serve_requests)
     gk = None if args.no_gram_kernels else gram_kernels(torch, lsba, dev)
     skt = None if args.no_skeletons else skeleton_table(torch, lsba, dev, stream)
+    tun = None if args.no_autotune else autotune_table(torch, lsba, dev, stream)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -688,7 +724,7 @@ def main():
             "gpu_launches": gpu_launches, "clocks": clocks, "time_to_tol": time_to_tol,
             "fp64_plain": fp64_plain, "df48": df48, "mixed_precision": mixed,
             "graph_workload": rgg,
-            "serving": served, "gram_kernels": gk, "skeletons": skt,
+            "serving": served, "gram_kernels": gk, "skeletons": skt, "autotune": tun,
         }
         print(json.dumps(line))
     if pg:

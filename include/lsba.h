@@ -272,25 +272,56 @@ int lsba_spmm(lsba_handle h, const lsba_csr* A, const double* d_V, double* d_W, 
 int lsba_gram(lsba_handle h, const double* d_L, int a, const double* d_R, int b,
               int64_t n, int s, double* d_G);
 
-/* Autotuner of the kernel choices of the double-float lagged skeletons
- * (BCGSI+LS, BMGS-CWY/ICWY) at s = 8, where two kernels can run the same step:
- * for every iteration k = 2..m+1 of a cycle it times, on the handle's stream
- * with CUDA events (one warm-up and three runs each, on pseudo-random n x 8
- * operands whose digits are all busy, and their stored digit planes),
- * the stored-digit tensor-core Gram of Alg. 7 line 10 against the FP32-pipe
- * Gram, and the tensor-core basis update (Alg. 7 lines 16-17) with two against
- * three CTAs per SM.  Later solves on this handle with the same n and s take
- * the faster choice at each k (otherwise fixed rules: the tensor-core Gram
- * from k = 5, three update CTAs per SM wherever they fit).  The two Gram
- * kernels round differently (both to 48-bit accuracy), so tuned and untuned
- * solves agree to rounding, not bit for bit.  The workspace is (re)allocated
- * for (n, 8, m); the basis contents are overwritten.
- * gram_choice[k] (k < cap): 1 tensor-core Gram, 0 FP32-pipe Gram, -1 no choice;
- * update_ctas[k]: 2 or 3, 0 no choice.  Host arrays of cap entries (may be
- * NULL when cap = 0).  Returns LSBA_OK, LSBA_INVALID_ARG (s != 8, n < 1, m < 1
- * or m too large), LSBA_OUT_OF_MEMORY, LSBA_DEVICE_TIMEOUT or LSBA_CUDA_ERROR. */
+/* Autotuner of the double-float lagged skeletons (BCGSI+LS, BMGS-CWY/ICWY) for
+ * any block size s (Sec. 2.1 treats the inner product and the basis update as
+ * separately tunable functions).  For every iteration k = 2..m+1 of a cycle it
+ * times, on the handle's stream with CUDA events (one warm-up and three runs
+ * each, on pseudo-random n x s operands whose digits are all busy, and their
+ * stored digit planes where a kernel reads them), the candidate shapes of the
+ * iteration's two passes and keeps the fastest:
+ *   Gram [V_1..V_{k-1}, U]^T [U, W] (Alg. 7 line 10): the FP32-pipe kernel
+ *     with 1..4 CTAs per SM and its default or half its pipeline chunk rows
+ *     (shapes whose shared memory cannot stay resident at that CTA count are
+ *     skipped), the split-digit tensor-core kernel where its shape allows, and
+ *     at s = 8 the stored-digit tensor-core kernel (tensor-core candidates only
+ *     when options.tensor_cores != 0);
+ *   update (Alg. 7 lines 16-17): at s = 8 with tensor cores the stored-digit
+ *     tensor-core update with two or three CTAs per SM, else the FP32-pipe
+ *     update with 1, 2, 4 or 8 CTAs per SM.
+ * Later solves on this handle with the same n and s run the tuned shape at each
+ * k (otherwise fixed rules: the stored-digit Gram from k = 5, the FP32-pipe
+ * kernels' default grids).  Kernels round differently (all to 48-bit
+ * accuracy), so tuned and untuned solves agree to rounding, not bit for bit;
+ * the shapes of one kernel give the same bits.  The workspace is (re)allocated
+ * for (n, s, m); the basis contents are overwritten.
+ * gram_choice[k] (k < cap): 0 FP32-pipe Gram, 1 split-digit tensor-core Gram,
+ * 2 stored-digit tensor-core Gram, -1 no choice; update_ctas[k]: CTAs per SM of
+ * the chosen update, 0 no choice.  Host arrays of cap entries (may be NULL when
+ * cap = 0).  Returns LSBA_OK, LSBA_INVALID_ARG (n < 1, s outside 1..32, m < 1
+ * or (m + 1) s too large), LSBA_OUT_OF_MEMORY, LSBA_DEVICE_TIMEOUT or
+ * LSBA_CUDA_ERROR. */
 int lsba_autotune(lsba_handle h, int64_t n, int s, int m, int8_t* gram_choice,
                   int8_t* update_ctas, int cap);
+
+/* One tuned iteration of the last lsba_autotune on this handle. */
+typedef struct {
+  int32_t k;                    /* iteration (its Gram reads k + 1 blocks) */
+  int32_t gram_kernel;          /* 0 FP32 pipe, 1 split-digit tensor cores, 2 stored-digit tensor cores */
+  int32_t gram_ctas_per_sm;     /* FP32-pipe Gram: CTAs per SM (else 0) */
+  int32_t gram_rows;            /* FP32-pipe Gram: cap on the rows of a pipeline chunk (0: default) */
+  int32_t update_kernel;        /* 0 FP32-pipe update, 1 stored-digit tensor-core update */
+  int32_t update_ctas_per_sm;   /* CTAs per SM of that update */
+  float gram_us;                /* measured time of the chosen Gram shape, microseconds a launch */
+  float update_us;              /* measured time of the chosen update shape, microseconds a launch */
+  float gram_default_us;        /* the untuned rule's Gram, microseconds (0: not measured) */
+  float update_default_us;      /* the untuned rule's update, microseconds */
+} lsba_tune_entry;
+
+/* The table of the last lsba_autotune (iterations in increasing k): *count is
+ * the number of entries, of which the first min(cap, *count) are written to
+ * out (host array).  LSBA_OK, or LSBA_INVALID_ARG for a NULL handle, count,
+ * or out with cap > 0. */
+int lsba_autotune_table(lsba_handle h, lsba_tune_entry* out, int cap, int* count);
 
 /* The same G as lsba_gram, computed by the double-float Gram kernels of the
  * solver (the block inner product of every skeleton, Sec. 2): L and R are
@@ -319,7 +350,7 @@ int lsba_combine(lsba_handle h, const double* d_in, int nin, int64_t n, int s,
  * the solver runs for BCGSI+LS and BMGS-CWY/ICWY at s = 8 in FP64).
  * Every FP64 value is split, relative to the maximum of its (128-row tile,
  * column) group, into seven 8-bit digits carrying 53 bits (F = trunc(x
- * 2^(54 - E)) for max |x| < 2^E); the bf16 tensor cores sum the digit products
+ * 2^(54 - E)) for max |x| < 2^E); the fp16 tensor cores sum the digit products
  * by level exactly in FP32 over windows of at most 128 products, and each
  * window's levels 0..7 are combined in 64-bit integers and added into FP64
  * accumulators.  Error per product term about 2^-53 (max|x| |y| + |x| max|y|).

@@ -105,11 +105,10 @@ struct lsba_ctx {
   uint64_t graph_clock = 0;
   std::vector<uint8_t> side_recorded;  // side events recorded in the current cycle
   bool own_stream = false;     // stream created by the handle (caller passed NULL)
-  // lsba_autotune: measured kernel choices per lagged iteration k for one (n, s)
+  // lsba_autotune: measured kernel shapes per lagged iteration k for one (n, s)
   int64_t tune_n = 0;
   int tune_s = 0;
-  std::vector<int8_t> tune_gram;   // 1: stored-digit tensor-core Gram, 0: FP32-pipe Gram
-  std::vector<int8_t> tune_minb;   // CTAs per SM of the tensor-core update (2 or 3)
+  std::vector<lsba_tune_entry> tune;   // indexed by k; gram_kernel < 0: no choice
   int tune_gen = 0;
 };
 
@@ -236,6 +235,12 @@ static size_t max_partials(int64_t n, int s, int mmax, int sms, size_t* qmax_out
       if ((size_t)p.q > qmax) qmax = p.q;
       for (int tc = 0; tc < 3; tc += 2) {
         GramPlan pd = plan_gram_df(n, s, a, b, sms, tc);
+        v = (size_t)pd.grid_x * pd.q;
+        if (v > best) best = v;
+      }
+      {
+        // the autotuner's largest FP32-pipe grid
+        GramPlan pd = plan_gram_df(n, s, a, b, sms, 0, LSBA_TUNE_MAX_CPS, 1);
         v = (size_t)pd.grid_x * pd.q;
         if (v > best) best = v;
       }
@@ -510,10 +515,14 @@ static bool lagged(int skel) { return skel == SK_LS || skel == SK_ICWY || skel =
 // Precision dispatch of the three bandwidth-shaped passes (profiled).  In the
 // double-float mode every block vector buffer holds float2 (hi, lo) pairs.
 static void do_gram(lsba_ctx* h, const BlockPtrs& L, int a, const BlockPtrs& R, int b, int64_t n,
-                    int s, const Ctl* ctl, int guard) {
+                    int s, const Ctl* ctl, int guard, const lsba_tune_entry* tk = nullptr) {
   prof_begin(h, LSBA_K_GRAM);
   if (h->mode == MODE_DF) {
-    GramPlan p = plan_gram_df(n, s, a, b, h->num_sms, h->opt.tensor_cores);
+    // a tuned shape: kernel 1 the split-digit tensor-core Gram, 0 the FP32-pipe
+    // Gram with the tuned CTAs per SM and chunk rows
+    GramPlan p = tk ? plan_gram_df(n, s, a, b, h->num_sms, tk->gram_kernel == 1 ? 2 : 0, tk->gram_ctas_per_sm,
+                                   tk->gram_rows)
+                    : plan_gram_df(n, s, a, b, h->num_sms, h->opt.tensor_cores);
     launch_gram_df(h->stream, p, L, a, R, b, n, s, (float2*)h->partials, h->Gbuf, ctl, guard,
                    &h->d_ctl->error);
   } else if (h->mode == MODE_F32) {
@@ -543,11 +552,11 @@ static void do_spmm(lsba_ctx* h, const lsba_csr* A, const double* V, double* W, 
 
 static void do_update(lsba_ctx* h, const BlockPtrs& in, int nin, int64_t n, int s, double* out1,
                       const double* coef1, const double* tri1, double* out2, const double* coef2,
-                      const double* chain, const double* tri2, const Ctl* ctl, int step) {
+                      const double* chain, const double* tri2, const Ctl* ctl, int step, int cps = 0) {
   prof_begin(h, LSBA_K_UPDATE);
   if (h->mode == MODE_DF)
     launch_update_df(h->stream, in, nin, n, s, (float2*)out1, coef1, tri1, (float2*)out2, coef2,
-                     chain, tri2, h->cdf, ctl, step, h->num_sms);
+                     chain, tri2, h->cdf, ctl, step, h->num_sms, cps);
   else if (h->mode == MODE_F32)
     launch_update_f32(h->stream, in, nin, n, s, (float*)out1, coef1, tri1, (float*)out2, coef2,
                       chain, tri2, (float*)h->cdf, ctl, step, h->num_sms);
@@ -834,10 +843,14 @@ static void enqueue_cycle(lsba_ctx* h, const lsba_csr* A, const double* Rstart, 
         R.p[1] = h->Wb;
         // The stored-digit Gram has a fixed cost of about 90 us (its per-chunk
         // chain); below k = 5 the FP32-pipe Gram over the few blocks is faster.
-        const bool tuned = h->tune_n == n && h->tune_s == s && k < (int)h->tune_gram.size();
-        if (h->use_tcs && gram_tcs_eligible(s, k, 2) && (tuned ? h->tune_gram[k] == 1 : k >= 5))
+        // An autotuned handle takes the measured shape of iteration k instead.
+        const lsba_tune_entry* tk = (h->mode == MODE_DF && h->tune_n == n && h->tune_s == s &&
+                                     k < (int)h->tune.size() && h->tune[k].gram_kernel >= 0)
+                                        ? &h->tune[k]
+                                        : nullptr;
+        if (h->use_tcs && gram_tcs_eligible(s, k, 2) && (tk ? tk->gram_kernel == 2 : k >= 5))
           do_gram_tcs(h, k, n, s, ctl);
-        else do_gram(h, L, k, R, 2, n, s, ctl, 1);
+        else do_gram(h, L, k, R, 2, n, s, ctl, 1, tk && tk->gram_kernel != 2 ? tk : nullptr);
         wait_side(h, k - 1);
         PROF(LSBA_K_SMALL, launch_small_step(st, w, k, 0));
         enqueue_side(h, k);
@@ -853,11 +866,13 @@ static void enqueue_cycle(lsba_ctx* h, const lsba_csr* A, const double* Rstart, 
                             w.tri1, w.coef2, w.chain, skel == SK_LS ? w.tri2 : nullptr, h->cdf,
                             h->dig + (size_t)(k - 1) * digit_block_bytes(n, s),
                             h->dexp + (size_t)(k - 1) * digit_exp_count(n, s), ctl, k,
-                            &h->d_ctl->error, h->num_sms, tuned ? h->tune_minb[k] : 0);
+                            &h->d_ctl->error, h->num_sms,
+                            tk && tk->update_kernel == 1 ? tk->update_ctas_per_sm : 0);
           prof_end(h);
         } else {
           do_update(h, in, k + 1, n, s, Vk, w.coef1, w.tri1, h->Ub, w.coef2, w.chain,
-                    skel == SK_LS ? w.tri2 : nullptr, ctl, k);
+                    skel == SK_LS ? w.tri2 : nullptr, ctl, k,
+                    tk && tk->update_kernel == 0 ? tk->update_ctas_per_sm : 0);
           if (h->use_tcs) split_basis(h, k - 1, n, s, ctl, k);
         }
       }
@@ -1687,18 +1702,20 @@ int lsba_gram(lsba_handle h, const double* d_L, int a, const double* d_R, int b,
 // stored digit planes.
 int lsba_autotune(lsba_handle h, int64_t n, int s, int m, int8_t* gram_choice,
                   int8_t* update_ctas, int cap) {
-  if (!h || n < 1 || s != 8 || m < 1 || (int64_t)(m + 1) * s > LSBA_MAX_MS || m + 3 > LSBA_MAXB ||
-      cap < 0 || (cap > 0 && (!gram_choice || !update_ctas)))
+  if (!h || n < 1 || s < 1 || s > LSBA_MAX_S || m < 1 || (int64_t)(m + 1) * s > LSBA_MAX_MS ||
+      m + 3 > LSBA_MAXB || cap < 0 || (cap > 0 && (!gram_choice || !update_ctas)))
     return LSBA_INVALID_ARG;
   CK(cudaSetDevice(h->device));
   int rc = ensure_ws(h, n, s, m);
   if (rc != LSBA_OK) return rc;
-  if ((rc = ensure_digits(h)) != LSBA_OK) return rc;
+  // the stored-digit kernels (s = 8, tensor cores allowed) as the solver runs them
+  const bool tcs = s == 8 && h->opt.tensor_cores != 0;
+  if (tcs && (rc = ensure_digits(h)) != LSBA_OK) return rc;
   h->mode = MODE_DF;
   cudaStream_t st = h->stream;
   const size_t blk = (size_t)n * s;
-  // Operands with every digit busy (not zeros): pseudo-random blocks and
-  // their stored digit planes.
+  // Operands with every digit busy (not zeros): pseudo-random blocks and, for
+  // the stored-digit kernels, their digit planes.
   launch_fill_df(st, (int64_t)(blk * (m + 1)), 0x5EED0001ull, (float2*)h->basis);
   launch_fill_df(st, (int64_t)blk, 0x5EED0002ull, (float2*)h->Ub);
   launch_fill_df(st, (int64_t)blk, 0x5EED0003ull, (float2*)h->Wb);
@@ -1707,12 +1724,14 @@ int lsba_autotune(lsba_handle h, int64_t n, int s, int m, int8_t* gram_choice,
   c->update_step = -1;
   c->error = 0;
   if ((rc = push_ctl(h)) != LSBA_OK) return rc;
-  for (int i = 0; i <= m; ++i) split_basis(h, i, n, s, h->d_ctl, -1);
+  if (tcs)
+    for (int i = 0; i <= m; ++i) split_basis(h, i, n, s, h->d_ctl, -1);
   Ctl* ctl = h->d_ctl;
   const SmallWs& w = h->ws;
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
+  // microseconds a launch: one warm-up run, then three timed
   auto timed = [&](auto&& run) -> float {
     run();
     cudaEventRecord(e0, st);
@@ -1721,23 +1740,86 @@ int lsba_autotune(lsba_handle h, int64_t n, int s, int m, int8_t* gram_choice,
     cudaEventSynchronize(e1);
     float ms = 0.f;
     cudaEventElapsedTime(&ms, e0, e1);
-    return ms;
+    return ms * 1000.f / 3.f;
   };
-  std::vector<int8_t> tg(m + 2, -1), tm(m + 2, 0);
+  std::vector<lsba_tune_entry> tab(m + 2);
+  for (auto& e : tab) {
+    memset(&e, 0, sizeof(e));
+    e.gram_kernel = -1;
+  }
   for (int k = 2; k <= m + 1; ++k) {
+    lsba_tune_entry& e = tab[k];
+    e.k = k;
     BlockPtrs L = basis_list(h, n, s, k - 1);
     L.p[k - 1] = h->Ub;
     BlockPtrs R;
     memset(&R, 0, sizeof(R));
     R.p[0] = h->Ub;
     R.p[1] = h->Wb;
-    if (gram_tcs_eligible(s, k, 2)) {
-      const float t_tc = timed([&] { do_gram_tcs(h, k, n, s, ctl); });
-      const float t_fp = timed([&] { do_gram(h, L, k, R, 2, n, s, ctl, 1); });
-      tg[k] = t_tc < t_fp ? 1 : 0;
+    // ---- Gram of iteration k: [V_1..V_{k-1}, U]^T [U, W]
+    float best = 3.4e38f, dflt = 0.f;
+    auto try_gram = [&](int kernel, int cps, int rows, float t) {
+      if (t < best) {
+        best = t;
+        e.gram_kernel = kernel;
+        e.gram_ctas_per_sm = cps;
+        e.gram_rows = rows;
+      }
+    };
+    // untuned rule: the stored-digit Gram from k = 5, else plan_gram_df's choice
+    const bool def_tcs = tcs && gram_tcs_eligible(s, k, 2) && k >= 5;
+    if (tcs && gram_tcs_eligible(s, k, 2)) {
+      const float t = timed([&] { do_gram_tcs(h, k, n, s, ctl); });
+      if (def_tcs) dflt = t;
+      try_gram(2, 0, 0, t);
     }
-    if (update_tcs_eligible(s, k + 1, true)) {
-      double* Vk = h->basis + (size_t)(k - 1) * blk;
+    if (h->opt.tensor_cores != 0 && gram_tc_eligible(s, k, 2)) {
+      lsba_tune_entry tk = e;
+      tk.gram_kernel = 1;
+      const float t = timed([&] { do_gram(h, L, k, R, 2, n, s, ctl, 1, &tk); });
+      if (!def_tcs && plan_gram_df(n, s, k, 2, h->num_sms, h->opt.tensor_cores).tc) dflt = t;
+      try_gram(1, 0, 0, t);
+    }
+    {
+      const GramPlan d0 = plan_gram_df(n, s, k, 2, h->num_sms, 0);
+      // candidates with the same launch shape (grid, chunk rows) are timed once
+      int seen_grid[2 * LSBA_TUNE_MAX_CPS], seen_rc[2 * LSBA_TUNE_MAX_CPS], nseen = 0;
+      float seen_t[2 * LSBA_TUNE_MAX_CPS];
+      const bool def_fp = !def_tcs && !plan_gram_df(n, s, k, 2, h->num_sms, h->opt.tensor_cores).tc;
+      for (int cps = 1; cps <= LSBA_TUNE_MAX_CPS; ++cps)
+        for (int half = 0; half < 2; ++half) {
+          const int rows = half ? (d0.rows_per_chunk + 1) / 2 : 0;
+          const GramPlan pc = plan_gram_df(n, s, k, 2, h->num_sms, 0, cps, rows);
+          // a CTA count the shared memory cannot hold resident is not a candidate,
+          // except the rule's own shape
+          const bool is_def = pc.grid_x == d0.grid_x && pc.rows_per_chunk == d0.rows_per_chunk;
+          if (!is_def && cps > 1 && (size_t)cps * (pc.smem + 1024) > (size_t)228 * 1024) continue;
+          int hit = -1;
+          for (int i = 0; i < nseen; ++i)
+            if (seen_grid[i] == pc.grid_x && seen_rc[i] == pc.rows_per_chunk) hit = i;
+          float t;
+          if (hit >= 0) {
+            t = seen_t[hit];
+          } else {
+            lsba_tune_entry tk = e;
+            tk.gram_kernel = 0;
+            tk.gram_ctas_per_sm = cps;
+            tk.gram_rows = rows;
+            t = timed([&] { do_gram(h, L, k, R, 2, n, s, ctl, 1, &tk); });
+            seen_grid[nseen] = pc.grid_x;
+            seen_rc[nseen] = pc.rows_per_chunk;
+            seen_t[nseen++] = t;
+          }
+          if (def_fp && is_def) dflt = t;
+          try_gram(0, cps, rows, t);
+        }
+    }
+    e.gram_us = best;
+    e.gram_default_us = dflt;
+    // ---- basis update of iteration k (two outputs, k + 1 inputs)
+    double* Vk = h->basis + (size_t)(k - 1) * blk;
+    if (tcs && update_tcs_eligible(s, k + 1, true)) {
+      e.update_kernel = 1;
       auto upd = [&](int minb) {
         launch_update_tcs(st, h->dig, h->dexp, k - 1, (const float2*)h->Ub, (const float2*)h->Wb,
                           nullptr, n, (float2*)Vk, (float2*)h->Ub, w.coef1, nullptr, w.coef2,
@@ -1746,13 +1828,28 @@ int lsba_autotune(lsba_handle h, int64_t n, int s, int m, int8_t* gram_choice,
                           h->dexp + (size_t)(k - 1) * digit_exp_count(n, s), ctl, -1,
                           &h->d_ctl->error, h->num_sms, minb);
       };
-      if (3 * (update_tcs_smem(k + 1) + 1024) <= 228 * 1024) {
-        const float t2 = timed([&] { upd(2); });
-        const float t3 = timed([&] { upd(0); });
-        tm[k] = t2 < t3 ? 2 : 3;
-      } else {
-        tm[k] = 2;
+      const float t3 = 3 * (update_tcs_smem(k + 1) + 1024) <= 228 * 1024 ? timed([&] { upd(0); }) : 3.4e38f;
+      const float t2 = timed([&] { upd(2); });
+      e.update_ctas_per_sm = t2 < t3 ? 2 : 3;
+      e.update_us = t2 < t3 ? t2 : t3;
+      e.update_default_us = t3 < 3.4e38f ? t3 : t2;
+    } else {
+      e.update_kernel = 0;
+      BlockPtrs in = basis_list(h, n, s, k - 1);
+      in.p[k - 1] = h->Ub;
+      in.p[k] = h->Wb;
+      float bu = 3.4e38f;
+      for (int cps : {1, 2, 4, 8}) {
+        const float t = timed([&] {
+          do_update(h, in, k + 1, n, s, Vk, w.coef1, nullptr, h->Ub, w.coef2, nullptr, nullptr, ctl, -1, cps);
+        });
+        if (cps == 4) e.update_default_us = t;
+        if (t < bu) {
+          bu = t;
+          e.update_ctas_per_sm = cps;
+        }
       }
+      e.update_us = bu;
     }
   }
   cudaEventDestroy(e0);
@@ -1760,15 +1857,26 @@ int lsba_autotune(lsba_handle h, int64_t n, int s, int m, int8_t* gram_choice,
   CK(cudaGetLastError());
   if ((rc = pull_ctl(h)) != LSBA_OK) return rc;
   if (c->error) return LSBA_DEVICE_TIMEOUT;
-  h->tune_gram = tg;
-  h->tune_minb = tm;
+  h->tune = tab;
   h->tune_n = n;
   h->tune_s = s;
   ++h->tune_gen;
   for (int k = 0; k < cap; ++k) {
-    gram_choice[k] = k < (int)tg.size() ? tg[k] : -1;
-    update_ctas[k] = k < (int)tm.size() ? tm[k] : 0;
+    gram_choice[k] = k < (int)tab.size() ? (int8_t)tab[k].gram_kernel : -1;
+    update_ctas[k] = k < (int)tab.size() && tab[k].gram_kernel >= 0 ? (int8_t)tab[k].update_ctas_per_sm : 0;
   }
+  return LSBA_OK;
+}
+
+int lsba_autotune_table(lsba_handle h, lsba_tune_entry* out, int cap, int* count) {
+  if (!h || cap < 0 || (cap > 0 && !out) || !count) return LSBA_INVALID_ARG;
+  int nk = 0;
+  for (const auto& e : h->tune)
+    if (e.gram_kernel >= 0) {
+      if (nk < cap) out[nk] = e;
+      ++nk;
+    }
+  *count = nk;
   return LSBA_OK;
 }
 

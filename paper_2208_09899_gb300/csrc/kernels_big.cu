@@ -149,7 +149,16 @@ __global__ void __launch_bounds__(256) k_gram_reduce(const double* __restrict__ 
   const int x0 = (int)((int64_t)warp * nparts / 8), x1 = (int)((int64_t)(warp + 1) * nparts / 8);
   double a[4] = {0.0, 0.0, 0.0, 0.0};
   if (e < q) {
-    for (int x = x0; x < x1; ++x) a[(x - x0) & 3] += partials[(int64_t)x * q + e];
+    // all loads of a chunk issued before the sums (one memory round trip a
+    // chunk); the sums keep the order x0, x0 + 1, .. into a[(x - x0) % 4]
+    for (int c0 = x0; c0 < x1; c0 += 24) {
+      double v[24];
+#pragma unroll
+      for (int i = 0; i < 24; ++i) v[i] = c0 + i < x1 ? partials[(int64_t)(c0 + i) * q + e] : 0.0;
+#pragma unroll
+      for (int i = 0; i < 24; ++i)
+        if (c0 + i < x1) a[i & 3] += v[i];   // (c0 - x0) is a multiple of 4
+    }
   }
   part[warp][lane] = (a[0] + a[1]) + (a[2] + a[3]);
   __syncthreads();

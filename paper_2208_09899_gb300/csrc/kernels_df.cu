@@ -509,7 +509,15 @@ __global__ void __launch_bounds__(256) k_gram_reduce_df(const float2* __restrict
   if (e < q) {
     const int per = (nparts + 7) / 8;
     const int x0 = gy * per, x1 = min(nparts, x0 + per);
-    for (int x = x0; x < x1; ++x) df_add_to(acc, partials[(int64_t)x * q + e]);
+    // all loads of a chunk issued before the (ordered) sums
+    for (int c0 = x0; c0 < x1; c0 += 24) {
+      float2 v[24];
+#pragma unroll
+      for (int i = 0; i < 24; ++i) v[i] = c0 + i < x1 ? partials[(int64_t)(c0 + i) * q + e] : make_float2(0.f, 0.f);
+#pragma unroll
+      for (int i = 0; i < 24; ++i)
+        if (c0 + i < x1) df_add_to(acc, v[i]);
+    }
   }
   part[gy][ox] = df_value(acc);
   __syncthreads();
@@ -526,7 +534,8 @@ void launch_gram_reduce_df(cudaStream_t st, const float2* partials, int nparts, 
   k_gram_reduce_df<<<(q + 31) / 32, 256, 0, st>>>(partials, nparts, q, G, ctl, guard);
 }
 
-GramPlan plan_gram_df(int64_t n, int s, int a, int b, int num_sms, int tensor_cores) {
+GramPlan plan_gram_df(int64_t n, int s, int a, int b, int num_sms, int tensor_cores, int cps,
+                      int rc_cap) {
   if ((tensor_cores == 2 && gram_tc_eligible(s, a, b)) ||
       (tensor_cores == 1 && gram_tc_profitable(s, a, b))) {
     GramPlan t = plan_gram_tc(n, s, a, b, num_sms);
@@ -569,6 +578,17 @@ GramPlan plan_gram_df(int64_t n, int s, int a, int b, int num_sms, int tensor_co
     if (rc < 1) rc = 1;
     p.smem = row_bytes * rc > red_bytes ? row_bytes * rc : red_bytes;
     ctas_per_sm = 2;
+  }
+  // tuned shape: CTAs per SM and a cap on the rows of a pipeline chunk
+  if (cps > 0) ctas_per_sm = cps;
+  if (rc_cap > 0 && rc > rc_cap) {
+    rc = rc_cap;
+    if (sp == s) {
+      const size_t stages = 128 + 2 * (size_t)(p.nl_max + b) * s * sizeof(float2) * rc;
+      p.smem = stages > 128 + red_bytes ? stages : 128 + red_bytes;
+    } else {
+      p.smem = row_bytes * rc > red_bytes ? row_bytes * rc : red_bytes;
+    }
   }
   p.rows_per_chunk = rc;
   int gx = (ctas_per_sm * num_sms + p.grid_y - 1) / p.grid_y;
@@ -1031,7 +1051,7 @@ void launch_coef_df(cudaStream_t st, int nin, int s, bool two, const double* coe
 void launch_update_df(cudaStream_t st, const BlockPtrs& in, int nin, int64_t n, int s, float2* out1,
                       const double* coef1, const double* tri1, float2* out2, const double* coef2,
                       const double* chain, const double* tri2, float2* cdf, const Ctl* ctl,
-                      int step, int num_sms) {
+                      int step, int num_sms, int cps) {
   const bool two = out2 != nullptr;
   CoefDfArgs ca;
   ca.coef1 = coef1;
@@ -1076,7 +1096,7 @@ void launch_update_df(cudaStream_t st, const BlockPtrs& in, int nin, int64_t n, 
   });
   if (u.staged && (s == 4 || s == 8 || s == 16)) {
     int64_t need = (n + 255) / 256;
-    int64_t grid = 4LL * num_sms;
+    int64_t grid = (int64_t)(cps > 0 ? cps : 4) * num_sms;
     if (grid > need) grid = need;
     if (grid < 1) grid = 1;
 #define LAUNCH_ROW(SV)                                                        \
@@ -1090,7 +1110,7 @@ void launch_update_df(cudaStream_t st, const BlockPtrs& in, int nin, int64_t n, 
   }
   if (s == 32) {
     const int64_t need = (n + 127) / 128;
-    int64_t grid = 4LL * num_sms;
+    int64_t grid = (int64_t)(cps > 0 ? cps : 4) * num_sms;
     if (grid > need) grid = need;
     if (grid < 1) grid = 1;
     if (two) k_update_df_w32<true><<<(unsigned)grid, 256, 0, st>>>(u);
@@ -1099,7 +1119,7 @@ void launch_update_df(cudaStream_t st, const BlockPtrs& in, int nin, int64_t n, 
   }
   const int rows_per_cta = 256 / u.S2;
   const int64_t need = (n + rows_per_cta - 1) / rows_per_cta;
-  int64_t grid = 4LL * num_sms;
+  int64_t grid = (int64_t)(cps > 0 ? cps : 4) * num_sms;
   if (grid > need) grid = need;
   if (grid < 1) grid = 1;
   k_update_df<<<(unsigned)grid, 256, smem, st>>>(u);

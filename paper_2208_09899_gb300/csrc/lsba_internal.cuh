@@ -166,7 +166,11 @@ void launch_spmm_df(cudaStream_t st, int64_t n, const int32_t* rowptr, const int
                     const float2* vals, const float2* V, float2* W, int s, const Ctl* ctl, int guard);
 // tensor_cores: 0 FP32-pipe kernels only; 1 the tensor-core kernel where it
 // measured faster (gram_tc_profitable); 2 wherever its shape allows.
-GramPlan plan_gram_df(int64_t n, int s, int a, int b, int num_sms, int tensor_cores = 1);
+// cps > 0: CTAs per SM of the FP32-pipe kernel (else its default, 2 or 3);
+// rc_cap > 0: at most rc_cap rows a pipeline chunk (autotuned shapes).
+#define LSBA_TUNE_MAX_CPS 4   // most CTAs per SM the autotuner gives the FP32-pipe Gram
+GramPlan plan_gram_df(int64_t n, int s, int a, int b, int num_sms, int tensor_cores = 1, int cps = 0,
+                      int rc_cap = 0);
 // Tensor-core double-float Gram (kernels_tc.cu): shapes with s % 4 == 0,
 // b s <= 16 and a s + b s <= 256.
 bool gram_tc_eligible(int s, int a, int b);
@@ -222,7 +226,7 @@ size_t update_df_smem(int nin, int s, bool two);
 void launch_update_df(cudaStream_t st, const BlockPtrs& in, int nin, int64_t n, int s, float2* out1,
                       const double* coef1, const double* tri1, float2* out2, const double* coef2,
                       const double* chain, const double* tri2, float2* cdf, const Ctl* ctl,
-                      int step, int num_sms);
+                      int step, int num_sms, int cps = 0);   // cps > 0: CTAs per SM (default 4)
 
 // ---- FP32 variants (inner solver of FP64 iterative refinement); block vectors are float ----
 void launch_to_f32(cudaStream_t st, int64_t count, const double* in, float* out, double scale = 1.0);

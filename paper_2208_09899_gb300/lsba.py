@@ -27,7 +27,7 @@ MUSCLES = {"cholqr": 0, "mgs": 1}
 
 EXPORTED = ("lsba_default_options", "lsba_create", "lsba_set_options", "lsba_solve",
             "lsba_solve_host", "lsba_get_stats", "lsba_get_history", "lsba_status_string",
-            "lsba_autotune",
+            "lsba_autotune", "lsba_autotune_table",
             "lsba_destroy", "lsba_spmm", "lsba_gram", "lsba_combine", "lsba_get_profile",
             "lsba_reset_profile", "lsba_gram_noalloc", "lsba_release_workspace",
             "lsba_workspace_bytes", "lsba_gram_df", "lsba_gram_fp64tc", "lsba_combine_fp64tc")
@@ -64,6 +64,13 @@ class History(C.Structure):
                 ("gram_data", C.POINTER(C.c_double))]
 
 
+class TuneEntry(C.Structure):
+    _fields_ = [("k", C.c_int32), ("gram_kernel", C.c_int32), ("gram_ctas_per_sm", C.c_int32),
+                ("gram_rows", C.c_int32), ("update_kernel", C.c_int32),
+                ("update_ctas_per_sm", C.c_int32), ("gram_us", C.c_float), ("update_us", C.c_float),
+                ("gram_default_us", C.c_float), ("update_default_us", C.c_float)]
+
+
 class CSRDesc(C.Structure):
     _fields_ = [("n", C.c_int64), ("nnz", C.c_int64), ("d_rowptr", C.c_void_p),
                 ("d_colidx", C.c_void_p), ("d_vals", C.c_void_p)]
@@ -88,6 +95,7 @@ def load(path: str = LIB_PATH):
     lib.lsba_solve.argtypes = [vp, C.POINTER(CSRDesc), vp, vp, i32, i32, f64, i32]
     lib.lsba_solve_host.argtypes = [vp, i64, i64, vp, vp, vp, vp, vp, i32, i32, f64, i32]
     lib.lsba_autotune.argtypes = [vp, i64, i32, i32, vp, vp, i32]
+    lib.lsba_autotune_table.argtypes = [vp, C.POINTER(TuneEntry), i32, C.POINTER(C.c_int)]
     lib.lsba_get_stats.argtypes = [vp, C.POINTER(Stats)]
     lib.lsba_get_history.argtypes = [vp, C.POINTER(History)]
     lib.lsba_status_string.argtypes = [i32]
@@ -276,15 +284,23 @@ class Solver:
         return X, st
 
     def autotune(self, n: int, s: int, m: int) -> dict:
-        """Time the alternative kernels of the double-float lagged skeletons
-        (s = 8) for every iteration of an m-step cycle on n rows; later solves
-        with the same n and s use the faster ones.  Returns {k: (tensor-core
-        Gram?, update CTAs per SM)} for the iterations with a choice."""
+        """Time the candidate shapes of the double-float lagged skeletons'
+        Gram and update for every iteration of an m-step cycle on n rows, block
+        size s; later solves with the same n and s run the fastest.  Returns
+        {k: (Gram kernel, update CTAs per SM)} (kernel 0 FP32 pipe, 1
+        split-digit tensor cores, 2 stored-digit tensor cores)."""
         g = (C.c_int8 * (m + 2))()
         u = (C.c_int8 * (m + 2))()
         _check(self.lib.lsba_autotune(self.h, n, s, m, g, u, m + 2))
-        return {k: (g[k] == 1 if g[k] >= 0 else None, u[k] or None) for k in range(2, m + 2)
-                if g[k] >= 0 or u[k]}
+        return {k: (g[k], u[k]) for k in range(2, m + 2) if g[k] >= 0}
+
+    def tune_table(self) -> list:
+        """The last autotune's shapes and times, one dict per iteration k."""
+        cnt = C.c_int(0)
+        _check(self.lib.lsba_autotune_table(self.h, None, 0, C.byref(cnt)))
+        arr = (TuneEntry * max(cnt.value, 1))()
+        _check(self.lib.lsba_autotune_table(self.h, arr, cnt.value, C.byref(cnt)))
+        return [{f: getattr(arr[i], f) for f, _ in TuneEntry._fields_} for i in range(cnt.value)]
 
     def stats(self) -> dict:
         s = Stats()

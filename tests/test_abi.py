@@ -87,13 +87,13 @@ def _header_struct(name):
 
 
 def test_binding_structs_match_header():
-    """lsba_options, lsba_stats and lsba_history: the ctypes structures of the
+    """lsba_options, lsba_stats, lsba_history and lsba_tune_entry: the ctypes structures of the
     binding have the header's fields, in order, with the same sizes (a
     mismatch would shift every later option silently)."""
     import ctypes as C
     from paper_2208_09899_gb300 import lsba
     for cname, pystruct in (("lsba_options", lsba.Options), ("lsba_stats", lsba.Stats),
-                            ("lsba_history", lsba.History)):
+                            ("lsba_history", lsba.History), ("lsba_tune_entry", lsba.TuneEntry)):
         hdr = _header_struct(cname)
         py = pystruct._fields_
         assert [f for _, f, _ in hdr] == [f for f, _ in py], cname
@@ -103,5 +103,5 @@ def test_binding_structs_match_header():
             else:
                 base = ctype.replace("const ", "")
                 n = int(arr[1:-1]) if arr else 1
-                size = {"int32_t": 4, "int64_t": 8, "double": 8}[base] * n
+                size = {"int32_t": 4, "int64_t": 8, "double": 8, "float": 4}[base] * n
                 assert C.sizeof(pt) == size, (cname, field)

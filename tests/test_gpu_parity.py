@@ -543,19 +543,31 @@ def test_tensor_core_gram_in_solves(env, sk, s, m):
                    tensor_cores=2)
 
 
-def test_autotune_then_solve(env):
-    """The kernel autotuner (double-float lagged skeletons, s = 8) returns a
-    choice for every iteration of the cycle, and a solve on the tuned handle
-    still matches the oracle (restart log, counters, X)."""
+@pytest.mark.parametrize("s", [4, 8, 16])
+def test_autotune_then_solve(env, s):
+    """The kernel autotuner (double-float lagged skeletons) returns a shape for
+    every iteration of the cycle, each no slower than the untuned rule's as it
+    measured them, and a solve on the tuned handle still matches the oracle
+    (restart log, counters, X)."""
     torch, lsba = env
     A = W.laplacian_2d(64, 60)
-    B = W.gaussian_block(A.n, 8, 5)
-    m = 10
-    sv = lsba.Solver(0, modification="gmres", max_restarts=300, record_history=1)
-    ch = sv.autotune(A.n, 8, m)
+    B = W.gaussian_block(A.n, s, 5)
+    m = 10 if s < 16 else 8
+    sv = lsba.Solver(0, modification="gmres", max_restarts=300, record_history=1, precision="df")
+    ch = sv.autotune(A.n, s, m)
     assert set(ch) == set(range(2, m + 2))
-    for g, u in ch.values():
-        assert g in (True, False) and u in (2, 3)
+    tab = sv.tune_table()
+    assert [e["k"] for e in tab] == list(range(2, m + 2))
+    for e in tab:
+        print(f"TUNE s={s} k={e['k']:2d} gram kernel {e['gram_kernel']} ctas/SM {e['gram_ctas_per_sm']} "
+              f"rows {e['gram_rows']} {e['gram_us']:.1f} us (rule {e['gram_default_us']:.1f}); "
+              f"update kernel {e['update_kernel']} ctas/SM {e['update_ctas_per_sm']} "
+              f"{e['update_us']:.1f} us (rule {e['update_default_us']:.1f})")
+        assert e["gram_kernel"] in ((0, 1, 2) if s == 8 else (0, 1))
+        assert (e["update_kernel"], e["update_ctas_per_sm"]) in \
+            ({(1, 2), (1, 3)} if s == 8 else {(0, 1), (0, 2), (0, 4), (0, 8)})
+        assert e["gram_us"] <= e["gram_default_us"] or e["gram_default_us"] == 0
+        assert e["update_us"] <= e["update_default_us"]
     X, code = sv.solve_host(A, B, m, 1e-10, "bcgsi_ls")
     st, h = sv.stats(), sv.history()
     ref = O.solve(A, B, m, 1e-10, "bcgsi_ls", modification="gmres", max_restarts=300)
@@ -565,7 +577,7 @@ def test_autotune_then_solve(env):
         (ref.cycles, ref.steps, ref.a_calls, ref.syncs)
     assert _rel(X, ref.X) <= TOL_X
     with pytest.raises(lsba.LSBAError):
-        sv.autotune(A.n, 4, m)
+        sv.autotune(A.n, 33, m)
     sv.close()
 
 
