@@ -229,7 +229,8 @@ def summarize(results, t_first=None):
     t0 = min(r.arrival for r in results) if t_first is None else t_first
     t1 = max(r.end for r in results)
     ok = sum(1 for r in results if r.stats.get("status", -1) == 0)
-    return {"requests": len(results), "converged": ok,
+    errors = sorted({r.stats["error"] for r in results if "error" in r.stats})
+    return {"requests": len(results), "converged": ok, "errors": errors,
             "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
             "mean_wait_s": float(np.mean([r.wait for r in results])),
             "solves_per_s": len(results) / max(t1 - t0, 1e-9), "makespan_s": t1 - t0}
