@@ -102,8 +102,9 @@ typedef struct {
                                     representation error.  The small s x s / ks x s
                                     kernels are FP64 in all modes.  DF takes every
                                     s <= 32 and m.  FP64 runs the Gram and the
-                                    update of the lagged skeletons at s = 8,
-                                    m <= 22 as exact products of 8-bit digits on
+                                    update of the lagged skeletons, BCGS-PIP,
+                                    BCGS-PIO and BCGS at s = 8, m <= 22 as exact
+                                    products of 8-bit digits on
                                     the tensor cores (53 bits per value relative to
                                     its 128-row tile and column, FP64
                                     accumulation; tensor_cores = 0 turns this off).
@@ -123,7 +124,8 @@ typedef struct {
                                     Off while profile = 1.                            */
   int32_t tensor_cores;          /* 1 (default): the tensor-core digit kernels run
                                     where they are faster: in FP64 the Gram and
-                                    update of the lagged skeletons at s = 8, m <= 22;
+                                    update of the lagged skeletons, BCGS-PIP,
+                                    BCGS-PIO and BCGS at s = 8, m <= 22;
                                     in DF the passes of those skeletons at s = 8 and
                                     other Grams with b s = 16, a s >= 160,
                                     a s + b s <= 256 (exact digit products, 48-bit

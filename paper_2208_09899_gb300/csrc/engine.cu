@@ -656,6 +656,52 @@ static void enqueue_cycle_ftc(lsba_ctx* h, const lsba_csr* A, const double* Rsta
   PROF(LSBA_K_SMALL, launch_small_start(st, w, start_flags));
   do_update_ftc(h, Lp, Le, 1, nullptr, n, h->basis, h->fexp, h->fpl, nullptr, nullptr, nullptr,
                 w.coef1, w.tri1, nullptr, nullptr, nullptr, ctl, 0);
+  if (!lagged(skel)) {
+    // BCGS-PIP / BCGS-PIO (Alg. 3: one Gram [V_1..V_k, W]^T W, one update) and
+    // BCGS (Sec. 3.1: Gram V^T W, W' = W - V H, CholQR of W'), the same
+    // launch sequence as the FP64 kernels with every pass on digit planes
+    // (W' kept in U's buffers, which these skeletons use only at the cycle end)
+    for (int k = 1; k <= kmax; ++k) {
+      const double* Vk = h->basis + (size_t)(k - 1) * blk;
+      prof_begin(h, LSBA_K_SPMM);
+      launch_spmm_digits(st, A->n, A->d_rowptr, A->d_colidx, A->d_vals, Vk, h->Wb, h->fexp_W, h->fpl_W,
+                         ctl, 1);
+      prof_end(h);
+      for (int i = 0; i < k; ++i) {
+        Le[i] = basis_exp(h, n, s, i);
+        Lp[i] = basis_planes(h, n, i);
+      }
+      Le[k] = h->fexp_W;
+      Lp[k] = h->fpl_W;
+      double* Vnext = h->basis + (size_t)k * blk;
+      if (skel == SK_PIP || skel == SK_PIO) {
+        // R = [W], the last block of L
+        do_gram_ftc(h, Lp, Le, k + 1, Lp + k, Le + k, 1, true, n, s, ctl, 1);
+        wait_side(h, k - 1);
+        PROF(LSBA_K_SMALL, launch_small_step(st, w, k, 0));
+        enqueue_side(h, k);
+        do_update_ftc(h, Lp, Le, k + 1, nullptr, n, Vnext, basis_exp(h, n, s, k), basis_planes(h, n, k),
+                      nullptr, nullptr, nullptr, w.coef1, w.tri1, nullptr, nullptr, nullptr, ctl, k);
+      } else {
+        Rp[0] = h->fpl_W;
+        Re[0] = h->fexp_W;
+        do_gram_ftc(h, Lp, Le, k, Rp, Re, 1, false, n, s, ctl, 1);
+        wait_side(h, k - 1);
+        PROF(LSBA_K_SMALL, launch_small_step(st, w, k, 0));
+        do_update_ftc(h, Lp, Le, k + 1, nullptr, n, h->Ub, h->fexp_U, h->fpl_U, nullptr, nullptr, nullptr,
+                      w.coef1, nullptr, nullptr, nullptr, nullptr, ctl, k);
+        Rp[0] = h->fpl_U;
+        Re[0] = h->fexp_U;
+        do_gram_ftc(h, Rp, Re, 1, Rp, Re, 1, true, n, s, ctl, 1);
+        PROF(LSBA_K_SMALL, launch_small_step(st, w, k, 1));
+        enqueue_side(h, k);
+        do_update_ftc(h, Rp, Re, 1, nullptr, n, Vnext, basis_exp(h, n, s, k), basis_planes(h, n, k), nullptr,
+                      nullptr, nullptr, w.coef1, w.tri1, nullptr, nullptr, nullptr, ctl, k);
+      }
+    }
+    wait_side(h, kmax);
+    return;
+  }
   for (int k = 1; k <= kmax; ++k) {
     const double* U = (k == 1) ? h->basis : h->Ub;
     prof_begin(h, LSBA_K_SPMM);
@@ -707,7 +753,7 @@ static void enqueue_cycle(lsba_ctx* h, const lsba_csr* A, const double* Rstart, 
   Ctl* ctl = h->d_ctl;
   h->side_recorded.assign(h->ev_side.size(), 0);
   if (h->use_ftc) {
-    enqueue_cycle_ftc(h, A, Rstart, n, s, m_cur + 1, start_flags);
+    enqueue_cycle_ftc(h, A, Rstart, n, s, lagged(skel) ? m_cur + 1 : m_cur, start_flags);
     return;
   }
   BlockPtrs one;
@@ -1345,10 +1391,12 @@ static int solve_impl(lsba_handle h, const lsba_csr* A, const double* d_B, doubl
   // row kernels for s = 4, 8, 16 only and otherwise runs in double-float.
   const bool fits_f32 = (s == 4 || s == 8 || s == 16) && update_f32_smem(m + 3, s, true) <= 200 * 1024;
   const bool ir = prec == LSBA_PREC_FP32_IR && fits_f32;
-  // Shapes the FP64 tensor-core passes take (lagged skeletons, s = 8, m <= 22):
-  // under "auto" they run there, in FP64, rather than in double-float (they
-  // are faster on GB300 and keep 53 bits).
-  const bool ftc_shape = s == 8 && h->opt.tensor_cores != 0 && lagged(skel) &&
+  // Shapes the FP64 tensor-core passes take (the lagged skeletons, BCGS-PIP,
+  // BCGS-PIO and BCGS; s = 8, m <= 22): under "auto" the lagged ones run
+  // there, in FP64, rather than in double-float (they are faster on GB300 and
+  // keep 53 bits); the others run in FP64 anyway.
+  const bool ftc_skel = lagged(skel) || skel == SK_PIP || skel == SK_PIO || skel == SK_BCGS;
+  const bool ftc_shape = s == 8 && h->opt.tensor_cores != 0 && ftc_skel &&
                          gram_f64tc_eligible(s, m + 1, 2, true) && update_f64tc_eligible(s, m + 2);
   if (ir) h->mode = MODE_F32;
   else if (prec == LSBA_PREC_DF || prec == LSBA_PREC_FP32_IR ||
@@ -1382,8 +1430,7 @@ static int solve_impl(lsba_handle h, const lsba_csr* A, const double* d_B, doubl
   // Tensor-core Gram on stored digit planes: double-float lagged skeletons, s = 8.
   h->use_tcs = h->mode == MODE_DF && s == 8 && h->opt.tensor_cores != 0 && lagged(skel);
   if (h->use_tcs && ensure_digits(h) != LSBA_OK) h->use_tcs = false;
-  // FP64 on the tensor cores: lagged skeletons, s = 8, m <= 22 (classical inner
-  // product and CholQR, the paths whose passes it covers).
+  // FP64 on the tensor cores: the skeletons above at s = 8, m <= 22.
   h->use_ftc = h->mode == MODE_FP64 && ftc_shape;
   if (h->use_ftc && ensure_f64tc(h) != LSBA_OK) h->use_ftc = false;
   h->stats.tensor_cores = (h->use_tcs || h->use_ftc) ? 1 : 0;

@@ -1,6 +1,7 @@
 """FP64 on the tensor cores (exact digit products): the Gram and update
-kernels against the oracle's FP64 products, and solves of the lagged
-skeletons at s = 8 in FP64, which run on them, against the oracle.
+kernels against the oracle's FP64 products, and solves at s = 8 in FP64
+(lagged skeletons, BCGS-PIP, BCGS-PIO, BCGS), which run on them, against the
+oracle.
 
 Bound of the kernels (per output entry): every value is represented to
 2^-53 of its (128-row tile, column) maximum, so a product term L_ri R_rj is
@@ -139,7 +140,7 @@ def test_combine_fp64tc_matches_oracle(env, nin, n, tri, two):
         assert np.all(err <= bound)
 
 
-_SK8 = ["bcgsi_ls", "bmgs_icwy", "bmgs_cwy"]
+_SK8 = ["bcgsi_ls", "bmgs_icwy", "bmgs_cwy", "bcgs_pip", "bcgs_pio", "bcgs"]
 
 
 def _cmp(lsba, A, B, m, tol, sk, mod, **kw):
@@ -152,9 +153,10 @@ def _cmp(lsba, A, B, m, tol, sk, mod, **kw):
 @pytest.mark.parametrize("mod", ["gmres", "fom"])
 @pytest.mark.parametrize("sk", _SK8)
 def test_fp64_tensor_core_solves(env, sk, mod):
-    """Lagged skeletons at s = 8 in FP64 run their Gram and update passes on the
-    digit kernels: the oracle's restart log, counters, first-cycle Grams and
-    Hessenberg within 1e-11, estimates, and X within 1e-8."""
+    """The lagged skeletons, BCGS-PIP, BCGS-PIO and BCGS at s = 8 in FP64 run
+    their Gram and update passes on the digit kernels: the oracle's restart
+    log, counters, first-cycle Grams and Hessenberg within 1e-11, estimates,
+    and X within 1e-8."""
     torch, lsba = env
     A = W.laplacian_2d(40, 37)
     B = W.gaussian_block(A.n, 8, 3)
