@@ -89,6 +89,8 @@ def test_oversized_runs_alone_and_failure_reported():
     assert starts[1] == (1,)                    # the request above the cap ran alone
     assert out[3].X is None and "fake failure" in out[3].stats["error"]
     assert all(out[i].stats.get("status") == 0 for i in range(3))
+    sm = serve.summarize(out)
+    assert sm["converged"] == 3 and len(sm["errors"]) == 1 and "fake failure" in sm["errors"][0]
 
 
 def test_arrivals_honoured_and_summary():
@@ -101,7 +103,7 @@ def test_arrivals_honoured_and_summary():
     assert all(r.start >= r.arrival - 1e-6 for r in out)
     assert all(r.X is None for r in out)
     sm = serve.summarize(out)
-    assert sm["requests"] == 12 and sm["converged"] == 12
+    assert sm["requests"] == 12 and sm["converged"] == 12 and sm["errors"] == []
     assert 0 <= sm["p50_s"] <= sm["p99_s"] and sm["solves_per_s"] > 0
 
 
