@@ -57,6 +57,10 @@ def test_invalid_arguments_without_gpu(lib):
     assert lib.lsba_get_stats(None, None) == 3
     assert lib.lsba_destroy(None) == 3
     assert lib.lsba_create(None, 0, None, None) == 3
+    # the autotuner and its table refuse a missing handle before any device work
+    cnt = C.c_int(-1)
+    assert lib.lsba_autotune(None, 1000, 8, 10, None, None, 0) == 3
+    assert lib.lsba_autotune_table(None, None, 0, C.byref(cnt)) == 3 and cnt.value == -1
 
 
 def test_binding_enums_match_header():
